@@ -1,0 +1,240 @@
+/* rteaal.h -- C ABI of librteaal.so: GPU (sm_103a) cycle-accurate RTL simulation
+ * as a cascade of extended Einsums (RTeAAL Sim, arXiv 2601.18140).
+ *
+ * What one cycle computes (Sec. 4, Cascade 1 of the paper, loop order of
+ * Alg. 3 / Alg. 4):
+ *   for each layer i (iterative rank I):
+ *     OI       = LI_i . OIM_i                (gather the operands named by the mask)
+ *     LO_i     = op_u[n], then op_r[n] folded in ascending O order
+ *     LO_sel_i = op_s[n] over the O-fiber    (select operations, e.g. mux)
+ *     LI_{i+1} = LO_i | LO_sel_i
+ *   then every register commits its next state at the clock edge (Sec. 2.1,
+ *   Fig. 1), and the testbench drives the primary inputs at the cycle boundary
+ *   (Sec. 5.2, "Host-DUT Communication").
+ *
+ * Device form.  Identity operations are elided by giving every signal one
+ * global slot (Sec. 4.3): LI / LO of every layer are views of one state array
+ *     state[slot][lane]  (uint64, lane = stimulus instance, lane-minor),
+ * so that LI_{i+1} <- LO_i moves no data and is only a barrier.  OIM is lowered
+ * to per-layer operand lists whose operations are grouped by (opcode, width)
+ * -- the swizzled [I, N, S, O, R] order of the NU kernel (Sec. 4.4) -- with the
+ * S coordinates implicit (the outputs of a layer occupy consecutive slots) and
+ * the N / O payloads implied by the opcode (Sec. 4.3, "Compressing the OIM").
+ *
+ * ------------------------------------------------------------------------
+ * Netlist format "RTLN" version 1 (input of rteaal_design_load)
+ * ------------------------------------------------------------------------
+ * Little-endian.  Header: 10 x u32
+ *     magic 0x4E4C5452, version 1, n_inputs, n_regs, n_consts, n_ops,
+ *     n_mems, n_wports, n_args, 0
+ * then, in this order:
+ *     u64 reg_init[n_regs]        u64 const_value[n_consts]
+ *     u32 reg_d[n_regs]           u32 op_argoff[n_ops+1]   u32 args[n_args]
+ *     u32 mem_words[n_mems]       u32 wport[n_wports][4] = {mem, en, addr, data}
+ *     u8 input_width[n_inputs]    u8 reg_width[n_regs]     u8 const_width[n_consts]
+ *     u8 op_code[n_ops]  u8 op_width[n_ops]  u8 op_p0[n_ops]  u8 op_p1[n_ops]
+ *     u8 mem_width[n_mems]
+ * Signal ids: [0, n_inputs) inputs, then registers (their Q), then constants,
+ * then op outputs in topological order (every operand id < the op's own id).
+ * Op k's operands are args[op_argoff[k] .. op_argoff[k+1]) in O order.
+ *
+ * Value domain (reading: the paper supports "all FIRRTL primitive operations"
+ * but defines none): unsigned only; every signal has a width w in 1..64 and
+ * is stored zero-extended in 64 bits, always masked to w.  mask(w) = 2^w - 1.
+ * Every op result is masked to the op's width.  Opcodes (u8):
+ *   0 COPY a            1 AND a,b,...   2 OR a,b,...   3 XOR a,b,...  (fold in O order)
+ *   4 NOT ~a            5 ADD a,b,...   6 SUB a-b      7 MUL a*b*... (all mod 2^64)
+ *   8 SHL a<<p0         9 SHR a>>p0    10 DSHL a<<b   11 DSHR a>>b   (amount >= 64 -> 0)
+ *  12 BITS (a>>p1) & mask(p0-p1+1)  (hi = p0 >= lo = p1, hi <= 63)
+ *  13 CAT (a<<p0) | b   (p0 = width of b, 1..64; o0 is the high part)
+ *  14 EQ 15 NEQ 16 LT 17 LEQ 18 GT 19 GEQ   unsigned, result 0/1
+ *  20 MUX  (sel & 1) ? o1 : o2   (O=0 is the selector; App. A; FIRRTL order)
+ *  21 ANDR (a & mask(p0)) == mask(p0) (p0 = operand width)  22 ORR a != 0
+ *  23 XORR parity of a           24 MEMRD mem[p0 | p1<<8][a & (words-1)]
+ *  25 MUXCHAIN s0,v0,s1,v1,...,default: v_i of the first s_i with bit 0 set,
+ *     else default (operator fusion of mux chains, App. B.1)
+ * Classes (Cascade 1): op_u = unary ops (COPY NOT SHL SHR BITS ANDR ORR XORR
+ * MEMRD); op_r = reducible ops (the binary ones, folded in O order); op_s =
+ * select ops (MUX MUXCHAIN).
+ * Clock edge (reading; the paper has no reset or memories): Q <- (reset ?
+ * init : value(D)) & mask(w_Q).  Memories hold words x mem_width bits, are
+ * zero at rteaal_sim_create and untouched by reset; MEMRD sees the pre-edge
+ * contents; at the edge each write port, in port order, writes data &
+ * mask(mem_width) to addr & (words-1) when en & 1 (a later port wins).
+ * words must be a power of two.
+ * One cycle: (1) drive inputs (value & mask(w_in)); (2) all ops; (3) edge.
+ * ------------------------------------------------------------------------ */
+#ifndef RTEAAL_H
+#define RTEAAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rteaal_design rteaal_design; /* opaque, immutable after load   */
+typedef struct rteaal_sim rteaal_sim;       /* opaque, device state of a batch */
+
+/* Every entry point returns one of these (0 = success).  No C++ exception
+ * crosses the ABI.  On failure rteaal_last_error() describes the cause. */
+enum {
+  RTEAAL_OK = 0,
+  RTEAAL_E_INVALID = -1,     /* bad argument (null pointer, range, mode)            */
+  RTEAAL_E_FORMAT = -2,      /* netlist bytes malformed or violate the rules above  */
+  RTEAAL_E_NOMEM = -3,       /* device allocation failed / footprint refused        */
+  RTEAAL_E_CUDA = -4,        /* a CUDA call failed (message has the CUDA error)     */
+  RTEAAL_E_TIMEOUT = -5,     /* a bounded device-side wait gave up (grid barrier)   */
+  RTEAAL_E_BUSY = -6,        /* object still in use (e.g. design with live sims)    */
+  RTEAAL_E_UNSUPPORTED = -7  /* valid request this build cannot run                 */
+};
+
+/* Device-memory provider.  alloc returns a device pointer aligned to >= 256
+ * bytes or NULL; free releases it.  NULL provider = cudaMalloc / cudaFree.
+ * The Python binding passes PyTorch's caching allocator here. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *ctx);
+  void (*free)(void *ptr, size_t bytes, void *ctx);
+  void *ctx;
+} rteaal_allocator;
+
+/* ---------------------------------------------------------------- design */
+typedef struct {
+  const rteaal_allocator *allocator; /* nullable */
+  int device;                        /* CUDA ordinal; < 0 = current device */
+} rteaal_load_opts;
+
+typedef struct {
+  uint32_t n_signals, n_inputs, n_regs, n_consts, n_ops, n_mems, n_wports;
+  uint32_t n_layers;         /* levels after levelisation (Sec. 4.2)            */
+  uint32_t n_groups;         /* non-empty (layer, opcode, width) groups          */
+  uint32_t n_slots;          /* state rows per lane (signals + inserted copies)  */
+  uint32_t n_lowered_ops;    /* ops evaluated per cycle incl. inserted copies    */
+  uint32_t max_layer_ops;
+  uint64_t op_operands;      /* sum of operand counts over the n_ops netlist ops */
+  uint64_t mem_words_total;  /* words of all memories of one lane               */
+  uint64_t metadata_bytes;   /* device bytes owned by the design                */
+} rteaal_design_info;
+
+/* Parse, validate, levelise, group by (opcode, width) and upload the lowered
+ * operand lists.  netlist: host bytes (copied; caller keeps ownership).
+ * opts nullable.  *out receives a handle owned by the caller, released with
+ * rteaal_design_free.  Errors: E_INVALID, E_FORMAT, E_NOMEM, E_CUDA. */
+int rteaal_design_load(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
+                       rteaal_design **out);
+int rteaal_design_info(const rteaal_design *design, rteaal_design_info *out);
+/* Returns E_BUSY (and frees nothing) while sims created from it are alive. */
+int rteaal_design_free(rteaal_design *design);
+
+/* ---------------------------------------------------------------- simulation */
+enum {
+  RTEAAL_KERNEL_AUTO = 0,   /* TILE when lanes >= 64, else LAYER                   */
+  RTEAAL_KERNEL_LAYER = 1,  /* plain form: one launch per layer per cycle          */
+  RTEAAL_KERNEL_TILE = 2,   /* persistent: a CTA walks all layers and cycles of an
+                               instance tile, CTA barrier between layers           */
+  RTEAAL_KERNEL_GRID = 3,   /* persistent cooperative: the whole grid walks all
+                               layers, bounded grid barrier between layers         */
+  RTEAAL_KERNEL_LAYER_GRAPH = 4 /* plain form with the cycle loop as a CUDA graph  */
+};
+
+typedef struct {
+  const rteaal_allocator *allocator; /* nullable */
+  /* host [n_instances], nullable: expected cycle counts.  Lanes are ordered by
+   * descending count so that instances of a tile retire together (uneven
+   * cycle counts); lane order never changes the results. */
+  const uint32_t *expected_cycles;
+  /* host [n_inputs][n_instances], nullable: initial xorshift64 states for
+   * RTEAAL_STIM_XORSHIFT (copied).  A zero state stays zero. */
+  const uint64_t *xorshift_seed;
+  int kernel;              /* RTEAAL_KERNEL_*                                   */
+  uint32_t tile_lanes;     /* TILE: lanes per tile (power of two <= 64), 0 auto */
+  uint32_t threads;        /* threads per CTA (multiple of 32), 0 auto          */
+  uint32_t ctas_per_sm;    /* TILE / GRID residency target, 0 auto              */
+  uint32_t unroll;         /* operations in flight per thread (1, 2, 4), 0 auto */
+} rteaal_sim_opts;
+
+typedef struct {
+  uint32_t n_instances, n_lanes; /* n_lanes = padded lane count of the state    */
+  uint64_t device_bytes;         /* state + memories + stimulus + scratch        */
+  int kernel;                    /* kernel chosen                                */
+  uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid;
+} rteaal_sim_info;
+
+/* Allocates and zero-initialises the state of n_instances (>= 1) independent
+ * instances, writes the constants.  Registers are 0 until a reset cycle.
+ * design must outlive the sim.  Errors: E_INVALID, E_NOMEM, E_CUDA. */
+int rteaal_sim_create(const rteaal_design *design, uint32_t n_instances,
+                      const rteaal_sim_opts *opts, rteaal_sim **out);
+int rteaal_sim_info(const rteaal_sim *sim, rteaal_sim_info *out);
+void rteaal_sim_destroy(rteaal_sim *sim);
+
+/* Bytes of device memory rteaal_sim_create would take (footprint admission). */
+uint64_t rteaal_sim_footprint(const rteaal_design *design, uint32_t n_instances);
+
+typedef struct {
+  uint64_t uniform;              /* cycles for every instance if per_instance is NULL */
+  const uint32_t *per_instance;  /* host [n_instances], nullable (uneven cycles)      */
+} rteaal_cycles;
+
+enum { RTEAAL_STIM_HOLD = 0, RTEAAL_STIM_XORSHIFT = 1, RTEAAL_STIM_BUFFER = 2 };
+typedef struct {
+  int mode;
+  /* BUFFER: [cycles][n_inputs][n_instances] values (masked on use), instance
+   * order = user order, cycle index relative to the step.  Device pointer,
+   * or host pointer when values_on_host (copied inside the call; pinned
+   * memory makes the copy asynchronous). */
+  const uint64_t *values;
+  int values_on_host;
+} rteaal_stimulus;
+
+enum { RTEAAL_PROBE_LAST = 0, RTEAAL_PROBE_EVERY = 1 };
+typedef struct {
+  const uint32_t *signals;  /* host [n] signal ids */
+  uint32_t n;
+  int mode;                 /* LAST: out [n][n_instances] after the step;
+                               EVERY: out [cycles][n][n_instances], row c written
+                               for instances that ran cycle c (end-of-cycle values) */
+  uint64_t *out;            /* device pointer, or host if out_on_host          */
+  int out_on_host;          /* host: copied back and synchronised in the call  */
+} rteaal_probes;
+
+enum { RTEAAL_STEP_RESET = 1 };
+
+/* Advance every instance by its cycle count (0 allowed).  flags & RESET makes
+ * every cycle of the call a reset cycle.  Work is enqueued on stream (a
+ * cudaStream_t; NULL = legacy default stream) and is asynchronous unless a
+ * host buffer is involved.  Caller-owned device buffers must stay valid until
+ * the stream reaches the end of the step.  Errors: E_INVALID, E_CUDA,
+ * E_TIMEOUT (reported by this or the next call on the sim), E_UNSUPPORTED. */
+int rteaal_step(rteaal_sim *sim, const rteaal_cycles *cycles, const rteaal_stimulus *stimulus,
+                const rteaal_probes *probes /* nullable */, uint32_t flags, void *stream);
+
+/* Blocks until the sim's work on stream is done; returns any pending error. */
+int rteaal_sync(rteaal_sim *sim, void *stream);
+
+/* Copy signal values of instances [inst_begin, inst_begin + n_inst) to / from
+ * host memory laid out [n][n_inst].  Synchronises stream.  Writing a constant
+ * changes it for the rest of the simulation (checkpoint restore). */
+int rteaal_state_read(rteaal_sim *sim, const uint32_t *signals, uint32_t n, uint32_t inst_begin,
+                      uint32_t n_inst, uint64_t *host_out, void *stream);
+int rteaal_state_write(rteaal_sim *sim, const uint32_t *signals, uint32_t n, uint32_t inst_begin,
+                       uint32_t n_inst, const uint64_t *host_in, void *stream);
+/* Memory words of all memories (memory-major, word order), [words_total][n_inst]. */
+int rteaal_mem_read(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst, uint64_t *host_out,
+                    void *stream);
+int rteaal_mem_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst, const uint64_t *host_in,
+                     void *stream);
+/* xorshift64 states, [n_inputs][n_inst]. */
+int rteaal_stim_state_read(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst,
+                           uint64_t *host_out, void *stream);
+int rteaal_stim_state_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst,
+                            const uint64_t *host_in, void *stream);
+
+/* Thread-local description of the last failure on this thread. */
+const char *rteaal_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTEAAL_H */
