@@ -1,0 +1,387 @@
+"""Benchmark: op-evaluations/s of batched cycle-accurate RTL simulation on one GB300.
+
+Default workload ("batch-1M"): random layered DAG of 1,000,000 ops, 65,536
+registers, depth 80, 32 primary inputs, 4,096 stimulus instances with per-
+instance cycle budgets uniform in [1k, 100k], per-instance xorshift64
+stimulus, persistent tile kernel.  One step = one pass of the whole hot path
+(stimulus, every layer, clock edge) for a chunk of `--chunk` cycles over every
+instance that still has cycles left.  The timed window covers cycles
+[W*chunk, (W+K)*chunk) of the job; instances never finish inside it (budgets
+>= 1,000 cycles), so every instance-cycle in the window is active.
+
+value       op-evals/s (active instance-cycles x ops / device time), inputs resident
+e2e         same metric through the public API with host buffers: explicit
+            per-cycle stimulus copied from pinned host memory each step and
+            64 probed register values per instance copied back each step
+roofline    dominant kernel (k_tile): algorithmic bytes per launch / launch time
+cpu_baseline  the oracle on this host's cores, on a bounded sample
+
+--impl reference  times the oracle (gate-by-gate C interpreter) as the
+                  reference arm, on this host's cores, same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (spec factory, instances, cycle budget range, tile lanes)
+    "batch-1M": (synth.spec_batch, 4096, (1000, 100_000)),
+    "single-200k": (synth.spec_single, 1, (100_000, 100_000)),
+    "tiny-2k": (synth.spec_tiny, 1, (10_000, 10_000)),
+    "soc-5M": (synth.spec_soc, 1024, (20_000, 20_000)),
+}
+
+
+def algorithmic_bytes_per_instance_cycle(nl: synth.Netlist, tile_lanes: int) -> dict:
+    """Bytes one instance-cycle must move at minimum (every operand read once,
+    every result written once) plus the op descriptors amortised over a tile."""
+    arity = np.diff(nl.op_argoff.astype(np.int64))
+    ops = 8.0 * float(arity.sum() + nl.n_ops)                 # operands + result per op
+    regs = 16.0 * nl.n_regs                                   # read D, write Q
+    inputs = 24.0 * nl.n_inputs                               # xorshift state r/w + input write
+    memw = 8.0 * 3 * nl.n_wports                              # en/addr/data reads (writes ~ en rate)
+    meta = 16.0 * nl.n_ops / max(1, tile_lanes)               # 16-byte descriptor per op per tile
+    return {"ops": ops, "regs": regs, "inputs": inputs, "mem": memw, "meta": meta,
+            "total": ops + regs + inputs + memw + meta}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def profile_traffic(kernel_key: str) -> float | None:
+    """Per-launch DRAM bytes from the committed ncu summary, scaled to the bench launch."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 2 and parts[0] == kernel_key:
+            return float(parts[1])
+    return None
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows: list[list[str]] = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout
+                for line in out.strip().splitlines():
+                    self.rows.append([x.strip() for x in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self) -> dict:
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard(n: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous instance shard of one rank (replicas: no data-path exchange)."""
+    lo = n * rank // world
+    hi = n * (rank + 1) // world
+    return lo, hi
+
+
+# --------------------------------------------------------------------------- CPU
+def cpu_oracle_rate(nl: synth.Netlist, n_inst: int, cycles: int, seed: int, threads: int) -> dict:
+    import oracle
+    o = oracle.OracleSim(nl.to_bytes(), n_inst)
+    xs = synth.xorshift_seeds(seed, nl.n_inputs, n_inst)
+    o.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=xs, threads=threads)
+    t0 = time.perf_counter()
+    o.step(cycles, mode=oracle.STIM_XORSHIFT, xs=xs, threads=threads)
+    dt = time.perf_counter() - t0
+    evals = float(n_inst) * cycles * nl.n_ops
+    return {"value": evals / dt, "unit": "op-evals/s", "cores": threads, "kind": "oracle",
+            "seconds": dt,
+            "sample": "%d instances x %d cycles of the %d-op design (after reset), %d threads"
+                      % (n_inst, cycles, nl.n_ops, threads)}
+
+
+def cpu_sample_size(workload: str) -> tuple[int, int]:
+    return {"batch-1M": (64, 8), "single-200k": (1, 2000), "tiny-2k": (1, 10_000),
+            "soc-5M": (16, 4)}[workload]
+
+
+def run_reference(args) -> None:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    spec_fn, n_inst, _ = WORKLOADS[args.workload]
+    nl = synth.generate(spec_fn())
+    threads = os.cpu_count() or 1
+    si, sc = cpu_sample_size(args.workload)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(nl, si, max(1, sc // 4), 7, threads)
+    vals = [cpu_oracle_rate(nl, si, sc, 7, threads) for _ in range(args.steps)]
+    v = float(np.mean([x["value"] for x in vals]))
+    ms = float(np.mean([x["seconds"] for x in vals])) * 1e3
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": "op-evaluations/sec (ops x instances x cycles), bit-exact",
+            "value": v, "unit": "op-evals/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "instances": n_inst, "ops": nl.n_ops,
+                       "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "op-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------- GPU
+def run_ours(args) -> None:
+    import torch
+
+    import paper_2601_18140_gb300 as rt
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    spec_fn, n_total, (clo, chi) = WORKLOADS[args.workload]
+    nl = synth.generate(spec_fn())
+    lo, hi = shard(n_total, rank, world)
+    n = hi - lo
+    budgets_all = synth.cycle_budgets(5, n_total, clo, chi)
+    budgets = budgets_all[lo:hi].copy()
+    xs_all = synth.xorshift_seeds(5, nl.n_inputs, n_total)
+    xs = np.ascontiguousarray(xs_all[:, lo:hi])
+
+    design = rt.Design(nl.to_bytes())
+    kw = {}
+    if args.kernel == "tile":
+        kw = dict(tile_lanes=args.tile_lanes, threads=args.threads, unroll=args.unroll,
+                  ctas_per_sm=args.ctas_per_sm)
+    sim = rt.Sim(design, n, kernel=args.kernel, xorshift_seed=xs, expected_cycles=budgets, **kw)
+    info = sim.info
+    stream = torch.cuda.current_stream(dev)
+    remaining = budgets.astype(np.int64).copy()
+
+    # reset cycle (not counted)
+    sim.step(1, stimulus="xorshift", reset=True)
+    torch.cuda.synchronize()
+
+    C = args.chunk
+
+    def one_step():
+        per = np.minimum(remaining, C).astype(np.uint32)
+        sim.step(per, stimulus="xorshift")
+        remaining[:] -= per
+        return int(per.astype(np.int64).sum())
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launch_ms = []
+    inst_cycles = 0
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inst_cycles += one_step()
+            e1.record(stream)
+            launch_ms.append((e0, e1))
+        end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t_ms = start.elapsed_time(end)
+    step_ms = [a.elapsed_time(b) for a, b in launch_ms]
+    t_max = t_ms
+    evals = float(inst_cycles) * nl.n_ops
+    if world > 1:
+        t = torch.tensor([t_ms, evals], dtype=torch.float64, device=dev)
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        t_max, evals = float(tt[0]), float(t[1])
+    value = evals / (t_max / 1e3)
+
+    # ---- roofline of the dominant kernel (one k_tile launch per step)
+    bpc = algorithmic_bytes_per_instance_cycle(nl, info["tile_lanes"])
+    per_launch_bytes = bpc["total"] * (inst_cycles / args.steps)
+    avg_launch_s = float(np.mean(step_ms)) / 1e3
+    peaks = measured_peaks()
+    achieved = per_launch_bytes / avg_launch_s / 1e9
+    traffic = profile_traffic("k_tile:" + args.workload)
+    if traffic is not None:
+        traffic *= (inst_cycles / args.steps)                # stored per instance-cycle
+
+    # ---- sampled parity of the timed run against the oracle (bit-exact)
+    parity = None
+    if args.verify and rank == 0:
+        import oracle
+        run_cycles = budgets.astype(np.int64) - remaining
+        sample = np.array(sorted({0, n // 3, n - 1}), np.int64)
+        if True:
+            o = oracle.OracleSim(nl.to_bytes(), sample.size)
+            oxs = np.ascontiguousarray(xs[:, sample])
+            o.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=oxs, threads=os.cpu_count() or 1)
+            o.step(run_cycles[sample].astype(np.uint32), mode=oracle.STIM_XORSHIFT, xs=oxs,
+                   threads=os.cpu_count() or 1)
+            ok = all(np.array_equal(sim.read(None, int(i), 1)[:, 0], o.vals[k])
+                     for k, i in enumerate(sample))
+            parity = ("bit-exact" if ok else "MISMATCH") + " on instances %s after %s cycles" % (
+                list(map(int, sample)), list(map(int, run_cycles[sample])))
+            if not ok:
+                print("PARITY FAILURE", parity, file=sys.stderr)
+
+    # ---- e2e through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0 and args.kernel == "tile":
+        probes = (nl.reg_base + np.arange(min(64, nl.n_regs))).astype(np.uint32)
+        vals_host = torch.empty((C, nl.n_inputs, n), dtype=torch.int64).pin_memory()
+        vals_np = vals_host.numpy().view(np.uint64)
+        vals_np[:] = synth.stimulus_values(9, C, nl.n_inputs, n)
+        out_host = torch.empty((1, probes.size, n), dtype=torch.int64).pin_memory()
+        e2e_evals = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            per = np.minimum(remaining, C).astype(np.uint32)
+            cyc = rt.rteaal_cycles()
+            cyc.per_instance = per.ctypes.data_as(rt.ctypes.POINTER(rt.ctypes.c_uint32))
+            st = rt.rteaal_stimulus()
+            st.mode, st.values, st.values_on_host = rt.RTEAAL_STIM_BUFFER, vals_host.data_ptr(), 1
+            pr = rt.rteaal_probes()
+            pr.signals = probes.ctypes.data_as(rt.ctypes.POINTER(rt.ctypes.c_uint32))
+            pr.n, pr.mode, pr.out, pr.out_on_host = probes.size, rt.RTEAAL_PROBE_LAST, out_host.data_ptr(), 1
+            rt.rteaal_step(sim.handle, cyc, st, pr, 0, stream)
+            remaining[:] -= per
+            e2e_evals += int(per.astype(np.int64).sum()) * nl.n_ops
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": e2e_evals / e2e_s, "unit": "op-evals/s",
+               "h2d_bytes_per_step": int(C * nl.n_inputs * n * 8 + n * 4),
+               "d2h_bytes_per_step": int(probes.size * n * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        si, sc = cpu_sample_size(args.workload)
+        cpu = cpu_oracle_rate(nl, si, sc, 7, os.cpu_count() or 1)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": "op-evaluations/sec (ops x instances x cycles) on 1 GB300, bit-exact, % mem roofline",
+            "value": value, "unit": "op-evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "ops": nl.n_ops, "regs": nl.n_regs,
+                       "layers": design.info["n_layers"], "instances": n_total,
+                       "cycles_per_step": C, "kernel": args.kernel,
+                       "tile_lanes": info["tile_lanes"], "threads": info["threads"],
+                       "ctas_per_sm": info["ctas_per_sm"], "unroll": info["unroll"],
+                       "grid": info["grid"], "parallelism": "replicas" if world > 1 else "1 gpu",
+                       "l2": "state %.1f GB >> 129 MB L2 (no flush needed)"
+                             % (design.info["n_slots"] * n * 8 / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                         "traffic": traffic, "peak_source": peaks["source"],
+                         "bytes_per_instance_cycle": bpc["total"], "kernel": "k_tile"},
+            "gpu_launches": 1 * args.steps,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "parity": parity,
+        }
+        print(json.dumps(line))
+    sim.close()
+    design.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch-1M", choices=sorted(WORKLOADS))
+    ap.add_argument("--kernel", default="tile")
+    ap.add_argument("--chunk", type=int, default=8)
+    ap.add_argument("--tile-lanes", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--unroll", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-verify", dest="verify", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -115,7 +115,7 @@ typedef struct {
   uint64_t op_operands;      /* sum of operand counts over the n_ops netlist ops */
   uint64_t mem_words_total;  /* words of all memories of one lane               */
   uint64_t metadata_bytes;   /* device bytes owned by the design                */
-} rteaal_design_info;
+} rteaal_design_stats;
 
 /* Parse, validate, levelise, group by (opcode, width) and upload the lowered
  * operand lists.  netlist: host bytes (copied; caller keeps ownership).
@@ -123,7 +123,7 @@ typedef struct {
  * rteaal_design_free.  Errors: E_INVALID, E_FORMAT, E_NOMEM, E_CUDA. */
 int rteaal_design_load(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
                        rteaal_design **out);
-int rteaal_design_info(const rteaal_design *design, rteaal_design_info *out);
+int rteaal_design_info(const rteaal_design *design, rteaal_design_stats *out);
 /* Returns E_BUSY (and frees nothing) while sims created from it are alive. */
 int rteaal_design_free(rteaal_design *design);
 
@@ -159,14 +159,14 @@ typedef struct {
   uint64_t device_bytes;         /* state + memories + stimulus + scratch        */
   int kernel;                    /* kernel chosen                                */
   uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid;
-} rteaal_sim_info;
+} rteaal_sim_stats;
 
 /* Allocates and zero-initialises the state of n_instances (>= 1) independent
  * instances, writes the constants.  Registers are 0 until a reset cycle.
  * design must outlive the sim.  Errors: E_INVALID, E_NOMEM, E_CUDA. */
 int rteaal_sim_create(const rteaal_design *design, uint32_t n_instances,
                       const rteaal_sim_opts *opts, rteaal_sim **out);
-int rteaal_sim_info(const rteaal_sim *sim, rteaal_sim_info *out);
+int rteaal_sim_info(const rteaal_sim *sim, rteaal_sim_stats *out);
 void rteaal_sim_destroy(rteaal_sim *sim);
 
 /* Bytes of device memory rteaal_sim_create would take (footprint admission). */

@@ -1,0 +1,426 @@
+"""Python binding of librteaal.so (include/rteaal.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels; this module
+only converts Python / numpy / torch arguments to the C ABI.  There is no CPU
+fallback: if the compiled library is missing, importing the binding's
+functions raises.
+
+PyTorch is used for device memory (its caching allocator is handed to the
+library as the device-memory provider) and for streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Any
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librteaal.so")
+
+RTEAAL_OK, RTEAAL_E_INVALID, RTEAAL_E_FORMAT, RTEAAL_E_NOMEM = 0, -1, -2, -3
+RTEAAL_E_CUDA, RTEAAL_E_TIMEOUT, RTEAAL_E_BUSY, RTEAAL_E_UNSUPPORTED = -4, -5, -6, -7
+RTEAAL_KERNEL_AUTO, RTEAAL_KERNEL_LAYER, RTEAAL_KERNEL_TILE = 0, 1, 2
+RTEAAL_KERNEL_GRID, RTEAAL_KERNEL_LAYER_GRAPH = 3, 4
+RTEAAL_STIM_HOLD, RTEAAL_STIM_XORSHIFT, RTEAAL_STIM_BUFFER = 0, 1, 2
+RTEAAL_PROBE_LAST, RTEAAL_PROBE_EVERY = 0, 1
+RTEAAL_STEP_RESET = 1
+
+KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4}
+
+
+class RteaalError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("rteaal error %d: %s" % (code, msg))
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_ALLOC_FN = ctypes.CFUNCTYPE(_P, ctypes.c_size_t, _P)
+_FREE_FN = ctypes.CFUNCTYPE(None, _P, ctypes.c_size_t, _P)
+
+
+class rteaal_allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", _P)]
+
+
+class rteaal_load_opts(ctypes.Structure):
+    _fields_ = [("allocator", ctypes.POINTER(rteaal_allocator)), ("device", ctypes.c_int)]
+
+
+class rteaal_design_stats(ctypes.Structure):
+    _fields_ = [(n, _U32) for n in ["n_signals", "n_inputs", "n_regs", "n_consts", "n_ops",
+                                    "n_mems", "n_wports", "n_layers", "n_groups", "n_slots",
+                                    "n_lowered_ops", "max_layer_ops"]] + \
+               [(n, _U64) for n in ["op_operands", "mem_words_total", "metadata_bytes"]]
+
+
+class rteaal_sim_opts(ctypes.Structure):
+    _fields_ = [("allocator", ctypes.POINTER(rteaal_allocator)),
+                ("expected_cycles", ctypes.POINTER(_U32)),
+                ("xorshift_seed", ctypes.POINTER(_U64)),
+                ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
+                ("ctas_per_sm", _U32), ("unroll", _U32)]
+
+
+class rteaal_sim_stats(ctypes.Structure):
+    _fields_ = [("n_instances", _U32), ("n_lanes", _U32), ("device_bytes", _U64),
+                ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
+                ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32)]
+
+
+class rteaal_cycles(ctypes.Structure):
+    _fields_ = [("uniform", _U64), ("per_instance", ctypes.POINTER(_U32))]
+
+
+class rteaal_stimulus(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("values", _P), ("values_on_host", ctypes.c_int)]
+
+
+class rteaal_probes(ctypes.Structure):
+    _fields_ = [("signals", ctypes.POINTER(_U32)), ("n", _U32), ("mode", ctypes.c_int),
+                ("out", _P), ("out_on_host", ctypes.c_int)]
+
+
+EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rteaal_sim_create",
+           "rteaal_sim_info", "rteaal_sim_destroy", "rteaal_sim_footprint", "rteaal_step",
+           "rteaal_sync", "rteaal_state_read", "rteaal_state_write", "rteaal_mem_read",
+           "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
+           "rteaal_last_error"]
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library.  Raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("librteaal.so is not built (run __graft_entry__.build() or "
+                              "python paper_2601_18140_gb300/build.py); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        L.rteaal_last_error.restype = ctypes.c_char_p
+        L.rteaal_design_load.argtypes = [ctypes.c_char_p, ctypes.c_size_t,
+                                         ctypes.POINTER(rteaal_load_opts), ctypes.POINTER(_P)]
+        L.rteaal_design_info.argtypes = [_P, ctypes.POINTER(rteaal_design_stats)]
+        L.rteaal_design_free.argtypes = [_P]
+        L.rteaal_sim_create.argtypes = [_P, _U32, ctypes.POINTER(rteaal_sim_opts), ctypes.POINTER(_P)]
+        L.rteaal_sim_info.argtypes = [_P, ctypes.POINTER(rteaal_sim_stats)]
+        L.rteaal_sim_destroy.argtypes = [_P]
+        L.rteaal_sim_destroy.restype = None
+        L.rteaal_sim_footprint.argtypes = [_P, _U32]
+        L.rteaal_sim_footprint.restype = _U64
+        L.rteaal_step.argtypes = [_P, ctypes.POINTER(rteaal_cycles), ctypes.POINTER(rteaal_stimulus),
+                                  ctypes.POINTER(rteaal_probes), _U32, _P]
+        L.rteaal_sync.argtypes = [_P, _P]
+        for n in ["rteaal_state_read", "rteaal_state_write"]:
+            getattr(L, n).argtypes = [_P, ctypes.POINTER(_U32), _U32, _U32, _U32, _P, _P]
+        for n in ["rteaal_mem_read", "rteaal_mem_write", "rteaal_stim_state_read",
+                  "rteaal_stim_state_write"]:
+            getattr(L, n).argtypes = [_P, _U32, _U32, _P, _P]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != RTEAAL_OK:
+        raise RteaalError(rc, lib().rteaal_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a: np.ndarray | None, ctype):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _dev_ptr(x) -> int | None:
+    """Device (or pinned host) pointer of a torch tensor, or an int passed through."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError("expected a torch tensor, numpy array or int pointer")
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream) or None
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return int(stream.cuda_stream) or None
+
+
+# ------------------------------------------------------------ torch allocator
+_torch_alloc: rteaal_allocator | None = None
+
+
+def torch_allocator() -> rteaal_allocator:
+    """PyTorch's caching allocator as an rteaal_allocator (kept alive here)."""
+    global _torch_alloc
+    if _torch_alloc is None:
+        import torch
+
+        def _alloc(n, _ctx):
+            try:
+                dev = torch.cuda.current_device()
+                return int(torch.cuda.caching_allocator_alloc(int(n), dev,
+                                                              torch.cuda.current_stream(dev)))
+            except Exception:
+                return None
+
+        def _free(p, _n, _ctx):
+            torch.cuda.caching_allocator_delete(int(p))
+
+        a = rteaal_allocator()
+        a.alloc = _ALLOC_FN(_alloc)
+        a.free = _FREE_FN(_free)
+        a.ctx = None
+        a._keep = (a.alloc, a.free)
+        _torch_alloc = a
+    return _torch_alloc
+
+
+# ------------------------------------------------------------ C ABI, same names
+def rteaal_design_load(netlist: bytes, opts: rteaal_load_opts | None = None) -> int:
+    out = _P()
+    _check(lib().rteaal_design_load(netlist, len(netlist),
+                                    ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(out)))
+    return out.value
+
+
+def rteaal_design_info(design: int) -> dict:
+    st = rteaal_design_stats()
+    _check(lib().rteaal_design_info(design, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in st._fields_}
+
+
+def rteaal_design_free(design: int):
+    _check(lib().rteaal_design_free(design))
+
+
+def rteaal_sim_create(design: int, n_instances: int, opts: rteaal_sim_opts | None = None) -> int:
+    out = _P()
+    _check(lib().rteaal_sim_create(design, n_instances,
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(out)))
+    return out.value
+
+
+def rteaal_sim_info(sim: int) -> dict:
+    st = rteaal_sim_stats()
+    _check(lib().rteaal_sim_info(sim, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in st._fields_}
+
+
+def rteaal_sim_destroy(sim: int):
+    lib().rteaal_sim_destroy(sim)
+
+
+def rteaal_sim_footprint(design: int, n_instances: int) -> int:
+    return int(lib().rteaal_sim_footprint(design, n_instances))
+
+
+def rteaal_step(sim: int, cycles: rteaal_cycles, stimulus: rteaal_stimulus,
+                probes: rteaal_probes | None, flags: int, stream) -> None:
+    _check(lib().rteaal_step(sim, ctypes.byref(cycles), ctypes.byref(stimulus),
+                             ctypes.byref(probes) if probes is not None else None, flags,
+                             _stream_ptr(stream)))
+
+
+def rteaal_sync(sim: int, stream=None):
+    _check(lib().rteaal_sync(sim, _stream_ptr(stream)))
+
+
+def rteaal_state_read(sim: int, signals, inst_begin: int, n_inst: int, stream=None) -> np.ndarray:
+    sig = np.ascontiguousarray(np.asarray(signals, np.uint32).reshape(-1))
+    out = np.zeros((sig.size, n_inst), np.uint64)
+    _check(lib().rteaal_state_read(sim, _np_ptr(sig, _U32), sig.size, inst_begin, n_inst,
+                                   out.ctypes.data, _stream_ptr(stream)))
+    return out
+
+
+def rteaal_state_write(sim: int, signals, inst_begin: int, values: np.ndarray, stream=None):
+    sig = np.ascontiguousarray(np.asarray(signals, np.uint32).reshape(-1))
+    v = np.ascontiguousarray(values, np.uint64)
+    assert v.shape[0] == sig.size
+    _check(lib().rteaal_state_write(sim, _np_ptr(sig, _U32), sig.size, inst_begin, v.shape[1],
+                                    v.ctypes.data, _stream_ptr(stream)))
+
+
+def rteaal_mem_read(sim: int, inst_begin: int, n_inst: int, words: int, stream=None) -> np.ndarray:
+    out = np.zeros((words, n_inst), np.uint64)
+    _check(lib().rteaal_mem_read(sim, inst_begin, n_inst, out.ctypes.data, _stream_ptr(stream)))
+    return out
+
+
+def rteaal_mem_write(sim: int, inst_begin: int, values: np.ndarray, stream=None):
+    v = np.ascontiguousarray(values, np.uint64)
+    _check(lib().rteaal_mem_write(sim, inst_begin, v.shape[1], v.ctypes.data, _stream_ptr(stream)))
+
+
+def rteaal_stim_state_read(sim: int, inst_begin: int, n_inst: int, n_inputs: int,
+                           stream=None) -> np.ndarray:
+    out = np.zeros((n_inputs, n_inst), np.uint64)
+    _check(lib().rteaal_stim_state_read(sim, inst_begin, n_inst, out.ctypes.data,
+                                        _stream_ptr(stream)))
+    return out
+
+
+def rteaal_stim_state_write(sim: int, inst_begin: int, values: np.ndarray, stream=None):
+    v = np.ascontiguousarray(values, np.uint64)
+    _check(lib().rteaal_stim_state_write(sim, inst_begin, v.shape[1], v.ctypes.data,
+                                         _stream_ptr(stream)))
+
+
+def rteaal_last_error() -> str:
+    return lib().rteaal_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------ convenience objects
+class Design:
+    """A loaded netlist (owns the handle)."""
+
+    def __init__(self, netlist: bytes, use_torch_allocator: bool = True, device: int = -1):
+        self._opts = rteaal_load_opts()
+        self._opts.device = device
+        if use_torch_allocator:
+            self._alloc = torch_allocator()
+            self._opts.allocator = ctypes.pointer(self._alloc)
+        self.handle = rteaal_design_load(netlist, self._opts)
+        self.info = rteaal_design_info(self.handle)
+
+    def footprint(self, n_instances: int) -> int:
+        return rteaal_sim_footprint(self.handle, n_instances)
+
+    def close(self):
+        if self.handle:
+            rteaal_design_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sim:
+    """n_instances independent instances of a design, resident on the device."""
+
+    def __init__(self, design: Design, n_instances: int, kernel: str | int = "auto",
+                 xorshift_seed: np.ndarray | None = None, expected_cycles=None,
+                 tile_lanes: int = 0, threads: int = 0, ctas_per_sm: int = 0, unroll: int = 0,
+                 use_torch_allocator: bool = True):
+        self.design = design
+        self.n = n_instances
+        o = rteaal_sim_opts()
+        o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
+        keep: list[Any] = []
+        if use_torch_allocator:
+            self._alloc = torch_allocator()
+            o.allocator = ctypes.pointer(self._alloc)
+        if xorshift_seed is not None:
+            xs = np.ascontiguousarray(xorshift_seed, np.uint64)
+            assert xs.shape == (design.info["n_inputs"], n_instances)
+            keep.append(xs)
+            o.xorshift_seed = _np_ptr(xs, _U64)
+        if expected_cycles is not None:
+            ec = np.ascontiguousarray(expected_cycles, np.uint32)
+            keep.append(ec)
+            o.expected_cycles = _np_ptr(ec, _U32)
+        self.handle = rteaal_sim_create(design.handle, n_instances, o)
+        self.info = rteaal_sim_info(self.handle)
+
+    def step(self, cycles, stimulus: str = "hold", values=None, reset: bool = False,
+             probes=None, probe_mode: str = "last", probe_out=None, stream=None):
+        """cycles: int or per-instance uint32 array.  values: BUFFER stimulus
+        [cycles][n_inputs][n] as a device tensor / pointer, or a numpy array (host).
+        probes: signal ids; probe_out: device tensor or None (returns a numpy array)."""
+        cyc = rteaal_cycles()
+        keep = []
+        if np.isscalar(cycles):
+            cyc.uniform = int(cycles)
+        else:
+            pc = np.ascontiguousarray(cycles, np.uint32)
+            assert pc.size == self.n
+            keep.append(pc)
+            cyc.per_instance = _np_ptr(pc, _U32)
+        st = rteaal_stimulus()
+        st.mode = {"hold": 0, "xorshift": 1, "buffer": 2}[stimulus]
+        if values is not None:
+            if isinstance(values, np.ndarray):
+                v = np.ascontiguousarray(values, np.uint64)
+                keep.append(v)
+                st.values, st.values_on_host = int(v.ctypes.data), 1
+            else:
+                st.values, st.values_on_host = _dev_ptr(values), 0
+        pr = None
+        host_out = None
+        if probes is not None and len(probes):
+            sig = np.ascontiguousarray(np.asarray(probes, np.uint32))
+            keep.append(sig)
+            pr = rteaal_probes()
+            pr.signals, pr.n = _np_ptr(sig, _U32), sig.size
+            pr.mode = {"last": 0, "every": 1}[probe_mode]
+            if probe_out is None:
+                ncyc = int(np.max(cycles)) if not np.isscalar(cycles) else int(cycles)
+                rows = ncyc if probe_mode == "every" else 1
+                host_out = np.zeros((rows, sig.size, self.n), np.uint64)
+                pr.out, pr.out_on_host = int(host_out.ctypes.data), 1
+            else:
+                pr.out, pr.out_on_host = _dev_ptr(probe_out), 0
+        rteaal_step(self.handle, cyc, st, pr, RTEAAL_STEP_RESET if reset else 0, stream)
+        if host_out is not None:
+            return host_out if probe_mode == "every" else host_out[0]
+        return None
+
+    def sync(self, stream=None):
+        rteaal_sync(self.handle, stream)
+
+    def read(self, signals=None, inst_begin: int = 0, n_inst: int | None = None, stream=None):
+        if signals is None:
+            signals = np.arange(self.design.info["n_signals"], dtype=np.uint32)
+        return rteaal_state_read(self.handle, signals, inst_begin,
+                                 self.n - inst_begin if n_inst is None else n_inst, stream)
+
+    def write(self, signals, values: np.ndarray, inst_begin: int = 0, stream=None):
+        rteaal_state_write(self.handle, signals, inst_begin, values, stream)
+
+    def read_mem(self, inst_begin: int = 0, n_inst: int | None = None, stream=None):
+        return rteaal_mem_read(self.handle, inst_begin, self.n - inst_begin if n_inst is None else n_inst,
+                               int(self.design.info["mem_words_total"]), stream)
+
+    def write_mem(self, values: np.ndarray, inst_begin: int = 0, stream=None):
+        rteaal_mem_write(self.handle, inst_begin, values, stream)
+
+    def read_stim_state(self, inst_begin: int = 0, n_inst: int | None = None, stream=None):
+        return rteaal_stim_state_read(self.handle, inst_begin,
+                                      self.n - inst_begin if n_inst is None else n_inst,
+                                      int(self.design.info["n_inputs"]), stream)
+
+    def write_stim_state(self, values: np.ndarray, inst_begin: int = 0, stream=None):
+        rteaal_stim_state_write(self.handle, inst_begin, values, stream)
+
+    def close(self):
+        if self.handle:
+            rteaal_sim_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

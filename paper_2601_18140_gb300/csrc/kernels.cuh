@@ -1,0 +1,334 @@
+// kernels.cuh -- sm_103a kernels of one simulated cycle.
+//
+// State layout: state[slot][lane], uint64, lane-minor (lane = stimulus
+// instance).  One "item" is one operation evaluated for V consecutive lanes;
+// the lanes of an operation are spread over consecutive threads, so a warp
+// loads whole 8*V*32-byte segments of an operand row (coalesced), and the
+// operation's 16-byte descriptor is a broadcast read.  Operations of a layer
+// are stored grouped by (opcode, width), so neighbouring threads take the same
+// switch arm.  No tensor cores: this is integer gather work bound by memory.
+#pragma once
+#include <cstdint>
+
+#include "lower.hpp"
+
+namespace rteaal {
+
+struct DDesign {
+  const uint4* meta;          // [n_lowered] {a, b, c, ctl}
+  const uint32_t* ext;        // operand slots of ops with > 3 operands
+  const uint32_t* layer_off;  // [n_layers + 1]
+  const uint32_t* reg_src;    // [n_regs]
+  const uint32_t* reg_w;      // [n_regs]
+  const uint64_t* reg_init;   // [n_regs]
+  const uint4* wport;         // [n_wports] {mem, en, addr, data} grouped by memory
+  const uint4* mem_info;      // [n_mems + 1] {word offset, words-1, width, first port}
+  const uint32_t* in_w;       // [n_inputs]
+  uint32_t n_layers, n_regs, n_inputs, n_mems, op_base, reg_base;
+};
+
+// Divide by a runtime constant with a multiply-high (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Fig. 4.1):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q = (mulhi(m, n) + n) >> l.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+
+__host__ __device__ inline uint32_t fdiv(const FastDiv& f, uint32_t n) {
+#ifdef __CUDA_ARCH__
+  const uint64_t t = __umulhi(n, f.m);
+#else
+  const uint64_t t = ((uint64_t)n * f.m) >> 32;
+#endif
+  return (uint32_t)((t + n) >> f.l);
+}
+
+struct DSim {
+  uint64_t* state;
+  uint64_t* mem;
+  uint64_t* xs;                 // [n_inputs][n_pad] xorshift64 states
+  uint32_t n_pad, n_user;
+  const uint32_t* budget;       // [n_pad] cycles this step, or null -> uniform
+  uint32_t uniform;
+  const uint32_t* user_of_lane; // null = identity
+  int stim_mode;
+  const uint64_t* stim;         // [cycles][n_inputs][n_user]
+  int reset;
+  const uint32_t* probe_slot;   // EVERY-mode probes
+  uint32_t n_probe;
+  uint64_t* probe_out;          // [cycles][n_probe][n_user]
+  uint32_t* err;
+};
+
+// Item space over a lane range: item i -> (row i / tpo, lanes base + (i % tpo) * V).
+struct ItemSpace {
+  FastDiv tpo;        // chunks (of V lanes) per row
+  uint32_t lane_base;
+  uint32_t first, stride;
+};
+
+__device__ __forceinline__ uint64_t wmask(uint32_t w) { return ~0ull >> (64u - w); }
+
+__device__ __forceinline__ bool lane_active(const DSim& s, uint32_t lane, uint32_t cyc) {
+  return s.budget ? cyc < __ldg(&s.budget[lane]) : (lane < s.n_user && cyc < s.uniform);
+}
+
+__device__ __forceinline__ uint32_t user_of(const DSim& s, uint32_t lane) {
+  return s.user_of_lane ? __ldg(&s.user_of_lane[lane]) : lane;
+}
+
+// Every opcode except MEMRD and the extended-operand form, then masked to width.
+__device__ __forceinline__ uint64_t alu(uint32_t ctl, uint64_t a, uint64_t b, uint64_t c) {
+  const uint32_t op = ctl & 31u, ar = (ctl >> 5) & 3u;
+  const uint32_t p0 = (ctl >> 16) & 255u, p1 = ctl >> 24;
+  uint64_t r;
+  switch (op) {
+    case OP_COPY: r = a; break;
+    case OP_AND: r = a & b; if (ar == 3) r &= c; break;
+    case OP_OR: r = a | b; if (ar == 3) r |= c; break;
+    case OP_XOR: r = a ^ b; if (ar == 3) r ^= c; break;
+    case OP_NOT: r = ~a; break;
+    case OP_ADD: r = a + b; if (ar == 3) r += c; break;
+    case OP_SUB: r = a - b; break;
+    case OP_MUL: r = a * b; if (ar == 3) r *= c; break;
+    case OP_SHL: r = p0 >= 64u ? 0ull : a << p0; break;
+    case OP_SHR: r = p0 >= 64u ? 0ull : a >> p0; break;
+    case OP_DSHL: r = b >= 64ull ? 0ull : a << (uint32_t)b; break;
+    case OP_DSHR: r = b >= 64ull ? 0ull : a >> (uint32_t)b; break;
+    case OP_BITS: r = (a >> p1) & wmask(p0 - p1 + 1u); break;
+    case OP_CAT: r = (p0 >= 64u ? 0ull : a << p0) | b; break;
+    case OP_EQ: r = a == b; break;
+    case OP_NEQ: r = a != b; break;
+    case OP_LT: r = a < b; break;
+    case OP_LEQ: r = a <= b; break;
+    case OP_GT: r = a > b; break;
+    case OP_GEQ: r = a >= b; break;
+    case OP_MUX: r = (a & 1ull) ? b : c; break;
+    case OP_ANDR: { const uint64_t m = wmask(p0); r = (a & m) == m; } break;
+    case OP_ORR: r = a != 0ull; break;
+    case OP_XORR: r = (uint64_t)(__popcll(a) & 1); break;
+    default: r = 0; break;
+  }
+  return r & wmask((ctl >> 8) & 255u);
+}
+
+// Ops with more than three operands (variadic folds, long mux chains): one lane.
+__device__ __noinline__ uint64_t eval_ext(const DDesign& d, const DSim& s, uint4 m, uint32_t lane) {
+  const uint32_t op = m.w & 31u, n = m.y;
+  const uint32_t* a = d.ext + m.x;
+  const uint64_t* st = s.state + lane;
+  const size_t np = s.n_pad;
+  uint64_t r;
+  if (op == OP_MUXCHAIN) {
+    r = st[(size_t)a[n - 1] * np];
+    for (uint32_t i = 0; i + 1 < n; i += 2)
+      if (st[(size_t)a[i] * np] & 1ull) { r = st[(size_t)a[i + 1] * np]; break; }
+  } else {
+    r = st[(size_t)a[0] * np];
+    for (uint32_t i = 1; i < n; i++) {
+      const uint64_t x = st[(size_t)a[i] * np];
+      switch (op) {
+        case OP_AND: r &= x; break;
+        case OP_OR: r |= x; break;
+        case OP_XOR: r ^= x; break;
+        case OP_ADD: r += x; break;
+        case OP_MUL: r *= x; break;
+        default: break;
+      }
+    }
+  }
+  return r & wmask((m.w >> 8) & 255u);
+}
+
+__device__ __forceinline__ uint64_t eval_memrd(const DDesign& d, const DSim& s, uint32_t ctl,
+                                               uint64_t addr, uint32_t lane) {
+  const uint32_t mi = ((ctl >> 16) & 255u) | ((ctl >> 24) << 8);
+  const uint4 info = __ldg(&d.mem_info[mi]);
+  const uint64_t v = s.mem[((size_t)info.x + (addr & (uint64_t)info.y)) * s.n_pad + lane];
+  return v & wmask((ctl >> 8) & 255u);
+}
+
+template <int V>
+struct Lanes {
+  uint64_t x[V];
+};
+
+template <int V>
+__device__ __forceinline__ Lanes<V> ldl(const uint64_t* p) {
+  Lanes<V> r;
+  if constexpr (V == 2) {
+    const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
+    r.x[0] = t.x;
+    r.x[1] = t.y;
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; v++) r.x[v] = p[v];
+  }
+  return r;
+}
+
+template <int V>
+__device__ __forceinline__ void stl(uint64_t* p, const Lanes<V>& r, const DSim& s, uint32_t lane,
+                                    uint32_t cyc) {
+  if constexpr (V == 2) {
+    const bool a0 = lane_active(s, lane, cyc), a1 = lane_active(s, lane + 1, cyc);
+    if (a0 && a1) {
+      *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(r.x[0], r.x[1]);
+    } else {
+      if (a0) p[0] = r.x[0];
+      if (a1) p[1] = r.x[1];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; v++)
+      if (lane_active(s, lane + v, cyc)) p[v] = r.x[v];
+  }
+}
+
+// Evaluate ops [op0, op0 + n_ops) of the lowered list over the item space.
+// U items are issued per thread before any result is stored (memory-level
+// parallelism: all operand loads of the U items are in flight together).
+template <int V, int U>
+__device__ __forceinline__ void eval_ops(const DDesign& d, const DSim& s, uint32_t op0,
+                                         uint32_t n_items, const ItemSpace& is, uint32_t cyc) {
+  const size_t np = s.n_pad;
+  for (uint32_t i0 = is.first; i0 < n_items; i0 += is.stride * U) {
+    uint4 m[U];
+    uint32_t opi[U], lane[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const uint32_t i = i0 + u * is.stride;
+      ok[u] = i < n_items;
+      const uint32_t row = fdiv(is.tpo, i);
+      opi[u] = op0 + row;
+      lane[u] = is.lane_base + (i - row * is.tpo.d) * V;
+      m[u] = ok[u] ? __ldg(&d.meta[opi[u]]) : make_uint4(0, 0, 0, 0);
+    }
+    Lanes<V> va[U], vb[U], vc[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+#pragma unroll
+      for (int v = 0; v < V; v++) va[u].x[v] = vb[u].x[v] = vc[u].x[v] = 0;
+      if (ok[u] && !(m[u].w & CTL_EXT)) {
+        const uint32_t ar = (m[u].w >> 5) & 3u;
+        va[u] = ldl<V>(s.state + (size_t)m[u].x * np + lane[u]);
+        if (ar >= 2) vb[u] = ldl<V>(s.state + (size_t)m[u].y * np + lane[u]);
+        if (ar >= 3) vc[u] = ldl<V>(s.state + (size_t)m[u].z * np + lane[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (!ok[u]) continue;
+      const uint32_t ctl = m[u].w;
+      Lanes<V> r;
+      if (ctl & CTL_EXT) {
+#pragma unroll
+        for (int v = 0; v < V; v++) r.x[v] = eval_ext(d, s, m[u], lane[u] + v);
+      } else if ((ctl & 31u) == OP_MEMRD) {
+#pragma unroll
+        for (int v = 0; v < V; v++) r.x[v] = eval_memrd(d, s, ctl, va[u].x[v], lane[u] + v);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; v++) r.x[v] = alu(ctl, va[u].x[v], vb[u].x[v], vc[u].x[v]);
+      }
+      stl<V>(s.state + (size_t)(d.op_base + opi[u]) * np + lane[u], r, s, lane[u], cyc);
+    }
+  }
+}
+
+// (a1) primary inputs for cycle cyc.
+template <int V>
+__device__ __forceinline__ void stim_items(const DDesign& d, const DSim& s, const ItemSpace& is,
+                                           uint32_t cyc) {
+  if (s.stim_mode == 0) return;
+  const uint32_t n_items = d.n_inputs * is.tpo.d;
+  const size_t np = s.n_pad;
+  for (uint32_t i = is.first; i < n_items; i += is.stride) {
+    const uint32_t j = fdiv(is.tpo, i);
+    const uint32_t lane0 = is.lane_base + (i - j * is.tpo.d) * V;
+    const uint64_t mk = wmask(__ldg(&d.in_w[j]));
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      const uint32_t lane = lane0 + v;
+      if (!lane_active(s, lane, cyc)) continue;
+      uint64_t x;
+      if (s.stim_mode == 1) {  // xorshift64 (Marsaglia 2003), shifts 13, 7, 17
+        x = s.xs[(size_t)j * np + lane];
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        s.xs[(size_t)j * np + lane] = x;
+      } else {
+        x = __ldg(&s.stim[((size_t)cyc * d.n_inputs + j) * s.n_user + user_of(s, lane)]);
+      }
+      s.state[(size_t)j * np + lane] = x & mk;
+    }
+  }
+}
+
+// (a5) clock edge: registers, then memory write ports (port order per memory).
+template <int V>
+__device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, const ItemSpace& is,
+                                             uint32_t cyc) {
+  const size_t np = s.n_pad;
+  const uint32_t n_reg_items = d.n_regs * is.tpo.d;
+  const uint32_t n_items = n_reg_items + d.n_mems * is.tpo.d;
+  for (uint32_t i = is.first; i < n_items; i += is.stride) {
+    if (i < n_reg_items) {
+      const uint32_t r = fdiv(is.tpo, i);
+      const uint32_t lane = is.lane_base + (i - r * is.tpo.d) * V;
+      const uint64_t mk = wmask(__ldg(&d.reg_w[r]));
+      Lanes<V> v;
+      if (s.reset) {
+        const uint64_t init = __ldg(&d.reg_init[r]) & mk;
+#pragma unroll
+        for (int t = 0; t < V; t++) v.x[t] = init;
+      } else {
+        v = ldl<V>(s.state + (size_t)__ldg(&d.reg_src[r]) * np + lane);
+#pragma unroll
+        for (int t = 0; t < V; t++) v.x[t] &= mk;
+      }
+      stl<V>(s.state + (size_t)(d.reg_base + r) * np + lane, v, s, lane, cyc);
+    } else {
+      const uint32_t k = i - n_reg_items;
+      const uint32_t mi = fdiv(is.tpo, k);
+      const uint32_t lane0 = is.lane_base + (k - mi * is.tpo.d) * V;
+      const uint4 info = __ldg(&d.mem_info[mi]);
+      const uint32_t p1 = __ldg(&d.mem_info[mi + 1]).w;
+      const uint64_t mk = wmask(info.z);
+#pragma unroll
+      for (int t = 0; t < V; t++) {
+        const uint32_t lane = lane0 + t;
+        if (!lane_active(s, lane, cyc)) continue;
+        for (uint32_t p = info.w; p < p1; p++) {
+          const uint4 w = __ldg(&d.wport[p]);
+          if (s.state[(size_t)w.y * np + lane] & 1ull) {
+            const uint64_t a = s.state[(size_t)w.z * np + lane] & (uint64_t)info.y;
+            s.mem[((size_t)info.x + a) * np + lane] = s.state[(size_t)w.w * np + lane] & mk;
+          }
+        }
+      }
+    }
+  }
+}
+
+// (a7) per-cycle probes: end-of-cycle values of selected slots.
+template <int V>
+__device__ __forceinline__ void probe_items(const DSim& s, const ItemSpace& is, uint32_t cyc) {
+  const uint32_t n_items = s.n_probe * is.tpo.d;
+  for (uint32_t i = is.first; i < n_items; i += is.stride) {
+    const uint32_t p = fdiv(is.tpo, i);
+    const uint32_t lane0 = is.lane_base + (i - p * is.tpo.d) * V;
+    const uint32_t slot = __ldg(&s.probe_slot[p]);
+#pragma unroll
+    for (int t = 0; t < V; t++) {
+      const uint32_t lane = lane0 + t;
+      if (!lane_active(s, lane, cyc)) continue;
+      s.probe_out[((size_t)cyc * s.n_probe + p) * s.n_user + user_of(s, lane)] =
+          s.state[(size_t)slot * s.n_pad + lane];
+    }
+  }
+}
+
+}  // namespace rteaal

@@ -1,0 +1,262 @@
+// lower.cpp -- RTLN parsing / validation and the lowering to device tensors.
+#include "lower.hpp"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+namespace rteaal {
+
+namespace {
+
+template <typename T>
+void take(const uint8_t*& p, std::vector<T>& v, size_t n) {
+  v.resize(n);
+  if (n) std::memcpy(v.data(), p, n * sizeof(T));
+  p += n * sizeof(T);
+}
+
+bool fail(std::string& err, const std::string& msg) {
+  err = msg;
+  return false;
+}
+
+}  // namespace
+
+bool parse_netlist(const void* bytes, size_t nbytes, Netlist& n, std::string& err) {
+  if (!bytes || nbytes < 40) return fail(err, "netlist: shorter than the 40-byte header");
+  uint32_t h[10];
+  std::memcpy(h, bytes, sizeof(h));
+  if (h[0] != 0x4E4C5452u) return fail(err, "netlist: bad magic (expected RTLN)");
+  if (h[1] != 1u) return fail(err, "netlist: unsupported version");
+  n.ni = h[2]; n.nr = h[3]; n.nc = h[4]; n.no = h[5]; n.nm = h[6]; n.nw = h[7]; n.na = h[8];
+  const uint64_t need = 40ull + 8ull * n.nr + 8ull * n.nc + 4ull * n.nr + 4ull * (n.no + 1ull) +
+                        4ull * n.na + 4ull * n.nm + 16ull * n.nw + n.ni + n.nr + n.nc +
+                        4ull * n.no + n.nm;
+  if (need != nbytes) return fail(err, "netlist: size does not match the header counts");
+  if ((uint64_t)n.ni + n.nr + n.nc + n.no >= 0x7FFFFFFFull)
+    return fail(err, "netlist: too many signals");
+  const uint8_t* p = static_cast<const uint8_t*>(bytes) + 40;
+  take(p, n.reg_init, n.nr);
+  take(p, n.const_value, n.nc);
+  take(p, n.reg_d, n.nr);
+  take(p, n.argoff, n.no + 1ull);
+  take(p, n.args, n.na);
+  take(p, n.mem_words, n.nm);
+  take(p, n.wport, 4ull * n.nw);
+  take(p, n.in_w, n.ni);
+  take(p, n.reg_w, n.nr);
+  take(p, n.const_w, n.nc);
+  take(p, n.code, n.no);
+  take(p, n.width, n.no);
+  take(p, n.p0, n.no);
+  take(p, n.p1, n.no);
+  take(p, n.mem_w, n.nm);
+
+  const uint32_t nsig = n.n_signals(), opb = n.op_base();
+  auto wok = [](uint32_t w) { return w >= 1 && w <= 64; };
+  for (uint32_t i = 0; i < n.ni; i++)
+    if (!wok(n.in_w[i])) return fail(err, "netlist: input width outside 1..64");
+  for (uint32_t i = 0; i < n.nr; i++) {
+    if (!wok(n.reg_w[i])) return fail(err, "netlist: register width outside 1..64");
+    if (n.reg_d[i] >= nsig) return fail(err, "netlist: register D is not a signal");
+  }
+  for (uint32_t i = 0; i < n.nc; i++)
+    if (!wok(n.const_w[i])) return fail(err, "netlist: constant width outside 1..64");
+  if (n.argoff[0] != 0 || n.argoff[n.no] != n.na)
+    return fail(err, "netlist: operand offsets do not span the operand array");
+  for (uint32_t m = 0; m < n.nm; m++) {
+    const uint32_t w = n.mem_words[m];
+    if (w == 0 || (w & (w - 1)) != 0) return fail(err, "netlist: memory words not a power of two");
+    if (!wok(n.mem_w[m])) return fail(err, "netlist: memory width outside 1..64");
+  }
+  for (uint32_t k = 0; k < n.no; k++) {
+    const uint32_t c = n.code[k], a0 = n.argoff[k], a1 = n.argoff[k + 1];
+    if (a1 < a0) return fail(err, "netlist: operand offsets decrease");
+    if (!wok(n.width[k])) return fail(err, "netlist: op width outside 1..64");
+    if (c >= OP_COUNT) return fail(err, "netlist: unknown opcode");
+    const uint32_t cnt = a1 - a0;
+    for (uint32_t j = a0; j < a1; j++)
+      if (n.args[j] >= opb + k) return fail(err, "netlist: operand not earlier in topological order");
+    bool ok = true;
+    switch (c) {
+      case OP_AND: case OP_OR: case OP_XOR: case OP_ADD: case OP_MUL: ok = cnt >= 2; break;
+      case OP_SUB: case OP_DSHL: case OP_DSHR: case OP_EQ: case OP_NEQ: case OP_LT: case OP_LEQ:
+      case OP_GT: case OP_GEQ: ok = cnt == 2; break;
+      case OP_CAT: ok = cnt == 2 && n.p0[k] >= 1 && n.p0[k] <= 64; break;
+      case OP_MUX: ok = cnt == 3; break;
+      case OP_MUXCHAIN: ok = cnt >= 3 && (cnt & 1u); break;
+      case OP_BITS: ok = cnt == 1 && n.p0[k] >= n.p1[k] && n.p0[k] <= 63; break;
+      case OP_ANDR: ok = cnt == 1 && n.p0[k] >= 1 && n.p0[k] <= 64; break;
+      case OP_MEMRD: ok = cnt == 1 && (uint32_t)(n.p0[k] | (n.p1[k] << 8)) < n.nm; break;
+      default: ok = cnt == 1; break;
+    }
+    if (!ok) return fail(err, "netlist: op " + std::to_string(k) + " has bad operands/params");
+  }
+  for (uint32_t q = 0; q < n.nw; q++) {
+    const uint32_t* w = &n.wport[4ull * q];
+    if (w[0] >= n.nm || w[1] >= nsig || w[2] >= nsig || w[3] >= nsig)
+      return fail(err, "netlist: write port references a bad memory or signal");
+  }
+  return true;
+}
+
+void lower_netlist(const Netlist& nl, Lowered& L) {
+  const uint32_t nsig = nl.n_signals(), opb = nl.op_base();
+
+  // 1. levelisation: level(pool) = 0, level(op) = 1 + max level of its operands.
+  std::vector<uint32_t> level(nsig, 0);
+  for (uint32_t k = 0; k < nl.no; k++) {
+    uint32_t lv = 0;
+    for (uint32_t j = nl.argoff[k]; j < nl.argoff[k + 1]; j++) lv = std::max(lv, level[nl.args[j]]);
+    level[opb + k] = lv + 1;
+  }
+
+  // 2. lowered op list: netlist ops plus a COPY (level 1) for every register D or
+  //    write-port signal that is not an op output, so that the clock edge reads only
+  //    op slots (no hazard with the register writes or the next cycle's inputs).
+  struct LOp {
+    uint32_t level, code, width, p0, p1, src_sig;  // src_sig: netlist op index, or copy source
+    bool is_copy;
+  };
+  std::vector<LOp> ops;
+  ops.reserve(nl.no + 16);
+  for (uint32_t k = 0; k < nl.no; k++)
+    ops.push_back({level[opb + k], nl.code[k], nl.width[k], nl.p0[k], nl.p1[k], k, false});
+  std::unordered_map<uint32_t, uint32_t> copy_of;  // pool signal -> lowered op index
+  std::vector<uint8_t> sig_w(nsig);
+  for (uint32_t i = 0; i < nl.ni; i++) sig_w[i] = nl.in_w[i];
+  for (uint32_t i = 0; i < nl.nr; i++) sig_w[nl.ni + i] = nl.reg_w[i];
+  for (uint32_t i = 0; i < nl.nc; i++) sig_w[nl.ni + nl.nr + i] = nl.const_w[i];
+  for (uint32_t k = 0; k < nl.no; k++) sig_w[opb + k] = nl.width[k];
+  auto edge_src = [&](uint32_t sig) -> int64_t {  // lowered op index that holds sig
+    if (sig >= opb) return (int64_t)(sig - opb);
+    auto it = copy_of.find(sig);
+    if (it != copy_of.end()) return it->second;
+    const uint32_t idx = (uint32_t)ops.size();
+    ops.push_back({1u, OP_COPY, sig_w[sig], 0u, 0u, sig, true});
+    copy_of[sig] = idx;
+    return idx;
+  };
+  std::vector<int64_t> reg_lop(nl.nr);
+  for (uint32_t r = 0; r < nl.nr; r++) reg_lop[r] = edge_src(nl.reg_d[r]);
+  std::vector<int64_t> wp_lop(3ull * nl.nw);
+  for (uint32_t q = 0; q < nl.nw; q++)
+    for (int t = 0; t < 3; t++) wp_lop[3ull * q + t] = edge_src(nl.wport[4ull * q + 1 + t]);
+  L.n_copies = (uint32_t)copy_of.size();
+
+  // 3. order: by level, then (opcode, width) -- the N rank swizzled above S --
+  //    then original order.  Position = slot offset (S coordinates implicit).
+  std::vector<uint32_t> order(ops.size());
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    const LOp &a = ops[x], &b = ops[y];
+    if (a.level != b.level) return a.level < b.level;
+    if (a.code != b.code) return a.code < b.code;
+    return a.width < b.width;
+  });
+  std::vector<uint32_t> pos(ops.size());
+  for (uint32_t i = 0; i < order.size(); i++) pos[order[i]] = i;
+
+  L.input_base = 0;
+  L.reg_base = nl.ni;
+  L.const_base = nl.ni + nl.nr;
+  L.op_base = opb;
+  L.n_slots = opb + (uint32_t)ops.size();
+  L.sig2slot.resize(nsig);
+  for (uint32_t s = 0; s < opb; s++) L.sig2slot[s] = s;
+  for (uint32_t k = 0; k < nl.no; k++) L.sig2slot[opb + k] = opb + pos[k];
+
+  // 4. per-op metadata (operands as slots, ctl word)
+  L.meta.resize(ops.size());
+  L.ext_args.clear();
+  L.lowered_operands = 0;
+  L.op_operands = nl.na;
+  uint32_t n_layers = 0;
+  for (const LOp& o : ops) n_layers = std::max(n_layers, o.level);
+  L.layer_off.assign(n_layers + 1, 0);
+  L.group_off.clear();
+  for (uint32_t i = 0; i < order.size(); i++) {
+    const LOp& o = ops[order[i]];
+    std::vector<uint32_t> a;
+    uint32_t code = o.code;
+    if (o.is_copy) {
+      a.push_back(L.sig2slot[o.src_sig]);
+    } else {
+      const uint32_t k = o.src_sig;
+      for (uint32_t j = nl.argoff[k]; j < nl.argoff[k + 1]; j++) a.push_back(L.sig2slot[nl.args[j]]);
+      if (code == OP_MUXCHAIN && a.size() == 3) code = OP_MUX;  // one pair + default == mux
+    }
+    L.lowered_operands += a.size();
+    OpMeta m{};
+    uint32_t ctl = code | (o.width << 8) | (o.p0 << 16) | (o.p1 << 24);
+    if (a.size() <= 3) {
+      m.a = a[0];
+      m.b = a.size() > 1 ? a[1] : a[0];
+      m.c = a.size() > 2 ? a[2] : a[0];
+      ctl |= (uint32_t)a.size() << 5;
+    } else {
+      m.a = (uint32_t)L.ext_args.size();
+      m.b = (uint32_t)a.size();
+      m.c = 0;
+      L.ext_args.insert(L.ext_args.end(), a.begin(), a.end());
+      ctl |= CTL_EXT;
+    }
+    m.ctl = ctl;
+    L.meta[i] = m;
+    L.layer_off[o.level] = i + 1;  // running end of the layer
+    if (i == 0 || ops[order[i - 1]].level != o.level || ops[order[i - 1]].code != o.code ||
+        ops[order[i - 1]].width != o.width)
+      L.group_off.push_back(i);
+  }
+  L.group_off.push_back((uint32_t)order.size());
+  // layer_off[l] holds the end of level l (levels 1..n); shift to begin offsets
+  std::vector<uint32_t> ends(L.layer_off.begin() + 1, L.layer_off.end());
+  L.layer_off[0] = 0;
+  for (uint32_t l = 0; l < n_layers; l++) L.layer_off[l + 1] = ends[l];
+  L.max_layer_ops = 0;
+  for (uint32_t l = 0; l < n_layers; l++)
+    L.max_layer_ops = std::max(L.max_layer_ops, L.layer_off[l + 1] - L.layer_off[l]);
+
+  // 5. clock-edge tables
+  L.reg_src.resize(nl.nr);
+  L.reg_width.resize(nl.nr);
+  L.reg_init.resize(nl.nr);
+  for (uint32_t r = 0; r < nl.nr; r++) {
+    L.reg_src[r] = opb + pos[(uint32_t)reg_lop[r]];
+    L.reg_width[r] = nl.reg_w[r];
+    L.reg_init[r] = nl.reg_init[r];
+  }
+  L.in_width.assign(nl.in_w.begin(), nl.in_w.end());
+  L.const_value.resize(nl.nc);
+  for (uint32_t c = 0; c < nl.nc; c++) {
+    const uint32_t w = nl.const_w[c];
+    L.const_value[c] = nl.const_value[c] & (~0ull >> (64 - w));
+  }
+  // memories and their write ports (grouped by memory, port order preserved)
+  std::vector<uint32_t> pidx(nl.nw);
+  std::iota(pidx.begin(), pidx.end(), 0u);
+  std::stable_sort(pidx.begin(), pidx.end(),
+                   [&](uint32_t x, uint32_t y) { return nl.wport[4ull * x] < nl.wport[4ull * y]; });
+  L.wport.resize(4ull * nl.nw);
+  for (uint32_t i = 0; i < nl.nw; i++) {
+    const uint32_t q = pidx[i];
+    L.wport[4ull * i + 0] = nl.wport[4ull * q];
+    for (int t = 0; t < 3; t++) L.wport[4ull * i + 1 + t] = opb + pos[(uint32_t)wp_lop[3ull * q + t]];
+  }
+  L.mem_info.assign(4ull * (nl.nm + 1), 0);
+  uint64_t off = 0;
+  uint32_t port = 0;
+  for (uint32_t m = 0; m <= nl.nm; m++) {
+    while (port < nl.nw && L.wport[4ull * port] < m) port++;
+    L.mem_info[4ull * m + 0] = (uint32_t)off;
+    L.mem_info[4ull * m + 1] = m < nl.nm ? nl.mem_words[m] - 1 : 0;
+    L.mem_info[4ull * m + 2] = m < nl.nm ? nl.mem_w[m] : 0;
+    L.mem_info[4ull * m + 3] = port;
+    if (m < nl.nm) off += nl.mem_words[m];
+  }
+  L.mem_words_total = off;
+}
+
+}  // namespace rteaal

@@ -1,0 +1,68 @@
+// lower.hpp -- netlist parsing and the netlist -> device-tensor lowering.
+//
+// The lowering realises the paper's compile flow (Sec. 5.1, Fig. "compiler"):
+// levelisation by topological sort (Sec. 4.2), the OIM built per layer with
+// operations of one type grouped together (the swizzled [I, N, S, O, R] format
+// of the NU kernel, Sec. 4.4 / Fig. "opt-space:format"c), and identity
+// elision by assigning every signal one global slot (Sec. 4.3, Sec. 5.1).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace rteaal {
+
+enum Opcode : uint8_t {
+  OP_COPY = 0, OP_AND, OP_OR, OP_XOR, OP_NOT, OP_ADD, OP_SUB, OP_MUL, OP_SHL, OP_SHR, OP_DSHL,
+  OP_DSHR, OP_BITS, OP_CAT, OP_EQ, OP_NEQ, OP_LT, OP_LEQ, OP_GT, OP_GEQ, OP_MUX, OP_ANDR, OP_ORR,
+  OP_XORR, OP_MEMRD, OP_MUXCHAIN, OP_COUNT
+};
+
+// ctl word of a lowered op: opcode (5 bits) | arity (2 bits, 1..3) << 5 |
+// extended-operand flag << 7 | width << 8 | p0 << 16 | p1 << 24.
+constexpr uint32_t CTL_EXT = 1u << 7;
+
+struct Netlist {
+  uint32_t ni = 0, nr = 0, nc = 0, no = 0, nm = 0, nw = 0, na = 0;
+  std::vector<uint64_t> reg_init, const_value;
+  std::vector<uint32_t> reg_d, argoff, args, mem_words, wport;  // wport: 4 per port
+  std::vector<uint8_t> in_w, reg_w, const_w, code, width, p0, p1, mem_w;
+  uint32_t n_signals() const { return ni + nr + nc + no; }
+  uint32_t op_base() const { return ni + nr + nc; }
+};
+
+// Returns true on success; on failure err describes the first violation.
+bool parse_netlist(const void* bytes, size_t nbytes, Netlist& out, std::string& err);
+
+struct OpMeta {  // 16 bytes, one per lowered op (device uint4)
+  uint32_t a, b, c, ctl;
+};
+
+struct Lowered {
+  uint32_t n_slots = 0;
+  uint32_t input_base = 0, reg_base = 0, const_base = 0, op_base = 0;  // slot bases
+  std::vector<uint32_t> sig2slot;        // [n_signals]
+  std::vector<OpMeta> meta;              // [n_lowered] in slot order
+  std::vector<uint32_t> ext_args;        // operand slots of ops with > 3 operands
+  std::vector<uint32_t> layer_off;       // [n_layers + 1] into meta
+  std::vector<uint32_t> group_off;       // [n_groups + 1] into meta ((layer, opcode, width) runs)
+  std::vector<uint32_t> reg_src;         // [n_regs] slot of D (always an op slot)
+  std::vector<uint32_t> reg_width;       // [n_regs]
+  std::vector<uint64_t> reg_init;        // [n_regs]
+  std::vector<uint32_t> in_width;        // [n_inputs]
+  std::vector<uint64_t> const_value;     // [n_consts] masked
+  std::vector<uint32_t> mem_info;        // [n_mems][4] = word offset, words-1, width, first port
+  std::vector<uint32_t> wport;           // [n_wports][4] = mem, en slot, addr slot, data slot,
+                                         //   sorted by memory, port order kept
+  uint64_t mem_words_total = 0;
+  uint64_t op_operands = 0;              // sum of operand counts over netlist ops
+  uint32_t n_copies = 0;                 // copies inserted for edge sources
+  uint32_t max_layer_ops = 0;
+  // per-op-eval algorithmic bytes bookkeeping: sum over lowered ops of operands read
+  uint64_t lowered_operands = 0;
+};
+
+void lower_netlist(const Netlist& nl, Lowered& out);
+
+}  // namespace rteaal

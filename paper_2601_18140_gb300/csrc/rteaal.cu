@@ -1,0 +1,1004 @@
+// rteaal.cu -- kernels of the three execution forms and the C ABI (include/rteaal.h).
+//
+//   LAYER  plain form: per cycle one launch for the inputs, one per layer (the
+//          kernel boundary is the LI_{i+1} <- LO_i barrier), one for the edge.
+//   LAYER_GRAPH  the same launch sequence for one cycle captured as a CUDA graph
+//          and replayed once per cycle (cycle index kept on the device).
+//   TILE   persistent: each CTA takes a tile of lanes (instances) from an atomic
+//          queue, longest remaining work first, and walks every layer of every
+//          cycle of that tile with CTA barriers only.  Instances are
+//          independent, so no grid-wide synchronisation exists at all.
+//   GRID   persistent cooperative: the whole grid walks each layer for all
+//          lanes, separated by a software grid barrier with a bounded wait.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "lower.hpp"
+#include "rteaal.h"
+
+#define RT_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace rteaal {
+
+// ------------------------------------------------------------------ kernels
+
+template <int V, int U>
+__global__ void __launch_bounds__(256) k_layer_ops(DDesign d, DSim s, uint32_t op0,
+                                                   uint32_t n_items, FastDiv tpo, uint32_t cyc,
+                                                   const uint32_t* cyc_dev) {
+  if (cyc_dev) cyc = *cyc_dev;
+  ItemSpace is{tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  eval_ops<V, U>(d, s, op0, n_items, is, cyc);
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_layer_stim(DDesign d, DSim s, FastDiv tpo, uint32_t cyc,
+                                                    const uint32_t* cyc_dev) {
+  if (cyc_dev) cyc = *cyc_dev;
+  ItemSpace is{tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  stim_items<V>(d, s, is, cyc);
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_layer_commit(DDesign d, DSim s, FastDiv tpo, uint32_t cyc,
+                                                      const uint32_t* cyc_dev) {
+  if (cyc_dev) cyc = *cyc_dev;
+  ItemSpace is{tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  commit_items<V>(d, s, is, cyc);
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_layer_probe(DSim s, FastDiv tpo, uint32_t cyc,
+                                                     const uint32_t* cyc_dev) {
+  if (cyc_dev) cyc = *cyc_dev;
+  ItemSpace is{tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  probe_items<V>(s, is, cyc);
+}
+
+__global__ void k_tick(uint32_t* cyc_dev) { *cyc_dev += 1u; }
+
+struct TileArgs {
+  uint32_t* counter;             // scratch: next queue position
+  const uint32_t* order;         // queue position -> tile (longest first), null = identity
+  const uint32_t* tile_cycles;   // per tile, null -> uniform
+  uint32_t n_tiles, tile_lanes;
+  FastDiv tpo;                   // tile_lanes / V
+};
+
+template <int V, int U>
+__global__ void __launch_bounds__(512) k_tile(DDesign d, DSim s, TileArgs t) {
+  __shared__ uint32_t sh_q;
+  for (;;) {
+    if (threadIdx.x == 0) sh_q = atomicAdd(t.counter, 1u);
+    __syncthreads();
+    const uint32_t q = sh_q;
+    __syncthreads();
+    if (q >= t.n_tiles) return;
+    const uint32_t tile = t.order ? t.order[q] : q;
+    const ItemSpace is{t.tpo, tile * t.tile_lanes, threadIdx.x, blockDim.x};
+    const uint32_t ncyc = t.tile_cycles ? t.tile_cycles[tile] : s.uniform;
+    for (uint32_t c = 0; c < ncyc; c++) {
+      stim_items<V>(d, s, is, c);
+      __syncthreads();
+      for (uint32_t L = 0; L < d.n_layers; L++) {
+        const uint32_t o0 = __ldg(&d.layer_off[L]), o1 = __ldg(&d.layer_off[L + 1]);
+        eval_ops<V, U>(d, s, o0, (o1 - o0) * t.tpo.d, is, c);
+        __syncthreads();
+      }
+      commit_items<V>(d, s, is, c);
+      __syncthreads();
+      if (s.n_probe) {
+        probe_items<V>(s, is, c);
+        __syncthreads();
+      }
+    }
+  }
+}
+
+struct GridArgs {
+  uint32_t* count;        // scratch: arrivals at the current barrier
+  uint32_t* gen;          // scratch: barrier generation
+  uint32_t expected;      // arrivals that complete a barrier (= gridDim.x)
+  uint64_t timeout_ns;    // bounded wait per barrier
+  uint32_t ncyc;
+  FastDiv tpo;            // n_pad / V
+};
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Software grid barrier (sense by generation counter).  Every wait is bounded:
+// after timeout_ns the block sets *err and returns false; blocks that see *err
+// leave at their next barrier, so the kernel always ends.
+__device__ __forceinline__ bool grid_sync(const GridArgs& g, uint32_t* err, int* sh_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const uint32_t my = ld_acquire(g.gen);
+    __threadfence();
+    if (atomicAdd(g.count, 1u) == g.expected - 1u) {
+      atomicExch(g.count, 0u);
+      __threadfence();
+      atomicAdd(g.gen, 1u);
+    } else {
+      const uint64_t t0 = globaltimer();
+      while (ld_acquire(g.gen) == my) {
+        if (ld_acquire(err) != 0u) { ok = 0; break; }
+        if (globaltimer() - t0 > g.timeout_ns) { atomicOr(err, 1u); ok = 0; break; }
+        __nanosleep(100);
+      }
+    }
+    if (ld_acquire(err) != 0u) ok = 0;
+    __threadfence();
+    *sh_ok = ok;
+  }
+  __syncthreads();
+  return *sh_ok != 0;
+}
+
+template <int V, int U>
+__global__ void __launch_bounds__(512) k_grid(DDesign d, DSim s, GridArgs g) {
+  __shared__ int sh_ok;
+  const ItemSpace is{g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  for (uint32_t c = 0; c < g.ncyc; c++) {
+    stim_items<V>(d, s, is, c);
+    if (!grid_sync(g, s.err, &sh_ok)) return;
+    for (uint32_t L = 0; L < d.n_layers; L++) {
+      const uint32_t o0 = __ldg(&d.layer_off[L]), o1 = __ldg(&d.layer_off[L + 1]);
+      eval_ops<V, U>(d, s, o0, (o1 - o0) * g.tpo.d, is, c);
+      if (!grid_sync(g, s.err, &sh_ok)) return;
+    }
+    commit_items<V>(d, s, is, c);
+    if (!grid_sync(g, s.err, &sh_ok)) return;
+    if (s.n_probe) {
+      probe_items<V>(s, is, c);
+      if (!grid_sync(g, s.err, &sh_ok)) return;
+    }
+  }
+}
+
+// state[slot][lane] <-> host [n][n_inst] through a [n][n_inst] device buffer
+__global__ void k_gather(const uint64_t* src, uint32_t n_pad, const uint32_t* rows, uint32_t n_rows,
+                         const uint32_t* lane_of_user, uint32_t inst0, uint32_t n_inst,
+                         uint64_t* out) {
+  const size_t total = (size_t)n_rows * n_inst;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)(i / n_inst), k = (uint32_t)(i % n_inst);
+    const uint32_t row = rows ? rows[r] : r;
+    const uint32_t lane = lane_of_user ? lane_of_user[inst0 + k] : inst0 + k;
+    out[i] = src[(size_t)row * n_pad + lane];
+  }
+}
+
+__global__ void k_scatter(uint64_t* dst, uint32_t n_pad, const uint32_t* rows, uint32_t n_rows,
+                          const uint32_t* lane_of_user, uint32_t inst0, uint32_t n_inst,
+                          const uint64_t* in, const uint64_t* row_mask) {
+  const size_t total = (size_t)n_rows * n_inst;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)(i / n_inst), k = (uint32_t)(i % n_inst);
+    const uint32_t row = rows ? rows[r] : r;
+    const uint32_t lane = lane_of_user ? lane_of_user[inst0 + k] : inst0 + k;
+    dst[(size_t)row * n_pad + lane] = in[i] & (row_mask ? row_mask[r] : ~0ull);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+thread_local std::string g_err;
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      throw Error(RTEAAL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{d, 0, 0};
+  uint32_t l = 0;
+  while ((1ull << l) < d) l++;
+  f.l = l;
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1ull);
+  return f;
+}
+
+struct Allocator {
+  rteaal_allocator a{};
+  bool custom = false;
+  void* alloc(size_t n) {
+    if (n == 0) n = 256;
+    void* p = nullptr;
+    if (custom) {
+      p = a.alloc(n, a.ctx);
+    } else if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (!p) throw Error(RTEAAL_E_NOMEM, "device allocation of " + std::to_string(n) + " bytes failed");
+    return p;
+  }
+  void free(void* p, size_t n) {
+    if (!p) return;
+    if (n == 0) n = 256;
+    if (custom) a.free(p, n, a.ctx);
+    else cudaFree(p);
+  }
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace rteaal
+
+using namespace rteaal;
+
+struct rteaal_design {
+  Netlist nl;
+  Lowered L;
+  Allocator alloc;
+  int device = 0;
+  int n_sms = 0;
+  DDesign dd{};
+  std::vector<DevBuf> bufs;
+  int live_sims = 0;
+  std::mutex mu;
+  uint64_t metadata_bytes = 0;
+
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    DevBuf b;
+    b.n = std::max<size_t>(v.size() * sizeof(T), 16);
+    b.p = alloc.alloc(b.n);
+    bufs.push_back(b);
+    if (!v.empty()) CK(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    metadata_bytes += b.n;
+    return static_cast<T*>(b.p);
+  }
+  ~rteaal_design() {
+    for (auto& b : bufs) alloc.free(b.p, b.n);
+  }
+};
+
+struct rteaal_sim {
+  const rteaal_design* design = nullptr;
+  rteaal_design* design_mut = nullptr;
+  Allocator alloc;
+  uint32_t n_user = 0, n_pad = 0;
+  int kernel = RTEAAL_KERNEL_AUTO;
+  uint32_t tile_lanes = 0, threads = 0, ctas_per_sm = 0, unroll = 0, grid = 0;
+  int V = 2;
+  uint64_t* state = nullptr;
+  uint64_t* mem = nullptr;
+  uint64_t* xs = nullptr;
+  uint32_t* budget = nullptr;        // [n_pad]
+  uint32_t* user_of_lane = nullptr;  // [n_pad] or null
+  uint32_t* lane_of_user = nullptr;  // [n_user] or null
+  uint32_t* tile_order = nullptr;    // [n_tiles]
+  uint32_t* tile_cycles = nullptr;   // [n_tiles]
+  uint32_t* scratch = nullptr;       // [64]: 0 err, 1 tile counter, 2 bar count, 3 bar gen, 4 cycle
+  uint64_t* staging = nullptr;       // grown on demand (host stimulus / probe buffers)
+  size_t staging_bytes = 0;
+  uint32_t* probe_slots = nullptr;   // grown on demand
+  size_t probe_slots_cap = 0;
+  uint32_t* err_host = nullptr;      // pinned
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+  uint64_t device_bytes = 0;
+  std::vector<uint32_t> h_lane_of_user, h_user_of_lane;
+  std::vector<DevBuf> bufs;
+  uint64_t barrier_timeout_ns = 2000000000ull;
+  uint32_t barrier_extra = 0;        // test hook: arrivals withheld from every grid barrier
+
+  void* get(size_t n) {
+    DevBuf b;
+    b.n = n;
+    b.p = alloc.alloc(n);
+    bufs.push_back(b);
+    device_bytes += n;
+    return b.p;
+  }
+  ~rteaal_sim() {
+    if (done) cudaEventDestroy(done);
+    if (err_host) cudaFreeHost(err_host);
+    for (auto& b : bufs) alloc.free(b.p, b.n);
+  }
+};
+
+namespace {
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    f();
+    return RTEAAL_OK;
+  } catch (const Error& e) {
+    g_err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return RTEAAL_E_NOMEM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return RTEAAL_E_INVALID;
+  }
+}
+
+void require(bool c, const char* msg) {
+  if (!c) throw Error(RTEAAL_E_INVALID, msg);
+}
+
+uint32_t pad_lanes(uint32_t n) {
+  if (n <= 1) return 1;
+  uint32_t p = 1;
+  while (p < n && p < 64) p <<= 1;
+  return (n + p - 1) / p * p;
+}
+
+DSim dsim(const rteaal_sim* s) {
+  DSim x{};
+  x.state = s->state;
+  x.mem = s->mem;
+  x.xs = s->xs;
+  x.n_pad = s->n_pad;
+  x.n_user = s->n_user;
+  x.user_of_lane = s->user_of_lane;
+  x.err = s->scratch;
+  return x;
+}
+
+void check_pending(rteaal_sim* s) {
+  if (!s->pending) return;
+  cudaError_t q = cudaEventQuery(s->done);
+  if (q == cudaErrorNotReady) return;
+  if (q != cudaSuccess) throw Error(RTEAAL_E_CUDA, std::string("previous step: ") + cudaGetErrorString(q));
+  s->pending = false;
+  if (*s->err_host) {
+    *s->err_host = 0;
+    throw Error(RTEAAL_E_TIMEOUT, "a grid barrier wait timed out in a previous step");
+  }
+}
+
+void sync_sim(rteaal_sim* s, cudaStream_t st) {
+  CK(cudaStreamSynchronize(st));
+  if (s->pending) {
+    CK(cudaEventSynchronize(s->done));
+    s->pending = false;
+    if (*s->err_host) {
+      *s->err_host = 0;
+      throw Error(RTEAAL_E_TIMEOUT, "a grid barrier wait timed out");
+    }
+  }
+}
+
+template <int V>
+void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32_t c,
+                        const uint32_t* cyc_dev, cudaStream_t st, int n_sms) {
+  const FastDiv tpo = make_fastdiv(s->n_pad / V);
+  const uint32_t threads = 256;
+  auto blocks_for = [&](uint64_t items, uint32_t per_thread) {
+    uint64_t b = (items + (uint64_t)threads * per_thread - 1) / ((uint64_t)threads * per_thread);
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(b, (uint64_t)n_sms * 16));
+  };
+  const rteaal_design* D = s->design;
+  if (ds.stim_mode)
+    k_layer_stim<V><<<blocks_for((uint64_t)D->L.in_width.size() * tpo.d, 1), threads, 0, st>>>(
+        dd, ds, tpo, c, cyc_dev);
+  const uint32_t U = s->unroll;
+  for (uint32_t l = 0; l + 1 < D->L.layer_off.size(); l++) {
+    const uint32_t o0 = D->L.layer_off[l], o1 = D->L.layer_off[l + 1];
+    const uint64_t items = (uint64_t)(o1 - o0) * tpo.d;
+    if (U >= 4)
+      k_layer_ops<V, 4><<<blocks_for(items, 4), threads, 0, st>>>(dd, ds, o0, (uint32_t)items, tpo, c, cyc_dev);
+    else if (U == 2)
+      k_layer_ops<V, 2><<<blocks_for(items, 2), threads, 0, st>>>(dd, ds, o0, (uint32_t)items, tpo, c, cyc_dev);
+    else
+      k_layer_ops<V, 1><<<blocks_for(items, 1), threads, 0, st>>>(dd, ds, o0, (uint32_t)items, tpo, c, cyc_dev);
+  }
+  const uint64_t citems = (uint64_t)(D->L.reg_src.size() + (D->L.mem_info.size() / 4 - 1)) * tpo.d;
+  if (citems)
+    k_layer_commit<V><<<blocks_for(citems, 1), threads, 0, st>>>(dd, ds, tpo, c, cyc_dev);
+  if (ds.n_probe)
+    k_layer_probe<V><<<blocks_for((uint64_t)ds.n_probe * tpo.d, 1), threads, 0, st>>>(ds, tpo, c, cyc_dev);
+}
+
+template <int V, int U>
+void launch_tile(rteaal_sim* s, const DDesign& dd, const DSim& ds, const TileArgs& ta, uint32_t grid,
+                 cudaStream_t st) {
+  k_tile<V, U><<<grid, s->threads, 0, st>>>(dd, ds, ta);
+}
+
+template <int V, int U>
+cudaError_t launch_grid(rteaal_sim* s, const DDesign& dd, DSim ds, GridArgs ga, uint32_t grid,
+                        cudaStream_t st) {
+  void* args[] = {(void*)&dd, (void*)&ds, (void*)&ga};
+  return cudaLaunchCooperativeKernel((const void*)k_grid<V, U>, dim3(grid), dim3(s->threads), args, 0, st);
+}
+
+template <int V, int U>
+int grid_blocks_per_sm(uint32_t threads) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_grid<V, U>, (int)threads, 0);
+  return nb;
+}
+
+template <int V, int U>
+int tile_blocks_per_sm(uint32_t threads) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<V, U>, (int)threads, 0);
+  return nb;
+}
+
+int occupancy(rteaal_sim* s, bool grid) {
+  const uint32_t t = s->threads;
+  const bool v2 = s->V == 2;
+  const uint32_t U = s->unroll;
+  if (grid) {
+    if (v2) return U >= 4 ? grid_blocks_per_sm<2, 4>(t) : U == 2 ? grid_blocks_per_sm<2, 2>(t) : grid_blocks_per_sm<2, 1>(t);
+    return U >= 4 ? grid_blocks_per_sm<1, 4>(t) : U == 2 ? grid_blocks_per_sm<1, 2>(t) : grid_blocks_per_sm<1, 1>(t);
+  }
+  if (v2) return U >= 4 ? tile_blocks_per_sm<2, 4>(t) : U == 2 ? tile_blocks_per_sm<2, 2>(t) : tile_blocks_per_sm<2, 1>(t);
+  return U >= 4 ? tile_blocks_per_sm<1, 4>(t) : U == 2 ? tile_blocks_per_sm<1, 2>(t) : tile_blocks_per_sm<1, 1>(t);
+}
+
+void ensure_staging(rteaal_sim* s, size_t bytes) {
+  if (s->staging_bytes >= bytes) return;
+  if (s->staging) {
+    CK(cudaDeviceSynchronize());
+    for (auto it = s->bufs.begin(); it != s->bufs.end(); ++it)
+      if (it->p == s->staging) {
+        s->alloc.free(it->p, it->n);
+        s->device_bytes -= it->n;
+        s->bufs.erase(it);
+        break;
+      }
+  }
+  s->staging = static_cast<uint64_t*>(s->get(bytes));
+  s->staging_bytes = bytes;
+}
+
+void ensure_probe_slots(rteaal_sim* s, size_t n) {
+  if (s->probe_slots_cap >= n) return;
+  s->probe_slots = static_cast<uint32_t*>(s->get(std::max<size_t>(n, 64) * 4));
+  s->probe_slots_cap = std::max<size_t>(n, 64);
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+RT_EXPORT const char* rteaal_last_error(void) { return g_err.c_str(); }
+
+RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaal_load_opts* opts,
+                                 rteaal_design** out) {
+  return guarded([&] {
+    require(netlist && out, "rteaal_design_load: null argument");
+    *out = nullptr;
+    auto* d = new rteaal_design();
+    try {
+      std::string err;
+      if (!parse_netlist(netlist, nbytes, d->nl, err)) throw Error(RTEAAL_E_FORMAT, err);
+      if (opts && opts->allocator) {
+        d->alloc.a = *opts->allocator;
+        d->alloc.custom = d->alloc.a.alloc && d->alloc.a.free;
+      }
+      if (opts && opts->device >= 0) CK(cudaSetDevice(opts->device));
+      CK(cudaGetDevice(&d->device));
+      CK(cudaDeviceGetAttribute(&d->n_sms, cudaDevAttrMultiProcessorCount, d->device));
+      lower_netlist(d->nl, d->L);
+      const Lowered& L = d->L;
+      DDesign& dd = d->dd;
+      static_assert(sizeof(OpMeta) == sizeof(uint4), "descriptor is 16 bytes");
+      dd.meta = reinterpret_cast<const uint4*>(d->upload(L.meta));
+      dd.ext = d->upload(L.ext_args);
+      dd.layer_off = d->upload(L.layer_off);
+      dd.reg_src = d->upload(L.reg_src);
+      dd.reg_w = d->upload(L.reg_width);
+      dd.reg_init = d->upload(L.reg_init);
+      dd.wport = reinterpret_cast<const uint4*>(d->upload(L.wport));
+      dd.mem_info = reinterpret_cast<const uint4*>(d->upload(L.mem_info));
+      dd.in_w = d->upload(L.in_width);
+      dd.n_layers = (uint32_t)L.layer_off.size() - 1;
+      dd.n_regs = (uint32_t)L.reg_src.size();
+      dd.n_inputs = (uint32_t)L.in_width.size();
+      dd.n_mems = (uint32_t)(L.mem_info.size() / 4 - 1);
+      dd.op_base = L.op_base;
+      dd.reg_base = L.reg_base;
+    } catch (...) {
+      delete d;
+      throw;
+    }
+    *out = d;
+  });
+}
+
+RT_EXPORT int rteaal_design_info(const rteaal_design* d, rteaal_design_stats* o) {
+  return guarded([&] {
+    require(d && o, "rteaal_design_info: null argument");
+    const Lowered& L = d->L;
+    o->n_signals = d->nl.n_signals();
+    o->n_inputs = d->nl.ni;
+    o->n_regs = d->nl.nr;
+    o->n_consts = d->nl.nc;
+    o->n_ops = d->nl.no;
+    o->n_mems = d->nl.nm;
+    o->n_wports = d->nl.nw;
+    o->n_layers = (uint32_t)L.layer_off.size() - 1;
+    o->n_groups = (uint32_t)L.group_off.size() - 1;
+    o->n_slots = L.n_slots;
+    o->n_lowered_ops = (uint32_t)L.meta.size();
+    o->max_layer_ops = L.max_layer_ops;
+    o->op_operands = L.op_operands;
+    o->mem_words_total = L.mem_words_total;
+    o->metadata_bytes = d->metadata_bytes;
+  });
+}
+
+RT_EXPORT int rteaal_design_free(rteaal_design* d) {
+  if (!d) return RTEAAL_OK;
+  {
+    std::lock_guard<std::mutex> g(d->mu);
+    if (d->live_sims > 0) {
+      g_err = "rteaal_design_free: simulations created from this design are still alive";
+      return RTEAAL_E_BUSY;
+    }
+  }
+  delete d;
+  return RTEAAL_OK;
+}
+
+RT_EXPORT uint64_t rteaal_sim_footprint(const rteaal_design* d, uint32_t n) {
+  if (!d || n == 0) return 0;
+  const uint64_t np = pad_lanes(n);
+  const Lowered& L = d->L;
+  return np * 8ull * (L.n_slots + L.mem_words_total + L.in_width.size()) + np * 4ull * 4 + 4096;
+}
+
+RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, const rteaal_sim_opts* opts,
+                                rteaal_sim** out) {
+  return guarded([&] {
+    require(d && out && n_instances >= 1, "rteaal_sim_create: bad argument");
+    *out = nullptr;
+    auto* s = new rteaal_sim();
+    try {
+      s->design = d;
+      s->design_mut = const_cast<rteaal_design*>(d);
+      if (opts && opts->allocator) {
+        s->alloc.a = *opts->allocator;
+        s->alloc.custom = s->alloc.a.alloc && s->alloc.a.free;
+      }
+      CK(cudaSetDevice(d->device));
+      s->n_user = n_instances;
+      s->n_pad = pad_lanes(n_instances);
+      s->V = (s->n_pad % 2 == 0) ? 2 : 1;
+      s->kernel = opts ? opts->kernel : RTEAAL_KERNEL_AUTO;
+      if (s->kernel == RTEAAL_KERNEL_AUTO) s->kernel = s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
+      require(s->kernel >= RTEAAL_KERNEL_LAYER && s->kernel <= RTEAAL_KERNEL_LAYER_GRAPH,
+              "rteaal_sim_create: unknown kernel");
+      s->unroll = (opts && opts->unroll) ? opts->unroll : 2;
+      require(s->unroll == 1 || s->unroll == 2 || s->unroll == 4, "rteaal_sim_create: unroll must be 1, 2 or 4");
+      s->threads = (opts && opts->threads) ? opts->threads : 256;
+      require(s->threads % 32 == 0 && s->threads >= 32 && s->threads <= 512,
+              "rteaal_sim_create: threads must be a multiple of 32 in [32, 512]");
+      s->ctas_per_sm = opts ? opts->ctas_per_sm : 0;
+      s->tile_lanes = (opts && opts->tile_lanes) ? opts->tile_lanes : std::min<uint32_t>(32, s->n_pad);
+      if (s->kernel == RTEAAL_KERNEL_TILE) {
+        const uint32_t T = s->tile_lanes;
+        require(T >= 1 && T <= 64 && (T & (T - 1)) == 0, "rteaal_sim_create: tile_lanes must be a power of two <= 64");
+        require(s->n_pad % T == 0, "rteaal_sim_create: tile_lanes must divide the padded lane count");
+        if (T % 2) s->V = 1;
+      }
+      if (const char* e = getenv("RTEAAL_TEST_WITHHOLD_ARRIVAL")) s->barrier_extra = (uint32_t)atoi(e);
+      if (const char* e = getenv("RTEAAL_BARRIER_TIMEOUT_NS")) s->barrier_timeout_ns = strtoull(e, nullptr, 10);
+
+      const Lowered& L = d->L;
+      const size_t np = s->n_pad;
+      s->state = static_cast<uint64_t*>(s->get(np * 8 * L.n_slots));
+      s->mem = static_cast<uint64_t*>(s->get(std::max<size_t>(np * 8 * L.mem_words_total, 16)));
+      s->xs = static_cast<uint64_t*>(s->get(std::max<size_t>(np * 8 * L.in_width.size(), 16)));
+      s->budget = static_cast<uint32_t*>(s->get(np * 4));
+      const uint32_t n_tiles = (uint32_t)(np / std::max<uint32_t>(1, s->tile_lanes));
+      s->tile_order = static_cast<uint32_t*>(s->get(std::max<size_t>(n_tiles, 1) * 4));
+      s->tile_cycles = static_cast<uint32_t*>(s->get(std::max<size_t>(n_tiles, 1) * 4));
+      s->scratch = static_cast<uint32_t*>(s->get(256));
+      CK(cudaMemset(s->state, 0, np * 8 * L.n_slots));
+      CK(cudaMemset(s->mem, 0, std::max<size_t>(np * 8 * L.mem_words_total, 16)));
+      CK(cudaMemset(s->xs, 0, std::max<size_t>(np * 8 * L.in_width.size(), 16)));
+      CK(cudaMemset(s->scratch, 0, 256));
+      // lane order: descending expected cycles (stable), so tiles retire together
+      s->h_user_of_lane.assign(np, 0xFFFFFFFFu);
+      s->h_lane_of_user.resize(n_instances);
+      std::vector<uint32_t> ord(n_instances);
+      std::iota(ord.begin(), ord.end(), 0u);
+      if (opts && opts->expected_cycles) {
+        const uint32_t* ec = opts->expected_cycles;
+        std::stable_sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) { return ec[a] > ec[b]; });
+      }
+      bool identity = true;
+      for (uint32_t l = 0; l < n_instances; l++) {
+        s->h_user_of_lane[l] = ord[l];
+        s->h_lane_of_user[ord[l]] = l;
+        identity &= ord[l] == l;
+      }
+      if (!identity) {
+        s->user_of_lane = static_cast<uint32_t*>(s->get(np * 4));
+        s->lane_of_user = static_cast<uint32_t*>(s->get((size_t)n_instances * 4));
+        CK(cudaMemcpy(s->user_of_lane, s->h_user_of_lane.data(), np * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(s->lane_of_user, s->h_lane_of_user.data(), (size_t)n_instances * 4, cudaMemcpyHostToDevice));
+      }
+      // constants
+      if (!L.const_value.empty()) {
+        std::vector<uint64_t> h(L.const_value.size() * np, 0);
+        for (size_t c = 0; c < L.const_value.size(); c++)
+          for (size_t l = 0; l < n_instances; l++) h[c * np + l] = L.const_value[c];
+        CK(cudaMemcpy(s->state + (size_t)L.const_base * np, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+      }
+      if (opts && opts->xorshift_seed && !L.in_width.empty()) {
+        std::vector<uint64_t> h(L.in_width.size() * np, 0);
+        for (size_t j = 0; j < L.in_width.size(); j++)
+          for (uint32_t u = 0; u < n_instances; u++)
+            h[j * np + s->h_lane_of_user[u]] = opts->xorshift_seed[j * n_instances + u];
+        CK(cudaMemcpy(s->xs, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+      }
+      CK(cudaMallocHost(&s->err_host, 64));
+      *s->err_host = 0;
+      CK(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
+      // launch shape
+      if (s->kernel == RTEAAL_KERNEL_TILE || s->kernel == RTEAAL_KERNEL_GRID) {
+        const int occ = occupancy(s, s->kernel == RTEAAL_KERNEL_GRID);
+        require(occ >= 1, "rteaal_sim_create: kernel cannot be resident with these threads");
+        const uint32_t per_sm = s->ctas_per_sm ? std::min<uint32_t>(s->ctas_per_sm, occ) : (uint32_t)occ;
+        s->ctas_per_sm = per_sm;
+        s->grid = per_sm * (uint32_t)d->n_sms;
+        if (s->kernel == RTEAAL_KERNEL_TILE) s->grid = std::min<uint32_t>(s->grid, n_tiles);
+      }
+      {
+        std::lock_guard<std::mutex> g(s->design_mut->mu);
+        s->design_mut->live_sims++;
+      }
+    } catch (...) {
+      delete s;
+      throw;
+    }
+    *out = s;
+  });
+}
+
+RT_EXPORT int rteaal_sim_info(const rteaal_sim* s, rteaal_sim_stats* o) {
+  return guarded([&] {
+    require(s && o, "rteaal_sim_info: null argument");
+    o->n_instances = s->n_user;
+    o->n_lanes = s->n_pad;
+    o->device_bytes = s->device_bytes;
+    o->kernel = s->kernel;
+    o->tile_lanes = s->tile_lanes;
+    o->threads = s->threads;
+    o->ctas_per_sm = s->ctas_per_sm;
+    o->unroll = s->unroll;
+    o->grid = s->grid;
+  });
+}
+
+RT_EXPORT void rteaal_sim_destroy(rteaal_sim* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  {
+    std::lock_guard<std::mutex> g(s->design_mut->mu);
+    s->design_mut->live_sims--;
+  }
+  delete s;
+}
+
+RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rteaal_stimulus* stim,
+                          const rteaal_probes* probes, uint32_t flags, void* stream) {
+  return guarded([&] {
+    require(s && cycles && stim, "rteaal_step: null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(s->design->device));
+    check_pending(s);
+    const rteaal_design* D = s->design;
+    const Lowered& L = D->L;
+    const size_t np = s->n_pad;
+    require(stim->mode >= RTEAAL_STIM_HOLD && stim->mode <= RTEAAL_STIM_BUFFER, "rteaal_step: bad stimulus mode");
+    require(stim->mode != RTEAAL_STIM_BUFFER || stim->values, "rteaal_step: BUFFER stimulus without values");
+
+    DSim ds = dsim(s);
+    ds.reset = (flags & RTEAAL_STEP_RESET) ? 1 : 0;
+    ds.stim_mode = L.in_width.empty() ? 0 : stim->mode;
+
+    // per-lane cycle budgets
+    uint64_t max_cyc = 0;
+    std::vector<uint32_t> hb;
+    if (cycles->per_instance) {
+      hb.assign(np, 0);
+      for (uint32_t u = 0; u < s->n_user; u++) {
+        hb[s->h_lane_of_user[u]] = cycles->per_instance[u];
+        max_cyc = std::max<uint64_t>(max_cyc, cycles->per_instance[u]);
+      }
+      CK(cudaMemcpyAsync(s->budget, hb.data(), np * 4, cudaMemcpyHostToDevice, st));
+      ds.budget = s->budget;
+    } else {
+      require(cycles->uniform <= 0xFFFFFFFFull, "rteaal_step: at most 2^32-1 cycles per call");
+      max_cyc = cycles->uniform;
+      ds.uniform = (uint32_t)max_cyc;
+    }
+    if (max_cyc == 0) return;
+
+    // stimulus and probe buffers (host ones go through one device staging buffer)
+    const size_t stim_host_bytes = (ds.stim_mode == RTEAAL_STIM_BUFFER && stim->values_on_host)
+                                       ? (size_t)max_cyc * L.in_width.size() * s->n_user * 8 : 0;
+    int probe_mode = RTEAAL_PROBE_LAST;
+    size_t probe_bytes = 0;
+    const bool probing = probes && probes->n;
+    if (probing) {
+      require(probes->signals && probes->out, "rteaal_step: probes without signals / out");
+      probe_mode = probes->mode;
+      require(probe_mode == RTEAAL_PROBE_LAST || probe_mode == RTEAAL_PROBE_EVERY, "rteaal_step: bad probe mode");
+      probe_bytes = (probe_mode == RTEAAL_PROBE_EVERY ? (size_t)max_cyc : 1) * probes->n * s->n_user * 8;
+    }
+    const bool probe_host = probing && probes->out_on_host;
+    ensure_staging(s, stim_host_bytes + (probe_host ? probe_bytes : 0));
+    if (ds.stim_mode == RTEAAL_STIM_BUFFER) {
+      if (stim_host_bytes) {
+        CK(cudaMemcpyAsync(s->staging, stim->values, stim_host_bytes, cudaMemcpyHostToDevice, st));
+        ds.stim = s->staging;
+      } else {
+        ds.stim = stim->values;
+      }
+    }
+    uint64_t* probe_dev = nullptr;
+    if (probing) {
+      std::vector<uint32_t> slots(probes->n);
+      for (uint32_t p = 0; p < probes->n; p++) {
+        require(probes->signals[p] < D->nl.n_signals(), "rteaal_step: probe signal out of range");
+        slots[p] = L.sig2slot[probes->signals[p]];
+      }
+      ensure_probe_slots(s, slots.size());
+      CK(cudaMemcpyAsync(s->probe_slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice, st));
+      probe_dev = probe_host ? s->staging + stim_host_bytes / 8 : probes->out;
+      if (probe_mode == RTEAAL_PROBE_EVERY) {
+        ds.probe_slot = s->probe_slots;
+        ds.n_probe = probes->n;
+        ds.probe_out = probe_dev;
+      }
+    }
+
+    const uint32_t U = s->unroll;
+    if (s->kernel == RTEAAL_KERNEL_LAYER) {
+      for (uint64_t c = 0; c < max_cyc; c++) {
+        if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
+        else launch_layer_cycle<1>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
+      }
+      CK(cudaGetLastError());
+    } else if (s->kernel == RTEAAL_KERNEL_LAYER_GRAPH) {
+      uint32_t* cyc_dev = s->scratch + 4;
+      CK(cudaMemsetAsync(cyc_dev, 0, 4, st));
+      cudaStream_t cap;
+      CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      try {
+        CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
+        else launch_layer_cycle<1>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
+        k_tick<<<1, 1, 0, cap>>>(cyc_dev);
+        CK(cudaStreamEndCapture(cap, &g));
+        CK(cudaGraphInstantiate(&ge, g, 0));
+        for (uint64_t c = 0; c < max_cyc; c++) CK(cudaGraphLaunch(ge, st));
+      } catch (...) {
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        throw;
+      }
+      // the exec graph may be destroyed while launches are pending (CUDA keeps them alive)
+      cudaGraphExecDestroy(ge);
+      cudaGraphDestroy(g);
+      cudaStreamDestroy(cap);
+    } else if (s->kernel == RTEAAL_KERNEL_TILE) {
+      require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
+      const uint32_t T = s->tile_lanes;
+      const uint32_t n_tiles = (uint32_t)(np / T);
+      TileArgs ta{};
+      ta.counter = s->scratch + 1;
+      ta.n_tiles = n_tiles;
+      ta.tile_lanes = T;
+      ta.tpo = make_fastdiv(T / s->V);
+      if (cycles->per_instance) {
+        std::vector<uint32_t> tc(n_tiles, 0), order(n_tiles);
+        for (uint32_t t = 0; t < n_tiles; t++)
+          for (uint32_t l = 0; l < T; l++) tc[t] = std::max(tc[t], hb[(size_t)t * T + l]);
+        std::iota(order.begin(), order.end(), 0u);
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return tc[a] > tc[b]; });
+        CK(cudaMemcpyAsync(s->tile_cycles, tc.data(), n_tiles * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s->tile_order, order.data(), n_tiles * 4, cudaMemcpyHostToDevice, st));
+        ta.tile_cycles = s->tile_cycles;
+        ta.order = s->tile_order;
+      }
+      CK(cudaMemsetAsync(ta.counter, 0, 4, st));
+      const uint32_t grid = std::min<uint32_t>(s->grid, n_tiles);
+      if (s->V == 2) {
+        if (U >= 4) launch_tile<2, 4>(s, D->dd, ds, ta, grid, st);
+        else if (U == 2) launch_tile<2, 2>(s, D->dd, ds, ta, grid, st);
+        else launch_tile<2, 1>(s, D->dd, ds, ta, grid, st);
+      } else {
+        if (U >= 4) launch_tile<1, 4>(s, D->dd, ds, ta, grid, st);
+        else if (U == 2) launch_tile<1, 2>(s, D->dd, ds, ta, grid, st);
+        else launch_tile<1, 1>(s, D->dd, ds, ta, grid, st);
+      }
+      CK(cudaGetLastError());
+    } else {  // GRID
+      require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
+      GridArgs ga{};
+      ga.count = s->scratch + 2;
+      ga.gen = s->scratch + 3;
+      ga.expected = s->grid + s->barrier_extra;
+      ga.timeout_ns = s->barrier_timeout_ns;
+      ga.ncyc = (uint32_t)max_cyc;
+      ga.tpo = make_fastdiv((uint32_t)(np / s->V));
+      CK(cudaMemsetAsync(s->scratch, 0, 16, st));
+      cudaError_t e;
+      if (s->V == 2) {
+        e = U >= 4 ? launch_grid<2, 4>(s, D->dd, ds, ga, s->grid, st)
+            : U == 2 ? launch_grid<2, 2>(s, D->dd, ds, ga, s->grid, st)
+                     : launch_grid<2, 1>(s, D->dd, ds, ga, s->grid, st);
+      } else {
+        e = U >= 4 ? launch_grid<1, 4>(s, D->dd, ds, ga, s->grid, st)
+            : U == 2 ? launch_grid<1, 2>(s, D->dd, ds, ga, s->grid, st)
+                     : launch_grid<1, 1>(s, D->dd, ds, ga, s->grid, st);
+      }
+      if (e == cudaErrorCooperativeLaunchTooLarge)
+        throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
+      CK(e);
+      CK(cudaMemcpyAsync(s->err_host, s->scratch, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaEventRecord(s->done, st));
+      s->pending = true;
+    }
+
+    if (probing && probe_mode == RTEAAL_PROBE_LAST) {
+      const size_t total = (size_t)probes->n * s->n_user;
+      const uint32_t blocks = (uint32_t)std::min<size_t>((total + 255) / 256, 4096);
+      k_gather<<<blocks, 256, 0, st>>>(s->state, s->n_pad, s->probe_slots, probes->n, s->lane_of_user, 0,
+                                       s->n_user, probe_dev);
+      CK(cudaGetLastError());
+    }
+    if (probe_host) {
+      CK(cudaMemcpyAsync(probes->out, probe_dev, probe_bytes, cudaMemcpyDeviceToHost, st));
+      sync_sim(s, st);
+    } else if (stim_host_bytes) {
+      // the caller may reuse its host buffer once we return
+      sync_sim(s, st);
+    }
+  });
+}
+
+RT_EXPORT int rteaal_sync(rteaal_sim* s, void* stream) {
+  return guarded([&] {
+    require(s, "rteaal_sync: null sim");
+    sync_sim(s, static_cast<cudaStream_t>(stream));
+  });
+}
+
+namespace {
+
+enum class Region { STATE, MEM, XS };
+
+void transfer(rteaal_sim* s, Region region, const uint32_t* signals, uint32_t n, uint32_t inst0, uint32_t n_inst,
+              uint64_t* out, const uint64_t* in, cudaStream_t st) {
+  require(s, "null sim");
+  require(out || in, "null host buffer");
+  require((uint64_t)inst0 + n_inst <= s->n_user, "instance range out of bounds");
+  CK(cudaSetDevice(s->design->device));
+  const Lowered& L = s->design->L;
+  std::vector<uint32_t> rows;
+  std::vector<uint64_t> masks;
+  uint64_t* base = s->state;
+  uint32_t n_rows = n;
+  if (region == Region::STATE) {
+    require(signals || n == 0, "null signal list");
+    rows.resize(n);
+    masks.resize(n);
+    const uint32_t nsig = s->design->nl.n_signals();
+    for (uint32_t i = 0; i < n; i++) {
+      require(signals[i] < nsig, "signal id out of range");
+      rows[i] = L.sig2slot[signals[i]];
+      // width of the signal (writes are masked like every stored value)
+      const Netlist& nl = s->design->nl;
+      uint32_t sig = signals[i], w;
+      if (sig < nl.ni) w = nl.in_w[sig];
+      else if (sig < nl.ni + nl.nr) w = nl.reg_w[sig - nl.ni];
+      else if (sig < nl.op_base()) w = nl.const_w[sig - nl.ni - nl.nr];
+      else w = nl.width[sig - nl.op_base()];
+      masks[i] = ~0ull >> (64 - w);
+    }
+  } else if (region == Region::MEM) {
+    base = s->mem;
+    n_rows = (uint32_t)L.mem_words_total;
+  } else {
+    base = s->xs;
+    n_rows = (uint32_t)L.in_width.size();
+  }
+  const size_t total = (size_t)n_rows * n_inst;
+  if (total == 0) return;
+  sync_sim(s, st);
+  void* tmp = s->alloc.alloc(total * 8 + rows.size() * 4 + masks.size() * 8 + 64);
+  try {
+    uint64_t* buf = static_cast<uint64_t*>(tmp);
+    uint64_t* dmask = masks.empty() ? nullptr : buf + total;
+    uint32_t* drows = rows.empty() ? nullptr : reinterpret_cast<uint32_t*>(buf + total + masks.size());
+    if (drows) CK(cudaMemcpyAsync(drows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, st));
+    if (dmask) CK(cudaMemcpyAsync(dmask, masks.data(), masks.size() * 8, cudaMemcpyHostToDevice, st));
+    const uint32_t blocks = (uint32_t)std::min<size_t>((total + 255) / 256, 8192);
+    if (out) {
+      k_gather<<<blocks, 256, 0, st>>>(base, s->n_pad, drows, n_rows, s->lane_of_user, inst0, n_inst, buf);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(out, buf, total * 8, cudaMemcpyDeviceToHost, st));
+    } else {
+      CK(cudaMemcpyAsync(buf, in, total * 8, cudaMemcpyHostToDevice, st));
+      k_scatter<<<blocks, 256, 0, st>>>(base, s->n_pad, drows, n_rows, s->lane_of_user, inst0, n_inst, buf,
+                                        region == Region::STATE ? dmask : nullptr);
+      CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(st));
+  } catch (...) {
+    s->alloc.free(tmp, total * 8 + rows.size() * 4 + masks.size() * 8 + 64);
+    throw;
+  }
+  s->alloc.free(tmp, total * 8 + rows.size() * 4 + masks.size() * 8 + 64);
+}
+
+}  // namespace
+
+RT_EXPORT int rteaal_state_read(rteaal_sim* s, const uint32_t* signals, uint32_t n, uint32_t inst0,
+                                uint32_t n_inst, uint64_t* out, void* stream) {
+  return guarded([&] { transfer(s, Region::STATE, signals, n, inst0, n_inst, out, nullptr, (cudaStream_t)stream); });
+}
+
+RT_EXPORT int rteaal_state_write(rteaal_sim* s, const uint32_t* signals, uint32_t n, uint32_t inst0,
+                                 uint32_t n_inst, const uint64_t* in, void* stream) {
+  return guarded([&] { transfer(s, Region::STATE, signals, n, inst0, n_inst, nullptr, in, (cudaStream_t)stream); });
+}
+
+RT_EXPORT int rteaal_mem_read(rteaal_sim* s, uint32_t inst0, uint32_t n_inst, uint64_t* out, void* stream) {
+  return guarded([&] { transfer(s, Region::MEM, nullptr, 0, inst0, n_inst, out, nullptr, (cudaStream_t)stream); });
+}
+
+RT_EXPORT int rteaal_mem_write(rteaal_sim* s, uint32_t inst0, uint32_t n_inst, const uint64_t* in, void* stream) {
+  return guarded([&] { transfer(s, Region::MEM, nullptr, 0, inst0, n_inst, nullptr, in, (cudaStream_t)stream); });
+}
+
+RT_EXPORT int rteaal_stim_state_read(rteaal_sim* s, uint32_t inst0, uint32_t n_inst, uint64_t* out, void* stream) {
+  return guarded([&] { transfer(s, Region::XS, nullptr, 0, inst0, n_inst, out, nullptr, (cudaStream_t)stream); });
+}
+
+RT_EXPORT int rteaal_stim_state_write(rteaal_sim* s, uint32_t inst0, uint32_t n_inst, const uint64_t* in,
+                                      void* stream) {
+  return guarded([&] { transfer(s, Region::XS, nullptr, 0, inst0, n_inst, nullptr, in, (cudaStream_t)stream); });
+}
