@@ -201,6 +201,8 @@ def run_ours(args) -> None:
     dev = torch.device("cuda", local)
 
     spec_fn, n_total, (clo, chi) = WORKLOADS[args.workload]
+    if args.instances:
+        n_total = args.instances
     nl = synth.generate(spec_fn())
     lo, hi = shard(n_total, rank, world)
     n = hi - lo
@@ -210,18 +212,26 @@ def run_ours(args) -> None:
     xs = np.ascontiguousarray(xs_all[:, lo:hi])
 
     design = rt.Design(nl.to_bytes())
-    kw = {}
-    if args.kernel == "tile":
-        kw = dict(tile_lanes=args.tile_lanes, threads=args.threads, unroll=args.unroll,
-                  ctas_per_sm=args.ctas_per_sm)
+    kw = dict(tile_lanes=args.tile_lanes, threads=args.threads, unroll=args.unroll,
+              ctas_per_sm=args.ctas_per_sm)
     sim = rt.Sim(design, n, kernel=args.kernel, xorshift_seed=xs, expected_cycles=budgets, **kw)
-    info = sim.info
     stream = torch.cuda.current_stream(dev)
     remaining = budgets.astype(np.int64).copy()
 
     # reset cycle (not counted)
     sim.step(1, stimulus="xorshift", reset=True)
     torch.cuda.synchronize()
+    info = sim.info
+    tune = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        trials = sim.autotune(cycles_per_trial=1, kernels=args.tune_kernels.split(","))
+        info = sim.info
+        tune = {"trials": len(trials), "seconds": round(time.perf_counter() - t0, 2),
+                "best_ms_per_cycle": round(min(t["ms"] for t in trials), 3) if trials else None}
+        if args.tune_log:
+            with open(args.tune_log, "w") as f:
+                json.dump(trials, f, indent=0)
 
     C = args.chunk
 
@@ -271,7 +281,8 @@ def run_ours(args) -> None:
     avg_launch_s = float(np.mean(step_ms)) / 1e3
     peaks = measured_peaks()
     achieved = per_launch_bytes / avg_launch_s / 1e9
-    traffic = profile_traffic("k_tile:" + args.workload)
+    kname = {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops"}[info["kernel"]]
+    traffic = profile_traffic(kname + ":" + args.workload)
     if traffic is not None:
         traffic *= (inst_cycles / args.steps)                # stored per instance-cycle
 
@@ -296,7 +307,7 @@ def run_ours(args) -> None:
 
     # ---- e2e through the public API with host buffers
     e2e = None
-    if args.e2e_steps > 0 and args.kernel == "tile":
+    if args.e2e_steps > 0:
         probes = (nl.reg_base + np.arange(min(64, nl.n_regs))).astype(np.uint32)
         vals_host = torch.empty((C, nl.n_inputs, n), dtype=torch.int64).pin_memory()
         vals_np = vals_host.numpy().view(np.uint64)
@@ -338,15 +349,17 @@ def run_ours(args) -> None:
             "config": {"workload": args.workload, "ops": nl.n_ops, "regs": nl.n_regs,
                        "layers": design.info["n_layers"], "instances": n_total,
                        "cycles_per_step": C, "kernel": args.kernel,
+                       "kernel_used": {1: "layer", 2: "tile", 3: "grid", 4: "layer_graph"}[info["kernel"]],
                        "tile_lanes": info["tile_lanes"], "threads": info["threads"],
                        "ctas_per_sm": info["ctas_per_sm"], "unroll": info["unroll"],
-                       "grid": info["grid"], "parallelism": "replicas" if world > 1 else "1 gpu",
+                       "grid": info["grid"], "autotune": tune, "parallelism": "replicas" if world > 1 else "1 gpu",
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)"
                              % (design.info["n_slots"] * n * 8 / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                          "traffic": traffic, "peak_source": peaks["source"],
-                         "bytes_per_instance_cycle": bpc["total"], "kernel": "k_tile"},
+                         "bytes_per_instance_cycle": bpc["total"],
+                         "kernel": {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops"}[info["kernel"]]},
             "gpu_launches": 1 * args.steps,
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -369,11 +382,15 @@ def main():
     ap.add_argument("--workload", default="batch-1M", choices=sorted(WORKLOADS))
     ap.add_argument("--kernel", default="tile")
     ap.add_argument("--chunk", type=int, default=8)
+    ap.add_argument("--instances", type=int, default=0, help="override the instance count (profiling)")
     ap.add_argument("--tile-lanes", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--tune-kernels", default="tile,grid")
+    ap.add_argument("--tune-log", default="")
     ap.add_argument("--no-verify", dest="verify", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -149,7 +149,7 @@ typedef struct {
   const uint64_t *xorshift_seed;
   int kernel;              /* RTEAAL_KERNEL_*                                   */
   uint32_t tile_lanes;     /* TILE: lanes per tile (power of two <= 64), 0 auto */
-  uint32_t threads;        /* threads per CTA (multiple of 32), 0 auto          */
+  uint32_t threads;        /* threads per CTA (multiple of 32, <= 1024), 0 auto */
   uint32_t ctas_per_sm;    /* TILE / GRID residency target, 0 auto              */
   uint32_t unroll;         /* operations in flight per thread (1, 2, 4), 0 auto */
 } rteaal_sim_opts;
@@ -168,6 +168,29 @@ int rteaal_sim_create(const rteaal_design *design, uint32_t n_instances,
                       const rteaal_sim_opts *opts, rteaal_sim **out);
 int rteaal_sim_info(const rteaal_sim *sim, rteaal_sim_stats *out);
 void rteaal_sim_destroy(rteaal_sim *sim);
+
+/* Change the launch configuration (kernel, tile_lanes, threads, ctas_per_sm,
+ * unroll of opts; the other fields are ignored).  Results never depend on it.
+ * Errors: E_INVALID, E_UNSUPPORTED (no compiled variant). */
+int rteaal_sim_configure(rteaal_sim *sim, const rteaal_sim_opts *opts);
+
+typedef struct {
+  int kernel;
+  uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid;
+  float ms;                      /* device time of one trial step                 */
+} rteaal_tune_trial;
+
+/* Autotuner: times every candidate launch configuration of the kernels in
+ * kernel_mask (bit 1 << RTEAAL_KERNEL_*, 0 = TILE|GRID, or LAYER|GRID for
+ * fewer than 64 lanes) on this sim, one warm-up and one timed step of
+ * cycles_per_trial cycles each, keeps the fastest, and restores the state,
+ * memories and stimulus states exactly (device-to-device snapshot: needs
+ * free device memory equal to the sim's state).  trials (nullable) receives
+ * up to max_trials results; *n_trials (nullable) the number run.
+ * Synchronises stream.  Errors: E_NOMEM (no room for the snapshot), E_CUDA. */
+int rteaal_sim_autotune(rteaal_sim *sim, uint32_t cycles_per_trial, uint32_t kernel_mask,
+                        rteaal_tune_trial *trials, uint32_t max_trials, uint32_t *n_trials,
+                        void *stream);
 
 /* Bytes of device memory rteaal_sim_create would take (footprint admission). */
 uint64_t rteaal_sim_footprint(const rteaal_design *design, uint32_t n_instances);

@@ -72,6 +72,11 @@ class rteaal_sim_stats(ctypes.Structure):
                 ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32)]
 
 
+class rteaal_tune_trial(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
+                ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("ms", ctypes.c_float)]
+
+
 class rteaal_cycles(ctypes.Structure):
     _fields_ = [("uniform", _U64), ("per_instance", ctypes.POINTER(_U32))]
 
@@ -86,7 +91,7 @@ class rteaal_probes(ctypes.Structure):
 
 
 EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rteaal_sim_create",
-           "rteaal_sim_info", "rteaal_sim_destroy", "rteaal_sim_footprint", "rteaal_step",
+           "rteaal_sim_info", "rteaal_sim_destroy", "rteaal_sim_configure", "rteaal_sim_autotune", "rteaal_sim_footprint", "rteaal_step",
            "rteaal_sync", "rteaal_state_read", "rteaal_state_write", "rteaal_mem_read",
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
            "rteaal_last_error"]
@@ -111,6 +116,9 @@ def lib() -> ctypes.CDLL:
         L.rteaal_sim_info.argtypes = [_P, ctypes.POINTER(rteaal_sim_stats)]
         L.rteaal_sim_destroy.argtypes = [_P]
         L.rteaal_sim_destroy.restype = None
+        L.rteaal_sim_configure.argtypes = [_P, ctypes.POINTER(rteaal_sim_opts)]
+        L.rteaal_sim_autotune.argtypes = [_P, _U32, _U32, ctypes.POINTER(rteaal_tune_trial), _U32,
+                                          ctypes.POINTER(_U32), _P]
         L.rteaal_sim_footprint.argtypes = [_P, _U32]
         L.rteaal_sim_footprint.restype = _U64
         L.rteaal_step.argtypes = [_P, ctypes.POINTER(rteaal_cycles), ctypes.POINTER(rteaal_stimulus),
@@ -226,6 +234,20 @@ def rteaal_sim_info(sim: int) -> dict:
 
 def rteaal_sim_destroy(sim: int):
     lib().rteaal_sim_destroy(sim)
+
+
+def rteaal_sim_configure(sim: int, opts: rteaal_sim_opts):
+    _check(lib().rteaal_sim_configure(sim, ctypes.byref(opts)))
+
+
+def rteaal_sim_autotune(sim: int, cycles_per_trial: int = 1, kernel_mask: int = 0,
+                        max_trials: int = 256, stream=None) -> list[dict]:
+    buf = (rteaal_tune_trial * max_trials)()
+    n = _U32(0)
+    _check(lib().rteaal_sim_autotune(sim, cycles_per_trial, kernel_mask, buf, max_trials,
+                                     ctypes.byref(n), _stream_ptr(stream)))
+    return [{f: getattr(buf[i], f) for f, _ in rteaal_tune_trial._fields_}
+            for i in range(min(n.value, max_trials))]
 
 
 def rteaal_sim_footprint(design: int, n_instances: int) -> int:
@@ -389,6 +411,23 @@ class Sim:
 
     def sync(self, stream=None):
         rteaal_sync(self.handle, stream)
+
+    def configure(self, kernel: str | int = "auto", tile_lanes: int = 0, threads: int = 0,
+                  ctas_per_sm: int = 0, unroll: int = 0):
+        o = rteaal_sim_opts()
+        o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
+        rteaal_sim_configure(self.handle, o)
+        self.info = rteaal_sim_info(self.handle)
+
+    def autotune(self, cycles_per_trial: int = 1, kernels=None, stream=None) -> list[dict]:
+        """Time candidate launch configurations; keep the fastest; state is restored."""
+        mask = 0
+        for k in kernels or []:
+            mask |= 1 << (KERNELS[k] if isinstance(k, str) else int(k))
+        trials = rteaal_sim_autotune(self.handle, cycles_per_trial, mask, stream=stream)
+        self.info = rteaal_sim_info(self.handle)
+        return trials
 
     def read(self, signals=None, inst_begin: int = 0, n_inst: int | None = None, stream=None):
         if signals is None:

@@ -75,8 +75,8 @@ struct TileArgs {
   FastDiv tpo;                   // tile_lanes / V
 };
 
-template <int V, int U>
-__global__ void __launch_bounds__(512) k_tile(DDesign d, DSim s, TileArgs t) {
+template <int V, int U, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_tile(DDesign d, DSim s, TileArgs t) {
   __shared__ uint32_t sh_q;
   for (;;) {
     if (threadIdx.x == 0) sh_q = atomicAdd(t.counter, 1u);
@@ -155,8 +155,8 @@ __device__ __forceinline__ bool grid_sync(const GridArgs& g, uint32_t* err, int*
   return *sh_ok != 0;
 }
 
-template <int V, int U>
-__global__ void __launch_bounds__(512) k_grid(DDesign d, DSim s, GridArgs g) {
+template <int V, int U, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_grid(DDesign d, DSim s, GridArgs g) {
   __shared__ int sh_ok;
   const ItemSpace is{g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
   for (uint32_t c = 0; c < g.ncyc; c++) {
@@ -429,43 +429,27 @@ void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32
     k_layer_probe<V><<<blocks_for((uint64_t)ds.n_probe * tpo.d, 1), threads, 0, st>>>(ds, tpo, c, cyc_dev);
 }
 
-template <int V, int U>
-void launch_tile(rteaal_sim* s, const DDesign& dd, const DSim& ds, const TileArgs& ta, uint32_t grid,
-                 cudaStream_t st) {
-  k_tile<V, U><<<grid, s->threads, 0, st>>>(dd, ds, ta);
-}
+// Compiled variants of the persistent kernels: lanes per thread V, items in
+// flight per thread U, launch bound MAXT (threads per CTA).
+struct Variant {
+  int V, U, maxt;
+  const void* tile;
+  const void* grid;
+};
+#define RT_VARIANT(V, U, T) {V, U, T, (const void*)k_tile<V, U, T>, (const void*)k_grid<V, U, T>}
+const Variant kVariants[] = {
+    RT_VARIANT(2, 1, 512), RT_VARIANT(2, 2, 512), RT_VARIANT(2, 4, 512),
+    RT_VARIANT(2, 1, 1024), RT_VARIANT(2, 2, 1024),
+    RT_VARIANT(1, 1, 512), RT_VARIANT(1, 2, 512), RT_VARIANT(1, 4, 512),
+};
+#undef RT_VARIANT
 
-template <int V, int U>
-cudaError_t launch_grid(rteaal_sim* s, const DDesign& dd, DSim ds, GridArgs ga, uint32_t grid,
-                        cudaStream_t st) {
-  void* args[] = {(void*)&dd, (void*)&ds, (void*)&ga};
-  return cudaLaunchCooperativeKernel((const void*)k_grid<V, U>, dim3(grid), dim3(s->threads), args, 0, st);
-}
-
-template <int V, int U>
-int grid_blocks_per_sm(uint32_t threads) {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_grid<V, U>, (int)threads, 0);
-  return nb;
-}
-
-template <int V, int U>
-int tile_blocks_per_sm(uint32_t threads) {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<V, U>, (int)threads, 0);
-  return nb;
-}
-
-int occupancy(rteaal_sim* s, bool grid) {
-  const uint32_t t = s->threads;
-  const bool v2 = s->V == 2;
-  const uint32_t U = s->unroll;
-  if (grid) {
-    if (v2) return U >= 4 ? grid_blocks_per_sm<2, 4>(t) : U == 2 ? grid_blocks_per_sm<2, 2>(t) : grid_blocks_per_sm<2, 1>(t);
-    return U >= 4 ? grid_blocks_per_sm<1, 4>(t) : U == 2 ? grid_blocks_per_sm<1, 2>(t) : grid_blocks_per_sm<1, 1>(t);
-  }
-  if (v2) return U >= 4 ? tile_blocks_per_sm<2, 4>(t) : U == 2 ? tile_blocks_per_sm<2, 2>(t) : tile_blocks_per_sm<2, 1>(t);
-  return U >= 4 ? tile_blocks_per_sm<1, 4>(t) : U == 2 ? tile_blocks_per_sm<1, 2>(t) : tile_blocks_per_sm<1, 1>(t);
+const Variant* find_variant(int V, uint32_t U, uint32_t threads) {
+  const Variant* best = nullptr;
+  for (const Variant& v : kVariants)
+    if (v.V == V && (uint32_t)v.U == U && (uint32_t)v.maxt >= threads && (!best || v.maxt < best->maxt))
+      best = &v;
+  return best;
 }
 
 void ensure_staging(rteaal_sim* s, size_t bytes) {
@@ -581,6 +565,53 @@ RT_EXPORT uint64_t rteaal_sim_footprint(const rteaal_design* d, uint32_t n) {
   return np * 8ull * (L.n_slots + L.mem_words_total + L.in_width.size()) + np * 4ull * 4 + 4096;
 }
 
+namespace {
+
+// Validate and apply a launch configuration (never changes results).
+void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
+               uint32_t unroll) {
+  if (kernel == RTEAAL_KERNEL_AUTO) kernel = s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
+  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_LAYER_GRAPH, "unknown kernel");
+  if (!unroll) unroll = 2;
+  require(unroll == 1 || unroll == 2 || unroll == 4, "unroll must be 1, 2 or 4");
+  if (!threads) threads = 512;
+  require(threads % 32 == 0 && threads >= 32 && threads <= 1024, "threads must be a multiple of 32 in [32, 1024]");
+  if (!tile_lanes) tile_lanes = std::min<uint32_t>(16, s->n_pad);
+  int V = (s->n_pad % 2 == 0) ? 2 : 1;
+  uint32_t grid = 0;
+  if (kernel == RTEAAL_KERNEL_TILE) {
+    require(tile_lanes >= 1 && tile_lanes <= 64 && (tile_lanes & (tile_lanes - 1)) == 0,
+            "tile_lanes must be a power of two <= 64");
+    require(s->n_pad % tile_lanes == 0, "tile_lanes must divide the padded lane count");
+    if (tile_lanes % 2) V = 1;
+  }
+  if (kernel == RTEAAL_KERNEL_LAYER || kernel == RTEAAL_KERNEL_LAYER_GRAPH) threads = 256;
+  if (kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID) {
+    const Variant* v = find_variant(V, unroll, threads);
+    if (!v) throw Error(RTEAAL_E_UNSUPPORTED, "no compiled kernel variant for V=" + std::to_string(V) +
+                                                  " unroll=" + std::to_string(unroll) +
+                                                  " threads=" + std::to_string(threads));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel == RTEAAL_KERNEL_GRID ? v->grid : v->tile,
+                                                     (int)threads, 0));
+    require(occ >= 1, "kernel cannot be resident with these threads");
+    ctas_per_sm = ctas_per_sm ? std::min<uint32_t>(ctas_per_sm, (uint32_t)occ) : (uint32_t)occ;
+    grid = ctas_per_sm * (uint32_t)s->design->n_sms;
+    if (kernel == RTEAAL_KERNEL_TILE) grid = std::min<uint32_t>(grid, s->n_pad / tile_lanes);
+  } else {
+    ctas_per_sm = 0;
+  }
+  s->kernel = kernel;
+  s->tile_lanes = tile_lanes;
+  s->threads = threads;
+  s->ctas_per_sm = ctas_per_sm;
+  s->unroll = unroll;
+  s->V = V;
+  s->grid = grid;
+}
+
+}  // namespace
+
 RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, const rteaal_sim_opts* opts,
                                 rteaal_sim** out) {
   return guarded([&] {
@@ -597,24 +628,8 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       CK(cudaSetDevice(d->device));
       s->n_user = n_instances;
       s->n_pad = pad_lanes(n_instances);
-      s->V = (s->n_pad % 2 == 0) ? 2 : 1;
-      s->kernel = opts ? opts->kernel : RTEAAL_KERNEL_AUTO;
-      if (s->kernel == RTEAAL_KERNEL_AUTO) s->kernel = s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
-      require(s->kernel >= RTEAAL_KERNEL_LAYER && s->kernel <= RTEAAL_KERNEL_LAYER_GRAPH,
-              "rteaal_sim_create: unknown kernel");
-      s->unroll = (opts && opts->unroll) ? opts->unroll : 2;
-      require(s->unroll == 1 || s->unroll == 2 || s->unroll == 4, "rteaal_sim_create: unroll must be 1, 2 or 4");
-      s->threads = (opts && opts->threads) ? opts->threads : 256;
-      require(s->threads % 32 == 0 && s->threads >= 32 && s->threads <= 512,
-              "rteaal_sim_create: threads must be a multiple of 32 in [32, 512]");
-      s->ctas_per_sm = opts ? opts->ctas_per_sm : 0;
-      s->tile_lanes = (opts && opts->tile_lanes) ? opts->tile_lanes : std::min<uint32_t>(32, s->n_pad);
-      if (s->kernel == RTEAAL_KERNEL_TILE) {
-        const uint32_t T = s->tile_lanes;
-        require(T >= 1 && T <= 64 && (T & (T - 1)) == 0, "rteaal_sim_create: tile_lanes must be a power of two <= 64");
-        require(s->n_pad % T == 0, "rteaal_sim_create: tile_lanes must divide the padded lane count");
-        if (T % 2) s->V = 1;
-      }
+      configure(s, opts ? opts->kernel : 0, opts ? opts->tile_lanes : 0, opts ? opts->threads : 0,
+                opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0);
       if (const char* e = getenv("RTEAAL_TEST_WITHHOLD_ARRIVAL")) s->barrier_extra = (uint32_t)atoi(e);
       if (const char* e = getenv("RTEAAL_BARRIER_TIMEOUT_NS")) s->barrier_timeout_ns = strtoull(e, nullptr, 10);
 
@@ -624,9 +639,8 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       s->mem = static_cast<uint64_t*>(s->get(std::max<size_t>(np * 8 * L.mem_words_total, 16)));
       s->xs = static_cast<uint64_t*>(s->get(std::max<size_t>(np * 8 * L.in_width.size(), 16)));
       s->budget = static_cast<uint32_t*>(s->get(np * 4));
-      const uint32_t n_tiles = (uint32_t)(np / std::max<uint32_t>(1, s->tile_lanes));
-      s->tile_order = static_cast<uint32_t*>(s->get(std::max<size_t>(n_tiles, 1) * 4));
-      s->tile_cycles = static_cast<uint32_t*>(s->get(std::max<size_t>(n_tiles, 1) * 4));
+      s->tile_order = static_cast<uint32_t*>(s->get(np * 4));   // room for any tile size
+      s->tile_cycles = static_cast<uint32_t*>(s->get(np * 4));
       s->scratch = static_cast<uint32_t*>(s->get(256));
       CK(cudaMemset(s->state, 0, np * 8 * L.n_slots));
       CK(cudaMemset(s->mem, 0, std::max<size_t>(np * 8 * L.mem_words_total, 16)));
@@ -670,15 +684,6 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       CK(cudaMallocHost(&s->err_host, 64));
       *s->err_host = 0;
       CK(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
-      // launch shape
-      if (s->kernel == RTEAAL_KERNEL_TILE || s->kernel == RTEAAL_KERNEL_GRID) {
-        const int occ = occupancy(s, s->kernel == RTEAAL_KERNEL_GRID);
-        require(occ >= 1, "rteaal_sim_create: kernel cannot be resident with these threads");
-        const uint32_t per_sm = s->ctas_per_sm ? std::min<uint32_t>(s->ctas_per_sm, occ) : (uint32_t)occ;
-        s->ctas_per_sm = per_sm;
-        s->grid = per_sm * (uint32_t)d->n_sms;
-        if (s->kernel == RTEAAL_KERNEL_TILE) s->grid = std::min<uint32_t>(s->grid, n_tiles);
-      }
       {
         std::lock_guard<std::mutex> g(s->design_mut->mu);
         s->design_mut->live_sims++;
@@ -688,6 +693,14 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       throw;
     }
     *out = s;
+  });
+}
+
+RT_EXPORT int rteaal_sim_configure(rteaal_sim* s, const rteaal_sim_opts* o) {
+  return guarded([&] {
+    require(s && o, "rteaal_sim_configure: null argument");
+    CK(cudaSetDevice(s->design->device));
+    configure(s, o->kernel, o->tile_lanes, o->threads, o->ctas_per_sm, o->unroll);
   });
 }
 
@@ -714,6 +727,94 @@ RT_EXPORT void rteaal_sim_destroy(rteaal_sim* s) {
     s->design_mut->live_sims--;
   }
   delete s;
+}
+
+RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rteaal_stimulus* stim,
+                          const rteaal_probes* probes, uint32_t flags, void* stream);
+
+RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint32_t kernel_mask,
+                                  rteaal_tune_trial* trials, uint32_t max_trials, uint32_t* n_trials,
+                                  void* stream) {
+  return guarded([&] {
+    require(s, "rteaal_sim_autotune: null sim");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(s->design->device));
+    sync_sim(s, st);
+    if (!cycles_per_trial) cycles_per_trial = 1;
+    if (!kernel_mask)
+      kernel_mask = s->n_pad >= 64 ? ((1u << RTEAAL_KERNEL_TILE) | (1u << RTEAAL_KERNEL_GRID))
+                                   : ((1u << RTEAAL_KERNEL_LAYER) | (1u << RTEAAL_KERNEL_GRID));
+    const Lowered& L = s->design->L;
+    const size_t np = s->n_pad;
+    const size_t b_state = np * 8 * L.n_slots, b_mem = np * 8 * L.mem_words_total,
+                 b_xs = np * 8 * L.in_width.size();
+    // device snapshot of everything a trial can change
+    char* snap = static_cast<char*>(s->alloc.alloc(b_state + b_mem + b_xs + 256));
+    struct Free {
+      rteaal_sim* s; void* p; size_t n;
+      ~Free() { s->alloc.free(p, n); }
+    } guard{s, snap, b_state + b_mem + b_xs + 256};
+    CK(cudaMemcpyAsync(snap, s->state, b_state, cudaMemcpyDeviceToDevice, st));
+    if (b_mem) CK(cudaMemcpyAsync(snap + b_state, s->mem, b_mem, cudaMemcpyDeviceToDevice, st));
+    if (b_xs) CK(cudaMemcpyAsync(snap + b_state + b_mem, s->xs, b_xs, cudaMemcpyDeviceToDevice, st));
+
+    struct Cand { int kernel; uint32_t T, threads, U; };
+    std::vector<Cand> cands;
+    if (kernel_mask & (1u << RTEAAL_KERNEL_TILE))
+      for (uint32_t T : {4u, 8u, 16u, 32u, 64u})
+        if (T <= np && np % T == 0)
+          for (uint32_t th : {256u, 512u, 1024u})
+            for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_TILE, T, th, U});
+    if (kernel_mask & (1u << RTEAAL_KERNEL_GRID))
+      for (uint32_t th : {256u, 512u, 1024u})
+        for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_GRID, 0, th, U});
+    if (kernel_mask & (1u << RTEAAL_KERNEL_LAYER))
+      for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER, 0, 256, U});
+    if (kernel_mask & (1u << RTEAAL_KERNEL_LAYER_GRAPH))
+      for (uint32_t U : {2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER_GRAPH, 0, 256, U});
+
+    const int saved[5] = {s->kernel, (int)s->tile_lanes, (int)s->threads, (int)s->ctas_per_sm, (int)s->unroll};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    rteaal_cycles cyc{cycles_per_trial, nullptr};
+    rteaal_stimulus stim{L.in_width.empty() ? RTEAAL_STIM_HOLD : RTEAAL_STIM_XORSHIFT, nullptr, 0};
+    float best = 1e30f;
+    Cand best_c{saved[0], (uint32_t)saved[1], (uint32_t)saved[2], (uint32_t)saved[4]};
+    uint32_t best_ctas = (uint32_t)saved[3];
+    uint32_t nt = 0;
+    for (const Cand& c : cands) {
+      try {
+        configure(s, c.kernel, c.T, c.threads, 0, c.U);
+      } catch (const Error&) {
+        continue;  // not compiled / not resident
+      }
+      if (rteaal_step(s, &cyc, &stim, nullptr, 0, st) != RTEAAL_OK) { g_err.clear(); continue; }
+      CK(cudaEventRecord(e0, st));
+      if (rteaal_step(s, &cyc, &stim, nullptr, 0, st) != RTEAAL_OK) { g_err.clear(); continue; }
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      try { sync_sim(s, st); } catch (const Error&) { continue; }
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (trials && nt < max_trials)
+        trials[nt] = rteaal_tune_trial{s->kernel, s->tile_lanes, s->threads, s->ctas_per_sm, s->unroll, s->grid, ms};
+      nt++;
+      if (ms < best) {
+        best = ms;
+        best_c = c;
+        best_ctas = s->ctas_per_sm;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_trials) *n_trials = nt;
+    configure(s, best_c.kernel, best_c.T, best_c.threads, best_ctas, best_c.U);
+    CK(cudaMemcpyAsync(s->state, snap, b_state, cudaMemcpyDeviceToDevice, st));
+    if (b_mem) CK(cudaMemcpyAsync(s->mem, snap + b_state, b_mem, cudaMemcpyDeviceToDevice, st));
+    if (b_xs) CK(cudaMemcpyAsync(s->xs, snap + b_state + b_mem, b_xs, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  });
 }
 
 RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rteaal_stimulus* stim,
@@ -844,15 +945,10 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       }
       CK(cudaMemsetAsync(ta.counter, 0, 4, st));
       const uint32_t grid = std::min<uint32_t>(s->grid, n_tiles);
-      if (s->V == 2) {
-        if (U >= 4) launch_tile<2, 4>(s, D->dd, ds, ta, grid, st);
-        else if (U == 2) launch_tile<2, 2>(s, D->dd, ds, ta, grid, st);
-        else launch_tile<2, 1>(s, D->dd, ds, ta, grid, st);
-      } else {
-        if (U >= 4) launch_tile<1, 4>(s, D->dd, ds, ta, grid, st);
-        else if (U == 2) launch_tile<1, 2>(s, D->dd, ds, ta, grid, st);
-        else launch_tile<1, 1>(s, D->dd, ds, ta, grid, st);
-      }
+      const Variant* v = find_variant(s->V, U, s->threads);
+      require(v != nullptr, "rteaal_step: no kernel variant for this configuration");
+      void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ta};
+      CK(cudaLaunchKernel(v->tile, dim3(grid), dim3(s->threads), args, 0, st));
       CK(cudaGetLastError());
     } else {  // GRID
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
@@ -864,16 +960,10 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       ga.ncyc = (uint32_t)max_cyc;
       ga.tpo = make_fastdiv((uint32_t)(np / s->V));
       CK(cudaMemsetAsync(s->scratch, 0, 16, st));
-      cudaError_t e;
-      if (s->V == 2) {
-        e = U >= 4 ? launch_grid<2, 4>(s, D->dd, ds, ga, s->grid, st)
-            : U == 2 ? launch_grid<2, 2>(s, D->dd, ds, ga, s->grid, st)
-                     : launch_grid<2, 1>(s, D->dd, ds, ga, s->grid, st);
-      } else {
-        e = U >= 4 ? launch_grid<1, 4>(s, D->dd, ds, ga, s->grid, st)
-            : U == 2 ? launch_grid<1, 2>(s, D->dd, ds, ga, s->grid, st)
-                     : launch_grid<1, 1>(s, D->dd, ds, ga, s->grid, st);
-      }
+      const Variant* v = find_variant(s->V, U, s->threads);
+      require(v != nullptr, "rteaal_step: no kernel variant for this configuration");
+      void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ga};
+      cudaError_t e = cudaLaunchCooperativeKernel(v->grid, dim3(s->grid), dim3(s->threads), args, 0, st);
       if (e == cudaErrorCooperativeLaunchTooLarge)
         throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
       CK(e);
