@@ -60,12 +60,44 @@ struct DSim {
   uint32_t* err;
 };
 
-// Item space over a lane range: item i -> (row i / tpo, lanes base + (i % tpo) * V).
+constexpr uint32_t NO_ROW = 0xFFFFFFFFu;
+
+// Work of one thread over a lane range [lane_base, lane_base + tpo * V): rows
+// (operations, inputs, registers, ...) times chunks of V lanes.
+//  * fixed mapping (row_stride != 0): when the threads cover every chunk, each
+//    thread keeps one chunk and walks rows row0, row0 + row_stride, ...  No
+//    division per item and the lane activity is computed once per phase.
+//  * generic mapping (row_stride == 0): item i = first + k * stride,
+//    row = i / tpo, chunk = i % tpo (fewer threads than chunks).
 struct ItemSpace {
-  FastDiv tpo;        // chunks (of V lanes) per row
+  FastDiv tpo;
   uint32_t lane_base;
   uint32_t first, stride;
+  uint32_t lane, row0, row_stride;
 };
+
+template <int V>
+__device__ __forceinline__ ItemSpace make_space(FastDiv tpo, uint32_t lane_base, uint32_t t,
+                                                uint32_t nthreads) {
+  ItemSpace is;
+  is.tpo = tpo;
+  is.lane_base = lane_base;
+  is.first = t;
+  is.stride = nthreads;
+  is.lane = lane_base;
+  is.row0 = NO_ROW;
+  is.row_stride = 0;
+  if (nthreads >= tpo.d) {
+    const uint32_t per = fdiv(tpo, nthreads);
+    is.row_stride = per;
+    if (t < per * tpo.d) {
+      const uint32_t r = fdiv(tpo, t);
+      is.row0 = r;
+      is.lane = lane_base + (t - r * tpo.d) * V;
+    }
+  }
+  return is;
+}
 
 __device__ __forceinline__ uint64_t wmask(uint32_t w) { return ~0ull >> (64u - w); }
 
@@ -167,72 +199,153 @@ __device__ __forceinline__ Lanes<V> ldl(const uint64_t* p) {
   return r;
 }
 
+// Activity of V consecutive lanes as a bit mask (bit v = lane + v active).
 template <int V>
-__device__ __forceinline__ void stl(uint64_t* p, const Lanes<V>& r, const DSim& s, uint32_t lane,
-                                    uint32_t cyc) {
+__device__ __forceinline__ uint32_t act_mask(const DSim& s, uint32_t lane, uint32_t cyc) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int v = 0; v < V; v++)
+    if (lane_active(s, lane + v, cyc)) m |= 1u << v;
+  return m;
+}
+
+// Store the active lanes of a result (frozen instances keep their state).
+template <int V>
+__device__ __forceinline__ void stm(uint64_t* p, const Lanes<V>& r, uint32_t m) {
   if constexpr (V == 2) {
-    const bool a0 = lane_active(s, lane, cyc), a1 = lane_active(s, lane + 1, cyc);
-    if (a0 && a1) {
+    if (m == 3u) {
       *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(r.x[0], r.x[1]);
     } else {
-      if (a0) p[0] = r.x[0];
-      if (a1) p[1] = r.x[1];
+      if (m & 1u) p[0] = r.x[0];
+      if (m & 2u) p[1] = r.x[1];
     }
   } else {
 #pragma unroll
     for (int v = 0; v < V; v++)
-      if (lane_active(s, lane + v, cyc)) p[v] = r.x[v];
+      if (m & (1u << v)) p[v] = r.x[v];
   }
 }
 
-// Evaluate ops [op0, op0 + n_ops) of the lowered list over the item space.
-// U items are issued per thread before any result is stored (memory-level
-// parallelism: all operand loads of the U items are in flight together).
+// Operand gather of one op for V lanes (OI = LI . OIM for this s coordinate).
+template <int V>
+__device__ __forceinline__ void gather(const uint64_t* lanes, size_t np, const uint4& m, Lanes<V>& a,
+                                       Lanes<V>& b, Lanes<V>& c) {
+#pragma unroll
+  for (int v = 0; v < V; v++) a.x[v] = b.x[v] = c.x[v] = 0;
+  if (!(m.w & CTL_EXT)) {
+    const uint32_t ar = (m.w >> 5) & 3u;
+    a = ldl<V>(lanes + (size_t)m.x * np);
+    if (ar >= 2) b = ldl<V>(lanes + (size_t)m.y * np);
+    if (ar >= 3) c = ldl<V>(lanes + (size_t)m.z * np);
+  }
+}
+
+// op_u / op_r / op_s of one op for V lanes, from gathered operands.
+template <int V>
+__device__ __forceinline__ Lanes<V> apply(const DDesign& d, const DSim& s, const uint4& m,
+                                          const Lanes<V>& a, const Lanes<V>& b, const Lanes<V>& c,
+                                          uint32_t lane) {
+  const uint32_t ctl = m.w;
+  Lanes<V> r;
+  if (ctl & CTL_EXT) {
+#pragma unroll
+    for (int v = 0; v < V; v++) r.x[v] = eval_ext(d, s, m, lane + v);
+  } else if ((ctl & 31u) == OP_MEMRD) {
+#pragma unroll
+    for (int v = 0; v < V; v++) r.x[v] = eval_memrd(d, s, ctl, a.x[v], lane + v);
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; v++) r.x[v] = alu(ctl, a.x[v], b.x[v], c.x[v]);
+  }
+  return r;
+}
+
+// Generic mapping (more lane chunks than threads): kept out of line so that it
+// does not cost the fixed-mapping hot loop any registers.
 template <int V, int U>
-__device__ __forceinline__ void eval_ops(const DDesign& d, const DSim& s, uint32_t op0,
-                                         uint32_t n_items, const ItemSpace& is, uint32_t cyc) {
+__device__ __noinline__ void eval_ops_generic(const DDesign& d, const DSim& s, uint32_t op0,
+                                              uint32_t n_rows, const ItemSpace& is, uint32_t cyc) {
   const size_t np = s.n_pad;
+  const uint32_t n_items = n_rows * is.tpo.d;
   for (uint32_t i0 = is.first; i0 < n_items; i0 += is.stride * U) {
     uint4 m[U];
-    uint32_t opi[U], lane[U];
+    uint32_t row[U], lane[U];
     bool ok[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const uint32_t i = i0 + u * is.stride;
       ok[u] = i < n_items;
-      const uint32_t row = fdiv(is.tpo, i);
-      opi[u] = op0 + row;
-      lane[u] = is.lane_base + (i - row * is.tpo.d) * V;
-      m[u] = ok[u] ? __ldg(&d.meta[opi[u]]) : make_uint4(0, 0, 0, 0);
+      row[u] = fdiv(is.tpo, i);
+      lane[u] = is.lane_base + (i - row[u] * is.tpo.d) * V;
+      m[u] = ok[u] ? __ldg(&d.meta[op0 + row[u]]) : make_uint4(0, 0, 0, 0);
     }
     Lanes<V> va[U], vb[U], vc[U];
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-#pragma unroll
-      for (int v = 0; v < V; v++) va[u].x[v] = vb[u].x[v] = vc[u].x[v] = 0;
-      if (ok[u] && !(m[u].w & CTL_EXT)) {
-        const uint32_t ar = (m[u].w >> 5) & 3u;
-        va[u] = ldl<V>(s.state + (size_t)m[u].x * np + lane[u]);
-        if (ar >= 2) vb[u] = ldl<V>(s.state + (size_t)m[u].y * np + lane[u]);
-        if (ar >= 3) vc[u] = ldl<V>(s.state + (size_t)m[u].z * np + lane[u]);
-      }
-    }
+    for (int u = 0; u < U; u++)
+      if (ok[u]) gather<V>(s.state + lane[u], np, m[u], va[u], vb[u], vc[u]);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       if (!ok[u]) continue;
-      const uint32_t ctl = m[u].w;
-      Lanes<V> r;
-      if (ctl & CTL_EXT) {
+      const Lanes<V> res = apply<V>(d, s, m[u], va[u], vb[u], vc[u], lane[u]);
+      stm<V>(s.state + (size_t)(d.op_base + op0 + row[u]) * np + lane[u], res,
+             act_mask<V>(s, lane[u], cyc));
+    }
+  }
+}
+
+
+// (a2) evaluate ops [op0, op0 + n_rows) of the lowered list.  U ops are issued
+// per thread before any result is stored, so all their operand loads are in
+// flight together (memory-level parallelism).
+template <int V, int U>
+__device__ __forceinline__ void eval_ops(const DDesign& d, const DSim& s, uint32_t op0,
+                                         uint32_t n_rows, const ItemSpace& is, uint32_t cyc) {
+  const size_t np = s.n_pad;
+  if (!is.row_stride) {
+    eval_ops_generic<V, U>(d, s, op0, n_rows, is, cyc);
+    return;
+  }
+  {
+    if (is.row0 == NO_ROW) return;
+    const uint32_t am = act_mask<V>(s, is.lane, cyc);
+    if (!am) return;
+    const uint64_t* lanes = s.state + is.lane;
+    uint64_t* out = s.state + (size_t)(d.op_base + op0) * np + is.lane;
+    const uint4* meta = d.meta + op0;
+    for (uint32_t r0 = is.row0; r0 < n_rows; r0 += is.row_stride * U) {
+      uint4 m[U];
+      bool ok[U];
 #pragma unroll
-        for (int v = 0; v < V; v++) r.x[v] = eval_ext(d, s, m[u], lane[u] + v);
-      } else if ((ctl & 31u) == OP_MEMRD) {
-#pragma unroll
-        for (int v = 0; v < V; v++) r.x[v] = eval_memrd(d, s, ctl, va[u].x[v], lane[u] + v);
-      } else {
-#pragma unroll
-        for (int v = 0; v < V; v++) r.x[v] = alu(ctl, va[u].x[v], vb[u].x[v], vc[u].x[v]);
+      for (int u = 0; u < U; u++) {
+        const uint32_t r = r0 + u * is.row_stride;
+        ok[u] = r < n_rows;
+        m[u] = ok[u] ? __ldg(&meta[r]) : make_uint4(0, 0, 0, 0);
       }
-      stl<V>(s.state + (size_t)(d.op_base + opi[u]) * np + lane[u], r, s, lane[u], cyc);
+      Lanes<V> va[U], vb[U], vc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (ok[u]) gather<V>(lanes, np, m[u], va[u], vb[u], vc[u]);
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (!ok[u]) continue;
+        const Lanes<V> res = apply<V>(d, s, m[u], va[u], vb[u], vc[u], is.lane);
+        stm<V>(out + (size_t)(r0 + u * is.row_stride) * np, res, am);
+      }
+    }
+  }
+}
+
+// Visit (row, first lane) pairs of n_rows rows under either mapping.
+template <int V, typename F>
+__device__ __forceinline__ void for_rows(const ItemSpace& is, uint32_t n_rows, F&& f) {
+  if (is.row_stride) {
+    if (is.row0 == NO_ROW) return;
+    for (uint32_t r = is.row0; r < n_rows; r += is.row_stride) f(r, is.lane);
+  } else {
+    const uint32_t n_items = n_rows * is.tpo.d;
+    for (uint32_t i = is.first; i < n_items; i += is.stride) {
+      const uint32_t r = fdiv(is.tpo, i);
+      f(r, is.lane_base + (i - r * is.tpo.d) * V);
     }
   }
 }
@@ -242,11 +355,8 @@ template <int V>
 __device__ __forceinline__ void stim_items(const DDesign& d, const DSim& s, const ItemSpace& is,
                                            uint32_t cyc) {
   if (s.stim_mode == 0) return;
-  const uint32_t n_items = d.n_inputs * is.tpo.d;
   const size_t np = s.n_pad;
-  for (uint32_t i = is.first; i < n_items; i += is.stride) {
-    const uint32_t j = fdiv(is.tpo, i);
-    const uint32_t lane0 = is.lane_base + (i - j * is.tpo.d) * V;
+  for_rows<V>(is, d.n_inputs, [&](uint32_t j, uint32_t lane0) {
     const uint64_t mk = wmask(__ldg(&d.in_w[j]));
 #pragma unroll
     for (int v = 0; v < V; v++) {
@@ -264,20 +374,19 @@ __device__ __forceinline__ void stim_items(const DDesign& d, const DSim& s, cons
       }
       s.state[(size_t)j * np + lane] = x & mk;
     }
-  }
+  });
 }
 
-// (a5) clock edge: registers, then memory write ports (port order per memory).
+// (a5) clock edge: registers (rows [0, n_regs)), then memory write ports
+// (rows [n_regs, n_regs + n_mems), ports of one memory in port order).
 template <int V>
 __device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, const ItemSpace& is,
                                              uint32_t cyc) {
   const size_t np = s.n_pad;
-  const uint32_t n_reg_items = d.n_regs * is.tpo.d;
-  const uint32_t n_items = n_reg_items + d.n_mems * is.tpo.d;
-  for (uint32_t i = is.first; i < n_items; i += is.stride) {
-    if (i < n_reg_items) {
-      const uint32_t r = fdiv(is.tpo, i);
-      const uint32_t lane = is.lane_base + (i - r * is.tpo.d) * V;
+  for_rows<V>(is, d.n_regs + d.n_mems, [&](uint32_t r, uint32_t lane) {
+    const uint32_t am = act_mask<V>(s, lane, cyc);
+    if (!am) return;
+    if (r < d.n_regs) {
       const uint64_t mk = wmask(__ldg(&d.reg_w[r]));
       Lanes<V> v;
       if (s.reset) {
@@ -289,37 +398,32 @@ __device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, co
 #pragma unroll
         for (int t = 0; t < V; t++) v.x[t] &= mk;
       }
-      stl<V>(s.state + (size_t)(d.reg_base + r) * np + lane, v, s, lane, cyc);
+      stm<V>(s.state + (size_t)(d.reg_base + r) * np + lane, v, am);
     } else {
-      const uint32_t k = i - n_reg_items;
-      const uint32_t mi = fdiv(is.tpo, k);
-      const uint32_t lane0 = is.lane_base + (k - mi * is.tpo.d) * V;
+      const uint32_t mi = r - d.n_regs;
       const uint4 info = __ldg(&d.mem_info[mi]);
       const uint32_t p1 = __ldg(&d.mem_info[mi + 1]).w;
       const uint64_t mk = wmask(info.z);
 #pragma unroll
       for (int t = 0; t < V; t++) {
-        const uint32_t lane = lane0 + t;
-        if (!lane_active(s, lane, cyc)) continue;
+        if (!(am & (1u << t))) continue;
+        const uint32_t ln = lane + t;
         for (uint32_t p = info.w; p < p1; p++) {
           const uint4 w = __ldg(&d.wport[p]);
-          if (s.state[(size_t)w.y * np + lane] & 1ull) {
-            const uint64_t a = s.state[(size_t)w.z * np + lane] & (uint64_t)info.y;
-            s.mem[((size_t)info.x + a) * np + lane] = s.state[(size_t)w.w * np + lane] & mk;
+          if (s.state[(size_t)w.y * np + ln] & 1ull) {
+            const uint64_t a = s.state[(size_t)w.z * np + ln] & (uint64_t)info.y;
+            s.mem[((size_t)info.x + a) * np + ln] = s.state[(size_t)w.w * np + ln] & mk;
           }
         }
       }
     }
-  }
+  });
 }
 
 // (a7) per-cycle probes: end-of-cycle values of selected slots.
 template <int V>
 __device__ __forceinline__ void probe_items(const DSim& s, const ItemSpace& is, uint32_t cyc) {
-  const uint32_t n_items = s.n_probe * is.tpo.d;
-  for (uint32_t i = is.first; i < n_items; i += is.stride) {
-    const uint32_t p = fdiv(is.tpo, i);
-    const uint32_t lane0 = is.lane_base + (i - p * is.tpo.d) * V;
+  for_rows<V>(is, s.n_probe, [&](uint32_t p, uint32_t lane0) {
     const uint32_t slot = __ldg(&s.probe_slot[p]);
 #pragma unroll
     for (int t = 0; t < V; t++) {
@@ -328,7 +432,7 @@ __device__ __forceinline__ void probe_items(const DSim& s, const ItemSpace& is, 
       s.probe_out[((size_t)cyc * s.n_probe + p) * s.n_user + user_of(s, lane)] =
           s.state[(size_t)slot * s.n_pad + lane];
     }
-  }
+  });
 }
 
 }  // namespace rteaal

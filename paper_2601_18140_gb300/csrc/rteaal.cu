@@ -34,18 +34,18 @@ namespace rteaal {
 
 template <int V, int U>
 __global__ void __launch_bounds__(256) k_layer_ops(DDesign d, DSim s, uint32_t op0,
-                                                   uint32_t n_items, FastDiv tpo, uint32_t cyc,
+                                                   uint32_t n_rows, FastDiv tpo, uint32_t cyc,
                                                    const uint32_t* cyc_dev) {
   if (cyc_dev) cyc = *cyc_dev;
-  ItemSpace is{tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
-  eval_ops<V, U>(d, s, op0, n_items, is, cyc);
+  const ItemSpace is = make_space<V>(tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  eval_ops<V, U>(d, s, op0, n_rows, is, cyc);
 }
 
 template <int V>
 __global__ void __launch_bounds__(256) k_layer_stim(DDesign d, DSim s, FastDiv tpo, uint32_t cyc,
                                                     const uint32_t* cyc_dev) {
   if (cyc_dev) cyc = *cyc_dev;
-  ItemSpace is{tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  const ItemSpace is = make_space<V>(tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   stim_items<V>(d, s, is, cyc);
 }
 
@@ -53,7 +53,7 @@ template <int V>
 __global__ void __launch_bounds__(256) k_layer_commit(DDesign d, DSim s, FastDiv tpo, uint32_t cyc,
                                                       const uint32_t* cyc_dev) {
   if (cyc_dev) cyc = *cyc_dev;
-  ItemSpace is{tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  const ItemSpace is = make_space<V>(tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   commit_items<V>(d, s, is, cyc);
 }
 
@@ -61,7 +61,7 @@ template <int V>
 __global__ void __launch_bounds__(256) k_layer_probe(DSim s, FastDiv tpo, uint32_t cyc,
                                                      const uint32_t* cyc_dev) {
   if (cyc_dev) cyc = *cyc_dev;
-  ItemSpace is{tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  const ItemSpace is = make_space<V>(tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   probe_items<V>(s, is, cyc);
 }
 
@@ -75,8 +75,8 @@ struct TileArgs {
   FastDiv tpo;                   // tile_lanes / V
 };
 
-template <int V, int U, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_tile(DDesign d, DSim s, TileArgs t) {
+template <int V, int U, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_tile(DDesign d, DSim s, TileArgs t) {
   __shared__ uint32_t sh_q;
   for (;;) {
     if (threadIdx.x == 0) sh_q = atomicAdd(t.counter, 1u);
@@ -85,23 +85,24 @@ __global__ void __launch_bounds__(MAXT) k_tile(DDesign d, DSim s, TileArgs t) {
     __syncthreads();
     if (q >= t.n_tiles) return;
     const uint32_t tile = t.order ? t.order[q] : q;
-    const ItemSpace is{t.tpo, tile * t.tile_lanes, threadIdx.x, blockDim.x};
     const uint32_t ncyc = t.tile_cycles ? t.tile_cycles[tile] : s.uniform;
+#define RT_SPACE make_space<V>(t.tpo, tile * t.tile_lanes, threadIdx.x, blockDim.x)
     for (uint32_t c = 0; c < ncyc; c++) {
-      stim_items<V>(d, s, is, c);
+      stim_items<V>(d, s, RT_SPACE, c);
       __syncthreads();
       for (uint32_t L = 0; L < d.n_layers; L++) {
         const uint32_t o0 = __ldg(&d.layer_off[L]), o1 = __ldg(&d.layer_off[L + 1]);
-        eval_ops<V, U>(d, s, o0, (o1 - o0) * t.tpo.d, is, c);
+        eval_ops<V, U>(d, s, o0, o1 - o0, RT_SPACE, c);
         __syncthreads();
       }
-      commit_items<V>(d, s, is, c);
+      commit_items<V>(d, s, RT_SPACE, c);
       __syncthreads();
       if (s.n_probe) {
-        probe_items<V>(s, is, c);
+        probe_items<V>(s, RT_SPACE, c);
         __syncthreads();
       }
     }
+#undef RT_SPACE
   }
 }
 
@@ -155,25 +156,28 @@ __device__ __forceinline__ bool grid_sync(const GridArgs& g, uint32_t* err, int*
   return *sh_ok != 0;
 }
 
-template <int V, int U, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_grid(DDesign d, DSim s, GridArgs g) {
+template <int V, int U, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs g) {
   __shared__ int sh_ok;
-  const ItemSpace is{g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+  // the work mapping is recomputed per phase (a few integer ops) instead of
+  // being held in registers across every barrier
+#define RT_SPACE make_space<V>(g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x)
   for (uint32_t c = 0; c < g.ncyc; c++) {
-    stim_items<V>(d, s, is, c);
+    stim_items<V>(d, s, RT_SPACE, c);
     if (!grid_sync(g, s.err, &sh_ok)) return;
     for (uint32_t L = 0; L < d.n_layers; L++) {
       const uint32_t o0 = __ldg(&d.layer_off[L]), o1 = __ldg(&d.layer_off[L + 1]);
-      eval_ops<V, U>(d, s, o0, (o1 - o0) * g.tpo.d, is, c);
+      eval_ops<V, U>(d, s, o0, o1 - o0, RT_SPACE, c);
       if (!grid_sync(g, s.err, &sh_ok)) return;
     }
-    commit_items<V>(d, s, is, c);
+    commit_items<V>(d, s, RT_SPACE, c);
     if (!grid_sync(g, s.err, &sh_ok)) return;
     if (s.n_probe) {
-      probe_items<V>(s, is, c);
+      probe_items<V>(s, RT_SPACE, c);
       if (!grid_sync(g, s.err, &sh_ok)) return;
     }
   }
+#undef RT_SPACE
 }
 
 // state[slot][lane] <-> host [n][n_inst] through a [n][n_inst] device buffer
@@ -416,11 +420,11 @@ void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32
     const uint32_t o0 = D->L.layer_off[l], o1 = D->L.layer_off[l + 1];
     const uint64_t items = (uint64_t)(o1 - o0) * tpo.d;
     if (U >= 4)
-      k_layer_ops<V, 4><<<blocks_for(items, 4), threads, 0, st>>>(dd, ds, o0, (uint32_t)items, tpo, c, cyc_dev);
+      k_layer_ops<V, 4><<<blocks_for(items, 4), threads, 0, st>>>(dd, ds, o0, o1 - o0, tpo, c, cyc_dev);
     else if (U == 2)
-      k_layer_ops<V, 2><<<blocks_for(items, 2), threads, 0, st>>>(dd, ds, o0, (uint32_t)items, tpo, c, cyc_dev);
+      k_layer_ops<V, 2><<<blocks_for(items, 2), threads, 0, st>>>(dd, ds, o0, o1 - o0, tpo, c, cyc_dev);
     else
-      k_layer_ops<V, 1><<<blocks_for(items, 1), threads, 0, st>>>(dd, ds, o0, (uint32_t)items, tpo, c, cyc_dev);
+      k_layer_ops<V, 1><<<blocks_for(items, 1), threads, 0, st>>>(dd, ds, o0, o1 - o0, tpo, c, cyc_dev);
   }
   const uint64_t citems = (uint64_t)(D->L.reg_src.size() + (D->L.mem_info.size() / 4 - 1)) * tpo.d;
   if (citems)
@@ -430,17 +434,19 @@ void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32
 }
 
 // Compiled variants of the persistent kernels: lanes per thread V, items in
-// flight per thread U, launch bound MAXT (threads per CTA).
+// flight per thread U, launch bounds (MAXT threads per CTA, MINB CTAs per SM;
+// MAXT * MINB = 2048 keeps every variant at full occupancy within 65,536
+// registers per SM, except U = 4 which trades occupancy for in-flight items).
 struct Variant {
-  int V, U, maxt;
+  int V, U, maxt, minb;
   const void* tile;
   const void* grid;
 };
-#define RT_VARIANT(V, U, T) {V, U, T, (const void*)k_tile<V, U, T>, (const void*)k_grid<V, U, T>}
+#define RT_VARIANT(V, U, T, B) {V, U, T, B, (const void*)k_tile<V, U, T, B>, (const void*)k_grid<V, U, T, B>}
 const Variant kVariants[] = {
-    RT_VARIANT(2, 1, 512), RT_VARIANT(2, 2, 512), RT_VARIANT(2, 4, 512),
-    RT_VARIANT(2, 1, 1024), RT_VARIANT(2, 2, 1024),
-    RT_VARIANT(1, 1, 512), RT_VARIANT(1, 2, 512), RT_VARIANT(1, 4, 512),
+    RT_VARIANT(2, 1, 256, 8), RT_VARIANT(2, 1, 512, 4), RT_VARIANT(2, 1, 1024, 2),
+    RT_VARIANT(2, 2, 512, 2), RT_VARIANT(2, 4, 512, 1),
+    RT_VARIANT(1, 1, 512, 4), RT_VARIANT(1, 2, 512, 2), RT_VARIANT(1, 4, 512, 1),
 };
 #undef RT_VARIANT
 
