@@ -20,7 +20,11 @@ def test_configure_between_steps():
     nl = design()
     p = Pair(nl, 128, kernel="tile", seed=12)
     p.step(1, reset=True)
-    for cfg in [dict(kernel="tile", tile_lanes=8, threads=1024, unroll=2),
+    with pytest.raises(rt.RteaalError) as ei:                 # no such compiled variant
+        p.sim.configure(kernel="tile", tile_lanes=8, threads=1024, unroll=4)
+    assert ei.value.code == rt.RTEAAL_E_UNSUPPORTED
+    for cfg in [dict(kernel="tile", tile_lanes=8, threads=1024, unroll=1),
+                dict(kernel="tile", tile_lanes=16, threads=512, unroll=2),
                 dict(kernel="grid", threads=256, unroll=4),
                 dict(kernel="layer", unroll=1),
                 dict(kernel="tile", tile_lanes=64, threads=512, unroll=4),
