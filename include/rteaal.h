@@ -254,6 +254,40 @@ int rteaal_stim_state_read(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst
 int rteaal_stim_state_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst,
                             const uint64_t *host_in, void *stream);
 
+/* ---------------------------------------------------------------- allocation-free step
+ * No counterpart in the paper.  Some callers cannot allocate device memory at
+ * all -- a host process whose device memory is owned by another allocator or
+ * framework that forbids cudaMalloc / cudaFree from libraries, or that has
+ * already handed out every byte.  For them this entry point runs the
+ * persistent grid form over buffers they own and allocates nothing: no
+ * cudaMalloc / cudaFree and no allocating library routine.  Its scratch (grid
+ * barrier words, error word, per-lane cycle budgets) is a file-scope device
+ * array sized for RTEAAL_STATIC_MAX_LANES lanes (about 256 KB), which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * Buffers (caller-owned device memory, lane = instance, identity order):
+ *   state [n_slots][n_lanes] uint64  (rows in slot order; pool rows = signal ids:
+ *         inputs, registers, constants -- constants must hold their values)
+ *   mem   [mem_words_total][n_lanes] uint64 (nullable without memories)
+ *   xs    [n_inputs][n_lanes] uint64 xorshift64 states (nullable unless XORSHIFT)
+ * Slot order of op rows: by level, then (opcode, width), then netlist order;
+ * a register D or write-port signal that is not an op output gets a COPY op
+ * on level 1, ordered after the netlist's own ops of the same key.  16-byte aligned buffers with an even n_lanes
+ * use two lanes per thread.
+ * cycles: host [n_lanes] per-lane cycle counts, or NULL to run uniform_cycles.
+ * stim_mode: RTEAAL_STIM_HOLD or RTEAAL_STIM_XORSHIFT.  flags: RTEAAL_STEP_RESET.
+ * Sizes beyond RTEAAL_STATIC_MAX_LANES lanes are rejected (E_INVALID).
+ * The first call on each device looks up the array's device address (make it
+ * before any stream capture).  Every call shares the one array and leaves its
+ * contents behind; the barrier and error words are cleared at the start of
+ * each call.  Calls that overlap on the GPU (other streams, other threads) race
+ * on the array: serialise them.  Synchronises stream; returns E_TIMEOUT if a
+ * bounded barrier wait gave up. */
+#define RTEAAL_STATIC_MAX_LANES 65536u
+int rteaal_step_static(const rteaal_design *design, uint64_t *state, uint64_t *mem, uint64_t *xs,
+                       uint32_t n_lanes, const uint32_t *cycles, uint32_t uniform_cycles,
+                       int stim_mode, uint32_t flags, void *stream);
+
 /* Thread-local description of the last failure on this thread. */
 const char *rteaal_last_error(void);
 

@@ -94,7 +94,8 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_sim_info", "rteaal_sim_destroy", "rteaal_sim_configure", "rteaal_sim_autotune", "rteaal_sim_footprint", "rteaal_step",
            "rteaal_sync", "rteaal_state_read", "rteaal_state_write", "rteaal_mem_read",
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
-           "rteaal_last_error"]
+           "rteaal_last_error", "rteaal_step_static"]
+STATIC_MAX_LANES = 65536
 
 _lib = None
 
@@ -129,6 +130,8 @@ def lib() -> ctypes.CDLL:
         for n in ["rteaal_mem_read", "rteaal_mem_write", "rteaal_stim_state_read",
                   "rteaal_stim_state_write"]:
             getattr(L, n).argtypes = [_P, _U32, _U32, _P, _P]
+        L.rteaal_step_static.argtypes = [_P, _P, _P, _P, _U32, ctypes.POINTER(_U32), _U32,
+                                         ctypes.c_int, _U32, _P]
         _lib = L
     return _lib
 
@@ -304,6 +307,20 @@ def rteaal_stim_state_write(sim: int, inst_begin: int, values: np.ndarray, strea
     v = np.ascontiguousarray(values, np.uint64)
     _check(lib().rteaal_stim_state_write(sim, inst_begin, v.shape[1], v.ctypes.data,
                                          _stream_ptr(stream)))
+
+
+def rteaal_step_static(design: int, state, mem, xs, n_lanes: int, cycles=None,
+                       uniform_cycles: int = 0, stim_mode: int = RTEAAL_STIM_XORSHIFT,
+                       flags: int = 0, stream=None):
+    """Allocation-free step over caller-owned device buffers (see include/rteaal.h)."""
+    keep = None
+    cptr = None
+    if cycles is not None:
+        keep = np.ascontiguousarray(cycles, np.uint32)
+        cptr = _np_ptr(keep, _U32)
+    _check(lib().rteaal_step_static(design, _dev_ptr(state), _dev_ptr(mem), _dev_ptr(xs), n_lanes,
+                                    cptr, uniform_cycles, stim_mode, flags, _stream_ptr(stream)))
+    del keep
 
 
 def rteaal_last_error() -> str:

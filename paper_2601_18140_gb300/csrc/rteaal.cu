@@ -1098,3 +1098,106 @@ RT_EXPORT int rteaal_stim_state_write(rteaal_sim* s, uint32_t inst0, uint32_t n_
                                       void* stream) {
   return guarded([&] { transfer(s, Region::XS, nullptr, 0, inst0, n_inst, nullptr, in, (cudaStream_t)stream); });
 }
+
+// ================================================================== allocation-free step
+//
+// For callers that cannot allocate device memory themselves: everything the
+// persistent grid kernel needs besides the caller's buffers (barrier arrival
+// count, barrier generation, error word, per-lane cycle budgets) lives in one
+// file-scope device array.  Every GPU that loads this library holds the array
+// (RTEAAL_STATIC_MAX_LANES * 4 + 256 bytes) until the process exits.
+
+static __device__ __align__(256) uint32_t g_static_scratch[64 + RTEAAL_STATIC_MAX_LANES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+uint32_t* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up once per
+// device: host code only sees a host-side stand-in under that name).
+uint32_t* static_scratch(int dev) {
+  require(dev >= 0 && dev < kMaxDevices, "rteaal_step_static: device ordinal out of range");
+  std::lock_guard<std::mutex> g(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_addr[dev] = static_cast<uint32_t*>(p);
+  }
+  return g_static_addr[dev];
+}
+
+}  // namespace
+
+RT_EXPORT int rteaal_step_static(const rteaal_design* d, uint64_t* state, uint64_t* mem, uint64_t* xs,
+                                 uint32_t n_lanes, const uint32_t* cycles, uint32_t uniform_cycles,
+                                 int stim_mode, uint32_t flags, void* stream) {
+  return guarded([&] {
+    require(d && state, "rteaal_step_static: null design or state");
+    require(n_lanes >= 1, "rteaal_step_static: n_lanes must be at least 1");
+    if (n_lanes > RTEAAL_STATIC_MAX_LANES)
+      throw Error(RTEAAL_E_INVALID, "rteaal_step_static: n_lanes " + std::to_string(n_lanes) +
+                                        " exceeds the static scratch limit of " +
+                                        std::to_string(RTEAAL_STATIC_MAX_LANES) + " lanes");
+    require(stim_mode == RTEAAL_STIM_HOLD || stim_mode == RTEAAL_STIM_XORSHIFT,
+            "rteaal_step_static: stimulus mode must be HOLD or XORSHIFT");
+    const Lowered& L = d->L;
+    require(mem || L.mem_words_total == 0, "rteaal_step_static: design has memories but mem is null");
+    require(xs || stim_mode != RTEAAL_STIM_XORSHIFT || L.in_width.empty(),
+            "rteaal_step_static: XORSHIFT stimulus needs xs");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(d->device));
+    uint32_t* scratch = static_scratch(d->device);
+
+    uint32_t max_cyc = uniform_cycles;
+    if (cycles) {
+      max_cyc = 0;
+      for (uint32_t l = 0; l < n_lanes; l++) max_cyc = std::max(max_cyc, cycles[l]);
+    }
+    if (max_cyc == 0) return;
+    const bool aligned = ((uintptr_t)state % 16 == 0) && ((uintptr_t)mem % 16 == 0) && ((uintptr_t)xs % 16 == 0);
+    const int V = (n_lanes % 2 == 0 && aligned) ? 2 : 1;
+    const uint32_t threads = 512;
+    const Variant* v = find_variant(V, 1, threads);
+    require(v != nullptr, "rteaal_step_static: no kernel variant");
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v->grid, (int)threads, 0));
+    require(occ >= 1, "rteaal_step_static: kernel cannot be resident");
+    const uint32_t grid = (uint32_t)occ * (uint32_t)d->n_sms;
+
+    // the barrier and error words must start at zero; budgets are rewritten
+    CK(cudaMemsetAsync(scratch, 0, 64 * sizeof(uint32_t), st));
+    DSim ds{};
+    ds.state = state;
+    ds.mem = mem;
+    ds.xs = xs;
+    ds.n_pad = n_lanes;
+    ds.n_user = n_lanes;
+    ds.stim_mode = L.in_width.empty() ? 0 : stim_mode;
+    ds.reset = (flags & RTEAAL_STEP_RESET) ? 1 : 0;
+    ds.err = scratch;
+    if (cycles) {
+      CK(cudaMemcpyAsync(scratch + 64, cycles, (size_t)n_lanes * 4, cudaMemcpyHostToDevice, st));
+      ds.budget = scratch + 64;
+    } else {
+      ds.uniform = uniform_cycles;
+    }
+    GridArgs ga{};
+    ga.count = scratch + 1;
+    ga.gen = scratch + 2;
+    ga.expected = grid;
+    ga.timeout_ns = 2000000000ull;
+    ga.ncyc = max_cyc;
+    ga.tpo = make_fastdiv(n_lanes / V);
+    void* args[] = {(void*)&d->dd, (void*)&ds, (void*)&ga};
+    cudaError_t e = cudaLaunchCooperativeKernel(v->grid, dim3(grid), dim3(threads), args, 0, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge)
+      throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
+    CK(e);
+    uint32_t err = 0;
+    CK(cudaMemcpyAsync(&err, scratch, sizeof(err), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err) throw Error(RTEAAL_E_TIMEOUT, "rteaal_step_static: a grid barrier wait timed out");
+  });
+}
