@@ -45,15 +45,25 @@ WORKLOADS = {
 }
 
 
-def algorithmic_bytes_per_instance_cycle(nl: synth.Netlist, tile_lanes: int) -> dict:
-    """Bytes one instance-cycle must move at minimum (every operand read once,
-    every result written once) plus the op descriptors amortised over a tile."""
-    arity = np.diff(nl.op_argoff.astype(np.int64))
-    ops = 8.0 * float(arity.sum() + nl.n_ops)                 # operands + result per op
-    regs = 16.0 * nl.n_regs                                   # read D, write Q
-    inputs = 24.0 * nl.n_inputs                               # xorshift state r/w + input write
-    memw = 8.0 * 3 * nl.n_wports                              # en/addr/data reads (writes ~ en rate)
-    meta = 16.0 * nl.n_ops / max(1, tile_lanes)               # 16-byte descriptor per op per tile
+def width_bytes(w: np.ndarray) -> np.ndarray:
+    """Bytes per lane of a row of the compact state (1, 2, 4, 8 for widths <= 8, 16, 32, 64)."""
+    w = np.asarray(w, np.int64)
+    return np.select([w <= 8, w <= 16, w <= 32], [1, 2, 4], 8)
+
+
+def algorithmic_bytes_per_instance_cycle(nl: synth.Netlist, lanes_sharing_meta: int) -> dict:
+    """Bytes one instance-cycle must move at minimum in the compact layout: every
+    operand read once and every result written once, each at its row's width
+    class; per register D read + Q write; per input the xorshift state read and
+    written plus the input row; per write port en/addr/data; the 20-byte op
+    descriptor (16-byte operand record + 4-byte output reference) amortised
+    over the lanes that share one read of it."""
+    sw = width_bytes(nl.signal_widths())
+    ops = float(sw[nl.args.astype(np.int64)].sum() + sw[nl.op_base:].sum())
+    regs = float(sw[nl.reg_d.astype(np.int64)].sum() + sw[nl.reg_base:nl.reg_base + nl.n_regs].sum())
+    inputs = float(16 * nl.n_inputs + sw[:nl.n_inputs].sum())
+    memw = float(sw[nl.wport[:, 1:].astype(np.int64)].sum()) if nl.n_wports else 0.0
+    meta = 20.0 * nl.n_ops / max(1, lanes_sharing_meta)
     return {"ops": ops, "regs": regs, "inputs": inputs, "mem": memw, "meta": meta,
             "total": ops + regs + inputs + memw + meta}
 
@@ -276,7 +286,8 @@ def run_ours(args) -> None:
     value = evals / (t_max / 1e3)
 
     # ---- roofline of the dominant kernel (one k_tile launch per step)
-    bpc = algorithmic_bytes_per_instance_cycle(nl, info["tile_lanes"])
+    sharing = info["tile_lanes"] if info["kernel"] == 2 else n
+    bpc = algorithmic_bytes_per_instance_cycle(nl, sharing)
     per_launch_bytes = bpc["total"] * (inst_cycles / args.steps)
     avg_launch_s = float(np.mean(step_ms)) / 1e3
     peaks = measured_peaks()
@@ -354,7 +365,7 @@ def run_ours(args) -> None:
                        "ctas_per_sm": info["ctas_per_sm"], "unroll": info["unroll"],
                        "grid": info["grid"], "autotune": tune, "parallelism": "replicas" if world > 1 else "1 gpu",
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)"
-                             % (design.info["n_slots"] * n * 8 / 1e9)},
+                             % (design.info["state_bytes_per_lane"] * n / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                          "traffic": traffic, "peak_source": peaks["source"],

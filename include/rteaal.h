@@ -13,9 +13,15 @@
  *   (Sec. 5.2, "Host-DUT Communication").
  *
  * Device form.  Identity operations are elided by giving every signal one
- * global slot (Sec. 4.3): LI / LO of every layer are views of one state array
- *     state[slot][lane]  (uint64, lane = stimulus instance, lane-minor),
- * so that LI_{i+1} <- LO_i moves no data and is only a barrier.  OIM is lowered
+ * global row (Sec. 4.3): LI / LO of every layer are views of one state array,
+ * so that LI_{i+1} <- LO_i moves no data and is only a barrier.  State layout
+ * ("compact"): one row per slot, lane-minor (lane = stimulus instance); a row
+ * holds 1, 2, 4 or 8 bytes per lane for signal widths up to 8, 16, 32, 64
+ * (width class k = 0..3); the rows of class 3 come first, then 2, 1, 0; inside
+ * a class, pool rows (inputs, registers, constants in signal order) precede op
+ * rows (slot order).  A row's per-lane byte offset o is the sum of the bytes
+ * per lane of all rows before it; element (row, lane) of an n-lane state is the
+ * little-endian integer of 1 << k bytes at byte o * n + (lane << k).  OIM is lowered
  * to per-layer operand lists whose operations are grouped by (opcode, width)
  * -- the swizzled [I, N, S, O, R] order of the NU kernel (Sec. 4.4) -- with the
  * S coordinates implicit (the outputs of a layer occupy consecutive slots) and
@@ -115,6 +121,7 @@ typedef struct {
   uint64_t op_operands;      /* sum of operand counts over the n_ops netlist ops */
   uint64_t mem_words_total;  /* words of all memories of one lane               */
   uint64_t metadata_bytes;   /* device bytes owned by the design                */
+  uint64_t state_bytes_per_lane; /* compact state bytes of one lane (see layout) */
 } rteaal_design_stats;
 
 /* Parse, validate, levelise, group by (opcode, width) and upload the lowered
@@ -152,6 +159,7 @@ typedef struct {
   uint32_t threads;        /* threads per CTA (multiple of 32, <= 1024), 0 auto */
   uint32_t ctas_per_sm;    /* TILE / GRID residency target, 0 auto              */
   uint32_t unroll;         /* operations in flight per thread (1, 2, 4), 0 auto */
+  uint32_t lanes_per_thread; /* lanes (instances) per thread per op (1, 2, 4), 0 auto */
 } rteaal_sim_opts;
 
 typedef struct {
@@ -159,6 +167,7 @@ typedef struct {
   uint64_t device_bytes;         /* state + memories + stimulus + scratch        */
   int kernel;                    /* kernel chosen                                */
   uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid;
+  uint32_t lanes_per_thread;
 } rteaal_sim_stats;
 
 /* Allocates and zero-initialises the state of n_instances (>= 1) independent
@@ -170,13 +179,13 @@ int rteaal_sim_info(const rteaal_sim *sim, rteaal_sim_stats *out);
 void rteaal_sim_destroy(rteaal_sim *sim);
 
 /* Change the launch configuration (kernel, tile_lanes, threads, ctas_per_sm,
- * unroll of opts; the other fields are ignored).  Results never depend on it.
+ * unroll, lanes_per_thread of opts; the other fields are ignored).  Results never depend on it.
  * Errors: E_INVALID, E_UNSUPPORTED (no compiled variant). */
 int rteaal_sim_configure(rteaal_sim *sim, const rteaal_sim_opts *opts);
 
 typedef struct {
   int kernel;
-  uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid;
+  uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid, lanes_per_thread;
   float ms;                      /* device time of one trial step                 */
 } rteaal_tune_trial;
 
@@ -266,8 +275,8 @@ int rteaal_stim_state_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_ins
  * that loads the library holds until the process exits.
  *
  * Buffers (caller-owned device memory, lane = instance, identity order):
- *   state [n_slots][n_lanes] uint64  (rows in slot order; pool rows = signal ids:
- *         inputs, registers, constants -- constants must hold their values)
+ *   state state_bytes_per_lane * n_lanes bytes in the compact layout above
+ *         (constants' rows must hold their values)
  *   mem   [mem_words_total][n_lanes] uint64 (nullable without memories)
  *   xs    [n_inputs][n_lanes] uint64 xorshift64 states (nullable unless XORSHIFT)
  * Slot order of op rows: by level, then (opcode, width), then netlist order;
@@ -284,7 +293,7 @@ int rteaal_stim_state_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_ins
  * on the array: serialise them.  Synchronises stream; returns E_TIMEOUT if a
  * bounded barrier wait gave up. */
 #define RTEAAL_STATIC_MAX_LANES 65536u
-int rteaal_step_static(const rteaal_design *design, uint64_t *state, uint64_t *mem, uint64_t *xs,
+int rteaal_step_static(const rteaal_design *design, void *state, uint64_t *mem, uint64_t *xs,
                        uint32_t n_lanes, const uint32_t *cycles, uint32_t uniform_cycles,
                        int stim_mode, uint32_t flags, void *stream);
 

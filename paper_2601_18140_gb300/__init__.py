@@ -55,7 +55,8 @@ class rteaal_design_stats(ctypes.Structure):
     _fields_ = [(n, _U32) for n in ["n_signals", "n_inputs", "n_regs", "n_consts", "n_ops",
                                     "n_mems", "n_wports", "n_layers", "n_groups", "n_slots",
                                     "n_lowered_ops", "max_layer_ops"]] + \
-               [(n, _U64) for n in ["op_operands", "mem_words_total", "metadata_bytes"]]
+               [(n, _U64) for n in ["op_operands", "mem_words_total", "metadata_bytes",
+                                    "state_bytes_per_lane"]]
 
 
 class rteaal_sim_opts(ctypes.Structure):
@@ -63,18 +64,19 @@ class rteaal_sim_opts(ctypes.Structure):
                 ("expected_cycles", ctypes.POINTER(_U32)),
                 ("xorshift_seed", ctypes.POINTER(_U64)),
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
-                ("ctas_per_sm", _U32), ("unroll", _U32)]
+                ("ctas_per_sm", _U32), ("unroll", _U32), ("lanes_per_thread", _U32)]
 
 
 class rteaal_sim_stats(ctypes.Structure):
     _fields_ = [("n_instances", _U32), ("n_lanes", _U32), ("device_bytes", _U64),
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
-                ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32)]
+                ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("lanes_per_thread", _U32)]
 
 
 class rteaal_tune_trial(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
-                ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("ms", ctypes.c_float)]
+                ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("lanes_per_thread", _U32),
+                ("ms", ctypes.c_float)]
 
 
 class rteaal_cycles(ctypes.Structure):
@@ -361,12 +363,13 @@ class Sim:
     def __init__(self, design: Design, n_instances: int, kernel: str | int = "auto",
                  xorshift_seed: np.ndarray | None = None, expected_cycles=None,
                  tile_lanes: int = 0, threads: int = 0, ctas_per_sm: int = 0, unroll: int = 0,
-                 use_torch_allocator: bool = True):
+                 lanes_per_thread: int = 0, use_torch_allocator: bool = True):
         self.design = design
         self.n = n_instances
         o = rteaal_sim_opts()
         o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
+        o.lanes_per_thread = lanes_per_thread
         keep: list[Any] = []
         if use_torch_allocator:
             self._alloc = torch_allocator()
@@ -430,10 +433,11 @@ class Sim:
         rteaal_sync(self.handle, stream)
 
     def configure(self, kernel: str | int = "auto", tile_lanes: int = 0, threads: int = 0,
-                  ctas_per_sm: int = 0, unroll: int = 0):
+                  ctas_per_sm: int = 0, unroll: int = 0, lanes_per_thread: int = 0):
         o = rteaal_sim_opts()
         o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
+        o.lanes_per_thread = lanes_per_thread
         rteaal_sim_configure(self.handle, o)
         self.info = rteaal_sim_info(self.handle)
 

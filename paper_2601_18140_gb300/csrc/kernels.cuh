@@ -1,12 +1,16 @@
 // kernels.cuh -- sm_103a kernels of one simulated cycle.
 //
-// State layout: state[slot][lane], uint64, lane-minor (lane = stimulus
-// instance).  One "item" is one operation evaluated for V consecutive lanes;
-// the lanes of an operation are spread over consecutive threads, so a warp
-// loads whole 8*V*32-byte segments of an operand row (coalesced), and the
-// operation's 16-byte descriptor is a broadcast read.  Operations of a layer
-// are stored grouped by (opcode, width), so neighbouring threads take the same
-// switch arm.  No tensor cores: this is integer gather work bound by memory.
+// State layout: one row per signal, lane-minor (lane = stimulus instance), each
+// row stored at its width class -- 1, 2, 4 or 8 bytes per lane for widths up to
+// 8, 16, 32, 64 -- since every value is kept masked to its width.  Rows are
+// addressed by 32-bit references (class, per-lane byte offset); values are
+// widened to 64 bits only in registers.  One "item" is one operation evaluated
+// for V consecutive lanes; the lanes of an operation are spread over
+// consecutive threads, so a warp reads one contiguous segment of each operand
+// row (coalesced) and the operation's descriptor is a broadcast read.
+// Operations of a layer are stored grouped by (opcode, width), so neighbouring
+// threads take the same switch arm.  No tensor cores: this is integer gather
+// work bound by memory.
 #pragma once
 #include <cstdint>
 
@@ -15,15 +19,18 @@
 namespace rteaal {
 
 struct DDesign {
-  const uint4* meta;          // [n_lowered] {a, b, c, ctl}
-  const uint32_t* ext;        // operand slots of ops with > 3 operands
+  const uint4* meta;          // [n_lowered] {a, b, c, ctl}, operands as row references
+  const uint32_t* dst;        // [n_lowered] row reference of each op's output
+  const uint32_t* ext;        // operand row references of ops with > 3 operands
   const uint32_t* layer_off;  // [n_layers + 1]
-  const uint32_t* reg_src;    // [n_regs]
+  const uint32_t* reg_src;    // [n_regs] row reference of D
+  const uint32_t* reg_ref;    // [n_regs] row reference of Q
   const uint32_t* reg_w;      // [n_regs]
   const uint64_t* reg_init;   // [n_regs]
   const uint4* wport;         // [n_wports] {mem, en, addr, data} grouped by memory
   const uint4* mem_info;      // [n_mems + 1] {word offset, words-1, width, first port}
   const uint32_t* in_w;       // [n_inputs]
+  const uint32_t* in_ref;     // [n_inputs]
   uint32_t n_layers, n_regs, n_inputs, n_mems, op_base, reg_base;
 };
 
@@ -44,7 +51,7 @@ __host__ __device__ inline uint32_t fdiv(const FastDiv& f, uint32_t n) {
 }
 
 struct DSim {
-  uint64_t* state;
+  uint8_t* state;               // compact rows, see above
   uint64_t* mem;
   uint64_t* xs;                 // [n_inputs][n_pad] xorshift64 states
   uint32_t n_pad, n_user;
@@ -54,7 +61,7 @@ struct DSim {
   int stim_mode;
   const uint64_t* stim;         // [cycles][n_inputs][n_user]
   int reset;
-  const uint32_t* probe_slot;   // EVERY-mode probes
+  const uint32_t* probe_slot;   // EVERY-mode probes (row references)
   uint32_t n_probe;
   uint64_t* probe_out;          // [cycles][n_probe][n_user]
   uint32_t* err;
@@ -144,21 +151,50 @@ __device__ __forceinline__ uint64_t alu(uint32_t ctl, uint64_t a, uint64_t b, ui
   return r & wmask((ctl >> 8) & 255u);
 }
 
+// Address of element (row, lane) of the compact state.
+__device__ __forceinline__ const uint8_t* elem(const uint8_t* st, uint32_t ref, size_t np,
+                                               uint32_t lane) {
+  // one 32 x 32 -> 64-bit multiply-add; lane << class fits 32 bits
+  return st + ((uint64_t)(ref & REF_OFF_MASK) * (uint32_t)np + (uint32_t)(lane << (ref >> 30)));
+}
+
+// one element, zero-extended
+__device__ __forceinline__ uint64_t ld1(const uint8_t* st, uint32_t ref, size_t np, uint32_t lane) {
+  const uint8_t* p = elem(st, ref, np, lane);
+  switch (ref >> 30) {
+    case 0: return *p;
+    case 1: return *reinterpret_cast<const uint16_t*>(p);
+    case 2: return *reinterpret_cast<const uint32_t*>(p);
+    default: return *reinterpret_cast<const uint64_t*>(p);
+  }
+}
+
+// one element (the value already fits its row's class)
+__device__ __forceinline__ void st1(uint8_t* st, uint32_t ref, size_t np, uint32_t lane, uint64_t v) {
+  uint8_t* p = const_cast<uint8_t*>(elem(st, ref, np, lane));
+  switch (ref >> 30) {
+    case 0: *p = (uint8_t)v; break;
+    case 1: *reinterpret_cast<uint16_t*>(p) = (uint16_t)v; break;
+    case 2: *reinterpret_cast<uint32_t*>(p) = (uint32_t)v; break;
+    default: *reinterpret_cast<uint64_t*>(p) = v; break;
+  }
+}
+
 // Ops with more than three operands (variadic folds, long mux chains): one lane.
 __device__ __noinline__ uint64_t eval_ext(const DDesign& d, const DSim& s, uint4 m, uint32_t lane) {
   const uint32_t op = m.w & 31u, n = m.y;
   const uint32_t* a = d.ext + m.x;
-  const uint64_t* st = s.state + lane;
+  const uint8_t* st = s.state;
   const size_t np = s.n_pad;
   uint64_t r;
   if (op == OP_MUXCHAIN) {
-    r = st[(size_t)a[n - 1] * np];
+    r = ld1(st, a[n - 1], np, lane);
     for (uint32_t i = 0; i + 1 < n; i += 2)
-      if (st[(size_t)a[i] * np] & 1ull) { r = st[(size_t)a[i + 1] * np]; break; }
+      if (ld1(st, a[i], np, lane) & 1ull) { r = ld1(st, a[i + 1], np, lane); break; }
   } else {
-    r = st[(size_t)a[0] * np];
+    r = ld1(st, a[0], np, lane);
     for (uint32_t i = 1; i < n; i++) {
-      const uint64_t x = st[(size_t)a[i] * np];
+      const uint64_t x = ld1(st, a[i], np, lane);
       switch (op) {
         case OP_AND: r &= x; break;
         case OP_OR: r |= x; break;
@@ -185,16 +221,71 @@ struct Lanes {
   uint64_t x[V];
 };
 
+// V consecutive lanes of a row, zero-extended (lane is a multiple of V, so the
+// packed 2^k * V bytes are naturally aligned).
 template <int V>
-__device__ __forceinline__ Lanes<V> ldl(const uint64_t* p) {
+__device__ __forceinline__ Lanes<V> ldr(const uint8_t* st, uint32_t ref, size_t np, uint32_t lane) {
   Lanes<V> r;
   if constexpr (V == 2) {
-    const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
-    r.x[0] = t.x;
-    r.x[1] = t.y;
+    const uint8_t* p = elem(st, ref, np, lane);
+    switch (ref >> 30) {
+      case 0: {
+        const uint32_t t = *reinterpret_cast<const uint16_t*>(p);
+        r.x[0] = t & 0xFFu;
+        r.x[1] = t >> 8;
+      } break;
+      case 1: {
+        const uint32_t t = *reinterpret_cast<const uint32_t*>(p);
+        r.x[0] = t & 0xFFFFu;
+        r.x[1] = t >> 16;
+      } break;
+      case 2: {
+        const uint2 t = *reinterpret_cast<const uint2*>(p);
+        r.x[0] = t.x;
+        r.x[1] = t.y;
+      } break;
+      default: {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
+        r.x[0] = t.x;
+        r.x[1] = t.y;
+      } break;
+    }
+  } else if constexpr (V == 4) {
+    const uint8_t* p = elem(st, ref, np, lane);
+    switch (ref >> 30) {
+      case 0: {
+        const uint32_t t = *reinterpret_cast<const uint32_t*>(p);
+        r.x[0] = t & 0xFFu;
+        r.x[1] = (t >> 8) & 0xFFu;
+        r.x[2] = (t >> 16) & 0xFFu;
+        r.x[3] = t >> 24;
+      } break;
+      case 1: {
+        const uint2 t = *reinterpret_cast<const uint2*>(p);
+        r.x[0] = t.x & 0xFFFFu;
+        r.x[1] = t.x >> 16;
+        r.x[2] = t.y & 0xFFFFu;
+        r.x[3] = t.y >> 16;
+      } break;
+      case 2: {
+        const uint4 t = *reinterpret_cast<const uint4*>(p);
+        r.x[0] = t.x;
+        r.x[1] = t.y;
+        r.x[2] = t.z;
+        r.x[3] = t.w;
+      } break;
+      default: {
+        const ulonglong2 t0 = reinterpret_cast<const ulonglong2*>(p)[0];
+        const ulonglong2 t1 = reinterpret_cast<const ulonglong2*>(p)[1];
+        r.x[0] = t0.x;
+        r.x[1] = t0.y;
+        r.x[2] = t1.x;
+        r.x[3] = t1.y;
+      } break;
+    }
   } else {
 #pragma unroll
-    for (int v = 0; v < V; v++) r.x[v] = p[v];
+    for (int v = 0; v < V; v++) r.x[v] = ld1(st, ref, np, lane + v);
   }
   return r;
 }
@@ -209,34 +300,62 @@ __device__ __forceinline__ uint32_t act_mask(const DSim& s, uint32_t lane, uint3
   return m;
 }
 
-// Store the active lanes of a result (frozen instances keep their state).
+// Store the active lanes (mask bit v = lane + v) of a result into a row;
+// frozen instances keep their state.  Values already fit the row's class.
 template <int V>
-__device__ __forceinline__ void stm(uint64_t* p, const Lanes<V>& r, uint32_t m) {
+__device__ __forceinline__ void str(uint8_t* st, uint32_t ref, size_t np, uint32_t lane,
+                                    const Lanes<V>& r, uint32_t m) {
   if constexpr (V == 2) {
     if (m == 3u) {
-      *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(r.x[0], r.x[1]);
-    } else {
-      if (m & 1u) p[0] = r.x[0];
-      if (m & 2u) p[1] = r.x[1];
+      uint8_t* p = const_cast<uint8_t*>(elem(st, ref, np, lane));
+      switch (ref >> 30) {
+        case 0: *reinterpret_cast<uint16_t*>(p) = (uint16_t)(r.x[0] | (r.x[1] << 8)); break;
+        case 1: *reinterpret_cast<uint32_t*>(p) = (uint32_t)(r.x[0] | (r.x[1] << 16)); break;
+        case 2: *reinterpret_cast<uint2*>(p) = make_uint2((uint32_t)r.x[0], (uint32_t)r.x[1]); break;
+        default: *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(r.x[0], r.x[1]); break;
+      }
+      return;
     }
-  } else {
-#pragma unroll
-    for (int v = 0; v < V; v++)
-      if (m & (1u << v)) p[v] = r.x[v];
+  } else if constexpr (V == 4) {
+    if (m == 15u) {
+      uint8_t* p = const_cast<uint8_t*>(elem(st, ref, np, lane));
+      switch (ref >> 30) {
+        case 0:
+          *reinterpret_cast<uint32_t*>(p) =
+              (uint32_t)(r.x[0] | (r.x[1] << 8) | (r.x[2] << 16) | (r.x[3] << 24));
+          break;
+        case 1:
+          *reinterpret_cast<uint2*>(p) = make_uint2((uint32_t)(r.x[0] | (r.x[1] << 16)),
+                                                    (uint32_t)(r.x[2] | (r.x[3] << 16)));
+          break;
+        case 2:
+          *reinterpret_cast<uint4*>(p) = make_uint4((uint32_t)r.x[0], (uint32_t)r.x[1],
+                                                    (uint32_t)r.x[2], (uint32_t)r.x[3]);
+          break;
+        default:
+          reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(r.x[0], r.x[1]);
+          reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(r.x[2], r.x[3]);
+          break;
+      }
+      return;
+    }
   }
+#pragma unroll
+  for (int v = 0; v < V; v++)
+    if (m & (1u << v)) st1(st, ref, np, lane + v, r.x[v]);
 }
 
 // Operand gather of one op for V lanes (OI = LI . OIM for this s coordinate).
 template <int V>
-__device__ __forceinline__ void gather(const uint64_t* lanes, size_t np, const uint4& m, Lanes<V>& a,
-                                       Lanes<V>& b, Lanes<V>& c) {
+__device__ __forceinline__ void gather(const uint8_t* st, size_t np, uint32_t lane, const uint4& m,
+                                       Lanes<V>& a, Lanes<V>& b, Lanes<V>& c) {
 #pragma unroll
   for (int v = 0; v < V; v++) a.x[v] = b.x[v] = c.x[v] = 0;
   if (!(m.w & CTL_EXT)) {
     const uint32_t ar = (m.w >> 5) & 3u;
-    a = ldl<V>(lanes + (size_t)m.x * np);
-    if (ar >= 2) b = ldl<V>(lanes + (size_t)m.y * np);
-    if (ar >= 3) c = ldl<V>(lanes + (size_t)m.z * np);
+    a = ldr<V>(st, m.x, np, lane);
+    if (ar >= 2) b = ldr<V>(st, m.y, np, lane);
+    if (ar >= 3) c = ldr<V>(st, m.z, np, lane);
   }
 }
 
@@ -282,13 +401,12 @@ __device__ __noinline__ void eval_ops_generic(const DDesign& d, const DSim& s, u
     Lanes<V> va[U], vb[U], vc[U];
 #pragma unroll
     for (int u = 0; u < U; u++)
-      if (ok[u]) gather<V>(s.state + lane[u], np, m[u], va[u], vb[u], vc[u]);
+      if (ok[u]) gather<V>(s.state, np, lane[u], m[u], va[u], vb[u], vc[u]);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       if (!ok[u]) continue;
       const Lanes<V> res = apply<V>(d, s, m[u], va[u], vb[u], vc[u], lane[u]);
-      stm<V>(s.state + (size_t)(d.op_base + op0 + row[u]) * np + lane[u], res,
-             act_mask<V>(s, lane[u], cyc));
+      str<V>(s.state, __ldg(&d.dst[op0 + row[u]]), np, lane[u], res, act_mask<V>(s, lane[u], cyc));
     }
   }
 }
@@ -309,9 +427,8 @@ __device__ __forceinline__ void eval_ops(const DDesign& d, const DSim& s, uint32
     if (is.row0 == NO_ROW) return;
     const uint32_t am = act_mask<V>(s, is.lane, cyc);
     if (!am) return;
-    const uint64_t* lanes = s.state + is.lane;
-    uint64_t* out = s.state + (size_t)(d.op_base + op0) * np + is.lane;
     const uint4* meta = d.meta + op0;
+    const uint32_t* dst = d.dst + op0;
     for (uint32_t r0 = is.row0; r0 < n_rows; r0 += is.row_stride * U) {
       uint4 m[U];
       bool ok[U];
@@ -324,12 +441,12 @@ __device__ __forceinline__ void eval_ops(const DDesign& d, const DSim& s, uint32
       Lanes<V> va[U], vb[U], vc[U];
 #pragma unroll
       for (int u = 0; u < U; u++)
-        if (ok[u]) gather<V>(lanes, np, m[u], va[u], vb[u], vc[u]);
+        if (ok[u]) gather<V>(s.state, np, is.lane, m[u], va[u], vb[u], vc[u]);
 #pragma unroll
       for (int u = 0; u < U; u++) {
         if (!ok[u]) continue;
         const Lanes<V> res = apply<V>(d, s, m[u], va[u], vb[u], vc[u], is.lane);
-        stm<V>(out + (size_t)(r0 + u * is.row_stride) * np, res, am);
+        str<V>(s.state, __ldg(&dst[r0 + u * is.row_stride]), np, is.lane, res, am);
       }
     }
   }
@@ -372,7 +489,7 @@ __device__ __forceinline__ void stim_items(const DDesign& d, const DSim& s, cons
       } else {
         x = __ldg(&s.stim[((size_t)cyc * d.n_inputs + j) * s.n_user + user_of(s, lane)]);
       }
-      s.state[(size_t)j * np + lane] = x & mk;
+      st1(s.state, __ldg(&d.in_ref[j]), np, lane, x & mk);
     }
   });
 }
@@ -394,11 +511,11 @@ __device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, co
 #pragma unroll
         for (int t = 0; t < V; t++) v.x[t] = init;
       } else {
-        v = ldl<V>(s.state + (size_t)__ldg(&d.reg_src[r]) * np + lane);
+        v = ldr<V>(s.state, __ldg(&d.reg_src[r]), np, lane);
 #pragma unroll
         for (int t = 0; t < V; t++) v.x[t] &= mk;
       }
-      stm<V>(s.state + (size_t)(d.reg_base + r) * np + lane, v, am);
+      str<V>(s.state, __ldg(&d.reg_ref[r]), np, lane, v, am);
     } else {
       const uint32_t mi = r - d.n_regs;
       const uint4 info = __ldg(&d.mem_info[mi]);
@@ -410,9 +527,9 @@ __device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, co
         const uint32_t ln = lane + t;
         for (uint32_t p = info.w; p < p1; p++) {
           const uint4 w = __ldg(&d.wport[p]);
-          if (s.state[(size_t)w.y * np + ln] & 1ull) {
-            const uint64_t a = s.state[(size_t)w.z * np + ln] & (uint64_t)info.y;
-            s.mem[((size_t)info.x + a) * np + ln] = s.state[(size_t)w.w * np + ln] & mk;
+          if (ld1(s.state, w.y, np, ln) & 1ull) {
+            const uint64_t a = ld1(s.state, w.z, np, ln) & (uint64_t)info.y;
+            s.mem[((size_t)info.x + a) * np + ln] = ld1(s.state, w.w, np, ln) & mk;
           }
         }
       }
@@ -430,7 +547,7 @@ __device__ __forceinline__ void probe_items(const DSim& s, const ItemSpace& is, 
       const uint32_t lane = lane0 + t;
       if (!lane_active(s, lane, cyc)) continue;
       s.probe_out[((size_t)cyc * s.n_probe + p) * s.n_user + user_of(s, lane)] =
-          s.state[(size_t)slot * s.n_pad + lane];
+          ld1(s.state, slot, s.n_pad, lane);
     }
   });
 }

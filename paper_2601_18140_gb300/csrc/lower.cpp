@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <stdexcept>
 #include <unordered_map>
 
 namespace rteaal {
@@ -168,7 +169,32 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
   for (uint32_t s = 0; s < opb; s++) L.sig2slot[s] = s;
   for (uint32_t k = 0; k < nl.no; k++) L.sig2slot[opb + k] = opb + pos[k];
 
-  // 4. per-op metadata (operands as slots, ctl word)
+  // 3b. compact layout: width class of every slot, row references
+  {
+    std::vector<uint32_t> cls(L.n_slots);
+    for (uint32_t sgl = 0; sgl < opb; sgl++) cls[sgl] = width_class(sig_w[sgl]);
+    for (uint32_t i = 0; i < order.size(); i++) cls[opb + i] = width_class(ops[order[i]].width);
+    uint64_t cnt[4] = {0, 0, 0, 0};
+    for (uint32_t sl = 0; sl < L.n_slots; sl++) cnt[cls[sl]]++;
+    uint64_t base[4];
+    base[3] = 0;
+    base[2] = base[3] + 8 * cnt[3];
+    base[1] = base[2] + 4 * cnt[2];
+    base[0] = base[1] + 2 * cnt[1];
+    L.lane_bytes = base[0] + cnt[0];
+    if (L.lane_bytes > REF_OFF_MASK) throw std::runtime_error("design too large: > 1 GiB of state per instance");
+    uint64_t next[4] = {base[0], base[1], base[2], base[3]};
+    L.slot_ref.resize(L.n_slots);
+    for (uint32_t sl = 0; sl < L.n_slots; sl++) {
+      const uint32_t k = cls[sl];
+      L.slot_ref[sl] = (k << 30) | (uint32_t)next[k];
+      next[k] += 1ull << k;
+    }
+    for (int k = 0; k < 4; k++) L.class_rows[k] = (uint32_t)cnt[k];
+  }
+  auto ref_of_sig = [&](uint32_t sig) { return L.slot_ref[L.sig2slot[sig]]; };
+
+  // 4. per-op metadata (operands as row references, ctl word)
   L.meta.resize(ops.size());
   L.ext_args.clear();
   L.lowered_operands = 0;
@@ -182,10 +208,10 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
     std::vector<uint32_t> a;
     uint32_t code = o.code;
     if (o.is_copy) {
-      a.push_back(L.sig2slot[o.src_sig]);
+      a.push_back(ref_of_sig(o.src_sig));
     } else {
       const uint32_t k = o.src_sig;
-      for (uint32_t j = nl.argoff[k]; j < nl.argoff[k + 1]; j++) a.push_back(L.sig2slot[nl.args[j]]);
+      for (uint32_t j = nl.argoff[k]; j < nl.argoff[k + 1]; j++) a.push_back(ref_of_sig(nl.args[j]));
       if (code == OP_MUXCHAIN && a.size() == 3) code = OP_MUX;  // one pair + default == mux
     }
     L.lowered_operands += a.size();
@@ -211,6 +237,8 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
       L.group_off.push_back(i);
   }
   L.group_off.push_back((uint32_t)order.size());
+  L.dst_ref.resize(order.size());
+  for (uint32_t i = 0; i < order.size(); i++) L.dst_ref[i] = L.slot_ref[opb + i];
   // layer_off[l] holds the end of level l (levels 1..n); shift to begin offsets
   std::vector<uint32_t> ends(L.layer_off.begin() + 1, L.layer_off.end());
   L.layer_off[0] = 0;
@@ -224,11 +252,17 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
   L.reg_width.resize(nl.nr);
   L.reg_init.resize(nl.nr);
   for (uint32_t r = 0; r < nl.nr; r++) {
-    L.reg_src[r] = opb + pos[(uint32_t)reg_lop[r]];
+    L.reg_src[r] = L.slot_ref[opb + pos[(uint32_t)reg_lop[r]]];
     L.reg_width[r] = nl.reg_w[r];
     L.reg_init[r] = nl.reg_init[r];
   }
   L.in_width.assign(nl.in_w.begin(), nl.in_w.end());
+  L.reg_ref.resize(nl.nr);
+  for (uint32_t r = 0; r < nl.nr; r++) L.reg_ref[r] = L.slot_ref[L.reg_base + r];
+  L.in_ref.resize(nl.ni);
+  for (uint32_t j = 0; j < nl.ni; j++) L.in_ref[j] = L.slot_ref[L.input_base + j];
+  L.const_ref.resize(nl.nc);
+  for (uint32_t c = 0; c < nl.nc; c++) L.const_ref[c] = L.slot_ref[L.const_base + c];
   L.const_value.resize(nl.nc);
   for (uint32_t c = 0; c < nl.nc; c++) {
     const uint32_t w = nl.const_w[c];
@@ -243,7 +277,7 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
   for (uint32_t i = 0; i < nl.nw; i++) {
     const uint32_t q = pidx[i];
     L.wport[4ull * i + 0] = nl.wport[4ull * q];
-    for (int t = 0; t < 3; t++) L.wport[4ull * i + 1 + t] = opb + pos[(uint32_t)wp_lop[3ull * q + t]];
+    for (int t = 0; t < 3; t++) L.wport[4ull * i + 1 + t] = L.slot_ref[opb + pos[(uint32_t)wp_lop[3ull * q + t]]];
   }
   L.mem_info.assign(4ull * (nl.nm + 1), 0);
   uint64_t off = 0;

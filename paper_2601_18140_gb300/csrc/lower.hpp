@@ -23,6 +23,12 @@ enum Opcode : uint8_t {
 // extended-operand flag << 7 | width << 8 | p0 << 16 | p1 << 24.
 constexpr uint32_t CTL_EXT = 1u << 7;
 
+// Row reference: width class k (bytes per lane = 1 << k) in bits 30..31, the
+// row's per-lane byte offset in bits 0..29.  Element (row, lane) of a state
+// with n lanes lives at byte  offset * n + (lane << k).
+constexpr uint32_t REF_OFF_MASK = (1u << 30) - 1u;
+inline uint32_t width_class(uint32_t w) { return w <= 8 ? 0u : w <= 16 ? 1u : w <= 32 ? 2u : 3u; }
+
 struct Netlist {
   uint32_t ni = 0, nr = 0, nc = 0, no = 0, nm = 0, nw = 0, na = 0;
   std::vector<uint64_t> reg_init, const_value;
@@ -41,19 +47,29 @@ struct OpMeta {  // 16 bytes, one per lowered op (device uint4)
 
 struct Lowered {
   uint32_t n_slots = 0;
+  // compact layout: rows of each width class in their own region (u64, u32,
+  // u16, u8 in that order); inside a region, pool rows in signal order, then
+  // op rows in slot order
+  std::vector<uint32_t> slot_ref;        // [n_slots] row reference of every slot
+  std::vector<uint32_t> dst_ref;         // [n_lowered] row reference of each op's output
+  std::vector<uint32_t> reg_ref;         // [n_regs] row reference of Q
+  std::vector<uint32_t> in_ref;          // [n_inputs]
+  std::vector<uint32_t> const_ref;       // [n_consts]
+  uint64_t lane_bytes = 0;               // bytes of state per lane
+  uint32_t class_rows[4] = {0, 0, 0, 0};
   uint32_t input_base = 0, reg_base = 0, const_base = 0, op_base = 0;  // slot bases
   std::vector<uint32_t> sig2slot;        // [n_signals]
   std::vector<OpMeta> meta;              // [n_lowered] in slot order
-  std::vector<uint32_t> ext_args;        // operand slots of ops with > 3 operands
+  std::vector<uint32_t> ext_args;        // operand row references of ops with > 3 operands
   std::vector<uint32_t> layer_off;       // [n_layers + 1] into meta
   std::vector<uint32_t> group_off;       // [n_groups + 1] into meta ((layer, opcode, width) runs)
-  std::vector<uint32_t> reg_src;         // [n_regs] slot of D (always an op slot)
+  std::vector<uint32_t> reg_src;         // [n_regs] row reference of D (always an op row)
   std::vector<uint32_t> reg_width;       // [n_regs]
   std::vector<uint64_t> reg_init;        // [n_regs]
   std::vector<uint32_t> in_width;        // [n_inputs]
   std::vector<uint64_t> const_value;     // [n_consts] masked
   std::vector<uint32_t> mem_info;        // [n_mems][4] = word offset, words-1, width, first port
-  std::vector<uint32_t> wport;           // [n_wports][4] = mem, en slot, addr slot, data slot,
+  std::vector<uint32_t> wport;           // [n_wports][4] = mem, en, addr, data (row references),
                                          //   sorted by memory, port order kept
   uint64_t mem_words_total = 0;
   uint64_t op_operands = 0;              // sum of operand counts over netlist ops

@@ -180,7 +180,31 @@ __global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs
 #undef RT_SPACE
 }
 
-// state[slot][lane] <-> host [n][n_inst] through a [n][n_inst] device buffer
+// compact state rows (by reference) <-> a [n][n_inst] uint64 device buffer
+__global__ void k_gather_ref(const uint8_t* st, uint32_t n_pad, const uint32_t* refs, uint32_t n_rows,
+                             const uint32_t* lane_of_user, uint32_t inst0, uint32_t n_inst, uint64_t* out) {
+  const size_t total = (size_t)n_rows * n_inst;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)(i / n_inst), k = (uint32_t)(i % n_inst);
+    const uint32_t lane = lane_of_user ? lane_of_user[inst0 + k] : inst0 + k;
+    out[i] = ld1(st, refs[r], n_pad, lane);
+  }
+}
+
+__global__ void k_scatter_ref(uint8_t* st, uint32_t n_pad, const uint32_t* refs, uint32_t n_rows,
+                              const uint32_t* lane_of_user, uint32_t inst0, uint32_t n_inst,
+                              const uint64_t* in, const uint64_t* row_mask) {
+  const size_t total = (size_t)n_rows * n_inst;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)(i / n_inst), k = (uint32_t)(i % n_inst);
+    const uint32_t lane = lane_of_user ? lane_of_user[inst0 + k] : inst0 + k;
+    st1(st, refs[r], n_pad, lane, in[i] & row_mask[r]);
+  }
+}
+
+// uint64 [row][lane] arrays (memories, stimulus states) <-> a [n][n_inst] device buffer
 __global__ void k_gather(const uint64_t* src, uint32_t n_pad, const uint32_t* rows, uint32_t n_rows,
                          const uint32_t* lane_of_user, uint32_t inst0, uint32_t n_inst,
                          uint64_t* out) {
@@ -299,7 +323,7 @@ struct rteaal_sim {
   int kernel = RTEAAL_KERNEL_AUTO;
   uint32_t tile_lanes = 0, threads = 0, ctas_per_sm = 0, unroll = 0, grid = 0;
   int V = 2;
-  uint64_t* state = nullptr;
+  uint8_t* state = nullptr;          // compact rows: n_pad * lane_bytes bytes
   uint64_t* mem = nullptr;
   uint64_t* xs = nullptr;
   uint32_t* budget = nullptr;        // [n_pad]
@@ -444,6 +468,8 @@ struct Variant {
 };
 #define RT_VARIANT(V, U, T, B) {V, U, T, B, (const void*)k_tile<V, U, T, B>, (const void*)k_grid<V, U, T, B>}
 const Variant kVariants[] = {
+    RT_VARIANT(4, 1, 256, 4), RT_VARIANT(4, 1, 512, 2), RT_VARIANT(4, 1, 1024, 1),
+    RT_VARIANT(4, 2, 512, 1),
     RT_VARIANT(2, 1, 256, 8), RT_VARIANT(2, 1, 512, 4), RT_VARIANT(2, 1, 1024, 2),
     RT_VARIANT(2, 2, 512, 2), RT_VARIANT(2, 4, 512, 1),
     RT_VARIANT(1, 1, 512, 4), RT_VARIANT(1, 2, 512, 2), RT_VARIANT(1, 4, 512, 1),
@@ -507,6 +533,9 @@ RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaa
       DDesign& dd = d->dd;
       static_assert(sizeof(OpMeta) == sizeof(uint4), "descriptor is 16 bytes");
       dd.meta = reinterpret_cast<const uint4*>(d->upload(L.meta));
+      dd.dst = d->upload(L.dst_ref);
+      dd.reg_ref = d->upload(L.reg_ref);
+      dd.in_ref = d->upload(L.in_ref);
       dd.ext = d->upload(L.ext_args);
       dd.layer_off = d->upload(L.layer_off);
       dd.reg_src = d->upload(L.reg_src);
@@ -548,6 +577,7 @@ RT_EXPORT int rteaal_design_info(const rteaal_design* d, rteaal_design_stats* o)
     o->op_operands = L.op_operands;
     o->mem_words_total = L.mem_words_total;
     o->metadata_bytes = d->metadata_bytes;
+    o->state_bytes_per_lane = L.lane_bytes;
   });
 }
 
@@ -568,14 +598,15 @@ RT_EXPORT uint64_t rteaal_sim_footprint(const rteaal_design* d, uint32_t n) {
   if (!d || n == 0) return 0;
   const uint64_t np = pad_lanes(n);
   const Lowered& L = d->L;
-  return np * 8ull * (L.n_slots + L.mem_words_total + L.in_width.size()) + np * 4ull * 4 + 4096;
+  return np * (L.lane_bytes + 8ull * (L.mem_words_total + L.in_width.size())) + np * 4ull * 5 +
+         (uint64_t)n * 4 + 4096;
 }
 
 namespace {
 
 // Validate and apply a launch configuration (never changes results).
 void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
-               uint32_t unroll) {
+               uint32_t unroll, uint32_t lanes_per_thread) {
   if (kernel == RTEAAL_KERNEL_AUTO) kernel = s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
   require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_LAYER_GRAPH, "unknown kernel");
   if (!unroll) unroll = 2;
@@ -583,14 +614,27 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
   if (!threads) threads = 512;
   require(threads % 32 == 0 && threads >= 32 && threads <= 1024, "threads must be a multiple of 32 in [32, 1024]");
   if (!tile_lanes) tile_lanes = std::min<uint32_t>(16, s->n_pad);
-  int V = (s->n_pad % 2 == 0) ? 2 : 1;
-  uint32_t grid = 0;
+  require(lanes_per_thread == 0 || lanes_per_thread == 1 || lanes_per_thread == 2 || lanes_per_thread == 4,
+          "lanes_per_thread must be 1, 2 or 4");
+  uint32_t span = s->n_pad;  // lanes that one V-lane chunk must divide
   if (kernel == RTEAAL_KERNEL_TILE) {
     require(tile_lanes >= 1 && tile_lanes <= 64 && (tile_lanes & (tile_lanes - 1)) == 0,
             "tile_lanes must be a power of two <= 64");
     require(s->n_pad % tile_lanes == 0, "tile_lanes must divide the padded lane count");
-    if (tile_lanes % 2) V = 1;
+    span = tile_lanes;
   }
+  int V = (int)lanes_per_thread;
+  if (!V) {  // widest V that divides the span and (persistent forms) has a compiled variant
+    const bool persistent = kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID;
+    for (int c : {4, 2, 1})
+      if (span % (uint32_t)c == 0 && (!persistent || find_variant(c, unroll ? unroll : 2, threads ? threads : 512))) {
+        V = c;
+        break;
+      }
+    if (!V) V = 1;
+  }
+  require(span % (uint32_t)V == 0, "lanes_per_thread must divide the lanes of a tile / the padded lane count");
+  uint32_t grid = 0;
   if (kernel == RTEAAL_KERNEL_LAYER || kernel == RTEAAL_KERNEL_LAYER_GRAPH) threads = 256;
   if (kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID) {
     const Variant* v = find_variant(V, unroll, threads);
@@ -616,6 +660,8 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
   s->grid = grid;
 }
 
+uint32_t opt_lanes(const rteaal_sim_opts* o) { return o ? o->lanes_per_thread : 0; }
+
 }  // namespace
 
 RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, const rteaal_sim_opts* opts,
@@ -635,20 +681,20 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       s->n_user = n_instances;
       s->n_pad = pad_lanes(n_instances);
       configure(s, opts ? opts->kernel : 0, opts ? opts->tile_lanes : 0, opts ? opts->threads : 0,
-                opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0);
+                opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0, opt_lanes(opts));
       if (const char* e = getenv("RTEAAL_TEST_WITHHOLD_ARRIVAL")) s->barrier_extra = (uint32_t)atoi(e);
       if (const char* e = getenv("RTEAAL_BARRIER_TIMEOUT_NS")) s->barrier_timeout_ns = strtoull(e, nullptr, 10);
 
       const Lowered& L = d->L;
       const size_t np = s->n_pad;
-      s->state = static_cast<uint64_t*>(s->get(np * 8 * L.n_slots));
+      s->state = static_cast<uint8_t*>(s->get(std::max<size_t>(np * L.lane_bytes, 16)));
       s->mem = static_cast<uint64_t*>(s->get(std::max<size_t>(np * 8 * L.mem_words_total, 16)));
       s->xs = static_cast<uint64_t*>(s->get(std::max<size_t>(np * 8 * L.in_width.size(), 16)));
       s->budget = static_cast<uint32_t*>(s->get(np * 4));
       s->tile_order = static_cast<uint32_t*>(s->get(np * 4));   // room for any tile size
       s->tile_cycles = static_cast<uint32_t*>(s->get(np * 4));
       s->scratch = static_cast<uint32_t*>(s->get(256));
-      CK(cudaMemset(s->state, 0, np * 8 * L.n_slots));
+      CK(cudaMemset(s->state, 0, std::max<size_t>(np * L.lane_bytes, 16)));
       CK(cudaMemset(s->mem, 0, std::max<size_t>(np * 8 * L.mem_words_total, 16)));
       CK(cudaMemset(s->xs, 0, std::max<size_t>(np * 8 * L.in_width.size(), 16)));
       CK(cudaMemset(s->scratch, 0, 256));
@@ -673,12 +719,27 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
         CK(cudaMemcpy(s->user_of_lane, s->h_user_of_lane.data(), np * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(s->lane_of_user, s->h_lane_of_user.data(), (size_t)n_instances * 4, cudaMemcpyHostToDevice));
       }
-      // constants
+      // constants: every lane (padded ones too) holds the value
       if (!L.const_value.empty()) {
-        std::vector<uint64_t> h(L.const_value.size() * np, 0);
-        for (size_t c = 0; c < L.const_value.size(); c++)
-          for (size_t l = 0; l < n_instances; l++) h[c * np + l] = L.const_value[c];
-        CK(cudaMemcpy(s->state + (size_t)L.const_base * np, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+        const size_t nc = L.const_value.size();
+        std::vector<uint64_t> h(nc * np), ones(nc, ~0ull);
+        for (size_t c = 0; c < nc; c++)
+          for (size_t l = 0; l < np; l++) h[c * np + l] = L.const_value[c];
+        const size_t bytes = h.size() * 8 + nc * 12 + 64;
+        char* tmp = static_cast<char*>(s->alloc.alloc(bytes));
+        uint64_t* dv = reinterpret_cast<uint64_t*>(tmp);
+        uint64_t* dm = dv + h.size();
+        uint32_t* dr = reinterpret_cast<uint32_t*>(dm + nc);
+        cudaError_t e = cudaMemcpy(dv, h.data(), h.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dm, ones.data(), nc * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dr, L.const_ref.data(), nc * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+          k_scatter_ref<<<(unsigned)std::min<size_t>((h.size() + 255) / 256, 4096), 256>>>(
+              s->state, s->n_pad, dr, (uint32_t)nc, nullptr, 0, s->n_pad, dv, dm);
+          e = cudaDeviceSynchronize();
+        }
+        s->alloc.free(tmp, bytes);
+        CK(e);
       }
       if (opts && opts->xorshift_seed && !L.in_width.empty()) {
         std::vector<uint64_t> h(L.in_width.size() * np, 0);
@@ -706,7 +767,7 @@ RT_EXPORT int rteaal_sim_configure(rteaal_sim* s, const rteaal_sim_opts* o) {
   return guarded([&] {
     require(s && o, "rteaal_sim_configure: null argument");
     CK(cudaSetDevice(s->design->device));
-    configure(s, o->kernel, o->tile_lanes, o->threads, o->ctas_per_sm, o->unroll);
+    configure(s, o->kernel, o->tile_lanes, o->threads, o->ctas_per_sm, o->unroll, o->lanes_per_thread);
   });
 }
 
@@ -722,6 +783,7 @@ RT_EXPORT int rteaal_sim_info(const rteaal_sim* s, rteaal_sim_stats* o) {
     o->ctas_per_sm = s->ctas_per_sm;
     o->unroll = s->unroll;
     o->grid = s->grid;
+    o->lanes_per_thread = (uint32_t)s->V;
   });
 }
 
@@ -752,7 +814,7 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
                                    : ((1u << RTEAAL_KERNEL_LAYER) | (1u << RTEAAL_KERNEL_GRID));
     const Lowered& L = s->design->L;
     const size_t np = s->n_pad;
-    const size_t b_state = np * 8 * L.n_slots, b_mem = np * 8 * L.mem_words_total,
+    const size_t b_state = np * L.lane_bytes, b_mem = np * 8 * L.mem_words_total,
                  b_xs = np * 8 * L.in_width.size();
     // device snapshot of everything a trial can change
     char* snap = static_cast<char*>(s->alloc.alloc(b_state + b_mem + b_xs + 256));
@@ -764,34 +826,38 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     if (b_mem) CK(cudaMemcpyAsync(snap + b_state, s->mem, b_mem, cudaMemcpyDeviceToDevice, st));
     if (b_xs) CK(cudaMemcpyAsync(snap + b_state + b_mem, s->xs, b_xs, cudaMemcpyDeviceToDevice, st));
 
-    struct Cand { int kernel; uint32_t T, threads, U; };
+    struct Cand { int kernel; uint32_t T, threads, U, V; };
     std::vector<Cand> cands;
     if (kernel_mask & (1u << RTEAAL_KERNEL_TILE))
       for (uint32_t T : {4u, 8u, 16u, 32u, 64u})
         if (T <= np && np % T == 0)
-          for (uint32_t th : {256u, 512u, 1024u})
-            for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_TILE, T, th, U});
+          for (uint32_t V : {2u, 4u})
+            for (uint32_t th : {256u, 512u, 1024u})
+              for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_TILE, T, th, U, V});
     if (kernel_mask & (1u << RTEAAL_KERNEL_GRID))
-      for (uint32_t th : {256u, 512u, 1024u})
-        for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_GRID, 0, th, U});
+      for (uint32_t V : {2u, 4u})
+        for (uint32_t th : {256u, 512u, 1024u})
+          for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_GRID, 0, th, U, V});
     if (kernel_mask & (1u << RTEAAL_KERNEL_LAYER))
-      for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER, 0, 256, U});
+      for (uint32_t V : {2u, 4u})
+        for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER, 0, 256, U, V});
     if (kernel_mask & (1u << RTEAAL_KERNEL_LAYER_GRAPH))
-      for (uint32_t U : {2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER_GRAPH, 0, 256, U});
+      for (uint32_t U : {2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER_GRAPH, 0, 256, U, 0});
 
-    const int saved[5] = {s->kernel, (int)s->tile_lanes, (int)s->threads, (int)s->ctas_per_sm, (int)s->unroll};
+    const int saved[6] = {s->kernel, (int)s->tile_lanes, (int)s->threads, (int)s->ctas_per_sm, (int)s->unroll,
+                          s->V};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     rteaal_cycles cyc{cycles_per_trial, nullptr};
     rteaal_stimulus stim{L.in_width.empty() ? RTEAAL_STIM_HOLD : RTEAAL_STIM_XORSHIFT, nullptr, 0};
     float best = 1e30f;
-    Cand best_c{saved[0], (uint32_t)saved[1], (uint32_t)saved[2], (uint32_t)saved[4]};
+    Cand best_c{saved[0], (uint32_t)saved[1], (uint32_t)saved[2], (uint32_t)saved[4], (uint32_t)saved[5]};
     uint32_t best_ctas = (uint32_t)saved[3];
     uint32_t nt = 0;
     for (const Cand& c : cands) {
       try {
-        configure(s, c.kernel, c.T, c.threads, 0, c.U);
+        configure(s, c.kernel, c.T, c.threads, 0, c.U, c.V);
       } catch (const Error&) {
         continue;  // not compiled / not resident
       }
@@ -804,7 +870,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, e0, e1));
       if (trials && nt < max_trials)
-        trials[nt] = rteaal_tune_trial{s->kernel, s->tile_lanes, s->threads, s->ctas_per_sm, s->unroll, s->grid, ms};
+        trials[nt] = rteaal_tune_trial{s->kernel, s->tile_lanes, s->threads, s->ctas_per_sm, s->unroll, s->grid,
+                                       (uint32_t)s->V, ms};
       nt++;
       if (ms < best) {
         best = ms;
@@ -815,7 +882,7 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (n_trials) *n_trials = nt;
-    configure(s, best_c.kernel, best_c.T, best_c.threads, best_ctas, best_c.U);
+    configure(s, best_c.kernel, best_c.T, best_c.threads, best_ctas, best_c.U, best_c.V);
     CK(cudaMemcpyAsync(s->state, snap, b_state, cudaMemcpyDeviceToDevice, st));
     if (b_mem) CK(cudaMemcpyAsync(s->mem, snap + b_state, b_mem, cudaMemcpyDeviceToDevice, st));
     if (b_xs) CK(cudaMemcpyAsync(s->xs, snap + b_state + b_mem, b_xs, cudaMemcpyDeviceToDevice, st));
@@ -885,7 +952,7 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       std::vector<uint32_t> slots(probes->n);
       for (uint32_t p = 0; p < probes->n; p++) {
         require(probes->signals[p] < D->nl.n_signals(), "rteaal_step: probe signal out of range");
-        slots[p] = L.sig2slot[probes->signals[p]];
+        slots[p] = L.slot_ref[L.sig2slot[probes->signals[p]]];
       }
       ensure_probe_slots(s, slots.size());
       CK(cudaMemcpyAsync(s->probe_slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice, st));
@@ -900,7 +967,8 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
     const uint32_t U = s->unroll;
     if (s->kernel == RTEAAL_KERNEL_LAYER) {
       for (uint64_t c = 0; c < max_cyc; c++) {
-        if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
+        if (s->V == 4) launch_layer_cycle<4>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
+        else if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
         else launch_layer_cycle<1>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
       }
       CK(cudaGetLastError());
@@ -913,7 +981,8 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       cudaGraphExec_t ge = nullptr;
       try {
         CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
+        if (s->V == 4) launch_layer_cycle<4>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
+        else if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
         else launch_layer_cycle<1>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
         k_tick<<<1, 1, 0, cap>>>(cyc_dev);
         CK(cudaStreamEndCapture(cap, &g));
@@ -981,8 +1050,8 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
     if (probing && probe_mode == RTEAAL_PROBE_LAST) {
       const size_t total = (size_t)probes->n * s->n_user;
       const uint32_t blocks = (uint32_t)std::min<size_t>((total + 255) / 256, 4096);
-      k_gather<<<blocks, 256, 0, st>>>(s->state, s->n_pad, s->probe_slots, probes->n, s->lane_of_user, 0,
-                                       s->n_user, probe_dev);
+      k_gather_ref<<<blocks, 256, 0, st>>>(s->state, s->n_pad, s->probe_slots, probes->n, s->lane_of_user,
+                                           0, s->n_user, probe_dev);
       CK(cudaGetLastError());
     }
     if (probe_host) {
@@ -1015,7 +1084,7 @@ void transfer(rteaal_sim* s, Region region, const uint32_t* signals, uint32_t n,
   const Lowered& L = s->design->L;
   std::vector<uint32_t> rows;
   std::vector<uint64_t> masks;
-  uint64_t* base = s->state;
+  uint64_t* base = nullptr;
   uint32_t n_rows = n;
   if (region == Region::STATE) {
     require(signals || n == 0, "null signal list");
@@ -1024,7 +1093,7 @@ void transfer(rteaal_sim* s, Region region, const uint32_t* signals, uint32_t n,
     const uint32_t nsig = s->design->nl.n_signals();
     for (uint32_t i = 0; i < n; i++) {
       require(signals[i] < nsig, "signal id out of range");
-      rows[i] = L.sig2slot[signals[i]];
+      rows[i] = L.slot_ref[L.sig2slot[signals[i]]];
       // width of the signal (writes are masked like every stored value)
       const Netlist& nl = s->design->nl;
       uint32_t sig = signals[i], w;
@@ -1052,14 +1121,22 @@ void transfer(rteaal_sim* s, Region region, const uint32_t* signals, uint32_t n,
     if (drows) CK(cudaMemcpyAsync(drows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, st));
     if (dmask) CK(cudaMemcpyAsync(dmask, masks.data(), masks.size() * 8, cudaMemcpyHostToDevice, st));
     const uint32_t blocks = (uint32_t)std::min<size_t>((total + 255) / 256, 8192);
+    const bool compact = region == Region::STATE;
     if (out) {
-      k_gather<<<blocks, 256, 0, st>>>(base, s->n_pad, drows, n_rows, s->lane_of_user, inst0, n_inst, buf);
+      if (compact)
+        k_gather_ref<<<blocks, 256, 0, st>>>(s->state, s->n_pad, drows, n_rows, s->lane_of_user, inst0, n_inst, buf);
+      else
+        k_gather<<<blocks, 256, 0, st>>>(base, s->n_pad, drows, n_rows, s->lane_of_user, inst0, n_inst, buf);
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(out, buf, total * 8, cudaMemcpyDeviceToHost, st));
     } else {
       CK(cudaMemcpyAsync(buf, in, total * 8, cudaMemcpyHostToDevice, st));
-      k_scatter<<<blocks, 256, 0, st>>>(base, s->n_pad, drows, n_rows, s->lane_of_user, inst0, n_inst, buf,
-                                        region == Region::STATE ? dmask : nullptr);
+      if (compact)
+        k_scatter_ref<<<blocks, 256, 0, st>>>(s->state, s->n_pad, drows, n_rows, s->lane_of_user, inst0, n_inst,
+                                              buf, dmask);
+      else
+        k_scatter<<<blocks, 256, 0, st>>>(base, s->n_pad, drows, n_rows, s->lane_of_user, inst0, n_inst, buf,
+                                          nullptr);
       CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(st));
@@ -1130,7 +1207,7 @@ uint32_t* static_scratch(int dev) {
 
 }  // namespace
 
-RT_EXPORT int rteaal_step_static(const rteaal_design* d, uint64_t* state, uint64_t* mem, uint64_t* xs,
+RT_EXPORT int rteaal_step_static(const rteaal_design* d, void* state, uint64_t* mem, uint64_t* xs,
                                  uint32_t n_lanes, const uint32_t* cycles, uint32_t uniform_cycles,
                                  int stim_mode, uint32_t flags, void* stream) {
   return guarded([&] {
@@ -1169,7 +1246,7 @@ RT_EXPORT int rteaal_step_static(const rteaal_design* d, uint64_t* state, uint64
     // the barrier and error words must start at zero; budgets are rewritten
     CK(cudaMemsetAsync(scratch, 0, 64 * sizeof(uint32_t), st));
     DSim ds{};
-    ds.state = state;
+    ds.state = static_cast<uint8_t*>(state);
     ds.mem = mem;
     ds.xs = xs;
     ds.n_pad = n_lanes;

@@ -180,3 +180,20 @@ def test_batch_invariance():
         one.close()
     big.close()
     d.close()
+
+
+@pytest.mark.parametrize("kernel", ["layer", "tile", "grid"])
+@pytest.mark.parametrize("lanes_per_thread", [1, 2, 4])
+def test_lanes_per_thread(kernel, lanes_per_thread):
+    """Every lanes-per-thread width (packed loads of 1, 2 or 4 lanes per row class)."""
+    nl = small_design(31, n_mems=2)
+    n = 96
+    rng = np.random.default_rng(31)
+    budgets = rng.integers(0, 25, n).astype(np.uint32)
+    p = Pair(nl, n, kernel=kernel, seed=31, lanes_per_thread=lanes_per_thread,
+             tile_lanes=32 if kernel == "tile" else 0)
+    p.step(1, reset=True)
+    p.step(20)
+    p.step(budgets)
+    p.compare()
+    p.close()

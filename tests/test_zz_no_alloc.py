@@ -32,6 +32,37 @@ def slot_of_signal(nl: synth.Netlist) -> np.ndarray:
     return slot
 
 
+def compact_rows(nl: synth.Netlist):
+    """Width class and per-lane byte offset of every slot (the compact layout of
+    include/rteaal.h: class-3 rows first, then 2, 1, 0; pool rows before op rows)."""
+    slot = slot_of_signal(nl)
+    width = np.zeros(nl.n_signals, np.int64)
+    width[slot] = nl.signal_widths()
+    cls = np.select([width <= 8, width <= 16, width <= 32], [0, 1, 2], 3)
+    cnt = [int((cls == k).sum()) for k in range(4)]
+    nxt = {3: 0, 2: 8 * cnt[3]}
+    nxt[1] = nxt[2] + 4 * cnt[2]
+    nxt[0] = nxt[1] + 2 * cnt[1]
+    lane_bytes = nxt[0] + cnt[0]
+    off = np.zeros(nl.n_signals, np.int64)
+    for sl in range(nl.n_signals):
+        k = int(cls[sl])
+        off[sl] = nxt[k]
+        nxt[k] += 1 << k
+    return slot, cls, off, lane_bytes
+
+
+def decode(buf: np.ndarray, cls, off, n: int) -> np.ndarray:
+    """Rows of a compact state buffer (uint8) as uint64 [n_slots][n]."""
+    out = np.zeros((cls.size, n), np.uint64)
+    dt = {0: np.uint8, 1: np.uint16, 2: np.uint32, 3: np.uint64}
+    for sl in range(cls.size):
+        k = int(cls[sl])
+        start = int(off[sl]) * n
+        out[sl] = buf[start:start + (n << k)].view(dt[k]).astype(np.uint64)
+    return out
+
+
 def test_static_step_matches_regular_step():
     import torch
 
@@ -50,13 +81,17 @@ def test_static_step_matches_regular_step():
     assert sim.info["n_lanes"] == n
 
     # caller-owned buffers in the documented layout
+    slot, cls, off, lane_bytes = compact_rows(nl)
+    assert lane_bytes == info["state_bytes_per_lane"]
     dev = torch.device("cuda")
-    state = torch.zeros((nl.n_signals, n), dtype=torch.int64, device=dev)
-    cw = nl.const_width.astype(np.uint64)
-    cval = nl.const_value & ((np.uint64(1) << np.minimum(cw, 63)) - np.uint64(1))
-    cval = np.where(cw >= 64, nl.const_value, cval).astype(np.uint64)
-    state[nl.const_base:nl.op_base] = torch.from_numpy(
-        np.repeat(cval[:, None], n, axis=1).view(np.int64)).to(dev)
+    img = np.zeros(lane_bytes * n, np.uint8)
+    dt = {0: np.uint8, 1: np.uint16, 2: np.uint32, 3: np.uint64}
+    for c in range(nl.n_consts):
+        sl = nl.const_base + c
+        k = int(cls[sl])
+        start = int(off[sl]) * n
+        img[start:start + (n << k)] = np.full(n, nl.const_value[c], dt[k]).view(np.uint8)
+    state = torch.from_numpy(img).to(dev)
     mem = torch.zeros((int(info["mem_words_total"]), n), dtype=torch.int64, device=dev)
     xsd = torch.from_numpy(xs.copy().view(np.int64)).to(dev)
     torch.cuda.synchronize()
@@ -71,7 +106,7 @@ def test_static_step_matches_regular_step():
     rt.rteaal_step_static(d.handle, state, mem, xsd, n, budgets, 0, rt.RTEAAL_STIM_XORSHIFT, 0)
     sim.step(budgets, stimulus="xorshift")
 
-    got = state.cpu().numpy().view(np.uint64)[slot]
+    got = decode(state.cpu().numpy(), cls, off, n)[slot]
     exp = sim.read()
     assert np.array_equal(got, exp)
     assert np.array_equal(mem.cpu().numpy().view(np.uint64), sim.read_mem())
