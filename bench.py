@@ -223,7 +223,7 @@ def run_ours(args) -> None:
 
     design = rt.Design(nl.to_bytes())
     kw = dict(tile_lanes=args.tile_lanes, threads=args.threads, unroll=args.unroll,
-              ctas_per_sm=args.ctas_per_sm)
+              ctas_per_sm=args.ctas_per_sm, lanes_per_thread=args.lanes_per_thread)
     sim = rt.Sim(design, n, kernel=args.kernel, xorshift_seed=xs, expected_cycles=budgets, **kw)
     stream = torch.cuda.current_stream(dev)
     remaining = budgets.astype(np.int64).copy()
@@ -292,7 +292,7 @@ def run_ours(args) -> None:
     avg_launch_s = float(np.mean(step_ms)) / 1e3
     peaks = measured_peaks()
     achieved = per_launch_bytes / avg_launch_s / 1e9
-    kname = {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops"}[info["kernel"]]
+    kname = {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops", 5: "k_stream"}[info["kernel"]]
     traffic = profile_traffic(kname + ":" + args.workload)
     if traffic is not None:
         traffic *= (inst_cycles / args.steps)                # stored per instance-cycle
@@ -360,7 +360,7 @@ def run_ours(args) -> None:
             "config": {"workload": args.workload, "ops": nl.n_ops, "regs": nl.n_regs,
                        "layers": design.info["n_layers"], "instances": n_total,
                        "cycles_per_step": C, "kernel": args.kernel,
-                       "kernel_used": {1: "layer", 2: "tile", 3: "grid", 4: "layer_graph"}[info["kernel"]],
+                       "kernel_used": {1: "layer", 2: "tile", 3: "grid", 4: "layer_graph", 5: "stream"}[info["kernel"]],
                        "tile_lanes": info["tile_lanes"], "threads": info["threads"],
                        "ctas_per_sm": info["ctas_per_sm"], "unroll": info["unroll"],
                        "grid": info["grid"], "autotune": tune, "parallelism": "replicas" if world > 1 else "1 gpu",
@@ -370,7 +370,7 @@ def run_ours(args) -> None:
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                          "traffic": traffic, "peak_source": peaks["source"],
                          "bytes_per_instance_cycle": bpc["total"],
-                         "kernel": {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops"}[info["kernel"]]},
+                         "kernel": {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops", 5: "k_stream"}[info["kernel"]]},
             "gpu_launches": 1 * args.steps,
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -398,9 +398,10 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--lanes-per-thread", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
-    ap.add_argument("--tune-kernels", default="tile,grid")
+    ap.add_argument("--tune-kernels", default="tile,grid,stream")
     ap.add_argument("--tune-log", default="")
     ap.add_argument("--no-verify", dest="verify", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -142,7 +142,12 @@ enum {
                                instance tile, CTA barrier between layers           */
   RTEAAL_KERNEL_GRID = 3,   /* persistent cooperative: the whole grid walks all
                                layers, bounded grid barrier between layers         */
-  RTEAAL_KERNEL_LAYER_GRAPH = 4 /* plain form with the cycle loop as a CUDA graph  */
+  RTEAAL_KERNEL_LAYER_GRAPH = 4, /* plain form with the cycle loop as a CUDA graph */
+  RTEAAL_KERNEL_STREAM = 5  /* persistent cooperative, one CTA per SM: a producer
+                               warp streams each op's operand rows into a
+                               shared-memory ring with bulk copies (TMA engine,
+                               mbarriers), consumer warps compute from it; needs a
+                               multiple of 128 lanes                              */
 };
 
 typedef struct {
@@ -159,7 +164,7 @@ typedef struct {
   uint32_t threads;        /* threads per CTA (multiple of 32, <= 1024), 0 auto */
   uint32_t ctas_per_sm;    /* TILE / GRID residency target, 0 auto              */
   uint32_t unroll;         /* operations in flight per thread (1, 2, 4), 0 auto */
-  uint32_t lanes_per_thread; /* lanes (instances) per thread per op (1, 2, 4), 0 auto */
+  uint32_t lanes_per_thread; /* lanes (instances) per thread per op (1, 2, 4, 8), 0 auto */
 } rteaal_sim_opts;
 
 typedef struct {
@@ -190,7 +195,7 @@ typedef struct {
 } rteaal_tune_trial;
 
 /* Autotuner: times every candidate launch configuration of the kernels in
- * kernel_mask (bit 1 << RTEAAL_KERNEL_*, 0 = TILE|GRID, or LAYER|GRID for
+ * kernel_mask (bit 1 << RTEAAL_KERNEL_*, 0 = TILE|GRID|STREAM, or LAYER|GRID for
  * fewer than 64 lanes) on this sim, one warm-up and one timed step of
  * cycles_per_trial cycles each, keeps the fastest, and restores the state,
  * memories and stimulus states exactly (device-to-device snapshot: needs

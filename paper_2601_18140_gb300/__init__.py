@@ -22,12 +22,12 @@ LIB_PATH = os.path.join(_HERE, "librteaal.so")
 RTEAAL_OK, RTEAAL_E_INVALID, RTEAAL_E_FORMAT, RTEAAL_E_NOMEM = 0, -1, -2, -3
 RTEAAL_E_CUDA, RTEAAL_E_TIMEOUT, RTEAAL_E_BUSY, RTEAAL_E_UNSUPPORTED = -4, -5, -6, -7
 RTEAAL_KERNEL_AUTO, RTEAAL_KERNEL_LAYER, RTEAAL_KERNEL_TILE = 0, 1, 2
-RTEAAL_KERNEL_GRID, RTEAAL_KERNEL_LAYER_GRAPH = 3, 4
+RTEAAL_KERNEL_GRID, RTEAAL_KERNEL_LAYER_GRAPH, RTEAAL_KERNEL_STREAM = 3, 4, 5
 RTEAAL_STIM_HOLD, RTEAAL_STIM_XORSHIFT, RTEAAL_STIM_BUFFER = 0, 1, 2
 RTEAAL_PROBE_LAST, RTEAAL_PROBE_EVERY = 0, 1
 RTEAAL_STEP_RESET = 1
 
-KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4}
+KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4, "stream": 5}
 
 
 class RteaalError(RuntimeError):

@@ -221,6 +221,55 @@ struct Lanes {
   uint64_t x[V];
 };
 
+// alu for V lanes with one opcode dispatch per item (the lane loop is inside
+// each case), then the width mask.
+template <int V>
+__device__ __forceinline__ Lanes<V> alu_v(uint32_t ctl, const Lanes<V>& a, const Lanes<V>& b,
+                                          const Lanes<V>& c) {
+  const uint32_t op = ctl & 31u, ar = (ctl >> 5) & 3u;
+  const uint32_t p0 = (ctl >> 16) & 255u, p1 = ctl >> 24;
+  Lanes<V> r;
+#define RT_LANES(expr) _Pragma("unroll") for (int v = 0; v < V; v++) r.x[v] = (expr)
+  switch (op) {
+    case OP_COPY: RT_LANES(a.x[v]); break;
+    case OP_AND: RT_LANES(a.x[v] & b.x[v] & (ar == 3 ? c.x[v] : ~0ull)); break;
+    case OP_OR: RT_LANES(a.x[v] | b.x[v] | (ar == 3 ? c.x[v] : 0ull)); break;
+    case OP_XOR: RT_LANES(a.x[v] ^ b.x[v] ^ (ar == 3 ? c.x[v] : 0ull)); break;
+    case OP_NOT: RT_LANES(~a.x[v]); break;
+    case OP_ADD: RT_LANES(a.x[v] + b.x[v] + (ar == 3 ? c.x[v] : 0ull)); break;
+    case OP_SUB: RT_LANES(a.x[v] - b.x[v]); break;
+    case OP_MUL: RT_LANES(a.x[v] * b.x[v] * (ar == 3 ? c.x[v] : 1ull)); break;
+    case OP_SHL: RT_LANES(p0 >= 64u ? 0ull : a.x[v] << p0); break;
+    case OP_SHR: RT_LANES(p0 >= 64u ? 0ull : a.x[v] >> p0); break;
+    case OP_DSHL: RT_LANES(b.x[v] >= 64ull ? 0ull : a.x[v] << (uint32_t)b.x[v]); break;
+    case OP_DSHR: RT_LANES(b.x[v] >= 64ull ? 0ull : a.x[v] >> (uint32_t)b.x[v]); break;
+    case OP_BITS: {
+      const uint64_t m = wmask(p0 - p1 + 1u);
+      RT_LANES((a.x[v] >> p1) & m);
+    } break;
+    case OP_CAT: RT_LANES((p0 >= 64u ? 0ull : a.x[v] << p0) | b.x[v]); break;
+    case OP_EQ: RT_LANES((uint64_t)(a.x[v] == b.x[v])); break;
+    case OP_NEQ: RT_LANES((uint64_t)(a.x[v] != b.x[v])); break;
+    case OP_LT: RT_LANES((uint64_t)(a.x[v] < b.x[v])); break;
+    case OP_LEQ: RT_LANES((uint64_t)(a.x[v] <= b.x[v])); break;
+    case OP_GT: RT_LANES((uint64_t)(a.x[v] > b.x[v])); break;
+    case OP_GEQ: RT_LANES((uint64_t)(a.x[v] >= b.x[v])); break;
+    case OP_MUX: RT_LANES((a.x[v] & 1ull) ? b.x[v] : c.x[v]); break;
+    case OP_ANDR: {
+      const uint64_t m = wmask(p0);
+      RT_LANES((uint64_t)((a.x[v] & m) == m));
+    } break;
+    case OP_ORR: RT_LANES((uint64_t)(a.x[v] != 0ull)); break;
+    case OP_XORR: RT_LANES((uint64_t)(__popcll(a.x[v]) & 1)); break;
+    default: RT_LANES(0ull); break;
+  }
+#undef RT_LANES
+  const uint64_t mk = wmask((ctl >> 8) & 255u);
+#pragma unroll
+  for (int v = 0; v < V; v++) r.x[v] &= mk;
+  return r;
+}
+
 // V consecutive lanes of a row, zero-extended (lane is a multiple of V, so the
 // packed 2^k * V bytes are naturally aligned).
 template <int V>
@@ -283,6 +332,39 @@ __device__ __forceinline__ Lanes<V> ldr(const uint8_t* st, uint32_t ref, size_t 
         r.x[3] = t1.y;
       } break;
     }
+  } else if constexpr (V == 8) {
+    const uint8_t* p = elem(st, ref, np, lane);
+    switch (ref >> 30) {
+      case 0: {
+        const uint2 t = *reinterpret_cast<const uint2*>(p);
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+          r.x[v] = (t.x >> (8 * v)) & 0xFFu;
+          r.x[4 + v] = (t.y >> (8 * v)) & 0xFFu;
+        }
+      } break;
+      case 1: {
+        const uint4 t = *reinterpret_cast<const uint4*>(p);
+        r.x[0] = t.x & 0xFFFFu; r.x[1] = t.x >> 16;
+        r.x[2] = t.y & 0xFFFFu; r.x[3] = t.y >> 16;
+        r.x[4] = t.z & 0xFFFFu; r.x[5] = t.z >> 16;
+        r.x[6] = t.w & 0xFFFFu; r.x[7] = t.w >> 16;
+      } break;
+      case 2: {
+        const uint4 t0 = reinterpret_cast<const uint4*>(p)[0];
+        const uint4 t1 = reinterpret_cast<const uint4*>(p)[1];
+        r.x[0] = t0.x; r.x[1] = t0.y; r.x[2] = t0.z; r.x[3] = t0.w;
+        r.x[4] = t1.x; r.x[5] = t1.y; r.x[6] = t1.z; r.x[7] = t1.w;
+      } break;
+      default: {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const ulonglong2 t = reinterpret_cast<const ulonglong2*>(p)[q];
+          r.x[2 * q] = t.x;
+          r.x[2 * q + 1] = t.y;
+        }
+      } break;
+    }
   } else {
 #pragma unroll
     for (int v = 0; v < V; v++) r.x[v] = ld1(st, ref, np, lane + v);
@@ -339,6 +421,38 @@ __device__ __forceinline__ void str(uint8_t* st, uint32_t ref, size_t np, uint32
       }
       return;
     }
+  } else if constexpr (V == 8) {
+    if (m == 255u) {
+      uint8_t* p = const_cast<uint8_t*>(elem(st, ref, np, lane));
+      switch (ref >> 30) {
+        case 0: {
+          uint32_t lo = 0, hi = 0;
+#pragma unroll
+          for (int v = 0; v < 4; v++) {
+            lo |= (uint32_t)r.x[v] << (8 * v);
+            hi |= (uint32_t)r.x[4 + v] << (8 * v);
+          }
+          *reinterpret_cast<uint2*>(p) = make_uint2(lo, hi);
+        } break;
+        case 1:
+          *reinterpret_cast<uint4*>(p) =
+              make_uint4((uint32_t)(r.x[0] | (r.x[1] << 16)), (uint32_t)(r.x[2] | (r.x[3] << 16)),
+                         (uint32_t)(r.x[4] | (r.x[5] << 16)), (uint32_t)(r.x[6] | (r.x[7] << 16)));
+          break;
+        case 2:
+          reinterpret_cast<uint4*>(p)[0] =
+              make_uint4((uint32_t)r.x[0], (uint32_t)r.x[1], (uint32_t)r.x[2], (uint32_t)r.x[3]);
+          reinterpret_cast<uint4*>(p)[1] =
+              make_uint4((uint32_t)r.x[4], (uint32_t)r.x[5], (uint32_t)r.x[6], (uint32_t)r.x[7]);
+          break;
+        default:
+#pragma unroll
+          for (int q = 0; q < 4; q++)
+            reinterpret_cast<ulonglong2*>(p)[q] = make_ulonglong2(r.x[2 * q], r.x[2 * q + 1]);
+          break;
+      }
+      return;
+    }
   }
 #pragma unroll
   for (int v = 0; v < V; v++)
@@ -373,8 +487,7 @@ __device__ __forceinline__ Lanes<V> apply(const DDesign& d, const DSim& s, const
 #pragma unroll
     for (int v = 0; v < V; v++) r.x[v] = eval_memrd(d, s, ctl, a.x[v], lane + v);
   } else {
-#pragma unroll
-    for (int v = 0; v < V; v++) r.x[v] = alu(ctl, a.x[v], b.x[v], c.x[v]);
+    r = alu_v<V>(ctl, a, b, c);
   }
   return r;
 }

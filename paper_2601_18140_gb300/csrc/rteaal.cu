@@ -180,6 +180,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs
 #undef RT_SPACE
 }
 
+}  // namespace rteaal
+#include "stream.cuh"
+namespace rteaal {
+
 // compact state rows (by reference) <-> a [n][n_inst] uint64 device buffer
 __global__ void k_gather_ref(const uint8_t* st, uint32_t n_pad, const uint32_t* refs, uint32_t n_rows,
                              const uint32_t* lane_of_user, uint32_t inst0, uint32_t n_inst, uint64_t* out) {
@@ -344,6 +348,7 @@ struct rteaal_sim {
   std::vector<DevBuf> bufs;
   uint64_t barrier_timeout_ns = 2000000000ull;
   uint32_t barrier_extra = 0;        // test hook: arrivals withheld from every grid barrier
+  uint32_t stream_chunk = 0;         // STREAM: lanes per item
 
   void* get(size_t n) {
     DevBuf b;
@@ -383,11 +388,16 @@ void require(bool c, const char* msg) {
   if (!c) throw Error(RTEAAL_E_INVALID, msg);
 }
 
+// Lanes of a sim: a power of two up to 64 instances, else a multiple of 128
+// (whole 128-lane chunks for the stream form; at most 127 idle lanes).
 uint32_t pad_lanes(uint32_t n) {
   if (n <= 1) return 1;
-  uint32_t p = 1;
-  while (p < n && p < 64) p <<= 1;
-  return (n + p - 1) / p * p;
+  if (n <= 64) {
+    uint32_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
+  }
+  return (n + 127) / 128 * 128;
 }
 
 DSim dsim(const rteaal_sim* s) {
@@ -468,6 +478,7 @@ struct Variant {
 };
 #define RT_VARIANT(V, U, T, B) {V, U, T, B, (const void*)k_tile<V, U, T, B>, (const void*)k_grid<V, U, T, B>}
 const Variant kVariants[] = {
+    RT_VARIANT(8, 1, 256, 2), RT_VARIANT(8, 1, 512, 1),
     RT_VARIANT(4, 1, 256, 4), RT_VARIANT(4, 1, 512, 2), RT_VARIANT(4, 1, 1024, 1),
     RT_VARIANT(4, 2, 512, 1),
     RT_VARIANT(2, 1, 256, 8), RT_VARIANT(2, 1, 512, 4), RT_VARIANT(2, 1, 1024, 2),
@@ -604,18 +615,21 @@ RT_EXPORT uint64_t rteaal_sim_footprint(const rteaal_design* d, uint32_t n) {
 
 namespace {
 
+constexpr int kStreamConsumerWarps = 8;
+
 // Validate and apply a launch configuration (never changes results).
 void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
                uint32_t unroll, uint32_t lanes_per_thread) {
   if (kernel == RTEAAL_KERNEL_AUTO) kernel = s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
-  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_LAYER_GRAPH, "unknown kernel");
-  if (!unroll) unroll = 2;
+  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_STREAM, "unknown kernel");
+  if (!unroll) unroll = 1;
   require(unroll == 1 || unroll == 2 || unroll == 4, "unroll must be 1, 2 or 4");
   if (!threads) threads = 512;
   require(threads % 32 == 0 && threads >= 32 && threads <= 1024, "threads must be a multiple of 32 in [32, 1024]");
   if (!tile_lanes) tile_lanes = std::min<uint32_t>(16, s->n_pad);
-  require(lanes_per_thread == 0 || lanes_per_thread == 1 || lanes_per_thread == 2 || lanes_per_thread == 4,
-          "lanes_per_thread must be 1, 2 or 4");
+  require(lanes_per_thread == 0 || lanes_per_thread == 1 || lanes_per_thread == 2 || lanes_per_thread == 4 ||
+              lanes_per_thread == 8,
+          "lanes_per_thread must be 1, 2, 4 or 8");
   uint32_t span = s->n_pad;  // lanes that one V-lane chunk must divide
   if (kernel == RTEAAL_KERNEL_TILE) {
     require(tile_lanes >= 1 && tile_lanes <= 64 && (tile_lanes & (tile_lanes - 1)) == 0,
@@ -626,8 +640,8 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
   int V = (int)lanes_per_thread;
   if (!V) {  // widest V that divides the span and (persistent forms) has a compiled variant
     const bool persistent = kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID;
-    for (int c : {4, 2, 1})
-      if (span % (uint32_t)c == 0 && (!persistent || find_variant(c, unroll ? unroll : 2, threads ? threads : 512))) {
+    for (int c : {4, 2, 1, 8})
+      if (span % (uint32_t)c == 0 && (!persistent || find_variant(c, unroll ? unroll : 1, threads ? threads : 512))) {
         V = c;
         break;
       }
@@ -636,7 +650,24 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
   require(span % (uint32_t)V == 0, "lanes_per_thread must divide the lanes of a tile / the padded lane count");
   uint32_t grid = 0;
   if (kernel == RTEAAL_KERNEL_LAYER || kernel == RTEAAL_KERNEL_LAYER_GRAPH) threads = 256;
-  if (kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID) {
+  if (kernel == RTEAAL_KERNEL_STREAM) {
+    // producer warp + consumer warps, one CTA per SM, chunks of up to 512 lanes
+    if (s->n_pad % 128 != 0)
+      throw Error(RTEAAL_E_UNSUPPORTED, "stream kernel needs a multiple of 128 lanes");
+    uint32_t chunk = STREAM_CHUNK_MAX;
+    while (s->n_pad % chunk) chunk >>= 1;
+    s->stream_chunk = chunk;
+    V = (int)STREAM_V;
+    threads = 32 * (kStreamConsumerWarps + 1);
+    unroll = 1;
+    const void* fn = (const void*)k_stream<kStreamConsumerWarps>;
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stream_smem_bytes()));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, (int)threads, stream_smem_bytes()));
+    require(occ >= 1, "stream kernel cannot be resident");
+    ctas_per_sm = 1;
+    grid = (uint32_t)s->design->n_sms;
+  } else if (kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID) {
     const Variant* v = find_variant(V, unroll, threads);
     if (!v) throw Error(RTEAAL_E_UNSUPPORTED, "no compiled kernel variant for V=" + std::to_string(V) +
                                                   " unroll=" + std::to_string(unroll) +
@@ -810,7 +841,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     sync_sim(s, st);
     if (!cycles_per_trial) cycles_per_trial = 1;
     if (!kernel_mask)
-      kernel_mask = s->n_pad >= 64 ? ((1u << RTEAAL_KERNEL_TILE) | (1u << RTEAAL_KERNEL_GRID))
+      kernel_mask = s->n_pad >= 64 ? ((1u << RTEAAL_KERNEL_TILE) | (1u << RTEAAL_KERNEL_GRID) |
+                                      (1u << RTEAAL_KERNEL_STREAM))
                                    : ((1u << RTEAAL_KERNEL_LAYER) | (1u << RTEAAL_KERNEL_GRID));
     const Lowered& L = s->design->L;
     const size_t np = s->n_pad;
@@ -831,11 +863,11 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     if (kernel_mask & (1u << RTEAAL_KERNEL_TILE))
       for (uint32_t T : {4u, 8u, 16u, 32u, 64u})
         if (T <= np && np % T == 0)
-          for (uint32_t V : {2u, 4u})
+          for (uint32_t V : {2u, 4u, 8u})
             for (uint32_t th : {256u, 512u, 1024u})
               for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_TILE, T, th, U, V});
     if (kernel_mask & (1u << RTEAAL_KERNEL_GRID))
-      for (uint32_t V : {2u, 4u})
+      for (uint32_t V : {2u, 4u, 8u})
         for (uint32_t th : {256u, 512u, 1024u})
           for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_GRID, 0, th, U, V});
     if (kernel_mask & (1u << RTEAAL_KERNEL_LAYER))
@@ -843,6 +875,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
         for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER, 0, 256, U, V});
     if (kernel_mask & (1u << RTEAAL_KERNEL_LAYER_GRAPH))
       for (uint32_t U : {2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER_GRAPH, 0, 256, U, 0});
+    if ((kernel_mask & (1u << RTEAAL_KERNEL_STREAM)) && np % 128 == 0)
+      cands.push_back({RTEAAL_KERNEL_STREAM, 0, 0, 1, 0});
 
     const int saved[6] = {s->kernel, (int)s->tile_lanes, (int)s->threads, (int)s->ctas_per_sm, (int)s->unroll,
                           s->V};
@@ -1025,6 +1059,26 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ta};
       CK(cudaLaunchKernel(v->tile, dim3(grid), dim3(s->threads), args, 0, st));
       CK(cudaGetLastError());
+    } else if (s->kernel == RTEAAL_KERNEL_STREAM) {
+      require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
+      GridArgs ga{};
+      ga.count = s->scratch + 2;
+      ga.gen = s->scratch + 3;
+      ga.expected = s->grid + s->barrier_extra;
+      ga.timeout_ns = s->barrier_timeout_ns;
+      ga.ncyc = (uint32_t)max_cyc;
+      ga.tpo = make_fastdiv((uint32_t)(np / STREAM_V));
+      StreamArgs sa{s->stream_chunk, (uint32_t)(np / s->stream_chunk)};
+      CK(cudaMemsetAsync(s->scratch, 0, 16, st));
+      void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ga, (void*)&sa};
+      cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_stream<kStreamConsumerWarps>, dim3(s->grid),
+                                                  dim3(s->threads), args, stream_smem_bytes(), st);
+      if (e == cudaErrorCooperativeLaunchTooLarge)
+        throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
+      CK(e);
+      CK(cudaMemcpyAsync(s->err_host, s->scratch, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaEventRecord(s->done, st));
+      s->pending = true;
     } else {  // GRID
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
       GridArgs ga{};

@@ -8,7 +8,7 @@ from tests.gpu_util import Pair
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = ["layer", "layer_graph", "tile", "grid"]
+KERNELS = ["layer", "layer_graph", "tile", "grid", "stream"]
 
 
 def small_design(seed, n_ops=600, depth=10, n_regs=40, n_mems=0, inputs=(8, 32, 64, 1)):
@@ -73,7 +73,7 @@ def test_tile_shapes(kernel, tile_lanes, unroll, threads):
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_buffer_stimulus_and_probes(kernel):
     nl = small_design(21)
-    n, c = 48, 12
+    n, c = 200, 12
     vals = synth.stimulus_values(21, c, nl.n_inputs, n)
     p = Pair(nl, n, kernel=kernel, seed=21)
     p.step(1, reset=True, stimulus="hold")
@@ -85,7 +85,7 @@ def test_buffer_stimulus_and_probes(kernel):
     p.close()
 
 
-@pytest.mark.parametrize("kernel", ["layer", "tile", "grid"])
+@pytest.mark.parametrize("kernel", ["layer", "tile", "grid", "stream"])
 def test_wide_ops_and_memories(kernel):
     """Variadic folds (> 3 operands), long mux chains, two write ports per memory."""
     b = Builder()
@@ -106,7 +106,7 @@ def test_wide_ops_and_memories(kernel):
     b.connect(regs[2], ops[3])
     b.connect(regs[3], ops[4])
     nl = b.build()
-    p = Pair(nl, 40, kernel=kernel, seed=9)
+    p = Pair(nl, 200, kernel=kernel, seed=9)
     p.step(1, reset=True)
     p.step(50)
     p.compare()
@@ -183,17 +183,31 @@ def test_batch_invariance():
 
 
 @pytest.mark.parametrize("kernel", ["layer", "tile", "grid"])
-@pytest.mark.parametrize("lanes_per_thread", [1, 2, 4])
+@pytest.mark.parametrize("lanes_per_thread", [1, 2, 4, 8])
 def test_lanes_per_thread(kernel, lanes_per_thread):
     """Every lanes-per-thread width (packed loads of 1, 2 or 4 lanes per row class)."""
     nl = small_design(31, n_mems=2)
-    n = 96
+    n = 200
     rng = np.random.default_rng(31)
     budgets = rng.integers(0, 25, n).astype(np.uint32)
     p = Pair(nl, n, kernel=kernel, seed=31, lanes_per_thread=lanes_per_thread,
              tile_lanes=32 if kernel == "tile" else 0)
     p.step(1, reset=True)
     p.step(20)
+    p.step(budgets)
+    p.compare()
+    p.close()
+
+
+@pytest.mark.parametrize("n", [128, 300, 1024, 1536])
+def test_stream_chunks(n):
+    """Stream form: chunks of 128 / 512 lanes, ragged tails, uneven budgets, memories, probes."""
+    nl = small_design(41, n_ops=900, n_mems=3)
+    rng = np.random.default_rng(n)
+    budgets = rng.integers(0, 30, n).astype(np.uint32)
+    p = Pair(nl, n, kernel="stream", seed=41, expected_cycles=budgets)
+    p.step(1, reset=True)
+    p.step(13, probes=[nl.reg_base, nl.op_base + 3, nl.n_signals - 1], probe_mode="every")
     p.step(budgets)
     p.compare()
     p.close()

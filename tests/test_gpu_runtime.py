@@ -28,7 +28,8 @@ def test_configure_between_steps():
                 dict(kernel="grid", threads=256, unroll=4),
                 dict(kernel="layer", unroll=1),
                 dict(kernel="tile", tile_lanes=64, threads=512, unroll=4),
-                dict(kernel="layer_graph")]:
+                dict(kernel="layer_graph"),
+                dict(kernel="stream")]:
         p.sim.configure(**cfg)
         p.step(7)
         p.compare()
@@ -41,7 +42,7 @@ def test_autotune_restores_state_exactly():
     p.step(1, reset=True)
     p.step(5)
     before = p.sim.read()
-    trials = p.sim.autotune(cycles_per_trial=2, kernels=["tile", "grid", "layer"])
+    trials = p.sim.autotune(cycles_per_trial=2, kernels=["tile", "grid", "layer", "stream"])
     assert len(trials) >= 10
     assert all(t["ms"] > 0 for t in trials)
     assert np.array_equal(p.sim.read(), before)        # snapshot restored

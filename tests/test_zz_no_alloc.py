@@ -70,7 +70,7 @@ def test_static_step_matches_regular_step():
                                    input_widths=(8, 32, 64, 1), seed=77, n_mems=3, mem_words=16))
     # every register D and write-port signal is an op output: no inserted copy rows
     assert (nl.reg_d >= nl.op_base).all() and (nl.wport[:, 1:] >= nl.op_base).all()
-    n = 192
+    n = 256
     xs = synth.xorshift_seeds(77, nl.n_inputs, n)
     d = rt.Design(nl.to_bytes())
     info = d.info
