@@ -542,6 +542,32 @@ __device__ __forceinline__ void eval_ops(const DDesign& d, const DSim& s, uint32
     if (!am) return;
     const uint4* meta = d.meta + op0;
     const uint32_t* dst = d.dst + op0;
+    if constexpr (U == 1) {
+      // descriptor of the next row fetched one step ahead: the dependent chain of
+      // an item is then operand loads -> compute -> store
+      uint32_t r = is.row0;
+      if (r >= n_rows) return;
+      uint4 m = __ldg(&meta[r]);
+      uint32_t dref = __ldg(&dst[r]);
+      for (;;) {
+        const uint32_t rn = r + is.row_stride;
+        uint4 mn = make_uint4(0, 0, 0, 0);
+        uint32_t dn = 0;
+        if (rn < n_rows) {
+          mn = __ldg(&meta[rn]);
+          dn = __ldg(&dst[rn]);
+        }
+        Lanes<V> va, vb, vc;
+        gather<V>(s.state, np, is.lane, m, va, vb, vc);
+        const Lanes<V> res = apply<V>(d, s, m, va, vb, vc, is.lane);
+        str<V>(s.state, dref, np, is.lane, res, am);
+        if (rn >= n_rows) break;
+        r = rn;
+        m = mn;
+        dref = dn;
+      }
+      return;
+    }
     for (uint32_t r0 = is.row0; r0 < n_rows; r0 += is.row_stride * U) {
       uint4 m[U];
       bool ok[U];

@@ -480,6 +480,8 @@ struct Variant {
 const Variant kVariants[] = {
     RT_VARIANT(8, 1, 256, 2), RT_VARIANT(8, 1, 512, 1),
     RT_VARIANT(4, 1, 256, 4), RT_VARIANT(4, 1, 512, 2), RT_VARIANT(4, 1, 1024, 1),
+    RT_VARIANT(4, 1, 384, 4), RT_VARIANT(4, 1, 256, 6), RT_VARIANT(4, 1, 256, 8),
+    RT_VARIANT(4, 1, 640, 3), RT_VARIANT(4, 1, 448, 4),
     RT_VARIANT(4, 2, 512, 1),
     RT_VARIANT(2, 1, 256, 8), RT_VARIANT(2, 1, 512, 4), RT_VARIANT(2, 1, 1024, 2),
     RT_VARIANT(2, 2, 512, 2), RT_VARIANT(2, 4, 512, 1),
@@ -487,8 +489,16 @@ const Variant kVariants[] = {
 };
 #undef RT_VARIANT
 
-const Variant* find_variant(int V, uint32_t U, uint32_t threads) {
+// Variant for (V, U, threads): the one compiled for exactly `threads` per CTA
+// (with `minb` CTAs per SM when given, else the highest occupancy target), else
+// the smallest launch bound above `threads`.
+const Variant* find_variant(int V, uint32_t U, uint32_t threads, uint32_t minb = 0) {
   const Variant* best = nullptr;
+  for (const Variant& v : kVariants)
+    if (v.V == V && (uint32_t)v.U == U && (uint32_t)v.maxt == threads && (!minb || (uint32_t)v.minb == minb) &&
+        (!best || v.minb > best->minb))
+      best = &v;
+  if (best) return best;
   for (const Variant& v : kVariants)
     if (v.V == V && (uint32_t)v.U == U && (uint32_t)v.maxt >= threads && (!best || v.maxt < best->maxt))
       best = &v;
@@ -615,7 +625,8 @@ RT_EXPORT uint64_t rteaal_sim_footprint(const rteaal_design* d, uint32_t n) {
 
 namespace {
 
-constexpr int kStreamConsumerWarps = 8;
+constexpr int kStreamConsumerWarps = 16;
+
 
 // Validate and apply a launch configuration (never changes results).
 void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
@@ -668,7 +679,7 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     ctas_per_sm = 1;
     grid = (uint32_t)s->design->n_sms;
   } else if (kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID) {
-    const Variant* v = find_variant(V, unroll, threads);
+    const Variant* v = find_variant(V, unroll, threads, ctas_per_sm);
     if (!v) throw Error(RTEAAL_E_UNSUPPORTED, "no compiled kernel variant for V=" + std::to_string(V) +
                                                   " unroll=" + std::to_string(unroll) +
                                                   " threads=" + std::to_string(threads));
@@ -860,16 +871,18 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
 
     struct Cand { int kernel; uint32_t T, threads, U, V; };
     std::vector<Cand> cands;
+    struct CandX { int kernel; uint32_t T, threads, U, V, ctas; };
+    std::vector<CandX> candx;
     if (kernel_mask & (1u << RTEAAL_KERNEL_TILE))
-      for (uint32_t T : {4u, 8u, 16u, 32u, 64u})
+      for (uint32_t T : {8u, 16u, 32u, 64u})
         if (T <= np && np % T == 0)
-          for (uint32_t V : {2u, 4u, 8u})
-            for (uint32_t th : {256u, 512u, 1024u})
-              for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_TILE, T, th, U, V});
+          for (const Variant& v : kVariants)
+            if (v.V >= 2 && T % (uint32_t)v.V == 0)
+              candx.push_back({RTEAAL_KERNEL_TILE, T, (uint32_t)v.maxt, (uint32_t)v.U, (uint32_t)v.V, (uint32_t)v.minb});
     if (kernel_mask & (1u << RTEAAL_KERNEL_GRID))
-      for (uint32_t V : {2u, 4u, 8u})
-        for (uint32_t th : {256u, 512u, 1024u})
-          for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_GRID, 0, th, U, V});
+      for (const Variant& v : kVariants)
+        if (v.V >= 2 && np % (uint32_t)v.V == 0)
+          candx.push_back({RTEAAL_KERNEL_GRID, 0, (uint32_t)v.maxt, (uint32_t)v.U, (uint32_t)v.V, (uint32_t)v.minb});
     if (kernel_mask & (1u << RTEAAL_KERNEL_LAYER))
       for (uint32_t V : {2u, 4u})
         for (uint32_t U : {1u, 2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER, 0, 256, U, V});
@@ -877,6 +890,7 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
       for (uint32_t U : {2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER_GRAPH, 0, 256, U, 0});
     if ((kernel_mask & (1u << RTEAAL_KERNEL_STREAM)) && np % 128 == 0)
       cands.push_back({RTEAAL_KERNEL_STREAM, 0, 0, 1, 0});
+    for (const Cand& c : cands) candx.push_back({c.kernel, c.T, c.threads, c.U, c.V, 0});
 
     const int saved[6] = {s->kernel, (int)s->tile_lanes, (int)s->threads, (int)s->ctas_per_sm, (int)s->unroll,
                           s->V};
@@ -886,12 +900,13 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     rteaal_cycles cyc{cycles_per_trial, nullptr};
     rteaal_stimulus stim{L.in_width.empty() ? RTEAAL_STIM_HOLD : RTEAAL_STIM_XORSHIFT, nullptr, 0};
     float best = 1e30f;
-    Cand best_c{saved[0], (uint32_t)saved[1], (uint32_t)saved[2], (uint32_t)saved[4], (uint32_t)saved[5]};
+    CandX best_c{saved[0], (uint32_t)saved[1], (uint32_t)saved[2], (uint32_t)saved[4], (uint32_t)saved[5],
+                 (uint32_t)saved[3]};
     uint32_t best_ctas = (uint32_t)saved[3];
     uint32_t nt = 0;
-    for (const Cand& c : cands) {
+    for (const CandX& c : candx) {
       try {
-        configure(s, c.kernel, c.T, c.threads, 0, c.U, c.V);
+        configure(s, c.kernel, c.T, c.threads, c.ctas, c.U, c.V);
       } catch (const Error&) {
         continue;  // not compiled / not resident
       }
@@ -910,7 +925,7 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
       if (ms < best) {
         best = ms;
         best_c = c;
-        best_ctas = s->ctas_per_sm;
+        best_ctas = c.ctas ? c.ctas : s->ctas_per_sm;  // the variant's target selects it again
       }
     }
     cudaEventDestroy(e0);

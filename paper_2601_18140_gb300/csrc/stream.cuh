@@ -25,9 +25,9 @@
 
 namespace rteaal {
 
-constexpr uint32_t STREAM_NS = 16;                     // ring slots
-constexpr uint32_t STREAM_CHUNK_MAX = 512;             // lanes per item
-constexpr uint32_t STREAM_SLOT = 3 * STREAM_CHUNK_MAX * 8;  // three u64 operand segments
+constexpr uint32_t STREAM_NS = 64;                     // item (descriptor) slots
+constexpr uint32_t STREAM_CHUNK_MAX = 2048;            // lanes per item
+constexpr uint32_t STREAM_RING = 160 * 1024;           // operand bytes in flight per SM
 constexpr uint32_t STREAM_V = 4;                       // lanes per consumer thread per step
 constexpr uint32_t STREAM_ACT_WORDS = 2048;            // activity bitmap: up to 65,536 lanes
 
@@ -38,11 +38,14 @@ struct StreamArgs {
 
 struct __align__(16) SlotInfo {
   uint4 meta;
-  uint32_t dst, lane0, pad0, pad1;
+  uint32_t dst, lane0;
+  uint32_t off[3];               // ring byte offset of each operand segment
+  uint32_t pad;
+  unsigned long long start;      // monotonic ring position of the item's first byte
 };
 
 constexpr uint32_t stream_smem_bytes() {
-  return STREAM_NS * STREAM_SLOT + STREAM_NS * (uint32_t)sizeof(SlotInfo) + 2 * STREAM_NS * 8 +
+  return STREAM_RING + STREAM_NS * (uint32_t)sizeof(SlotInfo) + 2 * STREAM_NS * 8 +
          STREAM_ACT_WORDS * 4 + 64;
 }
 
@@ -141,16 +144,16 @@ __device__ __forceinline__ Lanes<STREAM_V> lds4(const uint8_t* seg, uint32_t k, 
 
 // Evaluate one item from its ring slot (one consumer warp).
 __device__ __forceinline__ void stream_consume(const DDesign& d, const DSim& s, const SlotInfo& si,
-                                               const uint8_t* slot, uint32_t chunk, uint32_t cyc,
+                                               const uint8_t* ring, uint32_t chunk, uint32_t cyc,
                                                uint32_t lane_id, const uint32_t* act) {
   const uint4 m = si.meta;
   const uint32_t ctl = m.w;
   const size_t np = s.n_pad;
   const uint32_t ar = (ctl >> 5) & 3u;
   const uint32_t ka = m.x >> 30, kb = m.y >> 30, kc = m.z >> 30;
-  const uint8_t* sa = slot;
-  const uint8_t* sb = slot + STREAM_CHUNK_MAX * 8;
-  const uint8_t* sc = slot + 2 * STREAM_CHUNK_MAX * 8;
+  const uint8_t* sa = ring + si.off[0];
+  const uint8_t* sb = ring + si.off[1];
+  const uint8_t* sc = ring + si.off[2];
   for (uint32_t sub = lane_id * STREAM_V; sub < chunk; sub += 32 * STREAM_V) {
     const uint32_t lane = si.lane0 + sub;
     const uint32_t am = act ? (act[lane >> 5] >> (lane & 31u)) & 0xFu : act_mask<STREAM_V>(s, lane, cyc);
@@ -180,7 +183,7 @@ template <int NCW>
 __global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s, GridArgs g, StreamArgs sa) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* ring = smem;
-  SlotInfo* info = reinterpret_cast<SlotInfo*>(smem + STREAM_NS * STREAM_SLOT);
+  SlotInfo* info = reinterpret_cast<SlotInfo*>(smem + STREAM_RING);
   uint64_t* full = reinterpret_cast<uint64_t*>(info + STREAM_NS);
   uint64_t* empty = full + STREAM_NS;
   uint32_t* act_bits = reinterpret_cast<uint32_t*>(empty + STREAM_NS);
@@ -202,7 +205,9 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s,
   }
   __syncthreads();
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
-  uint32_t kk = 0;  // items this CTA has passed through its ring (all warps agree)
+  uint32_t kk = 0;      // items this CTA has passed through its ring (all warps agree)
+  unsigned long long pos = 0;  // producer: next free monotonic ring byte
+  uint32_t oldest = 0;         // producer: oldest item whose slot / bytes are not yet known free
 #define RT_SPACE make_space<STREAM_V>(g.tpo, 0u, gtid, nthreads)
   for (uint32_t c = 0; c < g.ncyc; c++) {
     if (act)
@@ -221,43 +226,57 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s,
       const uint32_t r1 = (uint32_t)((uint64_t)n_ops * (blockIdx.x + 1) / gridDim.x);
       const uint32_t n_items = (r1 - r0) * sa.n_chunks;
       if (producer) {
-        // lanes 0..NS-1 issue NS items at a time; item j uses slot (kk + j) % NS, so
-        // lane l keeps one slot for the whole layer
-        if (lane_id < STREAM_NS) {
-          if (lane_id == 0) fence_proxy_async();
-          __syncwarp(0xFFFFu);
+        // one issuing lane; monotonic byte positions: the ring segment of item k
+        // is [start, end); space is reclaimed from the oldest item still in use
+        if (lane_id == 0) {
           fence_proxy_async();
-          for (uint32_t jb = 0; jb < n_items; jb += STREAM_NS) {
+          for (uint32_t j = 0; j < n_items; j++) {
             if (*sh_bad) break;
-            const uint32_t j = jb + lane_id;
-            if (j >= n_items) break;
             const uint32_t k = kk + j, slot = k % STREAM_NS, par = (k / STREAM_NS) & 1u;
-            if (!mbar_wait(&empty[slot], par ^ 1u, g.timeout_ns)) {
-              atomicOr(s.err, 2u);
-              *sh_bad = 1;
-              break;
-            }
             const uint32_t jr = j / sa.n_chunks;
             const uint32_t op = o0 + r0 + jr;
             const uint32_t lane0 = (j - jr * sa.n_chunks) * sa.chunk;
             const uint4 m = __ldg(&d.meta[op]);
+            const uint32_t ar = (m.w & CTL_EXT) ? 0u : (m.w >> 5) & 3u;
+            const uint32_t refs[3] = {m.x, m.y, m.z};
+            uint32_t need = 0;
+            for (uint32_t o = 0; o < ar; o++) need += sa.chunk << (refs[o] >> 30);
+            // contiguous placement: skip to the next ring lap if the item would wrap
+            unsigned long long p0 = pos;
+            if ((p0 % STREAM_RING) + need > STREAM_RING) p0 = (p0 / STREAM_RING + 1) * STREAM_RING;
+            bool ok = true;
+            // free the descriptor slot (item k - NS) and the ring bytes up to p0 + need by
+            // waiting for the oldest items' release (item counters compared by difference)
+            while (ok && (k - oldest >= STREAM_NS ||
+                          (k != oldest && p0 + need > info[oldest % STREAM_NS].start + STREAM_RING))) {
+              ok = mbar_wait(&empty[oldest % STREAM_NS], (oldest / STREAM_NS) & 1u, g.timeout_ns);
+              oldest++;
+            }
+            if (!ok) {
+              atomicOr(s.err, 2u);
+              *sh_bad = 1;
+              break;
+            }
             SlotInfo& si = info[slot];
             si.meta = m;
             si.dst = __ldg(&d.dst[op]);
             si.lane0 = lane0;
-            uint8_t* dstp = ring + slot * STREAM_SLOT;
-            if (m.w & CTL_EXT) {
+            si.start = p0;
+            unsigned long long q = p0;
+            for (uint32_t o = 0; o < 3; o++) {
+              si.off[o] = (uint32_t)(q % STREAM_RING);
+              if (o < ar) q += sa.chunk << (refs[o] >> 30);
+            }
+            pos = q;
+            if (ar == 0) {
               mbar_arrive(&full[slot]);  // operands read from global by the consumer
             } else {
-              const uint32_t ar = (m.w >> 5) & 3u;
-              const uint32_t refs[3] = {m.x, m.y, m.z};
-              uint32_t bytes = 0;
-              for (uint32_t o = 0; o < ar; o++) bytes += sa.chunk << (refs[o] >> 30);
-              mbar_arrive_expect_tx(&full[slot], bytes);
+              mbar_arrive_expect_tx(&full[slot], need);
               for (uint32_t o = 0; o < ar; o++)
-                bulk_g2s(dstp + o * STREAM_CHUNK_MAX * 8, elem(s.state, refs[o], s.n_pad, lane0),
-                         sa.chunk << (refs[o] >> 30), &full[slot]);
+                bulk_g2s(ring + si.off[o], elem(s.state, refs[o], s.n_pad, lane0), sa.chunk << (refs[o] >> 30),
+                         &full[slot]);
             }
+            (void)par;
           }
         }
       } else {
@@ -273,7 +292,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s,
           }
           ok = __shfl_sync(0xFFFFFFFFu, ok, 0);  // warp-uniform decision
           if (ok != 1) break;
-          stream_consume(d, s, info[slot], ring + slot * STREAM_SLOT, sa.chunk, c, lane_id, act);
+          stream_consume(d, s, info[slot], ring, sa.chunk, c, lane_id, act);
           __syncwarp();
           if (lane_id == 0) mbar_arrive(&empty[slot]);
         }
