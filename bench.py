@@ -293,7 +293,9 @@ def run_ours(args) -> None:
     peaks = measured_peaks()
     achieved = per_launch_bytes / avg_launch_s / 1e9
     kname = {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops", 5: "k_stream"}[info["kernel"]]
-    traffic = profile_traffic(kname + ":" + args.workload)
+    variant = "%s<%d,%d,%d,%d>" % (kname, info["lanes_per_thread"], info["unroll"], info["threads"],
+                                   info["ctas_per_sm"])
+    traffic = profile_traffic(variant + ":" + args.workload) if n_total == WORKLOADS[args.workload][1] else None
     if traffic is not None:
         traffic *= (inst_cycles / args.steps)                # stored per instance-cycle
 
