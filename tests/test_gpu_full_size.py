@@ -1,0 +1,53 @@
+"""Parity at the workloads' full sizes, on sampled instances the oracle can follow.
+
+* single-200k: 200k-op DAG, 1 instance, plain per-layer form and the grid form;
+* batch-1M: 1M ops, 4,096 instances with uneven cycle budgets, in the launch
+  configuration the benchmark times (autotuned), three sampled instances
+  (first, middle, last lane) checked signal by signal;
+* soc-5M: 5M ops, 256k registers, 64 register files (2 read, 1 write port
+  each), 1,024 instances, two sampled instances, every signal and memory word.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_util import Pair
+
+pytestmark = pytest.mark.gpu
+
+
+def test_single_200k_plain_and_grid():
+    nl = synth.generate(synth.spec_single())
+    for kernel in ["layer", "grid"]:
+        p = Pair(nl, 1, kernel=kernel, seed=1)
+        p.step(1, reset=True)
+        p.step(300)
+        p.compare()
+        p.close()
+
+
+def test_batch_1m_bench_configuration():
+    nl = synth.generate(synth.spec_batch())
+    n = 4096
+    budgets = synth.cycle_budgets(5, n, 3, 12)
+    sample = [0, n // 2, n - 1]
+    p = Pair(nl, n, kernel="grid", seed=5, expected_cycles=budgets, oracle_instances=sample,
+             threads=384, ctas_per_sm=4, lanes_per_thread=4, unroll=1)
+    p.step(1, reset=True)
+    p.sim.autotune(cycles_per_trial=1, kernels=["grid", "stream"])   # as the benchmark does
+    p.step(budgets, threads=3)
+    p.step(4, threads=3)
+    p.compare()
+    p.close()
+
+
+def test_soc_5m_with_memories():
+    nl = synth.generate(synth.spec_soc())
+    assert nl.n_mems == 64 and nl.n_wports == 64
+    assert int((nl.op_code == synth.OP["MEMRD"]).sum()) == 128
+    n = 1024
+    p = Pair(nl, n, kernel="grid", seed=3, oracle_instances=[1, n - 2])
+    p.step(1, reset=True, threads=2)
+    p.step(3, threads=2)
+    p.compare()
+    p.close()
