@@ -386,13 +386,54 @@ def run_ours(args) -> None:
         torch.distributed.destroy_process_group()
 
 
+def run_serving(args) -> None:
+    """Serving trace: Poisson arrivals over three designs, continuous batching."""
+    import torch
+
+    from paper_2601_18140_gb300.serve import Job, build_server, latency_stats, poisson_trace
+
+    torch.cuda.set_device(0)
+    sizes = {"d50k": 50_000, "d500k": 500_000, "d5M": 5_000_000}
+    nls = {k: synth.generate(synth.spec_serving(v, seed=40 + i)) for i, (k, v) in enumerate(sizes.items())}
+    capacity = {"d50k": 512, "d500k": 512, "d5M": 256}
+    srv = build_server({k: v.to_bytes() for k, v in nls.items()}, capacity, quantum=args.quantum)
+    warm = [Job(10_000 + i, k, 1, 10, seed=1, arrival=0.0) for i, k in enumerate(sizes)]
+    srv.run(warm)
+    srv.done.clear()
+    trace = poisson_trace(4, args.serve_jobs, args.serve_rate, list(sizes), np.log(1e4), 1.0, 64,
+                          cycles_cap=args.cycles_cap or None)
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clk:
+        done = srv.run(trace)
+    wall = time.perf_counter() - t0
+    work = float(sum(j.n_instances * j.cycles * nls[j.design].n_ops for j in done))
+    span = max(j.arrival for j in trace)
+    st = latency_stats(done)
+    line = {"metric": "served op-evaluations/sec, continuous batching, p50/p99 job latency",
+            "value": work / wall, "unit": "op-evals/s", "n_gpus": 1, "steps": len(done), "warmup": len(warm),
+            "ms_per_step": wall * 1e3 / max(1, len(done)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "serving", "designs_ops": list(sizes.values()), "jobs": len(done),
+                       "rate_hz": args.serve_rate, "cycles": "lognormal(ln 10k, 1)" +
+                       (" capped at %d" % args.cycles_cap if args.cycles_cap else ""),
+                       "instances": "U{1..64}", "capacity_lanes": capacity, "quantum": args.quantum},
+            "latency": st, "offered_op_evals_per_s": work / max(span, 1e-9),
+            "served_op_evals_per_s": work / wall, "wall_s": wall, "rounds": srv.rounds,
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch-1M", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batch-1M", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--quantum", type=int, default=2000)
+    ap.add_argument("--cycles-cap", type=int, default=0)
     ap.add_argument("--kernel", default="tile")
     ap.add_argument("--chunk", type=int, default=8)
     ap.add_argument("--instances", type=int, default=0, help="override the instance count (profiling)")
@@ -410,6 +451,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -212,6 +212,10 @@ uint64_t rteaal_sim_footprint(const rteaal_design *design, uint32_t n_instances)
 typedef struct {
   uint64_t uniform;              /* cycles for every instance if per_instance is NULL */
   const uint32_t *per_instance;  /* host [n_instances], nullable (uneven cycles)      */
+  /* host [n_instances], nullable: the first r[i] cycles of this call are reset
+   * cycles for instance i (RTEAAL_STEP_RESET makes every cycle of every
+   * instance a reset cycle).  Lets one instance reset while others run. */
+  const uint32_t *reset_per_instance;
 } rteaal_cycles;
 
 enum { RTEAAL_STIM_HOLD = 0, RTEAAL_STIM_XORSHIFT = 1, RTEAAL_STIM_BUFFER = 2 };
@@ -246,6 +250,14 @@ enum { RTEAAL_STEP_RESET = 1 };
  * E_TIMEOUT (reported by this or the next call on the sim), E_UNSUPPORTED. */
 int rteaal_step(rteaal_sim *sim, const rteaal_cycles *cycles, const rteaal_stimulus *stimulus,
                 const rteaal_probes *probes /* nullable */, uint32_t flags, void *stream);
+
+/* Return instances [inst_begin, inst_begin + n_inst) to the state of a fresh
+ * sim -- every signal 0 except constants, memories 0 -- and set their
+ * xorshift64 states from host [n_inputs][n_inst] (nullable: all 0).  Other
+ * instances are untouched (a serving loop reuses freed instances this way).
+ * Enqueued on stream; the seed buffer is copied before return. */
+int rteaal_sim_reset_lanes(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst,
+                           const uint64_t *xorshift_seed, void *stream);
 
 /* Blocks until the sim's work on stream is done; returns any pending error. */
 int rteaal_sync(rteaal_sim *sim, void *stream);

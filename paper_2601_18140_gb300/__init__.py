@@ -80,7 +80,8 @@ class rteaal_tune_trial(ctypes.Structure):
 
 
 class rteaal_cycles(ctypes.Structure):
-    _fields_ = [("uniform", _U64), ("per_instance", ctypes.POINTER(_U32))]
+    _fields_ = [("uniform", _U64), ("per_instance", ctypes.POINTER(_U32)),
+                ("reset_per_instance", ctypes.POINTER(_U32))]
 
 
 class rteaal_stimulus(ctypes.Structure):
@@ -96,7 +97,7 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_sim_info", "rteaal_sim_destroy", "rteaal_sim_configure", "rteaal_sim_autotune", "rteaal_sim_footprint", "rteaal_step",
            "rteaal_sync", "rteaal_state_read", "rteaal_state_write", "rteaal_mem_read",
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
-           "rteaal_last_error", "rteaal_step_static"]
+           "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -127,6 +128,7 @@ def lib() -> ctypes.CDLL:
         L.rteaal_step.argtypes = [_P, ctypes.POINTER(rteaal_cycles), ctypes.POINTER(rteaal_stimulus),
                                   ctypes.POINTER(rteaal_probes), _U32, _P]
         L.rteaal_sync.argtypes = [_P, _P]
+        L.rteaal_sim_reset_lanes.argtypes = [_P, _U32, _U32, _P, _P]
         for n in ["rteaal_state_read", "rteaal_state_write"]:
             getattr(L, n).argtypes = [_P, ctypes.POINTER(_U32), _U32, _U32, _U32, _P, _P]
         for n in ["rteaal_mem_read", "rteaal_mem_write", "rteaal_stim_state_read",
@@ -266,6 +268,14 @@ def rteaal_step(sim: int, cycles: rteaal_cycles, stimulus: rteaal_stimulus,
                              _stream_ptr(stream)))
 
 
+def rteaal_sim_reset_lanes(sim: int, inst_begin: int, n_inst: int, xorshift_seed=None, stream=None):
+    seed = None
+    if xorshift_seed is not None:
+        seed = np.ascontiguousarray(xorshift_seed, np.uint64)
+    _check(lib().rteaal_sim_reset_lanes(sim, inst_begin, n_inst,
+                                        None if seed is None else seed.ctypes.data, _stream_ptr(stream)))
+
+
 def rteaal_sync(sim: int, stream=None):
     _check(lib().rteaal_sync(sim, _stream_ptr(stream)))
 
@@ -387,7 +397,8 @@ class Sim:
         self.info = rteaal_sim_info(self.handle)
 
     def step(self, cycles, stimulus: str = "hold", values=None, reset: bool = False,
-             probes=None, probe_mode: str = "last", probe_out=None, stream=None):
+             probes=None, probe_mode: str = "last", probe_out=None, stream=None,
+             reset_per_instance=None):
         """cycles: int or per-instance uint32 array.  values: BUFFER stimulus
         [cycles][n_inputs][n] as a device tensor / pointer, or a numpy array (host).
         probes: signal ids; probe_out: device tensor or None (returns a numpy array)."""
@@ -400,6 +411,11 @@ class Sim:
             assert pc.size == self.n
             keep.append(pc)
             cyc.per_instance = _np_ptr(pc, _U32)
+        if reset_per_instance is not None:
+            rp = np.ascontiguousarray(reset_per_instance, np.uint32)
+            assert rp.size == self.n
+            keep.append(rp)
+            cyc.reset_per_instance = _np_ptr(rp, _U32)
         st = rteaal_stimulus()
         st.mode = {"hold": 0, "xorshift": 1, "buffer": 2}[stimulus]
         if values is not None:
@@ -465,6 +481,9 @@ class Sim:
 
     def write_mem(self, values: np.ndarray, inst_begin: int = 0, stream=None):
         rteaal_mem_write(self.handle, inst_begin, values, stream)
+
+    def reset_lanes(self, inst_begin: int, n_inst: int, xorshift_seed=None, stream=None):
+        rteaal_sim_reset_lanes(self.handle, inst_begin, n_inst, xorshift_seed, stream)
 
     def read_stim_state(self, inst_begin: int = 0, n_inst: int | None = None, stream=None):
         return rteaal_stim_state_read(self.handle, inst_begin,

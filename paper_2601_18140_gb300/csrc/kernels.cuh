@@ -61,6 +61,7 @@ struct DSim {
   int stim_mode;
   const uint64_t* stim;         // [cycles][n_inputs][n_user]
   int reset;
+  const uint32_t* reset_lane;   // [n_pad] leading reset cycles per lane, or null
   const uint32_t* probe_slot;   // EVERY-mode probes (row references)
   uint32_t n_probe;
   uint64_t* probe_out;          // [cycles][n_probe][n_user]
@@ -653,6 +654,12 @@ __device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, co
         v = ldr<V>(s.state, __ldg(&d.reg_src[r]), np, lane);
 #pragma unroll
         for (int t = 0; t < V; t++) v.x[t] &= mk;
+        if (s.reset_lane) {  // instances still in their leading reset cycles
+          const uint64_t init = __ldg(&d.reg_init[r]) & mk;
+#pragma unroll
+          for (int t = 0; t < V; t++)
+            if (cyc < __ldg(&s.reset_lane[lane + t])) v.x[t] = init;
+        }
       }
       str<V>(s.state, __ldg(&d.reg_ref[r]), np, lane, v, am);
     } else {

@@ -208,6 +208,33 @@ __global__ void k_scatter_ref(uint8_t* st, uint32_t n_pad, const uint32_t* refs,
   }
 }
 
+// Fresh-sim values for the lanes of instances [inst0, inst0 + n_inst): every
+// slot 0 except constant slots, memories 0, stimulus states from `xs_in`.
+__global__ void k_reset_lanes(uint8_t* st, uint64_t* mem, uint64_t* xs, uint32_t n_pad,
+                              const uint32_t* slot_ref, uint32_t n_slots, uint32_t const_base,
+                              uint32_t n_consts, const uint64_t* const_value, uint64_t mem_words,
+                              uint32_t n_inputs, const uint64_t* xs_in, const uint32_t* lane_of_user,
+                              uint32_t inst0, uint32_t n_inst) {
+  const size_t n_state = (size_t)n_slots * n_inst, n_mem = (size_t)mem_words * n_inst,
+               n_xs = (size_t)n_inputs * n_inst;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_state + n_mem + n_xs;
+       i += (size_t)gridDim.x * blockDim.x) {
+    size_t j = i;
+    const uint32_t k = (uint32_t)(j % n_inst);
+    const uint32_t lane = lane_of_user ? lane_of_user[inst0 + k] : inst0 + k;
+    if (j < n_state) {
+      const uint32_t slot = (uint32_t)(j / n_inst);
+      const uint64_t v = (slot >= const_base && slot < const_base + n_consts) ? const_value[slot - const_base] : 0ull;
+      st1(st, slot_ref[slot], n_pad, lane, v);
+    } else if ((j -= n_state) < n_mem) {
+      mem[(j / n_inst) * n_pad + lane] = 0ull;
+    } else {
+      j -= n_mem;
+      xs[(j / n_inst) * n_pad + lane] = xs_in ? xs_in[j] : 0ull;
+    }
+  }
+}
+
 // uint64 [row][lane] arrays (memories, stimulus states) <-> a [n][n_inst] device buffer
 __global__ void k_gather(const uint64_t* src, uint32_t n_pad, const uint32_t* rows, uint32_t n_rows,
                          const uint32_t* lane_of_user, uint32_t inst0, uint32_t n_inst,
@@ -302,6 +329,8 @@ struct rteaal_design {
   std::vector<DevBuf> bufs;
   int live_sims = 0;
   std::mutex mu;
+  const uint32_t* d_slot_ref = nullptr;      // [n_slots] row reference of every slot
+  const uint64_t* d_const_value = nullptr;   // [n_consts]
   uint64_t metadata_bytes = 0;
 
   template <typename T>
@@ -331,6 +360,7 @@ struct rteaal_sim {
   uint64_t* mem = nullptr;
   uint64_t* xs = nullptr;
   uint32_t* budget = nullptr;        // [n_pad]
+  uint32_t* reset_lane = nullptr;    // [n_pad] per-lane leading reset cycles
   uint32_t* user_of_lane = nullptr;  // [n_pad] or null
   uint32_t* lane_of_user = nullptr;  // [n_user] or null
   uint32_t* tile_order = nullptr;    // [n_tiles]
@@ -565,6 +595,8 @@ RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaa
       dd.wport = reinterpret_cast<const uint4*>(d->upload(L.wport));
       dd.mem_info = reinterpret_cast<const uint4*>(d->upload(L.mem_info));
       dd.in_w = d->upload(L.in_width);
+      d->d_slot_ref = d->upload(L.slot_ref);
+      d->d_const_value = d->upload(L.const_value);
       dd.n_layers = (uint32_t)L.layer_off.size() - 1;
       dd.n_regs = (uint32_t)L.reg_src.size();
       dd.n_inputs = (uint32_t)L.in_width.size();
@@ -733,6 +765,7 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       s->mem = static_cast<uint64_t*>(s->get(std::max<size_t>(np * 8 * L.mem_words_total, 16)));
       s->xs = static_cast<uint64_t*>(s->get(std::max<size_t>(np * 8 * L.in_width.size(), 16)));
       s->budget = static_cast<uint32_t*>(s->get(np * 4));
+      s->reset_lane = static_cast<uint32_t*>(s->get(np * 4));
       s->tile_order = static_cast<uint32_t*>(s->get(np * 4));   // room for any tile size
       s->tile_cycles = static_cast<uint32_t*>(s->get(np * 4));
       s->scratch = static_cast<uint32_t*>(s->get(256));
@@ -973,6 +1006,12 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       ds.uniform = (uint32_t)max_cyc;
     }
     if (max_cyc == 0) return;
+    if (cycles->reset_per_instance) {
+      std::vector<uint32_t> hr(np, 0);
+      for (uint32_t u = 0; u < s->n_user; u++) hr[s->h_lane_of_user[u]] = cycles->reset_per_instance[u];
+      CK(cudaMemcpyAsync(s->reset_lane, hr.data(), np * 4, cudaMemcpyHostToDevice, st));
+      ds.reset_lane = s->reset_lane;
+    }
 
     // stimulus and probe buffers (host ones go through one device staging buffer)
     const size_t stim_host_bytes = (ds.stim_mode == RTEAAL_STIM_BUFFER && stim->values_on_host)
@@ -1130,6 +1169,34 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       // the caller may reuse its host buffer once we return
       sync_sim(s, st);
     }
+  });
+}
+
+RT_EXPORT int rteaal_sim_reset_lanes(rteaal_sim* s, uint32_t inst0, uint32_t n_inst, const uint64_t* seed,
+                                     void* stream) {
+  return guarded([&] {
+    require(s, "rteaal_sim_reset_lanes: null sim");
+    require((uint64_t)inst0 + n_inst <= s->n_user, "rteaal_sim_reset_lanes: instance range out of bounds");
+    if (n_inst == 0) return;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(s->design->device));
+    check_pending(s);
+    const rteaal_design* D = s->design;
+    const Lowered& L = D->L;
+    const uint32_t ni = (uint32_t)L.in_width.size();
+    const uint64_t* xs_in = nullptr;
+    if (seed && ni) {
+      ensure_staging(s, (size_t)ni * n_inst * 8);
+      CK(cudaMemcpyAsync(s->staging, seed, (size_t)ni * n_inst * 8, cudaMemcpyHostToDevice, st));
+      xs_in = s->staging;
+    }
+    const size_t total = ((size_t)L.n_slots + L.mem_words_total + ni) * n_inst;
+    const uint32_t blocks = (uint32_t)std::min<size_t>((total + 255) / 256, (size_t)D->n_sms * 32);
+    k_reset_lanes<<<blocks, 256, 0, st>>>(s->state, s->mem, s->xs, s->n_pad, D->d_slot_ref, L.n_slots, L.const_base,
+                                          (uint32_t)L.const_value.size(), D->d_const_value, L.mem_words_total,
+                                          ni, xs_in, s->lane_of_user, inst0, n_inst);
+    CK(cudaGetLastError());
+    if (xs_in) CK(cudaStreamSynchronize(st));  // the staging buffer may be reused by the next call
   });
 }
 
