@@ -142,6 +142,17 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(t_ms: float, evals: float, device) -> tuple[float, float]:
+    """Whole-job timing across replicas: the slowest rank's time, the sum of the work."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    ev = torch.tensor([evals], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+    return float(tt[0]), float(ev[0])
+
+
 def shard(n: int, rank: int, world: int) -> tuple[int, int]:
     """Contiguous instance shard of one rank (replicas: no data-path exchange)."""
     lo = n * rank // world
@@ -278,11 +289,7 @@ def run_ours(args) -> None:
     t_max = t_ms
     evals = float(inst_cycles) * nl.n_ops
     if world > 1:
-        t = torch.tensor([t_ms, evals], dtype=torch.float64, device=dev)
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        t_max, evals = float(tt[0]), float(t[1])
+        t_max, evals = reduce_over_ranks(t_ms, evals, dev)
     value = evals / (t_max / 1e3)
 
     # ---- roofline of the dominant kernel (one k_tile launch per step)

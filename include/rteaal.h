@@ -229,15 +229,31 @@ typedef struct {
   int values_on_host;
 } rteaal_stimulus;
 
-enum { RTEAAL_PROBE_LAST = 0, RTEAAL_PROBE_EVERY = 1 };
+enum { RTEAAL_PROBE_LAST = 0, RTEAAL_PROBE_EVERY = 1, RTEAAL_PROBE_CHANGES = 2 };
+
+/* One waveform event (RTEAAL_PROBE_CHANGES): probe `probe` of instance
+ * `instance` took `value` at the end of cycle `cycle` (cycle index relative to
+ * the step) and that differs from its value at the end of the previous cycle
+ * (for cycle 0: its value when the step began).  Waveform generation, Sec. 5.2:
+ * "record signal values when they change". */
+typedef struct {
+  uint32_t cycle, probe, instance, pad;
+  uint64_t value;
+} rteaal_change;
+
 typedef struct {
   const uint32_t *signals;  /* host [n] signal ids */
   uint32_t n;
   int mode;                 /* LAST: out [n][n_instances] after the step;
                                EVERY: out [cycles][n][n_instances], row c written
-                               for instances that ran cycle c (end-of-cycle values) */
+                               for instances that ran cycle c (end-of-cycle values);
+                               CHANGES: out = rteaal_change[capacity], unordered */
   uint64_t *out;            /* device pointer, or host if out_on_host          */
   int out_on_host;          /* host: copied back and synchronised in the call  */
+  uint64_t capacity;        /* CHANGES: records that fit in out                */
+  uint64_t *count;          /* CHANGES: host, receives the number of changes
+                               (more than capacity: the excess was dropped);
+                               the call synchronises                           */
 } rteaal_probes;
 
 enum { RTEAAL_STEP_RESET = 1 };

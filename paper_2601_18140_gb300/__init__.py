@@ -24,7 +24,7 @@ RTEAAL_E_CUDA, RTEAAL_E_TIMEOUT, RTEAAL_E_BUSY, RTEAAL_E_UNSUPPORTED = -4, -5, -
 RTEAAL_KERNEL_AUTO, RTEAAL_KERNEL_LAYER, RTEAAL_KERNEL_TILE = 0, 1, 2
 RTEAAL_KERNEL_GRID, RTEAAL_KERNEL_LAYER_GRAPH, RTEAAL_KERNEL_STREAM = 3, 4, 5
 RTEAAL_STIM_HOLD, RTEAAL_STIM_XORSHIFT, RTEAAL_STIM_BUFFER = 0, 1, 2
-RTEAAL_PROBE_LAST, RTEAAL_PROBE_EVERY = 0, 1
+RTEAAL_PROBE_LAST, RTEAAL_PROBE_EVERY, RTEAAL_PROBE_CHANGES = 0, 1, 2
 RTEAAL_STEP_RESET = 1
 
 KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4, "stream": 5}
@@ -90,7 +90,12 @@ class rteaal_stimulus(ctypes.Structure):
 
 class rteaal_probes(ctypes.Structure):
     _fields_ = [("signals", ctypes.POINTER(_U32)), ("n", _U32), ("mode", ctypes.c_int),
-                ("out", _P), ("out_on_host", ctypes.c_int)]
+                ("out", _P), ("out_on_host", ctypes.c_int), ("capacity", _U64),
+                ("count", ctypes.POINTER(_U64))]
+
+
+CHANGE_DTYPE = np.dtype([("cycle", "<u4"), ("probe", "<u4"), ("instance", "<u4"), ("pad", "<u4"),
+                         ("value", "<u8")])
 
 
 EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rteaal_sim_create",
@@ -398,7 +403,7 @@ class Sim:
 
     def step(self, cycles, stimulus: str = "hold", values=None, reset: bool = False,
              probes=None, probe_mode: str = "last", probe_out=None, stream=None,
-             reset_per_instance=None):
+             reset_per_instance=None, change_capacity: int = 1 << 16):
         """cycles: int or per-instance uint32 array.  values: BUFFER stimulus
         [cycles][n_inputs][n] as a device tensor / pointer, or a numpy array (host).
         probes: signal ids; probe_out: device tensor or None (returns a numpy array)."""
@@ -432,7 +437,16 @@ class Sim:
             keep.append(sig)
             pr = rteaal_probes()
             pr.signals, pr.n = _np_ptr(sig, _U32), sig.size
-            pr.mode = {"last": 0, "every": 1}[probe_mode]
+            pr.mode = {"last": 0, "every": 1, "changes": 2}[probe_mode]
+            if probe_mode == "changes":
+                recs = np.zeros(change_capacity, CHANGE_DTYPE)
+                count = np.zeros(1, np.uint64)
+                pr.out, pr.out_on_host = int(recs.ctypes.data), 1
+                pr.capacity = change_capacity
+                pr.count = _np_ptr(count, _U64)
+                rteaal_step(self.handle, cyc, st, pr, RTEAAL_STEP_RESET if reset else 0, stream)
+                n = int(count[0])
+                return recs[:min(n, change_capacity)], n
             if probe_out is None:
                 ncyc = int(np.max(cycles)) if not np.isscalar(cycles) else int(cycles)
                 rows = ncyc if probe_mode == "every" else 1

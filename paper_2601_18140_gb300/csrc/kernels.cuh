@@ -62,9 +62,13 @@ struct DSim {
   const uint64_t* stim;         // [cycles][n_inputs][n_user]
   int reset;
   const uint32_t* reset_lane;   // [n_pad] leading reset cycles per lane, or null
-  const uint32_t* probe_slot;   // EVERY-mode probes (row references)
+  const uint32_t* probe_slot;   // EVERY / CHANGES probes (row references)
   uint32_t n_probe;
-  uint64_t* probe_out;          // [cycles][n_probe][n_user]
+  uint64_t* probe_out;          // EVERY: [cycles][n_probe][n_user]; CHANGES: records
+  int probe_changes;            // CHANGES mode
+  uint64_t* probe_prev;         // CHANGES: [n_probe][n_pad] previous values
+  unsigned long long* change_count;
+  uint64_t change_cap;
   uint32_t* err;
 };
 
@@ -683,7 +687,8 @@ __device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, co
   });
 }
 
-// (a7) per-cycle probes: end-of-cycle values of selected slots.
+// (a7) per-cycle probes: end-of-cycle values of selected slots, or (waveform
+// mode) one record per value change.
 template <int V>
 __device__ __forceinline__ void probe_items(const DSim& s, const ItemSpace& is, uint32_t cyc) {
   for_rows<V>(is, s.n_probe, [&](uint32_t p, uint32_t lane0) {
@@ -692,8 +697,24 @@ __device__ __forceinline__ void probe_items(const DSim& s, const ItemSpace& is, 
     for (int t = 0; t < V; t++) {
       const uint32_t lane = lane0 + t;
       if (!lane_active(s, lane, cyc)) continue;
-      s.probe_out[((size_t)cyc * s.n_probe + p) * s.n_user + user_of(s, lane)] =
-          ld1(s.state, slot, s.n_pad, lane);
+      const uint64_t v = ld1(s.state, slot, s.n_pad, lane);
+      if (s.probe_changes) {
+        uint64_t* prev = s.probe_prev + (size_t)p * s.n_pad + lane;
+        if (*prev != v) {
+          *prev = v;
+          const unsigned long long k = atomicAdd(s.change_count, 1ull);
+          if (k < s.change_cap) {
+            // 24-byte record {cycle, probe, instance, pad, value}: three 8-byte words
+            // (records are only 8-byte aligned)
+            uint64_t* rec = s.probe_out + 3 * k;
+            rec[0] = (uint64_t)cyc | ((uint64_t)p << 32);
+            rec[1] = (uint64_t)user_of(s, lane);
+            rec[2] = v;
+          }
+        }
+      } else {
+        s.probe_out[((size_t)cyc * s.n_probe + p) * s.n_user + user_of(s, lane)] = v;
+      }
     }
   });
 }

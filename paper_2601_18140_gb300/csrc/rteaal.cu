@@ -369,6 +369,8 @@ struct rteaal_sim {
   uint64_t* staging = nullptr;       // grown on demand (host stimulus / probe buffers)
   size_t staging_bytes = 0;
   uint32_t* probe_slots = nullptr;   // grown on demand
+  uint64_t* probe_prev = nullptr;    // CHANGES probes: previous values [n][n_pad]
+  size_t probe_prev_bytes = 0;
   size_t probe_slots_cap = 0;
   uint32_t* err_host = nullptr;      // pinned
   cudaEvent_t done = nullptr;
@@ -1022,8 +1024,15 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
     if (probing) {
       require(probes->signals && probes->out, "rteaal_step: probes without signals / out");
       probe_mode = probes->mode;
-      require(probe_mode == RTEAAL_PROBE_LAST || probe_mode == RTEAAL_PROBE_EVERY, "rteaal_step: bad probe mode");
-      probe_bytes = (probe_mode == RTEAAL_PROBE_EVERY ? (size_t)max_cyc : 1) * probes->n * s->n_user * 8;
+      require(probe_mode == RTEAAL_PROBE_LAST || probe_mode == RTEAAL_PROBE_EVERY ||
+                  probe_mode == RTEAAL_PROBE_CHANGES,
+              "rteaal_step: bad probe mode");
+      if (probe_mode == RTEAAL_PROBE_CHANGES) {
+        require(probes->count != nullptr, "rteaal_step: CHANGES probes need a count pointer");
+        probe_bytes = (size_t)probes->capacity * sizeof(rteaal_change);
+      } else {
+        probe_bytes = (probe_mode == RTEAAL_PROBE_EVERY ? (size_t)max_cyc : 1) * probes->n * s->n_user * 8;
+      }
     }
     const bool probe_host = probing && probes->out_on_host;
     ensure_staging(s, stim_host_bytes + (probe_host ? probe_bytes : 0));
@@ -1045,10 +1054,28 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       ensure_probe_slots(s, slots.size());
       CK(cudaMemcpyAsync(s->probe_slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice, st));
       probe_dev = probe_host ? s->staging + stim_host_bytes / 8 : probes->out;
-      if (probe_mode == RTEAAL_PROBE_EVERY) {
+      if (probe_mode == RTEAAL_PROBE_EVERY || probe_mode == RTEAAL_PROBE_CHANGES) {
         ds.probe_slot = s->probe_slots;
         ds.n_probe = probes->n;
         ds.probe_out = probe_dev;
+      }
+      if (probe_mode == RTEAAL_PROBE_CHANGES) {
+        // previous values = the probes' values as the step begins, lane order
+        const size_t need = (size_t)probes->n * np * 8;
+        if (s->probe_prev_bytes < need) {
+          s->probe_prev = static_cast<uint64_t*>(s->get(need));
+          s->probe_prev_bytes = need;
+        }
+        const uint32_t blocks = (uint32_t)std::min<size_t>((probes->n * np + 255) / 256, 4096);
+        k_gather_ref<<<blocks, 256, 0, st>>>(s->state, s->n_pad, s->probe_slots, probes->n, nullptr, 0,
+                                             s->n_pad, s->probe_prev);
+        CK(cudaGetLastError());
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(s->scratch + 16);
+        CK(cudaMemsetAsync(cnt, 0, 8, st));
+        ds.probe_changes = 1;
+        ds.probe_prev = s->probe_prev;
+        ds.change_count = cnt;
+        ds.change_cap = probes->capacity;
       }
     }
 
@@ -1162,7 +1189,15 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
                                            0, s->n_user, probe_dev);
       CK(cudaGetLastError());
     }
-    if (probe_host) {
+    if (probing && probe_mode == RTEAAL_PROBE_CHANGES) {
+      uint64_t count = 0;
+      CK(cudaMemcpyAsync(&count, s->scratch + 16, 8, cudaMemcpyDeviceToHost, st));
+      sync_sim(s, st);
+      *probes->count = count;
+      if (probe_host && count)
+        CK(cudaMemcpy(probes->out, probe_dev, (size_t)std::min<uint64_t>(count, probes->capacity) *
+                                                  sizeof(rteaal_change), cudaMemcpyDeviceToHost));
+    } else if (probe_host) {
       CK(cudaMemcpyAsync(probes->out, probe_dev, probe_bytes, cudaMemcpyDeviceToHost, st));
       sync_sim(s, st);
     } else if (stim_host_bytes) {

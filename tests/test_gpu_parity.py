@@ -211,3 +211,30 @@ def test_stream_chunks(n):
     p.step(budgets)
     p.compare()
     p.close()
+
+
+@pytest.mark.parametrize("kernel", ["layer", "tile", "grid", "stream"])
+def test_waveform_changes(kernel):
+    """Device-side change records equal the changes derived from the oracle's trace."""
+    from oracle.waveform import changes
+    nl = small_design(51, n_mems=2)
+    n = 130
+    rng = np.random.default_rng(51)
+    budgets = rng.integers(0, 17, n).astype(np.uint32)
+    p = Pair(nl, n, kernel=kernel, seed=51)
+    p.step(1, reset=True)
+    p.step(5)
+    probes = [0, 3, nl.reg_base, nl.reg_base + 7, nl.op_base + 11, nl.op_base + 400, nl.n_signals - 1]
+    before = p.orc.read(probes)
+    recs, count = p.sim.step(budgets, stimulus="xorshift", probes=probes, probe_mode="changes")
+    tr = p.orc.step(budgets, mode=1, xs=p.oxs, probes=probes, probe_cycles=int(budgets.max()), threads=8)
+    exp = changes(before, tr, budgets)
+    assert count == len(exp) == len(recs)
+    got = np.array(sorted((int(r["cycle"]), int(r["probe"]), int(r["instance"]), int(r["value"]))
+                          for r in recs), dtype=np.uint64).reshape(-1, 4)
+    assert np.array_equal(got, exp)
+    p.compare()
+    recs2, count2 = p.sim.step(3, stimulus="xorshift", probes=probes, probe_mode="changes",
+                               change_capacity=5)
+    assert len(recs2) == min(5, count2)                       # overflow: count kept, records capped
+    p.close()

@@ -312,3 +312,31 @@ def test_reset_sets_init_and_counts_as_a_cycle():
     assert (sim.vals[:, nl.reg_base] == 42).all()
     sim.step(np.array([0, 1, 300], np.uint32))            # uneven cycle counts per instance
     assert [int(t) for t in sim.vals[:, nl.reg_base]] == [42, 43, (42 + 300) % 256]
+
+
+def test_waveform_changes_of_counter_bits():
+    """Bit k of a counter changes exactly at the cycles whose new value is a
+    multiple of 2^k (closed form of a binary counter's toggling)."""
+    from oracle.waveform import changes
+    b = Builder()
+    q = b.reg(8)
+    b.connect(q, b.op("ADD", 8, q, b.const(8, 1)))
+    bits = [b.op("BITS", 1, q, p0=k, p1=k) for k in range(4)]
+    nl = b.build()
+    sim = oracle.OracleSim(nl.to_bytes(), 1)
+    sim.step(1, reset=True)
+    probes = [b.sid(x) for x in bits]
+    before = sim.read(probes)
+    n = 40
+    tr = sim.step(n, probes=probes, probe_cycles=n)
+    ev = changes(before, tr, n)
+    # the bits are combinational on Q: during cycle c (0-based) Q = c, and the
+    # value recorded at the end of cycle c is bit k of c
+    exp = []
+    for c in range(n):
+        for k in range(4):
+            prev = ((c - 1) >> k) & 1 if c > 0 else 0
+            if ((c >> k) & 1) != prev:
+                exp.append((c, k, 0, (c >> k) & 1))
+    assert [tuple(int(x) for x in r) for r in ev] == sorted(exp)
+    assert sum(1 for r in ev if r[1] == 0) == n - 1          # bit 0 toggles every cycle after 0
