@@ -42,6 +42,7 @@ WORKLOADS = {
     "single-200k": (synth.spec_single, 1, (100_000, 100_000)),
     "tiny-2k": (synth.spec_tiny, 1, (10_000, 10_000)),
     "soc-5M": (synth.spec_soc, 1024, (20_000, 20_000)),
+    "mux-1M": (synth.spec_mux, 4096, (1000, 100_000)),
 }
 
 
@@ -77,14 +78,29 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def kernel_source_hash() -> str:
+    """Hash of the device and lowering sources: DRAM counters taken on another
+    version of the kernel do not describe this one."""
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2601_18140_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".cpp", ".hpp")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:12]
+
+
 def profile_traffic(kernel_key: str) -> float | None:
-    """Per-launch DRAM bytes from the committed ncu summary, scaled to the bench launch."""
+    """DRAM bytes per instance-cycle from the committed ncu summary, if they were
+    taken on this kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
+    src = kernel_source_hash()
     for line in open(p):
         parts = line.split()
-        if len(parts) >= 2 and parts[0] == kernel_key:
+        if len(parts) >= 3 and parts[0] == kernel_key and parts[2] == src:
             return float(parts[1])
     return None
 
@@ -178,7 +194,7 @@ def cpu_oracle_rate(nl: synth.Netlist, n_inst: int, cycles: int, seed: int, thre
 
 def cpu_sample_size(workload: str) -> tuple[int, int]:
     return {"batch-1M": (64, 8), "single-200k": (1, 2000), "tiny-2k": (1, 10_000),
-            "soc-5M": (16, 4)}[workload]
+            "soc-5M": (16, 4), "mux-1M": (64, 8)}[workload]
 
 
 def run_reference(args) -> None:
@@ -232,7 +248,7 @@ def run_ours(args) -> None:
     xs_all = synth.xorshift_seeds(5, nl.n_inputs, n_total)
     xs = np.ascontiguousarray(xs_all[:, lo:hi])
 
-    design = rt.Design(nl.to_bytes())
+    design = rt.Design(nl.to_bytes(), fuse_mux_chains=args.fuse_mux_chains)
     kw = dict(tile_lanes=args.tile_lanes, threads=args.threads, unroll=args.unroll,
               ctas_per_sm=args.ctas_per_sm, lanes_per_thread=args.lanes_per_thread)
     sim = rt.Sim(design, n, kernel=args.kernel, xorshift_seed=xs, expected_cycles=budgets, **kw)
@@ -318,7 +334,8 @@ def run_ours(args) -> None:
             o.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=oxs, threads=os.cpu_count() or 1)
             o.step(run_cycles[sample].astype(np.uint32), mode=oracle.STIM_XORSHIFT, xs=oxs,
                    threads=os.cpu_count() or 1)
-            ok = all(np.array_equal(sim.read(None, int(i), 1)[:, 0], o.vals[k])
+            live = design.present_signals()           # every signal unless fusion absorbed some
+            ok = all(np.array_equal(sim.read(live, int(i), 1)[:, 0], o.vals[k][live])
                      for k, i in enumerate(sample))
             parity = ("bit-exact" if ok else "MISMATCH") + " on instances %s after %s cycles" % (
                 list(map(int, sample)), list(map(int, run_cycles[sample])))
@@ -368,6 +385,7 @@ def run_ours(args) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "ops": nl.n_ops, "regs": nl.n_regs,
                        "layers": design.info["n_layers"], "instances": n_total,
+                       "fused_mux_ops": design.info["n_fused"],
                        "cycles_per_step": C, "kernel": args.kernel,
                        "kernel_used": {1: "layer", 2: "tile", 3: "grid", 4: "layer_graph", 5: "stream"}[info["kernel"]],
                        "tile_lanes": info["tile_lanes"], "threads": info["threads"],
@@ -442,6 +460,8 @@ def main():
     ap.add_argument("--quantum", type=int, default=2000)
     ap.add_argument("--cycles-cap", type=int, default=0)
     ap.add_argument("--kernel", default="tile")
+    ap.add_argument("--fuse-mux-chains", action="store_true",
+                    help="fuse single-fanout mux chains into one op (ops are still counted as in the netlist)")
     ap.add_argument("--chunk", type=int, default=8)
     ap.add_argument("--instances", type=int, default=0, help="override the instance count (profiling)")
     ap.add_argument("--tile-lanes", type=int, default=0)

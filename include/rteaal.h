@@ -109,6 +109,12 @@ typedef struct {
 typedef struct {
   const rteaal_allocator *allocator; /* nullable */
   int device;                        /* CUDA ordinal; < 0 = current device */
+  /* Operator fusion (App. B.1, mux-chain extraction): a MUX whose false operand
+   * is another MUX read nowhere else and at least as wide is absorbed, and the
+   * chain is evaluated as one MUXCHAIN.  Absorbed signals are not computed:
+   * reading or probing them is refused (E_INVALID), as the paper disables
+   * signal-eliminating optimizations when every signal must stay visible. */
+  int fuse_mux_chains;
 } rteaal_load_opts;
 
 typedef struct {
@@ -122,6 +128,7 @@ typedef struct {
   uint64_t mem_words_total;  /* words of all memories of one lane               */
   uint64_t metadata_bytes;   /* device bytes owned by the design                */
   uint64_t state_bytes_per_lane; /* compact state bytes of one lane (see layout) */
+  uint32_t n_fused;          /* muxes absorbed by operator fusion               */
 } rteaal_design_stats;
 
 /* Parse, validate, levelise, group by (opcode, width) and upload the lowered
@@ -131,6 +138,11 @@ typedef struct {
 int rteaal_design_load(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
                        rteaal_design **out);
 int rteaal_design_info(const rteaal_design *design, rteaal_design_stats *out);
+/* Which signals hold a row of the state: present[i] = 1 for signal i that can
+ * be read, written and probed, 0 for a mux absorbed by operator fusion.
+ * present: host array of n_signals bytes (caller-owned); n_signals must equal
+ * the design's signal count.  Errors: E_INVALID. */
+int rteaal_design_signals(const rteaal_design *design, uint8_t *present, uint64_t n_signals);
 /* Returns E_BUSY (and frees nothing) while sims created from it are alive. */
 int rteaal_design_free(rteaal_design *design);
 

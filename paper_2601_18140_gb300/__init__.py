@@ -48,7 +48,8 @@ class rteaal_allocator(ctypes.Structure):
 
 
 class rteaal_load_opts(ctypes.Structure):
-    _fields_ = [("allocator", ctypes.POINTER(rteaal_allocator)), ("device", ctypes.c_int)]
+    _fields_ = [("allocator", ctypes.POINTER(rteaal_allocator)), ("device", ctypes.c_int),
+                ("fuse_mux_chains", ctypes.c_int)]
 
 
 class rteaal_design_stats(ctypes.Structure):
@@ -56,7 +57,7 @@ class rteaal_design_stats(ctypes.Structure):
                                     "n_mems", "n_wports", "n_layers", "n_groups", "n_slots",
                                     "n_lowered_ops", "max_layer_ops"]] + \
                [(n, _U64) for n in ["op_operands", "mem_words_total", "metadata_bytes",
-                                    "state_bytes_per_lane"]]
+                                    "state_bytes_per_lane"]] + [("n_fused", _U32)]
 
 
 class rteaal_sim_opts(ctypes.Structure):
@@ -102,7 +103,8 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_sim_info", "rteaal_sim_destroy", "rteaal_sim_configure", "rteaal_sim_autotune", "rteaal_sim_footprint", "rteaal_step",
            "rteaal_sync", "rteaal_state_read", "rteaal_state_write", "rteaal_mem_read",
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
-           "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes"]
+           "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
+           "rteaal_design_signals"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -121,6 +123,7 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(rteaal_load_opts), ctypes.POINTER(_P)]
         L.rteaal_design_info.argtypes = [_P, ctypes.POINTER(rteaal_design_stats)]
         L.rteaal_design_free.argtypes = [_P]
+        L.rteaal_design_signals.argtypes = [_P, _P, _U64]
         L.rteaal_sim_create.argtypes = [_P, _U32, ctypes.POINTER(rteaal_sim_opts), ctypes.POINTER(_P)]
         L.rteaal_sim_info.argtypes = [_P, ctypes.POINTER(rteaal_sim_stats)]
         L.rteaal_sim_destroy.argtypes = [_P]
@@ -224,6 +227,13 @@ def rteaal_design_info(design: int) -> dict:
     st = rteaal_design_stats()
     _check(lib().rteaal_design_info(design, ctypes.byref(st)))
     return {n: getattr(st, n) for n, _ in st._fields_}
+
+
+def rteaal_design_signals(design: int, n_signals: int) -> np.ndarray:
+    """bool [n_signals]: True where the signal holds a row (False: fused away)."""
+    out = np.zeros(n_signals, np.uint8)
+    _check(lib().rteaal_design_signals(design, out.ctypes.data, n_signals))
+    return out.astype(bool)
 
 
 def rteaal_design_free(design: int):
@@ -348,9 +358,11 @@ def rteaal_last_error() -> str:
 class Design:
     """A loaded netlist (owns the handle)."""
 
-    def __init__(self, netlist: bytes, use_torch_allocator: bool = True, device: int = -1):
+    def __init__(self, netlist: bytes, use_torch_allocator: bool = True, device: int = -1,
+                 fuse_mux_chains: bool = False):
         self._opts = rteaal_load_opts()
         self._opts.device = device
+        self._opts.fuse_mux_chains = int(fuse_mux_chains)
         if use_torch_allocator:
             self._alloc = torch_allocator()
             self._opts.allocator = ctypes.pointer(self._alloc)
@@ -359,6 +371,10 @@ class Design:
 
     def footprint(self, n_instances: int) -> int:
         return rteaal_sim_footprint(self.handle, n_instances)
+
+    def present_signals(self) -> np.ndarray:
+        """Ids of the signals that hold a row (all of them unless fusion absorbed some)."""
+        return np.flatnonzero(rteaal_design_signals(self.handle, self.info["n_signals"])).astype(np.uint32)
 
     def close(self):
         if self.handle:

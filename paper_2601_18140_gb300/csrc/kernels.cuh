@@ -23,6 +23,7 @@ struct DDesign {
   const uint32_t* dst;        // [n_lowered] row reference of each op's output
   const uint32_t* ext;        // operand row references of ops with > 3 operands
   const uint32_t* layer_off;  // [n_layers + 1]
+  const uint32_t* layer_ext;  // [n_layers] first op with > 3 operands (they close each layer)
   const uint32_t* reg_src;    // [n_regs] row reference of D
   const uint32_t* reg_ref;    // [n_regs] row reference of Q
   const uint32_t* reg_w;      // [n_regs]
@@ -153,7 +154,7 @@ __device__ __forceinline__ uint64_t alu(uint32_t ctl, uint64_t a, uint64_t b, ui
     case OP_XORR: r = (uint64_t)(__popcll(a) & 1); break;
     default: r = 0; break;
   }
-  return r & wmask((ctl >> 8) & 255u);
+  return r & wmask(ctl_width(ctl));
 }
 
 // Address of element (row, lane) of the compact state.
@@ -185,40 +186,12 @@ __device__ __forceinline__ void st1(uint8_t* st, uint32_t ref, size_t np, uint32
   }
 }
 
-// Ops with more than three operands (variadic folds, long mux chains): one lane.
-__device__ __noinline__ uint64_t eval_ext(const DDesign& d, const DSim& s, uint4 m, uint32_t lane) {
-  const uint32_t op = m.w & 31u, n = m.y;
-  const uint32_t* a = d.ext + m.x;
-  const uint8_t* st = s.state;
-  const size_t np = s.n_pad;
-  uint64_t r;
-  if (op == OP_MUXCHAIN) {
-    r = ld1(st, a[n - 1], np, lane);
-    for (uint32_t i = 0; i + 1 < n; i += 2)
-      if (ld1(st, a[i], np, lane) & 1ull) { r = ld1(st, a[i + 1], np, lane); break; }
-  } else {
-    r = ld1(st, a[0], np, lane);
-    for (uint32_t i = 1; i < n; i++) {
-      const uint64_t x = ld1(st, a[i], np, lane);
-      switch (op) {
-        case OP_AND: r &= x; break;
-        case OP_OR: r |= x; break;
-        case OP_XOR: r ^= x; break;
-        case OP_ADD: r += x; break;
-        case OP_MUL: r *= x; break;
-        default: break;
-      }
-    }
-  }
-  return r & wmask((m.w >> 8) & 255u);
-}
-
 __device__ __forceinline__ uint64_t eval_memrd(const DDesign& d, const DSim& s, uint32_t ctl,
                                                uint64_t addr, uint32_t lane) {
   const uint32_t mi = ((ctl >> 16) & 255u) | ((ctl >> 24) << 8);
   const uint4 info = __ldg(&d.mem_info[mi]);
   const uint64_t v = s.mem[((size_t)info.x + (addr & (uint64_t)info.y)) * s.n_pad + lane];
-  return v & wmask((ctl >> 8) & 255u);
+  return v & wmask(ctl_width(ctl));
 }
 
 template <int V>
@@ -269,7 +242,7 @@ __device__ __forceinline__ Lanes<V> alu_v(uint32_t ctl, const Lanes<V>& a, const
     default: RT_LANES(0ull); break;
   }
 #undef RT_LANES
-  const uint64_t mk = wmask((ctl >> 8) & 255u);
+  const uint64_t mk = wmask(ctl_width(ctl));
 #pragma unroll
   for (int v = 0; v < V; v++) r.x[v] &= mk;
   return r;
@@ -377,6 +350,241 @@ __device__ __forceinline__ Lanes<V> ldr(const uint8_t* st, uint32_t ref, size_t 
   return r;
 }
 
+// ---- narrow ops (CTL_NARROW): operands and result of at most 32 bits, so the
+// whole item stays in 32-bit registers: half the registers, and one
+// instruction per lane where 64-bit arithmetic takes two.
+template <int V>
+struct Lanes32 {
+  uint32_t x[V];
+};
+
+__device__ __forceinline__ uint32_t wmask32(uint32_t w) { return 0xFFFFFFFFu >> (32u - w); }
+
+// V consecutive lanes of a row of class 0, 1 or 2, zero-extended to 32 bits.
+template <int V>
+__device__ __forceinline__ Lanes32<V> ldr32(const uint8_t* st, uint32_t ref, size_t np, uint32_t lane) {
+  Lanes32<V> r;
+  const uint8_t* p = elem(st, ref, np, lane);
+  const uint32_t k = ref >> 30;
+  if constexpr (V == 4) {
+    if (k == 0) {
+      const uint32_t t = *reinterpret_cast<const uint32_t*>(p);
+#pragma unroll
+      for (int v = 0; v < 4; v++) r.x[v] = __byte_perm(t, 0u, 0x4440u + v);
+    } else if (k == 1) {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+      r.x[0] = t.x & 0xFFFFu; r.x[1] = t.x >> 16;
+      r.x[2] = t.y & 0xFFFFu; r.x[3] = t.y >> 16;
+    } else {
+      const uint4 t = *reinterpret_cast<const uint4*>(p);
+      r.x[0] = t.x; r.x[1] = t.y; r.x[2] = t.z; r.x[3] = t.w;
+    }
+  } else if constexpr (V == 8) {
+    if (k == 0) {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        r.x[v] = __byte_perm(t.x, 0u, 0x4440u + v);
+        r.x[4 + v] = __byte_perm(t.y, 0u, 0x4440u + v);
+      }
+    } else if (k == 1) {
+      const uint4 t = *reinterpret_cast<const uint4*>(p);
+      r.x[0] = t.x & 0xFFFFu; r.x[1] = t.x >> 16;
+      r.x[2] = t.y & 0xFFFFu; r.x[3] = t.y >> 16;
+      r.x[4] = t.z & 0xFFFFu; r.x[5] = t.z >> 16;
+      r.x[6] = t.w & 0xFFFFu; r.x[7] = t.w >> 16;
+    } else {
+      const uint4 t0 = reinterpret_cast<const uint4*>(p)[0];
+      const uint4 t1 = reinterpret_cast<const uint4*>(p)[1];
+      r.x[0] = t0.x; r.x[1] = t0.y; r.x[2] = t0.z; r.x[3] = t0.w;
+      r.x[4] = t1.x; r.x[5] = t1.y; r.x[6] = t1.z; r.x[7] = t1.w;
+    }
+  } else if constexpr (V == 2) {
+    if (k == 0) {
+      const uint32_t t = *reinterpret_cast<const uint16_t*>(p);
+      r.x[0] = t & 0xFFu; r.x[1] = t >> 8;
+    } else if (k == 1) {
+      const uint32_t t = *reinterpret_cast<const uint32_t*>(p);
+      r.x[0] = t & 0xFFFFu; r.x[1] = t >> 16;
+    } else {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+      r.x[0] = t.x; r.x[1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; v++) r.x[v] = (uint32_t)ld1(st, ref, np, lane + v);
+  }
+  return r;
+}
+
+// Store the active lanes (mask bit v = lane + v) of a narrow result (class 0..2).
+template <int V>
+__device__ __forceinline__ void str32(uint8_t* st, uint32_t ref, size_t np, uint32_t lane,
+                                      const Lanes32<V>& r, uint32_t m) {
+  uint8_t* p = const_cast<uint8_t*>(elem(st, ref, np, lane));
+  const uint32_t k = ref >> 30;
+  if constexpr (V == 4) {
+    if (m == 15u) {
+      if (k == 0)
+        *reinterpret_cast<uint32_t*>(p) = r.x[0] | (r.x[1] << 8) | (r.x[2] << 16) | (r.x[3] << 24);
+      else if (k == 1)
+        *reinterpret_cast<uint2*>(p) = make_uint2(r.x[0] | (r.x[1] << 16), r.x[2] | (r.x[3] << 16));
+      else
+        *reinterpret_cast<uint4*>(p) = make_uint4(r.x[0], r.x[1], r.x[2], r.x[3]);
+      return;
+    }
+  } else if constexpr (V == 8) {
+    if (m == 255u) {
+      if (k == 0) {
+        *reinterpret_cast<uint2*>(p) =
+            make_uint2(r.x[0] | (r.x[1] << 8) | (r.x[2] << 16) | (r.x[3] << 24),
+                       r.x[4] | (r.x[5] << 8) | (r.x[6] << 16) | (r.x[7] << 24));
+      } else if (k == 1) {
+        *reinterpret_cast<uint4*>(p) = make_uint4(r.x[0] | (r.x[1] << 16), r.x[2] | (r.x[3] << 16),
+                                                  r.x[4] | (r.x[5] << 16), r.x[6] | (r.x[7] << 16));
+      } else {
+        reinterpret_cast<uint4*>(p)[0] = make_uint4(r.x[0], r.x[1], r.x[2], r.x[3]);
+        reinterpret_cast<uint4*>(p)[1] = make_uint4(r.x[4], r.x[5], r.x[6], r.x[7]);
+      }
+      return;
+    }
+  } else if constexpr (V == 2) {
+    if (m == 3u) {
+      if (k == 0) *reinterpret_cast<uint16_t*>(p) = (uint16_t)(r.x[0] | (r.x[1] << 8));
+      else if (k == 1) *reinterpret_cast<uint32_t*>(p) = r.x[0] | (r.x[1] << 16);
+      else *reinterpret_cast<uint2*>(p) = make_uint2(r.x[0], r.x[1]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; v++)
+    if (m & (1u << v)) st1(st, ref, np, lane + v, r.x[v]);
+}
+
+// alu_v in 32-bit arithmetic for narrow ops.  Exactness against the 64-bit
+// definition, with every operand < 2^32 and the result masked to w <= 32 bits:
+// +, -, *, ~, &, |, ^ agree mod 2^32; shifting left by 32 or more leaves no
+// bit below 32, shifting a 32-bit value right by 32 or more leaves 0 (so both
+// give 0, here explicitly); BITS has hi < 32 and ANDR p0 <= 32 (lowering).
+template <int V>
+__device__ __forceinline__ Lanes32<V> alu32_v(uint32_t ctl, const Lanes32<V>& a, const Lanes32<V>& b,
+                                              const Lanes32<V>& c) {
+  const uint32_t op = ctl & 31u, ar = (ctl >> 5) & 3u;
+  const uint32_t p0 = (ctl >> 16) & 255u, p1 = ctl >> 24;
+  Lanes32<V> r;
+#define RT_LANES(expr) _Pragma("unroll") for (int v = 0; v < V; v++) r.x[v] = (expr)
+  switch (op) {
+    case OP_COPY: RT_LANES(a.x[v]); break;
+    case OP_AND: RT_LANES(a.x[v] & b.x[v] & (ar == 3 ? c.x[v] : ~0u)); break;
+    case OP_OR: RT_LANES(a.x[v] | b.x[v] | (ar == 3 ? c.x[v] : 0u)); break;
+    case OP_XOR: RT_LANES(a.x[v] ^ b.x[v] ^ (ar == 3 ? c.x[v] : 0u)); break;
+    case OP_NOT: RT_LANES(~a.x[v]); break;
+    case OP_ADD: RT_LANES(a.x[v] + b.x[v] + (ar == 3 ? c.x[v] : 0u)); break;
+    case OP_SUB: RT_LANES(a.x[v] - b.x[v]); break;
+    case OP_MUL: RT_LANES(a.x[v] * b.x[v] * (ar == 3 ? c.x[v] : 1u)); break;
+    case OP_SHL: RT_LANES(p0 >= 32u ? 0u : a.x[v] << p0); break;
+    case OP_SHR: RT_LANES(p0 >= 32u ? 0u : a.x[v] >> p0); break;
+    case OP_DSHL: RT_LANES(b.x[v] >= 32u ? 0u : a.x[v] << b.x[v]); break;
+    case OP_DSHR: RT_LANES(b.x[v] >= 32u ? 0u : a.x[v] >> b.x[v]); break;
+    case OP_BITS: {
+      const uint32_t m = wmask32(p0 - p1 + 1u);
+      RT_LANES((a.x[v] >> p1) & m);
+    } break;
+    case OP_CAT: RT_LANES((p0 >= 32u ? 0u : a.x[v] << p0) | b.x[v]); break;
+    case OP_EQ: RT_LANES((uint32_t)(a.x[v] == b.x[v])); break;
+    case OP_NEQ: RT_LANES((uint32_t)(a.x[v] != b.x[v])); break;
+    case OP_LT: RT_LANES((uint32_t)(a.x[v] < b.x[v])); break;
+    case OP_LEQ: RT_LANES((uint32_t)(a.x[v] <= b.x[v])); break;
+    case OP_GT: RT_LANES((uint32_t)(a.x[v] > b.x[v])); break;
+    case OP_GEQ: RT_LANES((uint32_t)(a.x[v] >= b.x[v])); break;
+    case OP_MUX: RT_LANES((a.x[v] & 1u) ? b.x[v] : c.x[v]); break;
+    case OP_ANDR: {
+      const uint32_t m = wmask32(p0);
+      RT_LANES((uint32_t)((a.x[v] & m) == m));
+    } break;
+    case OP_ORR: RT_LANES((uint32_t)(a.x[v] != 0u)); break;
+    case OP_XORR: RT_LANES((uint32_t)(__popc(a.x[v]) & 1)); break;
+    default: RT_LANES(0u); break;
+  }
+#undef RT_LANES
+  const uint32_t mk = wmask32(ctl_width(ctl));
+#pragma unroll
+  for (int v = 0; v < V; v++) r.x[v] &= mk;
+  return r;
+}
+
+// Ops with more than three operands (long mux chains from operator fusion,
+// variadic folds), V lanes at a time: every operand row is one packed load.
+// LT is Lanes<V> (64-bit) or Lanes32<V> (narrow ops); ld(ref) loads a row.
+template <int V, typename LT, typename Load>
+__device__ __forceinline__ LT ext_eval(const uint32_t* a, uint32_t op, uint32_t n, Load&& ld) {
+  LT r;
+  if (op == OP_MUXCHAIN) {
+    // first set selector wins: walk the pairs in O order, a lane keeps the
+    // first value whose selector is set, else the default.  The first four
+    // pairs are unrolled so their operand loads are issued together.
+    const uint32_t pairs = (n - 1u) >> 1;
+    r = ld(__ldg(&a[n - 1]));
+    uint32_t done = 0;  // bit v: lane + v already decided
+    auto pair = [&](uint32_t i) {
+      const LT sel = ld(__ldg(&a[2 * i]));
+      const LT val = ld(__ldg(&a[2 * i + 1]));
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        const bool take = (sel.x[v] & 1u) && !((done >> v) & 1u);
+        r.x[v] = take ? val.x[v] : r.x[v];
+        done |= (uint32_t)(sel.x[v] & 1u) << v;
+      }
+    };
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+      if ((uint32_t)i < pairs) pair((uint32_t)i);
+    for (uint32_t i = 4; i < pairs; i++) pair(i);
+  } else {
+    r = ld(__ldg(&a[0]));
+    for (uint32_t i = 1; i < n; i++) {
+      const LT x = ld(__ldg(&a[i]));
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        switch (op) {
+          case OP_AND: r.x[v] &= x.x[v]; break;
+          case OP_OR: r.x[v] |= x.x[v]; break;
+          case OP_XOR: r.x[v] ^= x.x[v]; break;
+          case OP_ADD: r.x[v] += x.x[v]; break;
+          case OP_MUL: r.x[v] *= x.x[v]; break;
+          default: break;
+        }
+      }
+    }
+  }
+  return r;
+}
+
+template <int V>
+__device__ __forceinline__ Lanes<V> eval_ext_v(const DDesign& d, const DSim& s, uint4 m, uint32_t lane) {
+  Lanes<V> r = ext_eval<V, Lanes<V>>(d.ext + m.x, m.w & 31u, m.y, [&](uint32_t ref) {
+    return ldr<V>(s.state, ref, s.n_pad, lane);
+  });
+  const uint64_t mk = wmask(ctl_width(m.w));
+#pragma unroll
+  for (int v = 0; v < V; v++) r.x[v] &= mk;
+  return r;
+}
+
+// The same in 32-bit arithmetic for narrow ops (operands and result <= 32
+// bits; the folds agree mod 2^32, selection moves values unchanged).
+template <int V>
+__device__ __forceinline__ Lanes32<V> eval_ext32_v(const DDesign& d, const DSim& s, uint4 m,
+                                                   uint32_t lane) {
+  Lanes32<V> r = ext_eval<V, Lanes32<V>>(d.ext + m.x, m.w & 31u, m.y, [&](uint32_t ref) {
+    return ldr32<V>(s.state, ref, s.n_pad, lane);
+  });
+  const uint32_t mk = wmask32(ctl_width(m.w));
+#pragma unroll
+  for (int v = 0; v < V; v++) r.x[v] &= mk;
+  return r;
+}
+
 // Activity of V consecutive lanes as a bit mask (bit v = lane + v active).
 template <int V>
 __device__ __forceinline__ uint32_t act_mask(const DSim& s, uint32_t lane, uint32_t cyc) {
@@ -464,31 +672,42 @@ __device__ __forceinline__ void str(uint8_t* st, uint32_t ref, size_t np, uint32
     if (m & (1u << v)) st1(st, ref, np, lane + v, r.x[v]);
 }
 
-// Operand gather of one op for V lanes (OI = LI . OIM for this s coordinate).
+// One narrow item: gather, evaluate, store.
+template <int V>
+__device__ __forceinline__ void item32(uint8_t* st, size_t np, uint32_t lane, const uint4& m,
+                                       uint32_t dref, uint32_t am) {
+  Lanes32<V> a, b, c;
+  const uint32_t ar = (m.w >> 5) & 3u;
+  a = ldr32<V>(st, m.x, np, lane);
+#pragma unroll
+  for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0u;
+  if (ar >= 2) b = ldr32<V>(st, m.y, np, lane);
+  if (ar >= 3) c = ldr32<V>(st, m.z, np, lane);
+  str32<V>(st, dref, np, lane, alu32_v<V>(m.w, a, b, c), am);
+}
+
+// Operand gather of one op with at most three operands for V lanes
+// (OI = LI . OIM for this s coordinate).
 template <int V>
 __device__ __forceinline__ void gather(const uint8_t* st, size_t np, uint32_t lane, const uint4& m,
                                        Lanes<V>& a, Lanes<V>& b, Lanes<V>& c) {
 #pragma unroll
   for (int v = 0; v < V; v++) a.x[v] = b.x[v] = c.x[v] = 0;
-  if (!(m.w & CTL_EXT)) {
-    const uint32_t ar = (m.w >> 5) & 3u;
-    a = ldr<V>(st, m.x, np, lane);
-    if (ar >= 2) b = ldr<V>(st, m.y, np, lane);
-    if (ar >= 3) c = ldr<V>(st, m.z, np, lane);
-  }
+  const uint32_t ar = (m.w >> 5) & 3u;
+  a = ldr<V>(st, m.x, np, lane);
+  if (ar >= 2) b = ldr<V>(st, m.y, np, lane);
+  if (ar >= 3) c = ldr<V>(st, m.z, np, lane);
 }
 
-// op_u / op_r / op_s of one op for V lanes, from gathered operands.
+// op_u / op_r / op_s of one op with at most three operands for V lanes, from
+// gathered operands.
 template <int V>
 __device__ __forceinline__ Lanes<V> apply(const DDesign& d, const DSim& s, const uint4& m,
                                           const Lanes<V>& a, const Lanes<V>& b, const Lanes<V>& c,
                                           uint32_t lane) {
   const uint32_t ctl = m.w;
   Lanes<V> r;
-  if (ctl & CTL_EXT) {
-#pragma unroll
-    for (int v = 0; v < V; v++) r.x[v] = eval_ext(d, s, m, lane + v);
-  } else if ((ctl & 31u) == OP_MEMRD) {
+  if ((ctl & 31u) == OP_MEMRD) {
 #pragma unroll
     for (int v = 0; v < V; v++) r.x[v] = eval_memrd(d, s, ctl, a.x[v], lane + v);
   } else {
@@ -530,7 +749,8 @@ __device__ __noinline__ void eval_ops_generic(const DDesign& d, const DSim& s, u
 }
 
 
-// (a2) evaluate ops [op0, op0 + n_rows) of the lowered list.  U ops are issued
+// (a2) evaluate ops [op0, op0 + n_rows) of the lowered list, none of them with
+// more than three operands.  U ops are issued
 // per thread before any result is stored, so all their operand loads are in
 // flight together (memory-level parallelism).
 template <int V, int U>
@@ -562,10 +782,14 @@ __device__ __forceinline__ void eval_ops(const DDesign& d, const DSim& s, uint32
           mn = __ldg(&meta[rn]);
           dn = __ldg(&dst[rn]);
         }
-        Lanes<V> va, vb, vc;
-        gather<V>(s.state, np, is.lane, m, va, vb, vc);
-        const Lanes<V> res = apply<V>(d, s, m, va, vb, vc, is.lane);
-        str<V>(s.state, dref, np, is.lane, res, am);
+        if (m.w & CTL_NARROW) {
+          item32<V>(s.state, np, is.lane, m, dref, am);
+        } else {
+          Lanes<V> va, vb, vc;
+          gather<V>(s.state, np, is.lane, m, va, vb, vc);
+          const Lanes<V> res = apply<V>(d, s, m, va, vb, vc, is.lane);
+          str<V>(s.state, dref, np, is.lane, res, am);
+        }
         if (rn >= n_rows) break;
         r = rn;
         m = mn;
@@ -609,6 +833,50 @@ __device__ __forceinline__ void for_rows(const ItemSpace& is, uint32_t n_rows, F
       f(r, is.lane_base + (i - r * is.tpo.d) * V);
     }
   }
+}
+
+// Ops [op0, op0 + n_rows) with more than three operands (fused mux chains,
+// wide folds), after the layer's common loop.
+template <int V>
+__device__ __forceinline__ void eval_ext_rows(const DDesign& d, const DSim& s, uint32_t op0,
+                                           uint32_t n_rows, const ItemSpace& is, uint32_t cyc) {
+  if (is.row_stride) {  // fixed lane chunk: activity once, descriptor one row ahead
+    if (is.row0 == NO_ROW || is.row0 >= n_rows) return;
+    const uint32_t am = act_mask<V>(s, is.lane, cyc);
+    if (!am) return;
+    uint32_t r = is.row0;
+    uint4 m = __ldg(&d.meta[op0 + r]);
+    for (;;) {
+      const uint32_t rn = r + is.row_stride;
+      const uint4 mn = rn < n_rows ? __ldg(&d.meta[op0 + rn]) : m;
+      const uint32_t dref = __ldg(&d.dst[op0 + r]);
+      if (m.w & CTL_NARROW)
+        str32<V>(s.state, dref, s.n_pad, is.lane, eval_ext32_v<V>(d, s, m, is.lane), am);
+      else
+        str<V>(s.state, dref, s.n_pad, is.lane, eval_ext_v<V>(d, s, m, is.lane), am);
+      if (rn >= n_rows) break;
+      r = rn;
+      m = mn;
+    }
+    return;
+  }
+  for_rows<V>(is, n_rows, [&](uint32_t r, uint32_t lane) {
+    const uint32_t am = act_mask<V>(s, lane, cyc);
+    if (!am) return;
+    const Lanes<V> res = eval_ext_v<V>(d, s, __ldg(&d.meta[op0 + r]), lane);
+    str<V>(s.state, __ldg(&d.dst[op0 + r]), s.n_pad, lane, res, am);
+  });
+}
+
+// (a2) one layer: its ops with at most three operands, then the others, in
+// one phase (no dependence inside a layer).
+template <int V, int U>
+__device__ __forceinline__ void eval_layer(const DDesign& d, const DSim& s, uint32_t L,
+                                           const ItemSpace& is, uint32_t cyc) {
+  const uint32_t o0 = __ldg(&d.layer_off[L]), e = __ldg(&d.layer_ext[L]);
+  const uint32_t o1 = __ldg(&d.layer_off[L + 1]);
+  eval_ops<V, U>(d, s, o0, e - o0, is, cyc);
+  if (e < o1) eval_ext_rows<V>(d, s, e, o1 - e, is, cyc);
 }
 
 // (a1) primary inputs for cycle cyc.

@@ -103,28 +103,94 @@ bool parse_netlist(const void* bytes, size_t nbytes, Netlist& n, std::string& er
   return true;
 }
 
-void lower_netlist(const Netlist& nl, Lowered& L) {
+void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
   const uint32_t nsig = nl.n_signals(), opb = nl.op_base();
+  constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+  // 0. operator fusion (optional): a MUX whose false operand (O = 2) is another
+  //    MUX read nowhere else, and at least as wide, absorbs it; the chain becomes
+  //    one MUXCHAIN s0, v0, s1, v1, ..., default.  Every absorbed width >= the head
+  //    width, so the inner masks vanish under the head's mask.
+  std::vector<uint32_t> fanout(nsig, 0);
+  for (uint32_t j = 0; j < nl.na; j++) fanout[nl.args[j]]++;
+  for (uint32_t r = 0; r < nl.nr; r++) fanout[nl.reg_d[r]]++;
+  for (uint32_t q = 0; q < nl.nw; q++)
+    for (int t = 1; t < 4; t++) fanout[nl.wport[4ull * q + t]]++;
+  std::vector<uint8_t> absorbed(nl.no, 0);
+  std::vector<uint32_t> head_args_off, head_args;  // CSR of fused operand lists (signal ids)
+  std::vector<uint32_t> head_of(nl.no, NONE);      // netlist op -> index into head_args_off
+  if (fuse_mux_chains) {
+    auto fusable = [&](uint32_t sig, uint32_t head_w) {
+      if (sig < opb) return false;
+      const uint32_t k = sig - opb;
+      return nl.code[k] == OP_MUX && fanout[sig] == 1 && nl.width[k] >= head_w;
+    };
+    head_args_off.push_back(0);
+    for (int64_t kk = (int64_t)nl.no - 1; kk >= 0; kk--) {  // heads are found from the top down
+      const uint32_t k = (uint32_t)kk;
+      if (absorbed[k] || nl.code[k] != OP_MUX) continue;
+      const uint32_t w0 = nl.width[k];
+      uint32_t cur = k;
+      if (!fusable(nl.args[nl.argoff[cur] + 2], w0)) continue;
+      std::vector<uint32_t> a;
+      for (;;) {
+        const uint32_t* x = &nl.args[nl.argoff[cur]];
+        a.push_back(x[0]);
+        a.push_back(x[1]);
+        if (!fusable(x[2], w0)) {
+          a.push_back(x[2]);
+          break;
+        }
+        cur = x[2] - opb;
+        absorbed[cur] = 1;
+      }
+      head_of[k] = (uint32_t)head_args_off.size() - 1;
+      head_args.insert(head_args.end(), a.begin(), a.end());
+      head_args_off.push_back((uint32_t)head_args.size());
+    }
+  }
+  auto op_args = [&](uint32_t k, std::vector<uint32_t>& out) {
+    out.clear();
+    if (head_of[k] != NONE)
+      out.assign(head_args.begin() + head_args_off[head_of[k]], head_args.begin() + head_args_off[head_of[k] + 1]);
+    else
+      out.assign(nl.args.begin() + nl.argoff[k], nl.args.begin() + nl.argoff[k + 1]);
+  };
 
   // 1. levelisation: level(pool) = 0, level(op) = 1 + max level of its operands.
   std::vector<uint32_t> level(nsig, 0);
+  std::vector<uint32_t> tmp;
   for (uint32_t k = 0; k < nl.no; k++) {
+    if (absorbed[k]) continue;
+    op_args(k, tmp);
     uint32_t lv = 0;
-    for (uint32_t j = nl.argoff[k]; j < nl.argoff[k + 1]; j++) lv = std::max(lv, level[nl.args[j]]);
+    for (uint32_t x : tmp) lv = std::max(lv, level[x]);
     level[opb + k] = lv + 1;
   }
 
-  // 2. lowered op list: netlist ops plus a COPY (level 1) for every register D or
-  //    write-port signal that is not an op output, so that the clock edge reads only
-  //    op slots (no hazard with the register writes or the next cycle's inputs).
+  // 2. lowered op list: netlist ops (fused heads as MUXCHAIN, absorbed muxes
+  //    dropped) plus a COPY (level 1) for every register D or write-port signal
+  //    that is not an op output, so that the clock edge reads only op slots (no
+  //    hazard with the register writes or the next cycle's inputs).
   struct LOp {
     uint32_t level, code, width, p0, p1, src_sig;  // src_sig: netlist op index, or copy source
     bool is_copy;
+    bool is_ext;  // more than three operands: operand rows in the side array
   };
   std::vector<LOp> ops;
   ops.reserve(nl.no + 16);
-  for (uint32_t k = 0; k < nl.no; k++)
-    ops.push_back({level[opb + k], nl.code[k], nl.width[k], nl.p0[k], nl.p1[k], k, false});
+  std::vector<uint32_t> lop_of(nl.no, NONE);
+  L.n_fused = 0;
+  for (uint32_t k = 0; k < nl.no; k++) {
+    if (absorbed[k]) {
+      L.n_fused++;
+      continue;
+    }
+    lop_of[k] = (uint32_t)ops.size();
+    const uint32_t code = head_of[k] != NONE ? (uint32_t)OP_MUXCHAIN : nl.code[k];
+    op_args(k, tmp);
+    ops.push_back({level[opb + k], code, nl.width[k], nl.p0[k], nl.p1[k], k, false, tmp.size() > 3});
+  }
   std::unordered_map<uint32_t, uint32_t> copy_of;  // pool signal -> lowered op index
   std::vector<uint8_t> sig_w(nsig);
   for (uint32_t i = 0; i < nl.ni; i++) sig_w[i] = nl.in_w[i];
@@ -132,11 +198,11 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
   for (uint32_t i = 0; i < nl.nc; i++) sig_w[nl.ni + nl.nr + i] = nl.const_w[i];
   for (uint32_t k = 0; k < nl.no; k++) sig_w[opb + k] = nl.width[k];
   auto edge_src = [&](uint32_t sig) -> int64_t {  // lowered op index that holds sig
-    if (sig >= opb) return (int64_t)(sig - opb);
+    if (sig >= opb) return (int64_t)lop_of[sig - opb];
     auto it = copy_of.find(sig);
     if (it != copy_of.end()) return it->second;
     const uint32_t idx = (uint32_t)ops.size();
-    ops.push_back({1u, OP_COPY, sig_w[sig], 0u, 0u, sig, true});
+    ops.push_back({1u, OP_COPY, sig_w[sig], 0u, 0u, sig, true, false});
     copy_of[sig] = idx;
     return idx;
   };
@@ -147,13 +213,16 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
     for (int t = 0; t < 3; t++) wp_lop[3ull * q + t] = edge_src(nl.wport[4ull * q + 1 + t]);
   L.n_copies = (uint32_t)copy_of.size();
 
-  // 3. order: by level, then (opcode, width) -- the N rank swizzled above S --
-  //    then original order.  Position = slot offset (S coordinates implicit).
+  // 3. order: by level, then ops with at most three operands before the others
+  //    (so kernels walk each kind with its own loop), then (opcode, width) --
+  //    the N rank swizzled above S -- then original order.  Position = slot
+  //    offset (S coordinates implicit).
   std::vector<uint32_t> order(ops.size());
   std::iota(order.begin(), order.end(), 0u);
   std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
     const LOp &a = ops[x], &b = ops[y];
     if (a.level != b.level) return a.level < b.level;
+    if (a.is_ext != b.is_ext) return b.is_ext;
     if (a.code != b.code) return a.code < b.code;
     return a.width < b.width;
   });
@@ -167,7 +236,7 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
   L.n_slots = opb + (uint32_t)ops.size();
   L.sig2slot.resize(nsig);
   for (uint32_t s = 0; s < opb; s++) L.sig2slot[s] = s;
-  for (uint32_t k = 0; k < nl.no; k++) L.sig2slot[opb + k] = opb + pos[k];
+  for (uint32_t k = 0; k < nl.no; k++) L.sig2slot[opb + k] = lop_of[k] == NONE ? NONE : opb + pos[lop_of[k]];
 
   // 3b. compact layout: width class of every slot, row references
   {
@@ -202,6 +271,7 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
   uint32_t n_layers = 0;
   for (const LOp& o : ops) n_layers = std::max(n_layers, o.level);
   L.layer_off.assign(n_layers + 1, 0);
+  L.layer_ext.assign(n_layers, NONE);
   L.group_off.clear();
   for (uint32_t i = 0; i < order.size(); i++) {
     const LOp& o = ops[order[i]];
@@ -210,13 +280,17 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
     if (o.is_copy) {
       a.push_back(ref_of_sig(o.src_sig));
     } else {
-      const uint32_t k = o.src_sig;
-      for (uint32_t j = nl.argoff[k]; j < nl.argoff[k + 1]; j++) a.push_back(ref_of_sig(nl.args[j]));
+      op_args(o.src_sig, tmp);
+      for (uint32_t x : tmp) a.push_back(ref_of_sig(x));
       if (code == OP_MUXCHAIN && a.size() == 3) code = OP_MUX;  // one pair + default == mux
     }
     L.lowered_operands += a.size();
     OpMeta m{};
     uint32_t ctl = code | (o.width << 8) | (o.p0 << 16) | (o.p1 << 24);
+    bool narrow = o.width <= 32 && code != OP_MEMRD &&
+                  (code != OP_BITS || o.p0 < 32) && (code != OP_ANDR || o.p0 <= 32);
+    for (uint32_t r : a) narrow = narrow && (r >> 30) <= 2u;  // operand rows of at most 32 bits
+    if (narrow) ctl |= CTL_NARROW;
     if (a.size() <= 3) {
       m.a = a[0];
       m.b = a.size() > 1 ? a[1] : a[0];
@@ -231,6 +305,7 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
     }
     m.ctl = ctl;
     L.meta[i] = m;
+    if ((ctl & CTL_EXT) && L.layer_ext[o.level - 1] == NONE) L.layer_ext[o.level - 1] = i;
     L.layer_off[o.level] = i + 1;  // running end of the layer
     if (i == 0 || ops[order[i - 1]].level != o.level || ops[order[i - 1]].code != o.code ||
         ops[order[i - 1]].width != o.width)
@@ -243,6 +318,8 @@ void lower_netlist(const Netlist& nl, Lowered& L) {
   std::vector<uint32_t> ends(L.layer_off.begin() + 1, L.layer_off.end());
   L.layer_off[0] = 0;
   for (uint32_t l = 0; l < n_layers; l++) L.layer_off[l + 1] = ends[l];
+  for (uint32_t l = 0; l < n_layers; l++)
+    if (L.layer_ext[l] == NONE) L.layer_ext[l] = L.layer_off[l + 1];
   L.max_layer_ops = 0;
   for (uint32_t l = 0; l < n_layers; l++)
     L.max_layer_ops = std::max(L.max_layer_ops, L.layer_off[l + 1] - L.layer_off[l]);

@@ -20,8 +20,14 @@ enum Opcode : uint8_t {
 };
 
 // ctl word of a lowered op: opcode (5 bits) | arity (2 bits, 1..3) << 5 |
-// extended-operand flag << 7 | width << 8 | p0 << 16 | p1 << 24.
+// extended-operand flag << 7 | width (7 bits) << 8 | narrow flag << 15 |
+// p0 << 16 | p1 << 24.  Narrow: the result and every operand fit 32 bits, so
+// the op may be evaluated in 32-bit arithmetic (exact: the result is masked to
+// at most 32 bits, and every opcode's low 32 bits depend only on the operands'
+// low 32 bits or are 0 -- shifts by 32 or more, see the kernels).
 constexpr uint32_t CTL_EXT = 1u << 7;
+constexpr uint32_t CTL_NARROW = 1u << 15;
+inline constexpr uint32_t ctl_width(uint32_t ctl) { return (ctl >> 8) & 127u; }
 
 // Row reference: width class k (bytes per lane = 1 << k) in bits 30..31, the
 // row's per-lane byte offset in bits 0..29.  Element (row, lane) of a state
@@ -62,6 +68,8 @@ struct Lowered {
   std::vector<OpMeta> meta;              // [n_lowered] in slot order
   std::vector<uint32_t> ext_args;        // operand row references of ops with > 3 operands
   std::vector<uint32_t> layer_off;       // [n_layers + 1] into meta
+  std::vector<uint32_t> layer_ext;       // [n_layers] first op of the layer with > 3 operands
+                                         //   (they close the layer), or the layer's end
   std::vector<uint32_t> group_off;       // [n_groups + 1] into meta ((layer, opcode, width) runs)
   std::vector<uint32_t> reg_src;         // [n_regs] row reference of D (always an op row)
   std::vector<uint32_t> reg_width;       // [n_regs]
@@ -74,11 +82,14 @@ struct Lowered {
   uint64_t mem_words_total = 0;
   uint64_t op_operands = 0;              // sum of operand counts over netlist ops
   uint32_t n_copies = 0;                 // copies inserted for edge sources
+  uint32_t n_fused = 0;                  // muxes absorbed into mux chains
   uint32_t max_layer_ops = 0;
   // per-op-eval algorithmic bytes bookkeeping: sum over lowered ops of operands read
   uint64_t lowered_operands = 0;
 };
 
-void lower_netlist(const Netlist& nl, Lowered& out);
+// fuse_mux_chains: operator fusion of single-fanout mux chains into MUXCHAIN ops
+// (the absorbed muxes are not computed and their signals have no row).
+void lower_netlist(const Netlist& nl, Lowered& out, bool fuse_mux_chains = false);
 
 }  // namespace rteaal

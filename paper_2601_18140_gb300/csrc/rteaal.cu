@@ -33,12 +33,11 @@ namespace rteaal {
 // ------------------------------------------------------------------ kernels
 
 template <int V, int U>
-__global__ void __launch_bounds__(256) k_layer_ops(DDesign d, DSim s, uint32_t op0,
-                                                   uint32_t n_rows, FastDiv tpo, uint32_t cyc,
-                                                   const uint32_t* cyc_dev) {
+__global__ void __launch_bounds__(256) k_layer_ops(DDesign d, DSim s, uint32_t layer, FastDiv tpo,
+                                                   uint32_t cyc, const uint32_t* cyc_dev) {
   if (cyc_dev) cyc = *cyc_dev;
   const ItemSpace is = make_space<V>(tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-  eval_ops<V, U>(d, s, op0, n_rows, is, cyc);
+  eval_layer<V, U>(d, s, layer, is, cyc);
 }
 
 template <int V>
@@ -91,8 +90,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_tile(DDesign d, DSim s, TileArgs
       stim_items<V>(d, s, RT_SPACE, c);
       __syncthreads();
       for (uint32_t L = 0; L < d.n_layers; L++) {
-        const uint32_t o0 = __ldg(&d.layer_off[L]), o1 = __ldg(&d.layer_off[L + 1]);
-        eval_ops<V, U>(d, s, o0, o1 - o0, RT_SPACE, c);
+        eval_layer<V, U>(d, s, L, RT_SPACE, c);
         __syncthreads();
       }
       commit_items<V>(d, s, RT_SPACE, c);
@@ -166,8 +164,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs
     stim_items<V>(d, s, RT_SPACE, c);
     if (!grid_sync(g, s.err, &sh_ok)) return;
     for (uint32_t L = 0; L < d.n_layers; L++) {
-      const uint32_t o0 = __ldg(&d.layer_off[L]), o1 = __ldg(&d.layer_off[L + 1]);
-      eval_ops<V, U>(d, s, o0, o1 - o0, RT_SPACE, c);
+      eval_layer<V, U>(d, s, L, RT_SPACE, c);
       if (!grid_sync(g, s.err, &sh_ok)) return;
     }
     commit_items<V>(d, s, RT_SPACE, c);
@@ -486,11 +483,11 @@ void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32
     const uint32_t o0 = D->L.layer_off[l], o1 = D->L.layer_off[l + 1];
     const uint64_t items = (uint64_t)(o1 - o0) * tpo.d;
     if (U >= 4)
-      k_layer_ops<V, 4><<<blocks_for(items, 4), threads, 0, st>>>(dd, ds, o0, o1 - o0, tpo, c, cyc_dev);
+      k_layer_ops<V, 4><<<blocks_for(items, 4), threads, 0, st>>>(dd, ds, l, tpo, c, cyc_dev);
     else if (U == 2)
-      k_layer_ops<V, 2><<<blocks_for(items, 2), threads, 0, st>>>(dd, ds, o0, o1 - o0, tpo, c, cyc_dev);
+      k_layer_ops<V, 2><<<blocks_for(items, 2), threads, 0, st>>>(dd, ds, l, tpo, c, cyc_dev);
     else
-      k_layer_ops<V, 1><<<blocks_for(items, 1), threads, 0, st>>>(dd, ds, o0, o1 - o0, tpo, c, cyc_dev);
+      k_layer_ops<V, 1><<<blocks_for(items, 1), threads, 0, st>>>(dd, ds, l, tpo, c, cyc_dev);
   }
   const uint64_t citems = (uint64_t)(D->L.reg_src.size() + (D->L.mem_info.size() / 4 - 1)) * tpo.d;
   if (citems)
@@ -581,7 +578,7 @@ RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaa
       if (opts && opts->device >= 0) CK(cudaSetDevice(opts->device));
       CK(cudaGetDevice(&d->device));
       CK(cudaDeviceGetAttribute(&d->n_sms, cudaDevAttrMultiProcessorCount, d->device));
-      lower_netlist(d->nl, d->L);
+      lower_netlist(d->nl, d->L, opts && opts->fuse_mux_chains);
       const Lowered& L = d->L;
       DDesign& dd = d->dd;
       static_assert(sizeof(OpMeta) == sizeof(uint4), "descriptor is 16 bytes");
@@ -591,6 +588,7 @@ RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaa
       dd.in_ref = d->upload(L.in_ref);
       dd.ext = d->upload(L.ext_args);
       dd.layer_off = d->upload(L.layer_off);
+      dd.layer_ext = d->upload(L.layer_ext);
       dd.reg_src = d->upload(L.reg_src);
       dd.reg_w = d->upload(L.reg_width);
       dd.reg_init = d->upload(L.reg_init);
@@ -633,6 +631,15 @@ RT_EXPORT int rteaal_design_info(const rteaal_design* d, rteaal_design_stats* o)
     o->mem_words_total = L.mem_words_total;
     o->metadata_bytes = d->metadata_bytes;
     o->state_bytes_per_lane = L.lane_bytes;
+    o->n_fused = L.n_fused;
+  });
+}
+
+RT_EXPORT int rteaal_design_signals(const rteaal_design* d, uint8_t* present, uint64_t n) {
+  return guarded([&] {
+    require(d && present, "rteaal_design_signals: null argument");
+    require(n == d->L.sig2slot.size(), "rteaal_design_signals: n_signals differs from the design's");
+    for (uint64_t i = 0; i < n; i++) present[i] = d->L.sig2slot[i] != 0xFFFFFFFFu;
   });
 }
 
@@ -1049,6 +1056,8 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       std::vector<uint32_t> slots(probes->n);
       for (uint32_t p = 0; p < probes->n; p++) {
         require(probes->signals[p] < D->nl.n_signals(), "rteaal_step: probe signal out of range");
+        require(L.sig2slot[probes->signals[p]] != 0xFFFFFFFFu,
+                "rteaal_step: probed signal was fused away (operator fusion is enabled)");
         slots[p] = L.slot_ref[L.sig2slot[probes->signals[p]]];
       }
       ensure_probe_slots(s, slots.size());
@@ -1264,6 +1273,7 @@ void transfer(rteaal_sim* s, Region region, const uint32_t* signals, uint32_t n,
     const uint32_t nsig = s->design->nl.n_signals();
     for (uint32_t i = 0; i < n; i++) {
       require(signals[i] < nsig, "signal id out of range");
+      require(L.sig2slot[signals[i]] != 0xFFFFFFFFu, "signal was fused away (operator fusion is enabled)");
       rows[i] = L.slot_ref[L.sig2slot[signals[i]]];
       // width of the signal (writes are masked like every stored value)
       const Netlist& nl = s->design->nl;

@@ -160,8 +160,7 @@ __device__ __forceinline__ void stream_consume(const DDesign& d, const DSim& s, 
     if (!am) continue;
     Lanes<STREAM_V> r;
     if (ctl & CTL_EXT) {
-#pragma unroll
-      for (int v = 0; v < (int)STREAM_V; v++) r.x[v] = eval_ext(d, s, m, lane + v);
+      r = eval_ext_v<STREAM_V>(d, s, m, lane);
     } else {
       Lanes<STREAM_V> a = lds4(sa, ka, sub), b, c;
 #pragma unroll

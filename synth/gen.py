@@ -133,6 +133,7 @@ class DesignSpec:
     mem_read_ports: int = 2
     mem_write_ports: int = 1
     input_widths: tuple | None = None  # explicit primary-input widths (overrides the draw)
+    mux_chain_frac: float = 0.0       # P(a MUX's false operand is a MUX of the previous layer)
 
 
 # Named workloads: the sizes the parity tests and the benchmark use.
@@ -155,6 +156,12 @@ def spec_soc(seed: int = 3) -> DesignSpec:
     """5M-op SoC-like DAG, depth 120, 256k registers, 64 register files of 32 x 64 bit."""
     return DesignSpec(n_ops=5_000_000, n_regs=262_144, depth=120, n_inputs=32, seed=seed,
                       mix=dict(MIX_SOC), n_mems=64, mem_words=32)
+
+
+def spec_mux(seed: int = 4) -> DesignSpec:
+    """1M-op control-heavy DAG (SoC mix, 40% mux) whose muxes chain with probability 0.6."""
+    return DesignSpec(n_ops=1_000_000, n_regs=65_536, depth=80, n_inputs=32, seed=seed,
+                      mix=dict(MIX_SOC), mux_chain_frac=0.6)
 
 
 def spec_serving(n_ops: int, seed: int) -> DesignSpec:
@@ -273,6 +280,7 @@ def generate(spec: DesignSpec) -> Netlist:
             out[m] = layers[s][idx[m]]
         return out
 
+    chained = np.zeros(n_signals, bool)   # chain members: exactly one reader
     dag_pos = 0
     for L in range(1, spec.depth + 1):
         k = int(counts[L - 1])
@@ -348,6 +356,24 @@ def generate(spec: DesignSpec) -> Netlist:
                     mi = memrd_owner[pos]
                     q0[j], q1[j] = mi & 0xFF, mi >> 8
 
+        # mux chains (when/else chains): the false operand (O = 2) of some MUXes
+        # is a MUX of layer L-1 that nothing else reads (it leaves the operand
+        # pool, and register D / write-port draws skip it); the head is no wider
+        if spec.mux_chain_frac > 0 and L > 1:
+            prev = layers[L - 1]
+            cand = prev[(prev >= op_base + (5 if spec.counter_lfsr else 0))
+                        & (code[np.maximum(prev - op_base, 0)] == OP["MUX"])]
+            cand = cand[~np.isin(cand, a)]
+            m = np.flatnonzero((c == OP["MUX"]) & (rng.uniform(k) < spec.mux_chain_frac))
+            n = min(m.size, cand.size, max(0, prev.size - 8))
+            if n:
+                cand = cand[np.argsort(rng.u64(cand.size), kind="stable")][:n]
+                m = m[:n]
+                a[m, 2] = cand
+                w[m] = np.minimum(w[m], sig_width[cand])
+                chained[cand] = True
+                layers[L - 1] = prev[~chained[prev]]
+
         sl = slice(next_op, next_op + k)
         code[sl], width[sl], p0[sl], p1[sl] = c, w, q0, q1
         argv[sl] = a
@@ -368,6 +394,10 @@ def generate(spec: DesignSpec) -> Netlist:
     first_dag = op_base + (5 if spec.counter_lfsr else 0)
     reg_d = np.empty(n_regs, np.int64)
     reg_d[:n_rand_regs] = first_dag + rng.below(spec.n_ops, n_rand_regs)
+    redraw = chained[reg_d[:n_rand_regs]]
+    while redraw.any():
+        reg_d[:n_rand_regs][redraw] = first_dag + rng.below(spec.n_ops, int(redraw.sum()))
+        redraw = chained[reg_d[:n_rand_regs]]
     if spec.counter_lfsr:
         reg_d[n_rand_regs:] = special_d
 
@@ -378,6 +408,10 @@ def generate(spec: DesignSpec) -> Netlist:
     if nwp:
         wport[:, 0] = np.repeat(np.arange(spec.n_mems), spec.mem_write_ports)
         wport[:, 1:] = first_dag + rng.below(spec.n_ops, 3 * nwp).reshape(nwp, 3)
+        redraw = chained[wport[:, 1:]]
+        while redraw.any():
+            wport[:, 1:][redraw] = first_dag + rng.below(spec.n_ops, int(redraw.sum()))
+            redraw = chained[wport[:, 1:]]
 
     return Netlist(
         input_width=input_width.astype(np.uint8), reg_width=reg_width.astype(np.uint8),
