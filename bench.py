@@ -43,7 +43,16 @@ WORKLOADS = {
     "tiny-2k": (synth.spec_tiny, 1, (10_000, 10_000)),
     "soc-5M": (synth.spec_soc, 1024, (20_000, 20_000)),
     "mux-1M": (synth.spec_mux, 4096, (1000, 100_000)),
+    "quiet-1M": (synth.spec_quiet, 4096, (20_000, 20_000)),
 }
+# inputs after the reset cycle: xorshift64 every cycle, or held (the
+# enable-gated modular design, whose activity then comes from its enables)
+HELD_INPUTS = {"quiet-1M"}
+
+
+def make_netlist(workload: str) -> synth.Netlist:
+    spec = WORKLOADS[workload][0]()
+    return synth.generate_modular(spec) if isinstance(spec, synth.ModularSpec) else synth.generate(spec)
 
 
 def width_bytes(w: np.ndarray) -> np.ndarray:
@@ -194,15 +203,15 @@ def cpu_oracle_rate(nl: synth.Netlist, n_inst: int, cycles: int, seed: int, thre
 
 def cpu_sample_size(workload: str) -> tuple[int, int]:
     return {"batch-1M": (64, 8), "single-200k": (1, 2000), "tiny-2k": (1, 10_000),
-            "soc-5M": (16, 4), "mux-1M": (64, 8)}[workload]
+            "soc-5M": (16, 4), "mux-1M": (64, 8), "quiet-1M": (64, 8)}[workload]
 
 
 def run_reference(args) -> None:
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    spec_fn, n_inst, _ = WORKLOADS[args.workload]
-    nl = synth.generate(spec_fn())
+    _, n_inst, _ = WORKLOADS[args.workload]
+    nl = make_netlist(args.workload)
     threads = os.cpu_count() or 1
     si, sc = cpu_sample_size(args.workload)
     for _ in range(args.warmup):
@@ -237,10 +246,11 @@ def run_ours(args) -> None:
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    spec_fn, n_total, (clo, chi) = WORKLOADS[args.workload]
+    _, n_total, (clo, chi) = WORKLOADS[args.workload]
     if args.instances:
         n_total = args.instances
-    nl = synth.generate(spec_fn())
+    nl = make_netlist(args.workload)
+    run_stim = "hold" if args.workload in HELD_INPUTS else "xorshift"
     lo, hi = shard(n_total, rank, world)
     n = hi - lo
     budgets_all = synth.cycle_budgets(5, n_total, clo, chi)
@@ -249,9 +259,11 @@ def run_ours(args) -> None:
     xs = np.ascontiguousarray(xs_all[:, lo:hi])
 
     design = rt.Design(nl.to_bytes(), fuse_mux_chains=args.fuse_mux_chains)
+    spec_compile_s = design.specialize() if args.kernel == "specialized" else None
     kw = dict(tile_lanes=args.tile_lanes, threads=args.threads, unroll=args.unroll,
               ctas_per_sm=args.ctas_per_sm, lanes_per_thread=args.lanes_per_thread)
-    sim = rt.Sim(design, n, kernel=args.kernel, xorshift_seed=xs, expected_cycles=budgets, **kw)
+    sim = rt.Sim(design, n, kernel="grid" if args.activity else args.kernel, xorshift_seed=xs,
+                 expected_cycles=budgets, activity=args.activity, **kw)
     stream = torch.cuda.current_stream(dev)
     remaining = budgets.astype(np.int64).copy()
 
@@ -262,7 +274,8 @@ def run_ours(args) -> None:
     tune = None
     if args.autotune:
         t0 = time.perf_counter()
-        trials = sim.autotune(cycles_per_trial=1, kernels=args.tune_kernels.split(","))
+        trials = sim.autotune(cycles_per_trial=1,
+                              kernels=["grid"] if args.activity else args.tune_kernels.split(","))
         info = sim.info
         tune = {"trials": len(trials), "seconds": round(time.perf_counter() - t0, 2),
                 "best_ms_per_cycle": round(min(t["ms"] for t in trials), 3) if trials else None}
@@ -274,7 +287,7 @@ def run_ours(args) -> None:
 
     def one_step():
         per = np.minimum(remaining, C).astype(np.uint32)
-        sim.step(per, stimulus="xorshift")
+        sim.step(per, stimulus=run_stim)
         remaining[:] -= per
         return int(per.astype(np.int64).sum())
 
@@ -285,6 +298,7 @@ def run_ours(args) -> None:
         torch.distributed.barrier()
     torch.cuda.synchronize()
 
+    act0 = sim.activity() if args.activity else None
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launch_ms = []
     inst_cycles = 0
@@ -312,10 +326,19 @@ def run_ours(args) -> None:
     sharing = info["tile_lanes"] if info["kernel"] == 2 else n
     bpc = algorithmic_bytes_per_instance_cycle(nl, sharing)
     per_launch_bytes = bpc["total"] * (inst_cycles / args.steps)
+    activity = None
+    if args.activity:  # skipped items move no bytes: scale by the evaluated fraction
+        ev1, sk1 = sim.activity()
+        ev, sk = ev1 - act0[0], sk1 - act0[1]
+        frac_eval = ev / max(1, ev + sk)
+        activity = {"items_evaluated": ev, "items_skipped": sk, "evaluated_fraction": frac_eval,
+                    "item": "(op, lanes of one thread) with an active lane"}
+        per_launch_bytes *= frac_eval
     avg_launch_s = float(np.mean(step_ms)) / 1e3
     peaks = measured_peaks()
     achieved = per_launch_bytes / avg_launch_s / 1e9
-    kname = {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops", 5: "k_stream"}[info["kernel"]]
+    kname = {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops", 5: "k_stream",
+             6: "rteaal_spec"}[info["kernel"]]
     variant = "%s<%d,%d,%d,%d>" % (kname, info["lanes_per_thread"], info["unroll"], info["threads"],
                                    info["ctas_per_sm"])
     traffic = profile_traffic(variant + ":" + args.workload) if n_total == WORKLOADS[args.workload][1] else None
@@ -332,7 +355,8 @@ def run_ours(args) -> None:
             o = oracle.OracleSim(nl.to_bytes(), sample.size)
             oxs = np.ascontiguousarray(xs[:, sample])
             o.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=oxs, threads=os.cpu_count() or 1)
-            o.step(run_cycles[sample].astype(np.uint32), mode=oracle.STIM_XORSHIFT, xs=oxs,
+            o.step(run_cycles[sample].astype(np.uint32),
+                   mode=oracle.STIM_HOLD if run_stim == "hold" else oracle.STIM_XORSHIFT, xs=oxs,
                    threads=os.cpu_count() or 1)
             live = design.present_signals()           # every signal unless fusion absorbed some
             ok = all(np.array_equal(sim.read(live, int(i), 1)[:, 0], o.vals[k][live])
@@ -348,7 +372,10 @@ def run_ours(args) -> None:
         probes = (nl.reg_base + np.arange(min(64, nl.n_regs))).astype(np.uint32)
         vals_host = torch.empty((C, nl.n_inputs, n), dtype=torch.int64).pin_memory()
         vals_np = vals_host.numpy().view(np.uint64)
-        vals_np[:] = synth.stimulus_values(9, C, nl.n_inputs, n)
+        if run_stim == "hold":   # the testbench drives the values the inputs hold
+            vals_np[:] = sim.read(np.arange(nl.n_inputs))[None, :, :]
+        else:
+            vals_np[:] = synth.stimulus_values(9, C, nl.n_inputs, n)
         out_host = torch.empty((1, probes.size, n), dtype=torch.int64).pin_memory()
         e2e_evals = 0
         torch.cuda.synchronize()
@@ -385,20 +412,27 @@ def run_ours(args) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "ops": nl.n_ops, "regs": nl.n_regs,
                        "layers": design.info["n_layers"], "instances": n_total,
-                       "fused_mux_ops": design.info["n_fused"],
+                       "fused_mux_ops": design.info["n_fused"], "activity_aware": bool(args.activity),
+                       "specialize_compile_s": spec_compile_s,
+                       "inputs_after_reset": run_stim,
                        "cycles_per_step": C, "kernel": args.kernel,
-                       "kernel_used": {1: "layer", 2: "tile", 3: "grid", 4: "layer_graph", 5: "stream"}[info["kernel"]],
+                       "kernel_used": {1: "layer", 2: "tile", 3: "grid", 4: "layer_graph", 5: "stream",
+                                       6: "specialized"}[info["kernel"]],
                        "tile_lanes": info["tile_lanes"], "threads": info["threads"],
                        "ctas_per_sm": info["ctas_per_sm"], "unroll": info["unroll"],
                        "grid": info["grid"], "autotune": tune, "parallelism": "replicas" if world > 1 else "1 gpu",
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)"
                              % (design.info["state_bytes_per_lane"] * n / 1e9)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                         "traffic": traffic, "peak_source": peaks["source"],
-                         "bytes_per_instance_cycle": bpc["total"],
-                         "kernel": {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops", 5: "k_stream"}[info["kernel"]]},
+            "roofline": ({"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                          "traffic": traffic, "peak_source": peaks["source"],
+                          "bytes_per_instance_cycle": bpc["total"],
+                          "kernel": kname} if info["kernel"] != 6 else
+                         {"bound": "alu", "achieved": None, "peak": None, "frac": None, "kernel": kname,
+                          "note": "straight-line code per instance: the state moves once per step, the "
+                                  "kernel is bound by instruction issue"}),
             "gpu_launches": 1 * args.steps,
+            "activity": activity,
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -460,6 +494,8 @@ def main():
     ap.add_argument("--quantum", type=int, default=2000)
     ap.add_argument("--cycles-cap", type=int, default=0)
     ap.add_argument("--kernel", default="tile")
+    ap.add_argument("--activity", action="store_true",
+                    help="activity-aware evaluation (grid kernel): skip ops whose operands did not change")
     ap.add_argument("--fuse-mux-chains", action="store_true",
                     help="fuse single-fanout mux chains into one op (ops are still counted as in the netlist)")
     ap.add_argument("--chunk", type=int, default=8)

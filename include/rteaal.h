@@ -143,6 +143,12 @@ int rteaal_design_info(const rteaal_design *design, rteaal_design_stats *out);
  * present: host array of n_signals bytes (caller-owned); n_signals must equal
  * the design's signal count.  Errors: E_INVALID. */
 int rteaal_design_signals(const rteaal_design *design, uint8_t *present, uint64_t n_signals);
+/* Generate and compile the design-specialised kernel (RTEAAL_KERNEL_SPECIALIZED)
+ * now instead of at the first configure that asks for it; *compile_us
+ * (nullable) receives the generation + compile time of the first call (the
+ * kernel is kept with the design).  Errors: E_UNSUPPORTED (too many ops),
+ * E_CUDA (compile or load failure; the message holds the compiler log). */
+int rteaal_design_specialize(rteaal_design *design, uint64_t *compile_us);
 /* Returns E_BUSY (and frees nothing) while sims created from it are alive. */
 int rteaal_design_free(rteaal_design *design);
 
@@ -155,11 +161,18 @@ enum {
   RTEAAL_KERNEL_GRID = 3,   /* persistent cooperative: the whole grid walks all
                                layers, bounded grid barrier between layers         */
   RTEAAL_KERNEL_LAYER_GRAPH = 4, /* plain form with the cycle loop as a CUDA graph */
-  RTEAAL_KERNEL_STREAM = 5  /* persistent cooperative, one CTA per SM: a producer
+  RTEAAL_KERNEL_STREAM = 5, /* persistent cooperative, one CTA per SM: a producer
                                warp streams each op's operand rows into a
                                shared-memory ring with bulk copies (TMA engine,
                                mbarriers), consumer warps compute from it; needs a
                                multiple of 128 lanes                              */
+  RTEAAL_KERNEL_SPECIALIZED = 6 /* design-specialised (Sec. 4.4 SU / TI on the GPU):
+                               the op list unrolled into straight-line code compiled
+                               at run time (NVRTC), every signal a local variable,
+                               one thread per instance for all cycles of a step;
+                               state rows read once and written once per step.
+                               Probes: LAST only.  Designs up to 16,384 ops (the
+                               compile time grows superlinearly with the length). */
 };
 
 typedef struct {
@@ -177,6 +190,15 @@ typedef struct {
   uint32_t ctas_per_sm;    /* TILE / GRID residency target, 0 auto              */
   uint32_t unroll;         /* operations in flight per thread (1, 2, 4), 0 auto */
   uint32_t lanes_per_thread; /* lanes (instances) per thread per op (1, 2, 4, 8), 0 auto */
+  /* Activity-aware evaluation (the cascade-level optimisation "skipping
+   * partitions without activity" of App. B, at the finest grain): the sim
+   * keeps, per row and 128-lane chunk, the last cycle in which the row changed
+   * in any lane of the chunk; an op is evaluated for a chunk only if one of its
+   * operands changed there in the current cycle (memory reads always), and its
+   * result is stored only if it differs.  Exact -- results never depend on it.
+   * GRID kernel only (configure refuses the others: E_UNSUPPORTED); costs one
+   * byte of device memory per row and chunk.  Fixed at creation. */
+  int activity;
 } rteaal_sim_opts;
 
 typedef struct {
@@ -185,6 +207,7 @@ typedef struct {
   int kernel;                    /* kernel chosen                                */
   uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid;
   uint32_t lanes_per_thread;
+  int activity;                  /* activity-aware evaluation on                  */
 } rteaal_sim_stats;
 
 /* Allocates and zero-initialises the state of n_instances (>= 1) independent
@@ -217,6 +240,10 @@ typedef struct {
 int rteaal_sim_autotune(rteaal_sim *sim, uint32_t cycles_per_trial, uint32_t kernel_mask,
                         rteaal_tune_trial *trials, uint32_t max_trials, uint32_t *n_trials,
                         void *stream);
+
+/* Activity-aware sims: (op, 128-lane chunk) items evaluated and skipped since
+ * creation.  Synchronises stream.  Errors: E_INVALID. */
+int rteaal_sim_activity(rteaal_sim *sim, uint64_t *evaluated, uint64_t *skipped, void *stream);
 
 /* Bytes of device memory rteaal_sim_create would take (footprint admission). */
 uint64_t rteaal_sim_footprint(const rteaal_design *design, uint32_t n_instances);

@@ -27,7 +27,7 @@ RTEAAL_STIM_HOLD, RTEAAL_STIM_XORSHIFT, RTEAAL_STIM_BUFFER = 0, 1, 2
 RTEAAL_PROBE_LAST, RTEAAL_PROBE_EVERY, RTEAAL_PROBE_CHANGES = 0, 1, 2
 RTEAAL_STEP_RESET = 1
 
-KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4, "stream": 5}
+KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4, "stream": 5, "specialized": 6}
 
 
 class RteaalError(RuntimeError):
@@ -65,13 +65,15 @@ class rteaal_sim_opts(ctypes.Structure):
                 ("expected_cycles", ctypes.POINTER(_U32)),
                 ("xorshift_seed", ctypes.POINTER(_U64)),
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
-                ("ctas_per_sm", _U32), ("unroll", _U32), ("lanes_per_thread", _U32)]
+                ("ctas_per_sm", _U32), ("unroll", _U32), ("lanes_per_thread", _U32),
+                ("activity", ctypes.c_int)]
 
 
 class rteaal_sim_stats(ctypes.Structure):
     _fields_ = [("n_instances", _U32), ("n_lanes", _U32), ("device_bytes", _U64),
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
-                ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("lanes_per_thread", _U32)]
+                ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("lanes_per_thread", _U32),
+                ("activity", ctypes.c_int)]
 
 
 class rteaal_tune_trial(ctypes.Structure):
@@ -104,7 +106,7 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_sync", "rteaal_state_read", "rteaal_state_write", "rteaal_mem_read",
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
            "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
-           "rteaal_design_signals"]
+           "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -123,6 +125,7 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(rteaal_load_opts), ctypes.POINTER(_P)]
         L.rteaal_design_info.argtypes = [_P, ctypes.POINTER(rteaal_design_stats)]
         L.rteaal_design_free.argtypes = [_P]
+        L.rteaal_design_specialize.argtypes = [_P, ctypes.POINTER(_U64)]
         L.rteaal_design_signals.argtypes = [_P, _P, _U64]
         L.rteaal_sim_create.argtypes = [_P, _U32, ctypes.POINTER(rteaal_sim_opts), ctypes.POINTER(_P)]
         L.rteaal_sim_info.argtypes = [_P, ctypes.POINTER(rteaal_sim_stats)]
@@ -131,6 +134,7 @@ def lib() -> ctypes.CDLL:
         L.rteaal_sim_configure.argtypes = [_P, ctypes.POINTER(rteaal_sim_opts)]
         L.rteaal_sim_autotune.argtypes = [_P, _U32, _U32, ctypes.POINTER(rteaal_tune_trial), _U32,
                                           ctypes.POINTER(_U32), _P]
+        L.rteaal_sim_activity.argtypes = [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), _P]
         L.rteaal_sim_footprint.argtypes = [_P, _U32]
         L.rteaal_sim_footprint.restype = _U64
         L.rteaal_step.argtypes = [_P, ctypes.POINTER(rteaal_cycles), ctypes.POINTER(rteaal_stimulus),
@@ -291,6 +295,12 @@ def rteaal_sim_reset_lanes(sim: int, inst_begin: int, n_inst: int, xorshift_seed
                                         None if seed is None else seed.ctypes.data, _stream_ptr(stream)))
 
 
+def rteaal_sim_activity(sim: int, stream=None) -> tuple[int, int]:
+    ev, sk = _U64(0), _U64(0)
+    _check(lib().rteaal_sim_activity(sim, ctypes.byref(ev), ctypes.byref(sk), _stream_ptr(stream)))
+    return int(ev.value), int(sk.value)
+
+
 def rteaal_sync(sim: int, stream=None):
     _check(lib().rteaal_sync(sim, _stream_ptr(stream)))
 
@@ -372,6 +382,12 @@ class Design:
     def footprint(self, n_instances: int) -> int:
         return rteaal_sim_footprint(self.handle, n_instances)
 
+    def specialize(self) -> float:
+        """Compile the design-specialised kernel now; returns its generation + compile seconds."""
+        us = _U64(0)
+        _check(lib().rteaal_design_specialize(self.handle, ctypes.byref(us)))
+        return us.value / 1e6
+
     def present_signals(self) -> np.ndarray:
         """Ids of the signals that hold a row (all of them unless fusion absorbed some)."""
         return np.flatnonzero(rteaal_design_signals(self.handle, self.info["n_signals"])).astype(np.uint32)
@@ -394,13 +410,14 @@ class Sim:
     def __init__(self, design: Design, n_instances: int, kernel: str | int = "auto",
                  xorshift_seed: np.ndarray | None = None, expected_cycles=None,
                  tile_lanes: int = 0, threads: int = 0, ctas_per_sm: int = 0, unroll: int = 0,
-                 lanes_per_thread: int = 0, use_torch_allocator: bool = True):
+                 lanes_per_thread: int = 0, use_torch_allocator: bool = True, activity: bool = False):
         self.design = design
         self.n = n_instances
         o = rteaal_sim_opts()
         o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
         o.lanes_per_thread = lanes_per_thread
+        o.activity = int(activity)
         keep: list[Any] = []
         if use_torch_allocator:
             self._alloc = torch_allocator()
@@ -477,6 +494,10 @@ class Sim:
 
     def sync(self, stream=None):
         rteaal_sync(self.handle, stream)
+
+    def activity(self, stream=None) -> tuple[int, int]:
+        """(items evaluated, items skipped) since creation (activity-aware sims)."""
+        return rteaal_sim_activity(self.handle, stream)
 
     def configure(self, kernel: str | int = "auto", tile_lanes: int = 0, threads: int = 0,
                   ctas_per_sm: int = 0, unroll: int = 0, lanes_per_thread: int = 0):

@@ -42,7 +42,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     common = ["-O3", "-std=c++17", "-I", INCLUDE, "-I", CSRC]
     jobs = []
     objs = []
-    for f in ["lower.cpp", "rteaal.cu"]:
+    for f in ["lower.cpp", "specialize.cpp", "rteaal.cu"]:
         src = os.path.join(CSRC, f)
         obj = os.path.join(BUILD, f + ".o")
         cmd = [nvcc] + ARCH + common + ["-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
@@ -60,7 +60,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         if j.returncode != 0:
             raise RuntimeError("nvcc failed:\n" + out)
     tmp = OUT + ".tmp%d" % os.getpid()
-    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L" + cuda_lib, "-lnvrtc",
+                                                            "-Xlinker", "-rpath," + cuda_lib]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout)

@@ -33,6 +33,8 @@ struct DDesign {
   const uint32_t* in_w;       // [n_inputs]
   const uint32_t* in_ref;     // [n_inputs]
   uint32_t n_layers, n_regs, n_inputs, n_mems, op_base, reg_base;
+  uint4 cls_off;              // per class k: first per-lane byte offset of the class's rows
+  uint4 cls_idx;              // per class k: index of the class's first row (rows in layout order)
 };
 
 // Divide by a runtime constant with a multiply-high (Granlund & Montgomery,
@@ -71,6 +73,14 @@ struct DSim {
   unsigned long long* change_count;
   uint64_t change_cap;
   uint32_t* err;
+  // activity-aware evaluation (null act: off).  act[row][chunk] = low 8 bits
+  // of the last cycle in which the row changed in any lane of the 128-lane
+  // chunk; cycle numbers count from the sim's creation (act_g0 = this step's
+  // first).  act_force: the step's first cycle evaluates every op.
+  uint8_t* act;
+  uint32_t act_chunks, act_g0;
+  int act_force;
+  unsigned long long* act_count;  // [2]: items evaluated, items skipped
 };
 
 constexpr uint32_t NO_ROW = 0xFFFFFFFFu;
@@ -162,6 +172,19 @@ __device__ __forceinline__ const uint8_t* elem(const uint8_t* st, uint32_t ref, 
                                                uint32_t lane) {
   // one 32 x 32 -> 64-bit multiply-add; lane << class fits 32 bits
   return st + ((uint64_t)(ref & REF_OFF_MASK) * (uint32_t)np + (uint32_t)(lane << (ref >> 30)));
+}
+
+// Index of a row in layout order (class 3 rows first), from its reference.
+__device__ __forceinline__ uint32_t row_index(const DDesign& d, uint32_t ref) {
+  const uint32_t k = ref >> 30;
+  const uint32_t off = k == 0 ? d.cls_off.x : k == 1 ? d.cls_off.y : k == 2 ? d.cls_off.z : d.cls_off.w;
+  const uint32_t idx = k == 0 ? d.cls_idx.x : k == 1 ? d.cls_idx.y : k == 2 ? d.cls_idx.z : d.cls_idx.w;
+  return idx + (((ref & REF_OFF_MASK) - off) >> k);
+}
+
+// Activity stamp of (row, 128-lane chunk).
+__device__ __forceinline__ uint8_t* act_at(const DDesign& d, const DSim& s, uint32_t ref, uint32_t lane) {
+  return s.act + (size_t)row_index(d, ref) * s.act_chunks + (lane >> 7);
 }
 
 // one element, zero-extended
@@ -879,6 +902,160 @@ __device__ __forceinline__ void eval_layer(const DDesign& d, const DSim& s, uint
   if (e < o1) eval_ext_rows<V>(d, s, e, o1 - e, is, cyc);
 }
 
+// ---- activity-aware evaluation (the cascade-level "skip what did not change"
+// optimisation): an op is evaluated for a 128-lane chunk only if one of its
+// operand rows changed in that chunk during this cycle (stamp == cycle), and
+// its result is written and stamped only if it differs from the stored value.
+// Skipping is exact: an op whose operands are unchanged has an unchanged
+// result.  Stamps are 8-bit, so a stamp 256 cycles old reads as current --
+// that only evaluates an op again (no change, no stamp), never skips one.
+// Requires the fixed lane mapping (the launch guarantees it).
+template <int V>
+__device__ __forceinline__ bool any_diff(const Lanes<V>& a, const Lanes<V>& b, uint32_t am) {
+  bool d = false;
+#pragma unroll
+  for (int v = 0; v < V; v++) d |= ((am >> v) & 1u) && a.x[v] != b.x[v];
+  return d;
+}
+
+template <int V>
+__device__ __forceinline__ bool any_diff32(const Lanes32<V>& a, const Lanes32<V>& b, uint32_t am) {
+  bool d = false;
+#pragma unroll
+  for (int v = 0; v < V; v++) d |= ((am >> v) & 1u) && a.x[v] != b.x[v];
+  return d;
+}
+
+// Is row r hot for lane chunks [ch_lo, ch_hi]: an operand stamped this cycle?
+__device__ __forceinline__ bool row_hot(const DDesign& d, const DSim& s, const uint4& m, bool ext, uint32_t ch_lo,
+                                        uint32_t ch_hi, uint8_t g) {
+  if ((m.w & 31u) == OP_MEMRD) return true;  // memory contents carry no stamps
+  auto hot_ref = [&](uint32_t ref) {
+    const uint8_t* a = s.act + (size_t)row_index(d, ref) * s.act_chunks;
+    bool h = a[ch_lo] == g;
+    if (ch_hi != ch_lo) h |= a[ch_hi] == g;
+    return h;
+  };
+  if (ext) {
+    const uint32_t* a = d.ext + m.x;
+    for (uint32_t i = 0; i < m.y; i++)
+      if (hot_ref(__ldg(&a[i]))) return true;
+    return false;
+  }
+  const uint32_t ar = (m.w >> 5) & 3u;
+  bool h = hot_ref(m.x);
+  if (ar >= 2) h |= hot_ref(m.y);
+  if (ar >= 3) h |= hot_ref(m.z);
+  return h;
+}
+
+// Evaluate one hot row for this thread's V lanes; store and stamp on change.
+template <int V>
+__device__ __forceinline__ void act_item(const DDesign& d, const DSim& s, const uint4& m, uint32_t dref, bool ext,
+                                         uint32_t lane, uint32_t am, uint8_t g) {
+  const size_t np = s.n_pad;
+  bool changed;
+  if (m.w & CTL_NARROW) {
+    Lanes32<V> res;
+    if (ext) {
+      res = eval_ext32_v<V>(d, s, m, lane);
+    } else {
+      Lanes32<V> a, b, c;
+      const uint32_t ar = (m.w >> 5) & 3u;
+      a = ldr32<V>(s.state, m.x, np, lane);
+#pragma unroll
+      for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0u;
+      if (ar >= 2) b = ldr32<V>(s.state, m.y, np, lane);
+      if (ar >= 3) c = ldr32<V>(s.state, m.z, np, lane);
+      res = alu32_v<V>(m.w, a, b, c);
+    }
+    changed = any_diff32<V>(res, ldr32<V>(s.state, dref, np, lane), am);
+    if (changed) str32<V>(s.state, dref, np, lane, res, am);
+  } else {
+    Lanes<V> res;
+    if (ext) {
+      res = eval_ext_v<V>(d, s, m, lane);
+    } else {
+      Lanes<V> va, vb, vc;
+      gather<V>(s.state, np, lane, m, va, vb, vc);
+      res = apply<V>(d, s, m, va, vb, vc, lane);
+    }
+    changed = any_diff<V>(res, ldr<V>(s.state, dref, np, lane), am);
+    if (changed) str<V>(s.state, dref, np, lane, res, am);
+  }
+  if (changed) *act_at(d, s, dref, lane) = g;
+}
+
+template <int V>
+__device__ __forceinline__ void eval_ops_act(const DDesign& d, const DSim& s, uint32_t op0, uint32_t n_rows,
+                                             uint32_t n_plain, const ItemSpace& is, uint32_t cyc,
+                                             uint32_t& n_eval, uint32_t& n_skip) {
+  if (is.row0 == NO_ROW) return;
+  const uint32_t am = act_mask<V>(s, is.lane, cyc);
+  const uint8_t g = (uint8_t)(s.act_g0 + cyc);
+  const bool force = s.act_force && cyc == 0;
+  if (is.tpo.d % 32u == 0u) {
+    // Warp-cooperative: the warp's 32 threads share one row sequence and one
+    // lane range, so lane i checks row (base + i) of that sequence, a ballot
+    // collects the hot ones, and the whole warp evaluates only those -- one
+    // round of descriptor and stamp loads per 32 rows.
+    const uint32_t lid = threadIdx.x & 31u;
+    const uint32_t first = is.lane - lid * V;
+    const uint32_t ch_lo = first >> 7, ch_hi = (first + 32u * V - 1u) >> 7;
+    const bool warp_idle = __ballot_sync(0xFFFFFFFFu, am != 0u) == 0u;
+    if (warp_idle) return;
+    for (uint32_t base = 0;; base += 32u) {
+      const uint32_t r = is.row0 + (base + lid) * is.row_stride;
+      const bool valid = r < n_rows;
+      uint4 m = make_uint4(0, 0, 0, 0);
+      bool hot = false;
+      if (valid) {
+        m = __ldg(&d.meta[op0 + r]);
+        hot = force || row_hot(d, s, m, r >= n_plain, ch_lo, ch_hi, g);
+      }
+      uint32_t hm = __ballot_sync(0xFFFFFFFFu, hot);
+      const uint32_t vm = __ballot_sync(0xFFFFFFFFu, valid);
+      if (am) {
+        n_eval += __popc(hm);
+        n_skip += __popc(vm) - __popc(hm);
+      }
+      while (hm) {
+        const uint32_t k = __ffs(hm) - 1u;
+        hm &= hm - 1u;
+        uint4 mk;
+        mk.x = __shfl_sync(0xFFFFFFFFu, m.x, k);
+        mk.y = __shfl_sync(0xFFFFFFFFu, m.y, k);
+        mk.z = __shfl_sync(0xFFFFFFFFu, m.z, k);
+        mk.w = __shfl_sync(0xFFFFFFFFu, m.w, k);
+        const uint32_t rk = is.row0 + (base + k) * is.row_stride;
+        if (am) act_item<V>(d, s, mk, __ldg(&d.dst[op0 + rk]), rk >= n_plain, is.lane, am, g);
+      }
+      if (vm != 0xFFFFFFFFu) break;  // the sequence ended inside this round
+    }
+    return;
+  }
+  // one thread, one row at a time (lane ranges narrower than a warp)
+  if (!am) return;
+  for (uint32_t r = is.row0; r < n_rows; r += is.row_stride) {
+    const uint4 m = __ldg(&d.meta[op0 + r]);
+    const bool ext = r >= n_plain;
+    if (!(force || row_hot(d, s, m, ext, is.lane >> 7, is.lane >> 7, g))) {
+      n_skip++;
+      continue;
+    }
+    n_eval++;
+    act_item<V>(d, s, m, __ldg(&d.dst[op0 + r]), ext, is.lane, am, g);
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void eval_layer_act(const DDesign& d, const DSim& s, uint32_t L, const ItemSpace& is,
+                                               uint32_t cyc, uint32_t& n_eval, uint32_t& n_skip) {
+  const uint32_t o0 = __ldg(&d.layer_off[L]), e = __ldg(&d.layer_ext[L]);
+  const uint32_t o1 = __ldg(&d.layer_off[L + 1]);
+  eval_ops_act<V>(d, s, o0, o1 - o0, e - o0, is, cyc, n_eval, n_skip);
+}
+
 // (a1) primary inputs for cycle cyc.
 template <int V>
 __device__ __forceinline__ void stim_items(const DDesign& d, const DSim& s, const ItemSpace& is,
@@ -901,7 +1078,12 @@ __device__ __forceinline__ void stim_items(const DDesign& d, const DSim& s, cons
       } else {
         x = __ldg(&s.stim[((size_t)cyc * d.n_inputs + j) * s.n_user + user_of(s, lane)]);
       }
-      st1(s.state, __ldg(&d.in_ref[j]), np, lane, x & mk);
+      const uint32_t iref = __ldg(&d.in_ref[j]);
+      if (s.act) {  // stamp only a change (held or repeated values cost nothing downstream)
+        if (ld1(s.state, iref, np, lane) == (x & mk)) continue;
+        *act_at(d, s, iref, lane) = (uint8_t)(s.act_g0 + cyc);
+      }
+      st1(s.state, iref, np, lane, x & mk);
     }
   });
 }
@@ -933,7 +1115,16 @@ __device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, co
             if (cyc < __ldg(&s.reset_lane[lane + t])) v.x[t] = init;
         }
       }
-      str<V>(s.state, __ldg(&d.reg_ref[r]), np, lane, v, am);
+      const uint32_t qref = __ldg(&d.reg_ref[r]);
+      if (s.act) {  // write and stamp only what changes; visible from the next cycle
+        const Lanes<V> q = ldr<V>(s.state, qref, np, lane);
+        bool changed = false;
+#pragma unroll
+        for (int t = 0; t < V; t++) changed |= ((am >> t) & 1u) && q.x[t] != v.x[t];
+        if (!changed) return;
+        *act_at(d, s, qref, lane) = (uint8_t)(s.act_g0 + cyc + 1u);
+      }
+      str<V>(s.state, qref, np, lane, v, am);
     } else {
       const uint32_t mi = r - d.n_regs;
       const uint4 info = __ldg(&d.mem_info[mi]);

@@ -92,4 +92,10 @@ struct Lowered {
 // (the absorbed muxes are not computed and their signals have no row).
 void lower_netlist(const Netlist& nl, Lowered& out, bool fuse_mux_chains = false);
 
+// Design-specialised form (specialize.cpp): straight-line CUDA source of one
+// thread simulating one lane for all cycles of a step, and its NVRTC compile
+// for `arch` (e.g. "sm_103a").  compile returns false with the log on failure.
+std::string specialized_source(const Netlist& nl, const Lowered& L);
+bool compile_specialized(const std::string& src, const char* arch, std::vector<char>& cubin, std::string& log);
+
 }  // namespace rteaal

@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <chrono>
+
 #include "kernels.cuh"
 #include "lower.hpp"
 #include "rteaal.h"
@@ -175,6 +177,38 @@ __global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs
     }
   }
 #undef RT_SPACE
+}
+
+// GRID form with activity-aware evaluation (ops whose operands did not change
+// in a 128-lane chunk are skipped there); counts evaluated / skipped items.
+template <int V, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_grid_act(DDesign d, DSim s, GridArgs g) {
+  __shared__ int sh_ok;
+  uint32_t n_eval = 0, n_skip = 0;
+#define RT_SPACE make_space<V>(g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x)
+  for (uint32_t c = 0; c < g.ncyc; c++) {
+    stim_items<V>(d, s, RT_SPACE, c);
+    if (!grid_sync(g, s.err, &sh_ok)) return;
+    for (uint32_t L = 0; L < d.n_layers; L++) {
+      eval_layer_act<V>(d, s, L, RT_SPACE, c, n_eval, n_skip);
+      if (!grid_sync(g, s.err, &sh_ok)) return;
+    }
+    commit_items<V>(d, s, RT_SPACE, c);
+    if (!grid_sync(g, s.err, &sh_ok)) return;
+    if (s.n_probe) {
+      probe_items<V>(s, RT_SPACE, c);
+      if (!grid_sync(g, s.err, &sh_ok)) return;
+    }
+  }
+#undef RT_SPACE
+  for (int o = 16; o > 0; o >>= 1) {
+    n_eval += __shfl_xor_sync(0xFFFFFFFFu, n_eval, o);
+    n_skip += __shfl_xor_sync(0xFFFFFFFFu, n_skip, o);
+  }
+  if ((threadIdx.x & 31u) == 0 && (n_eval | n_skip)) {
+    atomicAdd(&s.act_count[0], (unsigned long long)n_eval);
+    atomicAdd(&s.act_count[1], (unsigned long long)n_skip);
+  }
 }
 
 }  // namespace rteaal
@@ -340,7 +374,14 @@ struct rteaal_design {
     metadata_bytes += b.n;
     return static_cast<T*>(b.p);
   }
+  // design-specialised kernel (compiled on first use)
+  std::mutex spec_mu;
+  cudaLibrary_t spec_lib = nullptr;
+  cudaKernel_t spec_kernel = nullptr;
+  uint64_t spec_compile_us = 0;
+
   ~rteaal_design() {
+    if (spec_lib) cudaLibraryUnload(spec_lib);
     for (auto& b : bufs) alloc.free(b.p, b.n);
   }
 };
@@ -378,6 +419,12 @@ struct rteaal_sim {
   uint64_t barrier_timeout_ns = 2000000000ull;
   uint32_t barrier_extra = 0;        // test hook: arrivals withheld from every grid barrier
   uint32_t stream_chunk = 0;         // STREAM: lanes per item
+  // activity-aware evaluation (GRID only)
+  bool activity = false;
+  uint8_t* act = nullptr;            // [n_slots][act_chunks] 8-bit change stamps
+  uint32_t act_chunks = 0;           // 128-lane chunks
+  uint64_t act_g = 1;                // cycle number of the next step's first cycle
+  bool act_force = true;             // next step's first cycle evaluates every op
 
   void* get(size_t n) {
     DevBuf b;
@@ -438,6 +485,13 @@ DSim dsim(const rteaal_sim* s) {
   x.n_user = s->n_user;
   x.user_of_lane = s->user_of_lane;
   x.err = s->scratch;
+  if (s->activity) {
+    x.act = s->act;
+    x.act_chunks = s->act_chunks;
+    x.act_g0 = (uint32_t)(s->act_g & 255u);
+    x.act_force = s->act_force ? 1 : 0;
+    x.act_count = reinterpret_cast<unsigned long long*>(s->scratch + 8);
+  }
   return x;
 }
 
@@ -517,6 +571,26 @@ const Variant kVariants[] = {
     RT_VARIANT(1, 1, 512, 4), RT_VARIANT(1, 2, 512, 2), RT_VARIANT(1, 4, 512, 1),
 };
 #undef RT_VARIANT
+
+struct ActVariant {
+  int V, maxt, minb;
+  const void* grid;
+};
+#define RT_ACT_VARIANT(V, T, B) {V, T, B, (const void*)k_grid_act<V, T, B>}
+const ActVariant kActVariants[] = {
+    RT_ACT_VARIANT(4, 384, 4), RT_ACT_VARIANT(4, 256, 8), RT_ACT_VARIANT(4, 512, 2),
+    RT_ACT_VARIANT(2, 512, 4), RT_ACT_VARIANT(8, 256, 2), RT_ACT_VARIANT(1, 512, 4),
+};
+#undef RT_ACT_VARIANT
+
+const ActVariant* find_act_variant(int V, uint32_t threads, uint32_t minb = 0) {
+  const ActVariant* best = nullptr;
+  for (const ActVariant& v : kActVariants)
+    if (v.V == V && (uint32_t)v.maxt == threads && (!minb || (uint32_t)v.minb == minb)) return &v;
+  for (const ActVariant& v : kActVariants)
+    if (v.V == V && (uint32_t)v.maxt >= threads && (!best || v.maxt < best->maxt)) best = &v;
+  return best;
+}
 
 // Variant for (V, U, threads): the one compiled for exactly `threads` per CTA
 // (with `minb` CTAs per SM when given, else the highest occupancy target), else
@@ -603,6 +677,12 @@ RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaa
       dd.n_mems = (uint32_t)(L.mem_info.size() / 4 - 1);
       dd.op_base = L.op_base;
       dd.reg_base = L.reg_base;
+      {  // class regions of the compact layout: class 3 first, then 2, 1, 0
+        const uint64_t c3 = L.class_rows[3], c2 = L.class_rows[2], c1 = L.class_rows[1];
+        dd.cls_off = make_uint4((uint32_t)(8 * c3 + 4 * c2 + 2 * c1), (uint32_t)(8 * c3 + 4 * c2),
+                                (uint32_t)(8 * c3), 0u);
+        dd.cls_idx = make_uint4((uint32_t)(c3 + c2 + c1), (uint32_t)(c3 + c2), (uint32_t)c3, 0u);
+      }
     } catch (...) {
       delete d;
       throw;
@@ -669,11 +749,38 @@ namespace {
 constexpr int kStreamConsumerWarps = 16;
 
 
+constexpr uint32_t kSpecMaxOps = 16384;
+constexpr uint32_t kSpecThreads = 128;
+
+// Generate, compile (NVRTC, sm_103a) and load the design-specialised kernel once.
+void ensure_specialized(rteaal_design* d) {
+  std::lock_guard<std::mutex> g(d->spec_mu);
+  if (d->spec_kernel) return;
+  if (d->nl.no > kSpecMaxOps)
+    throw Error(RTEAAL_E_UNSUPPORTED, "design-specialised kernel: more than 16,384 ops (compile time grows superlinearly)");
+  const auto t0 = std::chrono::steady_clock::now();
+  const std::string src = specialized_source(d->nl, d->L);
+  std::vector<char> cubin;
+  std::string log;
+  if (!compile_specialized(src, "sm_103a", cubin, log))
+    throw Error(RTEAAL_E_CUDA, "design-specialised kernel: compile failed: " + log.substr(0, 2000));
+  CK(cudaSetDevice(d->device));
+  CK(cudaLibraryLoadData(&d->spec_lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+  CK(cudaLibraryGetKernel(&d->spec_kernel, d->spec_lib, "rteaal_spec"));
+  d->spec_compile_us = (uint64_t)std::chrono::duration_cast<std::chrono::microseconds>(
+                           std::chrono::steady_clock::now() - t0).count();
+}
+
 // Validate and apply a launch configuration (never changes results).
 void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
                uint32_t unroll, uint32_t lanes_per_thread) {
-  if (kernel == RTEAAL_KERNEL_AUTO) kernel = s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
-  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_STREAM, "unknown kernel");
+  if (kernel == RTEAAL_KERNEL_AUTO)
+    kernel = s->activity ? RTEAAL_KERNEL_GRID : s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
+  if (s->activity && kernel != RTEAAL_KERNEL_GRID)
+    throw Error(RTEAAL_E_UNSUPPORTED, "activity-aware evaluation runs with the GRID kernel only");
+  if (s->activity && unroll > 1)
+    throw Error(RTEAAL_E_UNSUPPORTED, "activity-aware evaluation has no unrolled variants");
+  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_SPECIALIZED, "unknown kernel");
   if (!unroll) unroll = 1;
   require(unroll == 1 || unroll == 2 || unroll == 4, "unroll must be 1, 2 or 4");
   if (!threads) threads = 512;
@@ -702,7 +809,14 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
   require(span % (uint32_t)V == 0, "lanes_per_thread must divide the lanes of a tile / the padded lane count");
   uint32_t grid = 0;
   if (kernel == RTEAAL_KERNEL_LAYER || kernel == RTEAAL_KERNEL_LAYER_GRAPH) threads = 256;
-  if (kernel == RTEAAL_KERNEL_STREAM) {
+  if (kernel == RTEAAL_KERNEL_SPECIALIZED) {
+    ensure_specialized(s->design_mut);
+    threads = kSpecThreads;
+    V = 1;
+    unroll = 1;
+    ctas_per_sm = 0;
+    grid = (uint32_t)((s->n_pad + kSpecThreads - 1) / kSpecThreads);
+  } else if (kernel == RTEAAL_KERNEL_STREAM) {
     // producer warp + consumer warps, one CTA per SM, chunks of up to 512 lanes
     if (s->n_pad % 128 != 0)
       throw Error(RTEAAL_E_UNSUPPORTED, "stream kernel needs a multiple of 128 lanes");
@@ -719,6 +833,26 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     require(occ >= 1, "stream kernel cannot be resident");
     ctas_per_sm = 1;
     grid = (uint32_t)s->design->n_sms;
+  } else if (kernel == RTEAAL_KERNEL_GRID && s->activity) {
+    if (!lanes_per_thread && !find_act_variant(V, threads)) V = 4;
+    const ActVariant* v = find_act_variant(V, threads, ctas_per_sm);
+    if (!v)  // no variant for these threads: the first one compiled for this V, at its block size
+      for (const ActVariant& c : kActVariants)
+        if (c.V == V) {
+          v = &c;
+          threads = (uint32_t)c.maxt;
+          break;
+        }
+    if (!v) throw Error(RTEAAL_E_UNSUPPORTED, "no compiled activity-aware variant for V=" + std::to_string(V) +
+                                                  " threads=" + std::to_string(threads));
+    require(span % (uint32_t)V == 0, "lanes_per_thread must divide the padded lane count");
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v->grid, (int)threads, 0));
+    require(occ >= 1, "kernel cannot be resident with these threads");
+    ctas_per_sm = ctas_per_sm ? std::min<uint32_t>(ctas_per_sm, (uint32_t)occ) : (uint32_t)occ;
+    grid = ctas_per_sm * (uint32_t)s->design->n_sms;
+    if ((uint64_t)grid * threads < s->n_pad / (uint32_t)V)
+      throw Error(RTEAAL_E_UNSUPPORTED, "activity-aware evaluation needs a thread per lane chunk");
   } else if (kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID) {
     const Variant* v = find_variant(V, unroll, threads, ctas_per_sm);
     if (!v) throw Error(RTEAAL_E_UNSUPPORTED, "no compiled kernel variant for V=" + std::to_string(V) +
@@ -747,6 +881,14 @@ uint32_t opt_lanes(const rteaal_sim_opts* o) { return o ? o->lanes_per_thread : 
 
 }  // namespace
 
+RT_EXPORT int rteaal_design_specialize(rteaal_design* d, uint64_t* compile_us) {
+  return guarded([&] {
+    require(d, "rteaal_design_specialize: null design");
+    ensure_specialized(d);
+    if (compile_us) *compile_us = d->spec_compile_us;
+  });
+}
+
 RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, const rteaal_sim_opts* opts,
                                 rteaal_sim** out) {
   return guarded([&] {
@@ -763,6 +905,7 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       CK(cudaSetDevice(d->device));
       s->n_user = n_instances;
       s->n_pad = pad_lanes(n_instances);
+      s->activity = opts && opts->activity;
       configure(s, opts ? opts->kernel : 0, opts ? opts->tile_lanes : 0, opts ? opts->threads : 0,
                 opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0, opt_lanes(opts));
       if (const char* e = getenv("RTEAAL_TEST_WITHHOLD_ARRIVAL")) s->barrier_extra = (uint32_t)atoi(e);
@@ -782,6 +925,12 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       CK(cudaMemset(s->mem, 0, std::max<size_t>(np * 8 * L.mem_words_total, 16)));
       CK(cudaMemset(s->xs, 0, std::max<size_t>(np * 8 * L.in_width.size(), 16)));
       CK(cudaMemset(s->scratch, 0, 256));
+      if (s->activity) {
+        s->act_chunks = (uint32_t)((np + 127) / 128);
+        const size_t ab = std::max<size_t>((size_t)L.n_slots * s->act_chunks, 16);
+        s->act = static_cast<uint8_t*>(s->get(ab));
+        CK(cudaMemset(s->act, 0, ab));
+      }
       // lane order: descending expected cycles (stable), so tiles retire together
       s->h_user_of_lane.assign(np, 0xFFFFFFFFu);
       s->h_lane_of_user.resize(n_instances);
@@ -868,6 +1017,21 @@ RT_EXPORT int rteaal_sim_info(const rteaal_sim* s, rteaal_sim_stats* o) {
     o->unroll = s->unroll;
     o->grid = s->grid;
     o->lanes_per_thread = (uint32_t)s->V;
+    o->activity = s->activity ? 1 : 0;
+  });
+}
+
+RT_EXPORT int rteaal_sim_activity(rteaal_sim* s, uint64_t* evaluated, uint64_t* skipped, void* stream) {
+  return guarded([&] {
+    require(s && evaluated && skipped, "rteaal_sim_activity: null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(s->design->device));
+    sync_sim(s, st);
+    uint64_t c[2] = {0, 0};
+    CK(cudaMemcpyAsync(c, s->scratch + 8, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *evaluated = c[0];
+    *skipped = c[1];
   });
 }
 
@@ -974,6 +1138,7 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     cudaEventDestroy(e1);
     if (n_trials) *n_trials = nt;
     configure(s, best_c.kernel, best_c.T, best_c.threads, best_ctas, best_c.U, best_c.V);
+    s->act_force = true;  // restored below; stamps of the trials are stale
     CK(cudaMemcpyAsync(s->state, snap, b_state, cudaMemcpyDeviceToDevice, st));
     if (b_mem) CK(cudaMemcpyAsync(s->mem, snap + b_state, b_mem, cudaMemcpyDeviceToDevice, st));
     if (b_xs) CK(cudaMemcpyAsync(s->xs, snap + b_state + b_mem, b_xs, cudaMemcpyDeviceToDevice, st));
@@ -1122,6 +1287,22 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       cudaGraphExecDestroy(ge);
       cudaGraphDestroy(g);
       cudaStreamDestroy(cap);
+    } else if (s->kernel == RTEAAL_KERNEL_SPECIALIZED) {
+      require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
+      if (probing && probe_mode != RTEAAL_PROBE_LAST)
+        throw Error(RTEAAL_E_UNSUPPORTED, "design-specialised kernel: probes in LAST mode only");
+      uint8_t* a_st = s->state;
+      uint64_t* a_mem = s->mem;
+      uint64_t* a_xs = s->xs;
+      const uint64_t* a_stim = ds.stim;
+      const uint32_t* a_budget = ds.budget;
+      const uint32_t* a_rl = ds.reset_lane;
+      const uint32_t* a_uol = ds.user_of_lane;
+      uint32_t a_np = s->n_pad, a_nu = s->n_user, a_uni = ds.uniform;
+      int a_mode = ds.stim_mode, a_reset = ds.reset;
+      void* args[] = {&a_st, &a_mem, &a_xs, &a_stim, &a_budget, &a_rl, &a_uol, &a_np, &a_nu, &a_uni, &a_mode, &a_reset};
+      CK(cudaLaunchKernel((const void*)D->spec_kernel, dim3(s->grid), dim3(kSpecThreads), args, 0, st));
+      CK(cudaGetLastError());
     } else if (s->kernel == RTEAAL_KERNEL_TILE) {
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
       const uint32_t T = s->tile_lanes;
@@ -1179,10 +1360,25 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       ga.ncyc = (uint32_t)max_cyc;
       ga.tpo = make_fastdiv((uint32_t)(np / s->V));
       CK(cudaMemsetAsync(s->scratch, 0, 16, st));
-      const Variant* v = find_variant(s->V, U, s->threads);
-      require(v != nullptr, "rteaal_step: no kernel variant for this configuration");
+      const void* fn = nullptr;
+      if (s->activity) {
+        const ActVariant* av = find_act_variant(s->V, s->threads);
+        require(av != nullptr, "rteaal_step: no activity-aware variant for this configuration");
+        fn = av->grid;
+        // uneven budgets leave some lanes' last edge unseen by the next step's
+        // first cycle, which therefore evaluates everything
+        bool uneven = false;
+        if (cycles->per_instance)
+          for (uint32_t u = 0; u < s->n_user && !uneven; u++) uneven = cycles->per_instance[u] != max_cyc;
+        s->act_g += max_cyc;
+        s->act_force = uneven;
+      } else {
+        const Variant* v = find_variant(s->V, U, s->threads);
+        require(v != nullptr, "rteaal_step: no kernel variant for this configuration");
+        fn = v->grid;
+      }
       void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ga};
-      cudaError_t e = cudaLaunchCooperativeKernel(v->grid, dim3(s->grid), dim3(s->threads), args, 0, st);
+      cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(s->grid), dim3(s->threads), args, 0, st);
       if (e == cudaErrorCooperativeLaunchTooLarge)
         throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
       CK(e);
@@ -1236,6 +1432,7 @@ RT_EXPORT int rteaal_sim_reset_lanes(rteaal_sim* s, uint32_t inst0, uint32_t n_i
     }
     const size_t total = ((size_t)L.n_slots + L.mem_words_total + ni) * n_inst;
     const uint32_t blocks = (uint32_t)std::min<size_t>((total + 255) / 256, (size_t)D->n_sms * 32);
+    s->act_force = true;
     k_reset_lanes<<<blocks, 256, 0, st>>>(s->state, s->mem, s->xs, s->n_pad, D->d_slot_ref, L.n_slots, L.const_base,
                                           (uint32_t)L.const_value.size(), D->d_const_value, L.mem_words_total,
                                           ni, xs_in, s->lane_of_user, inst0, n_inst);
@@ -1258,6 +1455,7 @@ enum class Region { STATE, MEM, XS };
 void transfer(rteaal_sim* s, Region region, const uint32_t* signals, uint32_t n, uint32_t inst0, uint32_t n_inst,
               uint64_t* out, const uint64_t* in, cudaStream_t st) {
   require(s, "null sim");
+  if (in) s->act_force = true;  // written values carry no change stamps
   require(out || in, "null host buffer");
   require((uint64_t)inst0 + n_inst <= s->n_user, "instance range out of bounds");
   CK(cudaSetDevice(s->design->device));

@@ -422,6 +422,112 @@ def generate(spec: DesignSpec) -> Netlist:
 
 
 # ---------------------------------------------------------------------------
+# Modular, enable-gated designs (low activity)
+# ---------------------------------------------------------------------------
+@dataclass
+class ModularSpec:
+    """M independent modules (each a random layered DAG of its own signals and
+    primary inputs), a global 32-bit cycle counter, and per module an enable
+    that is true one cycle in 2^k_m (k_m uniform in [k_lo, k_hi]): every
+    register of module m loads its next state only when the enable is set,
+    else holds -- the structure of clock-gated blocks in real designs.  Driven
+    with inputs that change rarely (e.g. random values at reset, then held),
+    a module's logic sees a change only in the cycle after its enable."""
+    n_modules: int
+    ops_per_module: int
+    regs_per_module: int
+    depth: int
+    seed: int
+    inputs_per_module: int = 16
+    k_lo: int = 2
+    k_hi: int = 7
+
+
+def generate_modular(ms: ModularSpec) -> Netlist:
+    rng = Rng(ms.seed, stream=0x40D00000 + GEN_VERSION)
+    mods = [generate(DesignSpec(n_ops=ms.ops_per_module, n_regs=ms.regs_per_module, depth=ms.depth,
+                                n_inputs=ms.inputs_per_module, seed=ms.seed * 1000 + m))
+            for m in range(ms.n_modules)]
+    M = ms.n_modules
+    ks = ms.k_lo + rng.below(ms.k_hi - ms.k_lo + 1, M).astype(np.int64)
+    phase = rng.below(1 << 20, M).astype(np.int64) & ((np.int64(1) << ks) - 1)
+
+    def offs(v):
+        return np.concatenate([[0], np.cumsum(v)]).astype(np.int64)
+    in_off = offs([m.n_inputs for m in mods])
+    reg_off = offs([m.n_regs for m in mods])
+    const_off = offs([m.n_consts for m in mods])
+    op_off = offs([m.n_ops for m in mods])
+    I = int(in_off[-1])
+    R = int(reg_off[-1]) + 1                   # + the cycle counter (last register)
+    C = int(const_off[-1]) + 1 + M             # + const 1, + one phase constant per module
+    reg_base, const_base = I, I + R
+    op_base = I + R + C
+    cnt = reg_base + R - 1
+    c_one = const_base + int(const_off[-1])
+
+    def remap(m, x):
+        nl = mods[m]
+        x = np.asarray(x, np.int64)
+        return np.select(
+            [x < nl.reg_base, x < nl.const_base, x < nl.op_base],
+            [in_off[m] + x, reg_base + reg_off[m] + (x - nl.reg_base),
+             const_base + const_off[m] + (x - nl.const_base)],
+            op_base + op_off[m] + (x - nl.op_base))
+
+    # enable logic and hold muxes, appended after every module op
+    base_extra = op_base + int(op_off[-1])
+    n_extra = 1 + 2 * M + (R - 1)
+    e_code = np.zeros(n_extra, np.uint8)
+    e_w = np.zeros(n_extra, np.uint8)
+    e_p0 = np.zeros(n_extra, np.uint8)
+    e_args = np.zeros((n_extra, 3), np.int64)
+    e_ar = np.zeros(n_extra, np.int64)
+    e_code[0], e_w[0], e_args[0, :2], e_ar[0] = OP["ADD"], 32, (cnt, c_one), 2
+    for m in range(M):
+        j = 1 + 2 * m
+        e_code[j], e_w[j], e_p0[j], e_args[j, 0], e_ar[j] = OP["BITS"], 8, ks[m] - 1, cnt, 1
+        e_code[j + 1], e_w[j + 1], e_ar[j + 1] = OP["EQ"], 1, 2
+        e_args[j + 1, :2] = (base_extra + j, c_one + 1 + m)
+    new_d = []
+    j = 1 + 2 * M
+    for m, nl in enumerate(mods):
+        nr = nl.n_regs
+        sl = slice(j, j + nr)
+        e_code[sl], e_w[sl], e_ar[sl] = OP["MUX"], nl.reg_width, 3
+        e_args[sl, 0] = base_extra + 2 + 2 * m                          # enable of module m
+        e_args[sl, 1] = remap(m, nl.reg_d)                              # next state
+        e_args[sl, 2] = reg_base + reg_off[m] + np.arange(nr)           # hold
+        new_d.append(base_extra + np.arange(j, j + nr))
+        j += nr
+    e_flat = e_args[np.arange(3)[None, :] < e_ar[:, None]]
+
+    args = np.concatenate([remap(m, nl.args) for m, nl in enumerate(mods)] + [e_flat])
+    arity = np.concatenate([np.diff(nl.op_argoff.astype(np.int64)) for nl in mods] + [e_ar])
+    argoff = np.concatenate([[0], np.cumsum(arity)])
+    cat = np.concatenate
+    return Netlist(
+        input_width=cat([nl.input_width for nl in mods]).astype(np.uint8),
+        reg_width=cat([nl.reg_width for nl in mods] + [np.array([32])]).astype(np.uint8),
+        reg_d=cat(new_d + [np.array([base_extra])]).astype(np.uint32),
+        reg_init=cat([nl.reg_init for nl in mods] + [np.zeros(1, np.uint64)]).astype(np.uint64),
+        const_width=cat([nl.const_width for nl in mods] + [np.array([32] + [8] * M)]).astype(np.uint8),
+        const_value=cat([nl.const_value for nl in mods] + [np.array([1] + list(phase), np.uint64)]).astype(np.uint64),
+        op_code=cat([nl.op_code for nl in mods] + [e_code]).astype(np.uint8),
+        op_width=cat([nl.op_width for nl in mods] + [e_w]).astype(np.uint8),
+        op_p0=cat([nl.op_p0 for nl in mods] + [e_p0]).astype(np.uint8),
+        op_p1=cat([nl.op_p1 for nl in mods] + [np.zeros(n_extra, np.uint8)]).astype(np.uint8),
+        op_argoff=argoff.astype(np.uint32),
+        args=args.astype(np.uint32))
+
+
+def spec_quiet(seed: int = 6) -> ModularSpec:
+    """1M ops in 64 enable-gated modules of 15,625 ops, depth 80, 1,024 registers
+    and 16 inputs each."""
+    return ModularSpec(n_modules=64, ops_per_module=15_625, regs_per_module=1024, depth=80, seed=seed)
+
+
+# ---------------------------------------------------------------------------
 # Stimulus seeds and per-instance cycle budgets
 # ---------------------------------------------------------------------------
 def xorshift_seeds(seed: int, n_inputs: int, n_instances: int) -> np.ndarray:

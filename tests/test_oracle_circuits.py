@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 from synth import OP, Builder
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -340,3 +341,35 @@ def test_waveform_changes_of_counter_bits():
                 exp.append((c, k, 0, (c >> k) & 1))
     assert [tuple(int(x) for x in r) for r in ev] == sorted(exp)
     assert sum(1 for r in ev if r[1] == 0) == n - 1          # bit 0 toggles every cycle after 0
+
+
+def test_modular_generator_gates_registers_by_enable():
+    """Generator pin for the low-activity workload: a register of module m takes
+    a new value only in cycles whose counter value c has c mod 2^k_m = phase_m
+    (its hold mux selects Q otherwise); the cycle counter counts cycles."""
+    ms = synth.ModularSpec(n_modules=4, ops_per_module=300, regs_per_module=20, depth=6, seed=3,
+                           inputs_per_module=4)
+    nl = synth.generate_modular(ms)
+    o = oracle.OracleSim(nl.to_bytes(), 4)
+    xs = synth.xorshift_seeds(3, nl.n_inputs, 4)
+    o.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=xs)
+    cnt = nl.reg_base + nl.n_regs - 1
+    # module m's enable is op (1 + 2m + 1) of the appended block; its BITS p0 = k - 1,
+    # its phase constant is the EQ's second operand
+    extra0 = nl.n_ops - (1 + 2 * ms.n_modules + (nl.n_regs - 1))
+    ks, phases = [], []
+    for m in range(ms.n_modules):
+        bits = extra0 + 1 + 2 * m
+        ks.append(int(nl.op_p0[bits]) + 1)
+        phases.append(int(nl.const_value[int(nl.op_args(bits + 1)[1]) - nl.const_base]))
+    prev = o.read()
+    for c in range(40):
+        q = int(o.read([cnt])[0, 0])
+        assert q == c                                       # counter closed form
+        o.step(1, mode=oracle.STIM_HOLD, xs=xs)
+        cur = o.read()
+        for m in range(ms.n_modules):
+            regs = nl.reg_base + m * ms.regs_per_module + np.arange(ms.regs_per_module)
+            if q % (1 << ks[m]) != phases[m]:
+                assert np.array_equal(cur[regs], prev[regs]), (c, m)
+        prev = cur
