@@ -479,6 +479,22 @@ def run_serving(args) -> None:
             "latency": st, "offered_op_evals_per_s": work / max(span, 1e-9),
             "served_op_evals_per_s": work / wall, "wall_s": wall, "rounds": srv.rounds,
             "clocks": clk.summary()}
+    if args.serve_load > 0:
+        # the same job distribution at a Poisson rate that offers `serve_load` of the
+        # capacity just measured (work per second served at saturation)
+        mean_work = work / max(1, len(done))
+        rate = args.serve_load * (work / wall) / mean_work
+        trace2 = poisson_trace(5, args.serve_jobs, rate, list(sizes), np.log(1e4), 1.0, 64,
+                               cycles_cap=args.cycles_cap or None)
+        srv.done.clear()
+        t1 = time.perf_counter()
+        done2 = srv.run(trace2)
+        wall2 = time.perf_counter() - t1
+        work2 = float(sum(j.n_instances * j.cycles * nls[j.design].n_ops for j in done2))
+        line["sub_saturation"] = {
+            "load_target": args.serve_load, "rate_hz": rate, "jobs": len(done2),
+            "offered_op_evals_per_s": work2 / max(max(j.arrival for j in trace2), 1e-9),
+            "served_op_evals_per_s": work2 / wall2, "latency": latency_stats(done2), "wall_s": wall2}
     print(json.dumps(line))
 
 
@@ -491,6 +507,8 @@ def main():
     ap.add_argument("--workload", default="batch-1M", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-load", type=float, default=0.0,
+                    help="serving: also replay a trace offering this fraction of the measured capacity")
     ap.add_argument("--quantum", type=int, default=2000)
     ap.add_argument("--cycles-cap", type=int, default=0)
     ap.add_argument("--kernel", default="tile")
