@@ -403,6 +403,8 @@ def run_ours(args) -> None:
         si, sc = cpu_sample_size(args.workload)
         cpu = cpu_oracle_rate(nl, si, sc, 7, os.cpu_count() or 1)
         cpu.pop("seconds", None)
+        one = cpu_oracle_rate(nl, max(1, si // 16), sc, 7, 1)     # the same oracle on one core
+        cpu["single_core"] = {"value": one["value"], "sample": one["sample"]}
 
     if rank == 0:
         line = {
@@ -482,10 +484,15 @@ def run_serving(args) -> None:
     if args.serve_load > 0:
         # the same job distribution at a Poisson rate that offers `serve_load` of the
         # capacity just measured (work per second served at saturation)
-        mean_work = work / max(1, len(done))
-        rate = args.serve_load * (work / wall) / mean_work
-        trace2 = poisson_trace(5, args.serve_jobs, rate, list(sizes), np.log(1e4), 1.0, 64,
+        trace2 = poisson_trace(5, args.serve_jobs, 1.0, list(sizes), np.log(1e4), 1.0, 64,
                                cycles_cap=args.cycles_cap or None)
+        # stretch the arrivals so that this trace's own work arrives at the target load
+        w2 = float(sum(j.n_instances * j.cycles * nls[j.design].n_ops for j in trace2))
+        span2 = w2 / (args.serve_load * (work / wall))
+        last = max(j.arrival for j in trace2)
+        for j in trace2:
+            j.arrival *= span2 / last
+        rate = len(trace2) / span2
         srv.done.clear()
         t1 = time.perf_counter()
         done2 = srv.run(trace2)

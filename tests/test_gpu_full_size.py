@@ -1,6 +1,8 @@
 """Parity at the workloads' full sizes, on sampled instances the oracle can follow.
 
 * single-200k: 200k-op DAG, 1 instance, plain per-layer form and the grid form;
+  and the whole configuration -- reset + 100,000 cycles -- in the CUDA-graph
+  plain form, every signal checked (the oracle runs alongside on the host);
 * batch-1M: 1M ops, 4,096 instances with uneven cycle budgets, in the launch
   configuration the benchmark times (autotuned), three sampled instances
   (first, middle, last lane) checked signal by signal;
@@ -24,6 +26,33 @@ def test_single_200k_plain_and_grid():
         p.step(300)
         p.compare()
         p.close()
+
+
+def test_single_200k_full_length():
+    import threading
+
+    import oracle
+    import paper_2601_18140_gb300 as rt
+    nl = synth.generate(synth.spec_single())
+    xs = synth.xorshift_seeds(1, nl.n_inputs, 1)
+    o = oracle.OracleSim(nl.to_bytes(), 1)
+    oxs = xs.copy()
+
+    def run_oracle():
+        o.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=oxs)
+        o.step(100_000, mode=oracle.STIM_XORSHIFT, xs=oxs)
+
+    t = threading.Thread(target=run_oracle)    # the C oracle runs without the GIL
+    t.start()
+    d = rt.Design(nl.to_bytes())
+    s = rt.Sim(d, 1, kernel="layer_graph", xorshift_seed=xs)
+    s.step(1, stimulus="xorshift", reset=True)
+    s.step(100_000, stimulus="xorshift")
+    g = s.read()
+    t.join()
+    assert np.array_equal(g, o.read())
+    s.close()
+    d.close()
 
 
 def test_batch_1m_bench_configuration():
