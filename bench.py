@@ -351,20 +351,19 @@ def run_ours(args) -> None:
         import oracle
         run_cycles = budgets.astype(np.int64) - remaining
         sample = np.array(sorted({0, n // 3, n - 1}), np.int64)
-        if True:
-            o = oracle.OracleSim(nl.to_bytes(), sample.size)
-            oxs = np.ascontiguousarray(xs[:, sample])
-            o.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=oxs, threads=os.cpu_count() or 1)
-            o.step(run_cycles[sample].astype(np.uint32),
-                   mode=oracle.STIM_HOLD if run_stim == "hold" else oracle.STIM_XORSHIFT, xs=oxs,
-                   threads=os.cpu_count() or 1)
-            live = design.present_signals()           # every signal unless fusion absorbed some
-            ok = all(np.array_equal(sim.read(live, int(i), 1)[:, 0], o.vals[k][live])
-                     for k, i in enumerate(sample))
-            parity = ("bit-exact" if ok else "MISMATCH") + " on instances %s after %s cycles" % (
-                list(map(int, sample)), list(map(int, run_cycles[sample])))
-            if not ok:
-                print("PARITY FAILURE", parity, file=sys.stderr)
+        o = oracle.OracleSim(nl.to_bytes(), sample.size)
+        oxs = np.ascontiguousarray(xs[:, sample])
+        o.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=oxs, threads=os.cpu_count() or 1)
+        o.step(run_cycles[sample].astype(np.uint32),
+               mode=oracle.STIM_HOLD if run_stim == "hold" else oracle.STIM_XORSHIFT, xs=oxs,
+               threads=os.cpu_count() or 1)
+        live = design.present_signals()           # every signal unless fusion absorbed some
+        ok = all(np.array_equal(sim.read(live, int(i), 1)[:, 0], o.vals[k][live])
+                 for k, i in enumerate(sample))
+        parity = ("bit-exact" if ok else "MISMATCH") + " on instances %s after %s cycles" % (
+            list(map(int, sample)), list(map(int, run_cycles[sample])))
+        if not ok:
+            print("PARITY FAILURE", parity, file=sys.stderr)
 
     # ---- e2e through the public API with host buffers
     e2e = None

@@ -96,6 +96,8 @@ void lower_netlist(const Netlist& nl, Lowered& out, bool fuse_mux_chains = false
 // thread simulating one lane for all cycles of a step, and its NVRTC compile
 // for `arch` (e.g. "sm_103a").  compile returns false with the log on failure.
 std::string specialized_source(const Netlist& nl, const Lowered& L);
-bool compile_specialized(const std::string& src, const char* arch, std::vector<char>& cubin, std::string& log);
+// optimize: run the NVVM optimiser (its time grows superlinearly with the length).
+bool compile_specialized(const std::string& src, const char* arch, bool optimize, std::vector<char>& cubin,
+                         std::string& log);
 
 }  // namespace rteaal

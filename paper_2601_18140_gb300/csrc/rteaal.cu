@@ -751,6 +751,7 @@ constexpr int kStreamConsumerWarps = 16;
 
 constexpr uint32_t kSpecMaxOps = 16384;
 constexpr uint32_t kSpecThreads = 128;
+constexpr uint32_t kSpecOptimizeOps = 4096;  // NVVM optimiser on up to this many ops
 
 // Generate, compile (NVRTC, sm_103a) and load the design-specialised kernel once.
 void ensure_specialized(rteaal_design* d) {
@@ -762,7 +763,7 @@ void ensure_specialized(rteaal_design* d) {
   const std::string src = specialized_source(d->nl, d->L);
   std::vector<char> cubin;
   std::string log;
-  if (!compile_specialized(src, "sm_103a", cubin, log))
+  if (!compile_specialized(src, "sm_103a", d->nl.no <= kSpecOptimizeOps, cubin, log))
     throw Error(RTEAAL_E_CUDA, "design-specialised kernel: compile failed: " + log.substr(0, 2000));
   CK(cudaSetDevice(d->device));
   CK(cudaLibraryLoadData(&d->spec_lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));

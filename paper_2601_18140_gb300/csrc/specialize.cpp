@@ -18,6 +18,7 @@
 #include <sstream>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "lower.hpp"
 
@@ -205,19 +206,24 @@ struct Gen {
 
 std::string specialized_source(const Netlist& nl, const Lowered& L) { return Gen(nl, L).source(); }
 
-bool compile_specialized(const std::string& src, const char* arch, std::vector<char>& cubin, std::string& log) {
+bool compile_specialized(const std::string& src, const char* arch, bool optimize, std::vector<char>& cubin,
+                         std::string& log) {
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "rteaal_spec.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
     log = "nvrtcCreateProgram failed";
     return false;
   }
   const std::string a = std::string("--gpu-architecture=") + arch;
-  // The straight-line body is optimised by ptxas; the NVVM optimiser adds
-  // little on it but grows superlinearly with its length, so it is off unless
-  // RTEAAL_SPEC_NVRTC_OPT names another option (e.g. "-Xnvvm=-opt=3").
+  // Every signal is a local, so ptxas would take 255 registers and keep 8 warps
+  // per SM; a cap of 96 trades a few spills for 4x the resident warps.  With
+  // the cap, the NVVM optimiser pays (1.4x on a 2k-op design, 9.6 s compile);
+  // its time grows superlinearly with the body, so long designs go without it
+  // (ptxas still optimises).  RTEAAL_SPEC_NVRTC_OPT adds one more option.
   const char* extra = std::getenv("RTEAAL_SPEC_NVRTC_OPT");
-  const char* opts[] = {a.c_str(), "--std=c++17", "-w", extra ? extra : "-Xnvvm=-opt=0"};
-  const nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+  std::vector<const char*> opts = {a.c_str(), "--std=c++17", "-w", "--maxrregcount=96"};
+  if (!optimize) opts.push_back("-Xnvvm=-opt=0");
+  if (extra) opts.push_back(extra);
+  const nvrtcResult r = nvrtcCompileProgram(prog, (int)opts.size(), opts.data());
   size_t n = 0;
   nvrtcGetProgramLogSize(prog, &n);
   log.assign(n, '\0');
