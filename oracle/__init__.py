@@ -51,7 +51,7 @@ def lib():
         P = ctypes.c_void_p
         L.oracle_sizes.argtypes = [u8p, ctypes.c_size_t, P]
         L.oracle_init.argtypes = [u8p, ctypes.c_size_t, ctypes.c_uint32, P, P]
-        L.oracle_run.argtypes = [u8p, ctypes.c_size_t, ctypes.c_uint32, P, P, P, ctypes.c_int,
+        L.oracle_run.argtypes = [u8p, ctypes.c_size_t, ctypes.c_uint32, P, P, P, P, ctypes.c_int,
                                  ctypes.c_int, P, ctypes.c_uint32, P, ctypes.c_uint32,
                                  ctypes.c_uint32, P, ctypes.c_uint32, P, ctypes.c_uint32,
                                  ctypes.c_int]
@@ -95,6 +95,7 @@ class OracleSim:
         self.mems = np.zeros((n_inst, max(self.mem_total, 1)), np.uint64)
         rc = lib().oracle_init(self.nl, len(self.nl), n_inst, _ptr(self.vals), _ptr(self.mems))
         assert rc == 0
+        self.ticks = np.zeros(n_inst, np.uint32)   # non-reset cycles since reset (clock domains)
 
     def step(self, cycles, reset: bool = False, mode: int = STIM_HOLD, xs: np.ndarray | None = None,
              buf: np.ndarray | None = None, probes=None, probe_cycles: int = 0,
@@ -117,7 +118,7 @@ class OracleSim:
             psig = np.ascontiguousarray(np.asarray(probes, np.uint32))
             out = np.zeros((probe_cycles, psig.size, self.n_inst), np.uint64)
         rc = lib().oracle_run(self.nl, len(self.nl), self.n_inst, _ptr(self.vals), _ptr(self.mems),
-                              _ptr(cyc), int(reset), mode, _ptr(xs), self.n_inst, _ptr(buf),
+                              _ptr(self.ticks), _ptr(cyc), int(reset), mode, _ptr(xs), self.n_inst, _ptr(buf),
                               self.n_inst, stim_cycles, _ptr(psig),
                               0 if psig is None else psig.size, _ptr(out), probe_cycles, threads)
         if rc:

@@ -14,6 +14,11 @@
  *   3. at the edge: every register takes reset ? init : v[D] (masked to its
  *      width); memory write ports apply in port order;
  *   4. the next cycle reads the new register values.
+ * Clock domains (optional; the paper's multi-clock reading, Sec. 5.2 "Multiple
+ * Clock Domains"): each instance counts t, the non-reset cycles completed since
+ * its last reset cycle; at the edge of a non-reset cycle a register of domain
+ * (period p, phase f) takes v[D] only if (t + f) mod p == 0, else it keeps its
+ * value; a reset cycle resets every register and sets t = 0.
  * Operation semantics are the readings written down in include/rteaal.h
  * (UInt only, every value zero-extended in 64 bits, masked to its width).
  *
@@ -38,6 +43,9 @@ typedef struct {
   const uint64_t *reg_init, *const_value;
   const uint32_t *reg_d, *argoff, *args, *mem_words, *wport;
   const uint8_t *in_w, *reg_w, *const_w, *code, *width, *p0, *p1, *mem_w;
+  uint32_t nd;                          /* clock domains (0: one clock)       */
+  const uint32_t *dom_period, *dom_phase;
+  const uint8_t *reg_dom;
   uint64_t *mem_off; /* word offset of each memory inside one instance's memory block */
   uint64_t mem_total;
 } onl;
@@ -60,10 +68,11 @@ static int onl_parse(const uint8_t *bytes, size_t nbytes, onl *n) {
   const uint32_t *h = (const uint32_t *)n->buf;
   if (h[0] != 0x4E4C5452u || h[1] != 1u) goto bad;
   n->ni = h[2]; n->nr = h[3]; n->nc = h[4]; n->no = h[5]; n->nm = h[6]; n->nw = h[7]; n->na = h[8];
+  n->nd = h[9];
   {
     uint64_t need = 40 + 8ull * n->nr + 8ull * n->nc + 4ull * n->nr + 4ull * (n->no + 1ull) +
-                    4ull * n->na + 4ull * n->nm + 16ull * n->nw + n->ni + n->nr + n->nc +
-                    4ull * n->no + n->nm;
+                    4ull * n->na + 4ull * n->nm + 16ull * n->nw + 8ull * n->nd + n->ni + n->nr +
+                    n->nc + 4ull * n->no + n->nm + (n->nd ? n->nr : 0);
     if (need != nbytes) goto bad;
   }
   {
@@ -75,6 +84,8 @@ static int onl_parse(const uint8_t *bytes, size_t nbytes, onl *n) {
     n->args = (const uint32_t *)p; p += 4ull * n->na;
     n->mem_words = (const uint32_t *)p; p += 4ull * n->nm;
     n->wport = (const uint32_t *)p; p += 16ull * n->nw;
+    n->dom_period = (const uint32_t *)p; p += 4ull * n->nd;
+    n->dom_phase = (const uint32_t *)p; p += 4ull * n->nd;
     n->in_w = p; p += n->ni;
     n->reg_w = p; p += n->nr;
     n->const_w = p; p += n->nc;
@@ -82,8 +93,14 @@ static int onl_parse(const uint8_t *bytes, size_t nbytes, onl *n) {
     n->width = p; p += n->no;
     n->p0 = p; p += n->no;
     n->p1 = p; p += n->no;
-    n->mem_w = p;
+    n->mem_w = p; p += n->nm;
+    n->reg_dom = n->nd ? p : NULL;
   }
+  for (uint32_t d = 0; d < n->nd; d++) {
+    uint32_t per = n->dom_period[d];
+    if (per == 0 || per > (1u << 31) || (per & (per - 1)) != 0 || n->dom_phase[d] >= per) goto bad;
+  }
+  for (uint32_t r = 0; n->nd && r < n->nr; r++) if (n->reg_dom[r] >= n->nd) goto bad;
   n->reg_base = n->ni;
   n->const_base = n->ni + n->nr;
   n->op_base = n->ni + n->nr + n->nc;
@@ -197,6 +214,7 @@ typedef struct {
   const onl *n;
   uint32_t n_inst, i0, i1;
   uint64_t *vals, *mems;
+  uint32_t *ticks;                      /* [n_inst] t of each instance (domains) */
   const uint32_t *cycles;
   int reset, stim_mode;
   uint64_t *xs; uint32_t xs_ld;
@@ -232,8 +250,17 @@ static void *run_range(void *arg) {
       /* 2. every operation, in topological order */
       for (uint32_t k = 0; k < n->no; k++) v[n->op_base + k] = eval_op(n, k, v, mem);
       /* 3. clock edge: next states from pre-edge values, memory writes, then commit */
-      for (uint32_t r = 0; r < n->nr; r++)
-        next[r] = (j->reset ? n->reg_init[r] : v[n->reg_d[r]]) & mask_w(n->reg_w[r]);
+      for (uint32_t r = 0; r < n->nr; r++) {
+        if (j->reset) {
+          next[r] = n->reg_init[r] & mask_w(n->reg_w[r]);
+        } else if (n->nd && (uint32_t)(j->ticks[i] + n->dom_phase[n->reg_dom[r]]) %
+                                    n->dom_period[n->reg_dom[r]] != 0) {
+          next[r] = v[n->reg_base + r];     /* its domain does not tick this cycle */
+        } else {
+          next[r] = v[n->reg_d[r]] & mask_w(n->reg_w[r]);
+        }
+      }
+      if (n->nd) j->ticks[i] = j->reset ? 0u : j->ticks[i] + 1u;
       for (uint32_t p = 0; p < n->nw; p++) {
         const uint32_t *w = n->wport + 4ull * p;
         if (v[w[1]] & 1u) {
@@ -283,19 +310,21 @@ int oracle_init(const uint8_t *nl, size_t nb, uint32_t n_inst, uint64_t *vals, u
   return 0;
 }
 
-/* Runs cycles[i] cycles on instance i.  stim_mode: 0 hold, 1 xorshift (xs is
+/* Runs cycles[i] cycles on instance i; ticks [n_inst] (needed with clock
+ * domains, else nullable) holds each instance's t and is updated.  stim_mode: 0 hold, 1 xorshift (xs is
  * [n_inputs][xs_ld], updated in place), 2 explicit values stim[cycle][input][stim_ld].
  * probe_out (nullable) receives [cycle][probe][n_inst] for cycle < probe_cycles.
  * Returns 0, -1 (bad argument) or -2 (format). */
 int oracle_run(const uint8_t *nl, size_t nb, uint32_t n_inst, uint64_t *vals, uint64_t *mems,
-               const uint32_t *cycles, int reset, int stim_mode, uint64_t *xs, uint32_t xs_ld,
+               uint32_t *ticks, const uint32_t *cycles, int reset, int stim_mode, uint64_t *xs, uint32_t xs_ld,
                const uint64_t *stim, uint32_t stim_ld, uint32_t stim_cycles,
                const uint32_t *probe_sig, uint32_t n_probe, uint64_t *probe_out,
                uint32_t probe_cycles, int n_threads) {
   onl n;
   int rc = onl_parse(nl, nb, &n);
   if (rc) return rc;
-  if ((stim_mode == 1 && !xs) || (stim_mode == 2 && !stim) || stim_mode < 0 || stim_mode > 2) {
+  if ((stim_mode == 1 && !xs) || (stim_mode == 2 && !stim) || stim_mode < 0 || stim_mode > 2 ||
+      (n.nd && !ticks)) {
     onl_free(&n);
     return -1;
   }
@@ -309,7 +338,7 @@ int oracle_run(const uint8_t *nl, size_t nb, uint32_t n_inst, uint64_t *vals, ui
     j->n = &n; j->n_inst = n_inst;
     j->i0 = (uint32_t)((uint64_t)n_inst * t / n_threads);
     j->i1 = (uint32_t)((uint64_t)n_inst * (t + 1) / n_threads);
-    j->vals = vals; j->mems = mems; j->cycles = cycles; j->reset = reset;
+    j->vals = vals; j->mems = mems; j->ticks = ticks; j->cycles = cycles; j->reset = reset;
     j->stim_mode = stim_mode; j->xs = xs; j->xs_ld = xs_ld;
     j->stim = stim; j->stim_ld = stim_ld; j->stim_cycles = stim_cycles;
     j->probe_sig = probe_sig; j->n_probe = n_probe; j->probe_out = probe_out;

@@ -62,6 +62,11 @@ class Netlist:
     mem_words: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint32))  # u32 [n_mems]
     mem_width: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint8))   # u8 [n_mems]
     wport: np.ndarray = field(default_factory=lambda: np.zeros((0, 4), np.uint32))  # u32 [n_wports][mem,en,addr,data]
+    # optional clock domains: per domain a period (power of two) and a phase in
+    # base-clock cycles; per register its domain (no domains: one base clock)
+    dom_period: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint32))  # u32 [n_domains]
+    dom_phase: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint32))   # u32 [n_domains]
+    reg_domain: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint8))   # u8 [n_regs] if domains
 
     # ---- sizes -------------------------------------------------------------
     @property
@@ -76,6 +81,8 @@ class Netlist:
     def n_mems(self) -> int: return int(self.mem_words.size)
     @property
     def n_wports(self) -> int: return int(self.wport.shape[0])
+    @property
+    def n_domains(self) -> int: return int(self.dom_period.size)
     @property
     def n_signals(self) -> int: return self.n_inputs + self.n_regs + self.n_consts + self.n_ops
     @property
@@ -94,8 +101,9 @@ class Netlist:
 
     # ---- serialisation -----------------------------------------------------
     def to_bytes(self) -> bytes:
+        nd = self.n_domains
         hdr = HEADER.pack(MAGIC, VERSION, self.n_inputs, self.n_regs, self.n_consts,
-                          self.n_ops, self.n_mems, self.n_wports, int(self.args.size), 0)
+                          self.n_ops, self.n_mems, self.n_wports, int(self.args.size), nd)
         parts = [hdr,
                  np.ascontiguousarray(self.reg_init, "<u8").tobytes(),
                  np.ascontiguousarray(self.const_value, "<u8").tobytes(),
@@ -104,6 +112,8 @@ class Netlist:
                  np.ascontiguousarray(self.args, "<u4").tobytes(),
                  np.ascontiguousarray(self.mem_words, "<u4").tobytes(),
                  np.ascontiguousarray(self.wport.reshape(-1, 4), "<u4").tobytes(),
+                 np.ascontiguousarray(self.dom_period, "<u4").tobytes() if nd else b"",
+                 np.ascontiguousarray(self.dom_phase, "<u4").tobytes() if nd else b"",
                  np.ascontiguousarray(self.input_width, "u1").tobytes(),
                  np.ascontiguousarray(self.reg_width, "u1").tobytes(),
                  np.ascontiguousarray(self.const_width, "u1").tobytes(),
@@ -111,12 +121,13 @@ class Netlist:
                  np.ascontiguousarray(self.op_width, "u1").tobytes(),
                  np.ascontiguousarray(self.op_p0, "u1").tobytes(),
                  np.ascontiguousarray(self.op_p1, "u1").tobytes(),
-                 np.ascontiguousarray(self.mem_width, "u1").tobytes()]
+                 np.ascontiguousarray(self.mem_width, "u1").tobytes(),
+                 np.ascontiguousarray(self.reg_domain, "u1").tobytes() if nd else b""]
         return b"".join(parts)
 
     @staticmethod
     def from_bytes(buf: bytes) -> "Netlist":
-        (magic, ver, ni, nr, nc, no, nm, nw, na, _r) = HEADER.unpack_from(buf, 0)
+        (magic, ver, ni, nr, nc, no, nm, nw, na, nd) = HEADER.unpack_from(buf, 0)
         if magic != MAGIC or ver != VERSION:
             raise ValueError("not an RTLN v1 netlist")
         off = HEADER.size
@@ -134,6 +145,8 @@ class Netlist:
         args = take("<u4", na).astype(np.uint32)
         mem_words = take("<u4", nm).astype(np.uint32)
         wport = take("<u4", 4 * nw).astype(np.uint32).reshape(nw, 4)
+        dom_period = take("<u4", nd).astype(np.uint32)
+        dom_phase = take("<u4", nd).astype(np.uint32)
         input_width = take("u1", ni)
         reg_width = take("u1", nr)
         const_width = take("u1", nc)
@@ -142,11 +155,12 @@ class Netlist:
         op_p0 = take("u1", no)
         op_p1 = take("u1", no)
         mem_width = take("u1", nm)
+        reg_domain = take("u1", nr if nd else 0)
         if off != len(buf):
             raise ValueError("trailing bytes in netlist")
         return Netlist(input_width, reg_width, reg_d, reg_init, const_width, const_value,
                        op_code, op_width, op_p0, op_p1, op_argoff, args,
-                       mem_words, mem_width, wport)
+                       mem_words, mem_width, wport, dom_period, dom_phase, reg_domain)
 
 
 class Builder:
@@ -159,6 +173,8 @@ class Builder:
         self.ops: list[tuple] = []          # (code, width, p0, p1, args-as-handles)
         self.mems: list[tuple] = []         # (words, width)
         self.wports: list[tuple] = []       # (mem, en, addr, data) as handles
+        self.domains: list[tuple] = []      # (period, phase)
+        self.reg_dom: dict[int, int] = {}   # register index -> domain
 
     # Handles are ("i", k), ("r", k), ("c", k), ("o", k); resolved at build().
     def input(self, width: int):
@@ -186,6 +202,14 @@ class Builder:
 
     def connect(self, reg, d):
         self.regs[reg[1]][1] = d
+
+    def domain(self, period: int, phase: int = 0) -> int:
+        """A clock domain ticking when (t + phase) mod period == 0 (t: cycles since reset)."""
+        self.domains.append((period, phase))
+        return len(self.domains) - 1
+
+    def clock(self, reg, domain: int):
+        self.reg_dom[reg[1]] = domain
 
     def build(self) -> Netlist:
         ni, nr, nc = len(self.inputs), len(self.regs), len(self.consts)
@@ -219,6 +243,10 @@ class Builder:
             mem_width=np.array([m[1] for m in self.mems], np.uint8),
             wport=np.array([[m, sid(e), sid(a), sid(d)] for (m, e, a, d) in self.wports],
                            np.uint32).reshape(-1, 4),
+            dom_period=np.array([d[0] for d in self.domains], np.uint32),
+            dom_phase=np.array([d[1] for d in self.domains], np.uint32),
+            reg_domain=(np.array([self.reg_dom.get(r, 0) for r in range(nr)], np.uint8)
+                        if self.domains else np.zeros(0, np.uint8)),
         )
 
     def sid(self, h) -> int:

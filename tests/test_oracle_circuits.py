@@ -373,3 +373,51 @@ def test_modular_generator_gates_registers_by_enable():
             if q % (1 << ks[m]) != phases[m]:
                 assert np.array_equal(cur[regs], prev[regs]), (c, m)
         prev = cur
+
+
+def _domain_counters(specs):
+    """One 16-bit counter register (Q <- Q + 1) per (period, phase) domain, plus
+    a base-clock counter."""
+    b = Builder()
+    one = b.const(16, 1)
+    regs = []
+    for per, ph in [(1, 0)] + list(specs):
+        d = b.domain(per, ph)
+        r = b.reg(16)
+        b.connect(r, b.op("ADD", 16, r, one))
+        b.clock(r, d)
+        regs.append(r)
+    return b.build(), [b.sid(r) for r in regs]
+
+
+def test_clock_domains_count_their_ticks():
+    """Multi-clock reading: a register of domain (p, f) loads only in cycles with
+    (t + f) mod p == 0, t = non-reset cycles since reset; so a counter there holds
+    #{t < n : (t + f) mod p == 0} after reset + n cycles (closed form)."""
+    specs = [(2, 0), (2, 1), (4, 3), (8, 0), (16, 5)]
+    nl, sig = _domain_counters(specs)
+    o = oracle.OracleSim(nl.to_bytes(), 3)
+    o.step(1, reset=True)
+    done = 0
+    for n in [1, 2, 5, 13, 40, 100]:
+        o.step(n - done)
+        done = n
+        vals = o.read(sig)[:, 0]
+        assert int(vals[0]) == n
+        for (per, ph), v in zip(specs, vals[1:]):
+            assert int(v) == sum(1 for t in range(n) if (t + ph) % per == 0), (per, ph, n)
+    o.step(1, reset=True)                 # a reset restarts t
+    o.step(3)
+    vals = o.read(sig)[:, 0]
+    assert [int(x) for x in vals] == [3] + [sum(1 for t in range(3) if (t + f) % p == 0) for p, f in specs]
+
+
+def test_clock_domains_format_and_validation():
+    nl, _ = _domain_counters([(4, 1)])
+    assert synth.Netlist.from_bytes(nl.to_bytes()).to_bytes() == nl.to_bytes()
+    bad = nl.to_bytes()
+    # period 3 is not a power of two: the oracle refuses the netlist
+    nl.dom_period = np.array([1, 3], np.uint32)
+    with pytest.raises(ValueError):
+        oracle.OracleSim(nl.to_bytes(), 1)
+    assert oracle.OracleSim(bad, 1).n_regs == 2
