@@ -32,17 +32,29 @@
  * ------------------------------------------------------------------------
  * Little-endian.  Header: 10 x u32
  *     magic 0x4E4C5452, version 1, n_inputs, n_regs, n_consts, n_ops,
- *     n_mems, n_wports, n_args, 0
- * then, in this order:
+ *     n_mems, n_wports, n_args, n_domains (0: one clock)
+ * then, in this order (the [..] parts only when n_domains > 0):
  *     u64 reg_init[n_regs]        u64 const_value[n_consts]
  *     u32 reg_d[n_regs]           u32 op_argoff[n_ops+1]   u32 args[n_args]
  *     u32 mem_words[n_mems]       u32 wport[n_wports][4] = {mem, en, addr, data}
+ *     [u32 domain_period[n_domains]   u32 domain_phase[n_domains]]
  *     u8 input_width[n_inputs]    u8 reg_width[n_regs]     u8 const_width[n_consts]
  *     u8 op_code[n_ops]  u8 op_width[n_ops]  u8 op_p0[n_ops]  u8 op_p1[n_ops]
- *     u8 mem_width[n_mems]
+ *     u8 mem_width[n_mems]        [u8 reg_domain[n_regs]]
  * Signal ids: [0, n_inputs) inputs, then registers (their Q), then constants,
  * then op outputs in topological order (every operand id < the op's own id).
  * Op k's operands are args[op_argoff[k] .. op_argoff[k+1]) in O order.
+ *
+ * Clock domains (Sec. 5.2 "Multiple Clock Domains"; the rule is a reading):
+ * domain d has a period p (a power of two <= 2^31, in base-clock cycles) and a
+ * phase f < p; every register names its domain (at most 256).  Each instance
+ * counts t, the non-reset cycles since its last reset cycle; at the edge of a
+ * non-reset cycle a register of domain (p, f) takes its next state only if
+ * (t + f) mod p == 0, else it holds; a reset cycle resets every register and t.
+ * Memory write ports run on the base clock.  The library lowers the domains to
+ * one clock (a hidden 32-bit cycle counter and a hold mux per register of a
+ * slower domain), so every kernel form and option supports them; the hidden
+ * signals have no id.
  *
  * Value domain (reading: the paper supports "all FIRRTL primitive operations"
  * but defines none): unsigned only; every signal has a width w in 1..64 and

@@ -32,9 +32,11 @@ bool parse_netlist(const void* bytes, size_t nbytes, Netlist& n, std::string& er
   if (h[0] != 0x4E4C5452u) return fail(err, "netlist: bad magic (expected RTLN)");
   if (h[1] != 1u) return fail(err, "netlist: unsupported version");
   n.ni = h[2]; n.nr = h[3]; n.nc = h[4]; n.no = h[5]; n.nm = h[6]; n.nw = h[7]; n.na = h[8];
+  n.nd = h[9];
+  if (n.nd > 256) return fail(err, "netlist: more than 256 clock domains");
   const uint64_t need = 40ull + 8ull * n.nr + 8ull * n.nc + 4ull * n.nr + 4ull * (n.no + 1ull) +
-                        4ull * n.na + 4ull * n.nm + 16ull * n.nw + n.ni + n.nr + n.nc +
-                        4ull * n.no + n.nm;
+                        4ull * n.na + 4ull * n.nm + 16ull * n.nw + 8ull * n.nd + n.ni + n.nr + n.nc +
+                        4ull * n.no + n.nm + (n.nd ? n.nr : 0ull);
   if (need != nbytes) return fail(err, "netlist: size does not match the header counts");
   if ((uint64_t)n.ni + n.nr + n.nc + n.no >= 0x7FFFFFFFull)
     return fail(err, "netlist: too many signals");
@@ -46,6 +48,8 @@ bool parse_netlist(const void* bytes, size_t nbytes, Netlist& n, std::string& er
   take(p, n.args, n.na);
   take(p, n.mem_words, n.nm);
   take(p, n.wport, 4ull * n.nw);
+  take(p, n.dom_period, n.nd);
+  take(p, n.dom_phase, n.nd);
   take(p, n.in_w, n.ni);
   take(p, n.reg_w, n.nr);
   take(p, n.const_w, n.nc);
@@ -54,6 +58,7 @@ bool parse_netlist(const void* bytes, size_t nbytes, Netlist& n, std::string& er
   take(p, n.p0, n.no);
   take(p, n.p1, n.no);
   take(p, n.mem_w, n.nm);
+  take(p, n.reg_dom, n.nd ? n.nr : 0u);
 
   const uint32_t nsig = n.n_signals(), opb = n.op_base();
   auto wok = [](uint32_t w) { return w >= 1 && w <= 64; };
@@ -100,7 +105,106 @@ bool parse_netlist(const void* bytes, size_t nbytes, Netlist& n, std::string& er
     if (w[0] >= n.nm || w[1] >= nsig || w[2] >= nsig || w[3] >= nsig)
       return fail(err, "netlist: write port references a bad memory or signal");
   }
+  for (uint32_t d = 0; d < n.nd; d++) {
+    const uint32_t per = n.dom_period[d];
+    if (per == 0 || per > (1u << 31) || (per & (per - 1)) != 0 || n.dom_phase[d] >= per)
+      return fail(err, "netlist: clock domain period not a power of two, or phase >= period");
+  }
+  for (uint32_t r = 0; n.nd && r < n.nr; r++)
+    if (n.reg_dom[r] >= n.nd) return fail(err, "netlist: register clock domain out of range");
   return true;
+}
+
+Netlist lower_clock_domains(const Netlist& nl, std::vector<uint32_t>& user2x) {
+  const uint32_t nsig = nl.n_signals();
+  user2x.resize(nsig);
+  std::vector<uint32_t> gated;  // domains with period > 1
+  for (uint32_t d = 0; d < nl.nd; d++)
+    if (nl.dom_period[d] > 1) gated.push_back(d);
+  if (gated.empty()) {
+    for (uint32_t i = 0; i < nsig; i++) user2x[i] = i;
+    Netlist x = nl;
+    x.nd = 0;
+    x.dom_period.clear();
+    x.dom_phase.clear();
+    x.reg_dom.clear();
+    return x;
+  }
+  Netlist x;
+  x.ni = nl.ni;
+  x.nr = nl.nr + 1;                                      // + t
+  const uint32_t n_extra_c = 2 + 2 * (uint32_t)gated.size();  // 1, 0, then per domain phase, p - 1
+  x.nc = nl.nc + n_extra_c;
+  x.nm = nl.nm;
+  x.nw = nl.nw;
+  const uint32_t t_sig = nl.ni + nl.nr;
+  const uint32_t cbase = x.ni + x.nr, obase = cbase + x.nc;
+  for (uint32_t i = 0; i < nsig; i++) {
+    if (i < nl.ni + nl.nr) user2x[i] = i;
+    else if (i < nl.op_base()) user2x[i] = i + 1;
+    else user2x[i] = obase + (i - nl.op_base());
+  }
+  auto X = [&](uint32_t s) { return user2x[s]; };
+  // constants: the input's, then 1, 0, and per gated domain its phase and p - 1
+  x.const_value = nl.const_value;
+  x.const_w = nl.const_w;
+  const uint32_t c_one = cbase + nl.nc, c_zero = c_one + 1;
+  x.const_value.push_back(1);
+  x.const_w.push_back(32);
+  x.const_value.push_back(0);
+  x.const_w.push_back(1);
+  for (uint32_t d : gated) {
+    x.const_value.push_back(nl.dom_phase[d]);
+    x.const_w.push_back(32);
+    x.const_value.push_back(nl.dom_period[d] - 1u);
+    x.const_w.push_back(32);
+  }
+  // ops: the input's (operands renumbered), then t + 1, the enables, the hold muxes
+  x.code = nl.code;
+  x.width = nl.width;
+  x.p0 = nl.p0;
+  x.p1 = nl.p1;
+  x.argoff = nl.argoff;
+  x.args.resize(nl.args.size());
+  for (size_t j = 0; j < nl.args.size(); j++) x.args[j] = X(nl.args[j]);
+  auto put = [&](uint32_t code, uint32_t w, std::initializer_list<uint32_t> a) {
+    x.code.push_back((uint8_t)code);
+    x.width.push_back((uint8_t)w);
+    x.p0.push_back(0);
+    x.p1.push_back(0);
+    for (uint32_t v : a) x.args.push_back(v);
+    x.argoff.push_back((uint32_t)x.args.size());
+    return obase + (uint32_t)x.code.size() - 1u;
+  };
+  const uint32_t t_next = put(OP_ADD, 32, {t_sig, c_one});
+  std::vector<uint32_t> enable(nl.nd, 0xFFFFFFFFu);
+  for (size_t g = 0; g < gated.size(); g++) {
+    const uint32_t d = gated[g];
+    const uint32_t c_ph = c_zero + 1 + 2 * (uint32_t)g, c_mask = c_ph + 1;
+    const uint32_t sum = nl.dom_phase[d] ? put(OP_ADD, 32, {t_sig, c_ph}) : t_sig;
+    const uint32_t low = put(OP_AND, 32, {sum, c_mask});
+    enable[d] = put(OP_EQ, 1, {low, c_zero});
+  }
+  x.reg_init = nl.reg_init;
+  x.reg_init.push_back(0);
+  x.reg_w = nl.reg_w;
+  x.reg_w.push_back(32);
+  x.reg_d.resize(x.nr);
+  for (uint32_t r = 0; r < nl.nr; r++) {
+    const uint32_t d = nl.reg_dom[r];
+    x.reg_d[r] = enable[d] == 0xFFFFFFFFu ? X(nl.reg_d[r])
+                                           : put(OP_MUX, nl.reg_w[r], {enable[d], X(nl.reg_d[r]), nl.ni + r});
+  }
+  x.reg_d[nl.nr] = t_next;
+  x.no = (uint32_t)x.code.size();
+  x.na = (uint32_t)x.args.size();
+  x.in_w = nl.in_w;
+  x.mem_words = nl.mem_words;
+  x.mem_w = nl.mem_w;
+  x.wport = nl.wport;
+  for (uint32_t q = 0; q < nl.nw; q++)
+    for (int t = 1; t < 4; t++) x.wport[4ull * q + t] = X(nl.wport[4ull * q + t]);
+  return x;
 }
 
 void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {

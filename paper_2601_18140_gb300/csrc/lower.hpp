@@ -40,6 +40,9 @@ struct Netlist {
   std::vector<uint64_t> reg_init, const_value;
   std::vector<uint32_t> reg_d, argoff, args, mem_words, wport;  // wport: 4 per port
   std::vector<uint8_t> in_w, reg_w, const_w, code, width, p0, p1, mem_w;
+  uint32_t nd = 0;                                  // clock domains (0: one clock)
+  std::vector<uint32_t> dom_period, dom_phase;      // [nd]
+  std::vector<uint8_t> reg_dom;                     // [nr] when nd > 0
   uint32_t n_signals() const { return ni + nr + nc + no; }
   uint32_t op_base() const { return ni + nr + nc; }
 };
@@ -87,6 +90,14 @@ struct Lowered {
   // per-op-eval algorithmic bytes bookkeeping: sum over lowered ops of operands read
   uint64_t lowered_operands = 0;
 };
+
+// Multi-clock lowering (clock domains -> one clock): a hidden 32-bit register t
+// (init 0, next t + 1) counts the non-reset cycles since reset; a register of a
+// domain with period p > 1 and phase f loads through a hold mux enabled when
+// ((t + f) & (p - 1)) == 0.  Returns the single-clock netlist; user2x maps the
+// input's signal ids to its ids (the hidden signals come after them in each
+// section).  Without domains (or all periods 1) the netlist is unchanged.
+Netlist lower_clock_domains(const Netlist& nl, std::vector<uint32_t>& user2x);
 
 // fuse_mux_chains: operator fusion of single-fanout mux chains into MUXCHAIN ops
 // (the absorbed muxes are not computed and their signals have no row).

@@ -351,8 +351,10 @@ struct DevBuf {
 using namespace rteaal;
 
 struct rteaal_design {
-  Netlist nl;
-  Lowered L;
+  Netlist nl;                     // as loaded (the caller's signal ids)
+  Netlist nlx;                    // single-clock form that is lowered and run
+  std::vector<uint32_t> user2x;   // nl signal id -> nlx signal id
+  Lowered L;                      // lowering of nlx
   Allocator alloc;
   int device = 0;
   int n_sms = 0;
@@ -374,6 +376,9 @@ struct rteaal_design {
     metadata_bytes += b.n;
     return static_cast<T*>(b.p);
   }
+  // slot of a caller's signal (0xFFFFFFFF: fused away)
+  uint32_t slot_of(uint32_t sig) const { return L.sig2slot[user2x[sig]]; }
+
   // design-specialised kernel (compiled on first use)
   std::mutex spec_mu;
   cudaLibrary_t spec_lib = nullptr;
@@ -652,7 +657,8 @@ RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaa
       if (opts && opts->device >= 0) CK(cudaSetDevice(opts->device));
       CK(cudaGetDevice(&d->device));
       CK(cudaDeviceGetAttribute(&d->n_sms, cudaDevAttrMultiProcessorCount, d->device));
-      lower_netlist(d->nl, d->L, opts && opts->fuse_mux_chains);
+      d->nlx = lower_clock_domains(d->nl, d->user2x);
+      lower_netlist(d->nlx, d->L, opts && opts->fuse_mux_chains);
       const Lowered& L = d->L;
       DDesign& dd = d->dd;
       static_assert(sizeof(OpMeta) == sizeof(uint4), "descriptor is 16 bytes");
@@ -718,8 +724,8 @@ RT_EXPORT int rteaal_design_info(const rteaal_design* d, rteaal_design_stats* o)
 RT_EXPORT int rteaal_design_signals(const rteaal_design* d, uint8_t* present, uint64_t n) {
   return guarded([&] {
     require(d && present, "rteaal_design_signals: null argument");
-    require(n == d->L.sig2slot.size(), "rteaal_design_signals: n_signals differs from the design's");
-    for (uint64_t i = 0; i < n; i++) present[i] = d->L.sig2slot[i] != 0xFFFFFFFFu;
+    require(n == d->nl.n_signals(), "rteaal_design_signals: n_signals differs from the design's");
+    for (uint64_t i = 0; i < n; i++) present[i] = d->slot_of((uint32_t)i) != 0xFFFFFFFFu;
   });
 }
 
@@ -757,13 +763,13 @@ constexpr uint32_t kSpecOptimizeOps = 4096;  // NVVM optimiser on up to this man
 void ensure_specialized(rteaal_design* d) {
   std::lock_guard<std::mutex> g(d->spec_mu);
   if (d->spec_kernel) return;
-  if (d->nl.no > kSpecMaxOps)
+  if (d->nlx.no > kSpecMaxOps)
     throw Error(RTEAAL_E_UNSUPPORTED, "design-specialised kernel: more than 16,384 ops (compile time grows superlinearly)");
   const auto t0 = std::chrono::steady_clock::now();
-  const std::string src = specialized_source(d->nl, d->L);
+  const std::string src = specialized_source(d->nlx, d->L);
   std::vector<char> cubin;
   std::string log;
-  if (!compile_specialized(src, "sm_103a", d->nl.no <= kSpecOptimizeOps, cubin, log))
+  if (!compile_specialized(src, "sm_103a", d->nlx.no <= kSpecOptimizeOps, cubin, log))
     throw Error(RTEAAL_E_CUDA, "design-specialised kernel: compile failed: " + log.substr(0, 2000));
   CK(cudaSetDevice(d->device));
   CK(cudaLibraryLoadData(&d->spec_lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
@@ -1222,9 +1228,9 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       std::vector<uint32_t> slots(probes->n);
       for (uint32_t p = 0; p < probes->n; p++) {
         require(probes->signals[p] < D->nl.n_signals(), "rteaal_step: probe signal out of range");
-        require(L.sig2slot[probes->signals[p]] != 0xFFFFFFFFu,
+        require(D->slot_of(probes->signals[p]) != 0xFFFFFFFFu,
                 "rteaal_step: probed signal was fused away (operator fusion is enabled)");
-        slots[p] = L.slot_ref[L.sig2slot[probes->signals[p]]];
+        slots[p] = L.slot_ref[D->slot_of(probes->signals[p])];
       }
       ensure_probe_slots(s, slots.size());
       CK(cudaMemcpyAsync(s->probe_slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice, st));
@@ -1472,8 +1478,8 @@ void transfer(rteaal_sim* s, Region region, const uint32_t* signals, uint32_t n,
     const uint32_t nsig = s->design->nl.n_signals();
     for (uint32_t i = 0; i < n; i++) {
       require(signals[i] < nsig, "signal id out of range");
-      require(L.sig2slot[signals[i]] != 0xFFFFFFFFu, "signal was fused away (operator fusion is enabled)");
-      rows[i] = L.slot_ref[L.sig2slot[signals[i]]];
+      require(s->design->slot_of(signals[i]) != 0xFFFFFFFFu, "signal was fused away (operator fusion is enabled)");
+      rows[i] = L.slot_ref[s->design->slot_of(signals[i])];
       // width of the signal (writes are masked like every stored value)
       const Netlist& nl = s->design->nl;
       uint32_t sig = signals[i], w;
