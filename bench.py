@@ -339,9 +339,10 @@ def run_ours(args) -> None:
     achieved = per_launch_bytes / avg_launch_s / 1e9
     kname = {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops", 5: "k_stream",
              6: "rteaal_spec"}[info["kernel"]]
-    variant = "%s<%d,%d,%d,%d>" % (kname, info["lanes_per_thread"], info["unroll"], info["threads"],
-                                   info["ctas_per_sm"])
-    traffic = profile_traffic(variant + ":" + args.workload) if n_total == WORKLOADS[args.workload][1] else None
+    # DRAM bytes per instance-cycle of this kernel on this workload (from an ncu
+    # capture of one of its launch configurations; every configuration moves the
+    # same rows, only L2 reuse differs)
+    traffic = profile_traffic(kname + ":" + args.workload) if n_total == WORKLOADS[args.workload][1] else None
     if traffic is not None:
         traffic *= (inst_cycles / args.steps)                # stored per instance-cycle
 
@@ -421,6 +422,7 @@ def run_ours(args) -> None:
                                        6: "specialized"}[info["kernel"]],
                        "tile_lanes": info["tile_lanes"], "threads": info["threads"],
                        "ctas_per_sm": info["ctas_per_sm"], "unroll": info["unroll"],
+                       "lanes_per_thread": info["lanes_per_thread"],
                        "grid": info["grid"], "autotune": tune, "parallelism": "replicas" if world > 1 else "1 gpu",
                        "l2": "state %.1f GB >> 129 MB L2 (no flush needed)"
                              % (design.info["state_bytes_per_lane"] * n / 1e9)},

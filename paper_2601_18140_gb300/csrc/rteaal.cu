@@ -566,7 +566,8 @@ struct Variant {
 };
 #define RT_VARIANT(V, U, T, B) {V, U, T, B, (const void*)k_tile<V, U, T, B>, (const void*)k_grid<V, U, T, B>}
 const Variant kVariants[] = {
-    RT_VARIANT(8, 1, 256, 2), RT_VARIANT(8, 1, 512, 1),
+    RT_VARIANT(8, 1, 256, 2), RT_VARIANT(8, 1, 512, 1), RT_VARIANT(8, 1, 384, 2), RT_VARIANT(8, 1, 256, 4),
+    RT_VARIANT(8, 1, 384, 3), RT_VARIANT(8, 1, 512, 2), RT_VARIANT(8, 1, 128, 8),
     RT_VARIANT(4, 1, 256, 4), RT_VARIANT(4, 1, 512, 2), RT_VARIANT(4, 1, 1024, 1),
     RT_VARIANT(4, 1, 384, 4), RT_VARIANT(4, 1, 256, 6), RT_VARIANT(4, 1, 256, 8),
     RT_VARIANT(4, 1, 640, 3), RT_VARIANT(4, 1, 448, 4),
@@ -584,7 +585,7 @@ struct ActVariant {
 #define RT_ACT_VARIANT(V, T, B) {V, T, B, (const void*)k_grid_act<V, T, B>}
 const ActVariant kActVariants[] = {
     RT_ACT_VARIANT(4, 384, 4), RT_ACT_VARIANT(4, 256, 8), RT_ACT_VARIANT(4, 512, 2),
-    RT_ACT_VARIANT(2, 512, 4), RT_ACT_VARIANT(8, 256, 2), RT_ACT_VARIANT(1, 512, 4),
+    RT_ACT_VARIANT(2, 512, 4), RT_ACT_VARIANT(8, 256, 2), RT_ACT_VARIANT(1, 512, 4), RT_ACT_VARIANT(8, 512, 2),
 };
 #undef RT_ACT_VARIANT
 
