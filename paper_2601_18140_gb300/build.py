@@ -42,7 +42,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     common = ["-O3", "-std=c++17", "-I", INCLUDE, "-I", CSRC]
     jobs = []
     objs = []
-    for f in ["lower.cpp", "specialize.cpp", "rteaal.cu"]:
+    # the persistent-kernel variants are instantiated in their own units so that
+    # they compile in parallel with the runtime
+    for f in ["rteaal.cu", "variants_v8.cu", "variants_v4.cu", "variants_v2_v1.cu", "variants_act.cu",
+              "lower.cpp", "specialize.cpp"]:
         src = os.path.join(CSRC, f)
         obj = os.path.join(BUILD, f + ".o")
         cmd = [nvcc] + ARCH + common + ["-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",

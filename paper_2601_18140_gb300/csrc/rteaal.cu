@@ -1,15 +1,13 @@
-// rteaal.cu -- kernels of the three execution forms and the C ABI (include/rteaal.h).
+// rteaal.cu -- the runtime behind the C ABI (include/rteaal.h) and the kernels
+// of the plain forms.
 //
 //   LAYER  plain form: per cycle one launch for the inputs, one per layer (the
 //          kernel boundary is the LI_{i+1} <- LO_i barrier), one for the edge.
 //   LAYER_GRAPH  the same launch sequence for one cycle captured as a CUDA graph
 //          and replayed once per cycle (cycle index kept on the device).
-//   TILE   persistent: each CTA takes a tile of lanes (instances) from an atomic
-//          queue, longest remaining work first, and walks every layer of every
-//          cycle of that tile with CTA barriers only.  Instances are
-//          independent, so no grid-wide synchronisation exists at all.
-//   GRID   persistent cooperative: the whole grid walks each layer for all
-//          lanes, separated by a software grid barrier with a bounded wait.
+//   TILE, GRID (and GRID with activity-aware evaluation) are the persistent
+//          forms of persistent.cuh, STREAM the bulk-copy form of stream.cuh,
+//          SPECIALIZED the run-time-compiled form of specialize.cpp.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +24,7 @@
 
 #include "kernels.cuh"
 #include "lower.hpp"
+#include "persistent.cuh"
 #include "rteaal.h"
 
 #define RT_EXPORT extern "C" __attribute__((visibility("default")))
@@ -67,149 +66,6 @@ __global__ void __launch_bounds__(256) k_layer_probe(DSim s, FastDiv tpo, uint32
 }
 
 __global__ void k_tick(uint32_t* cyc_dev) { *cyc_dev += 1u; }
-
-struct TileArgs {
-  uint32_t* counter;             // scratch: next queue position
-  const uint32_t* order;         // queue position -> tile (longest first), null = identity
-  const uint32_t* tile_cycles;   // per tile, null -> uniform
-  uint32_t n_tiles, tile_lanes;
-  FastDiv tpo;                   // tile_lanes / V
-};
-
-template <int V, int U, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_tile(DDesign d, DSim s, TileArgs t) {
-  __shared__ uint32_t sh_q;
-  for (;;) {
-    if (threadIdx.x == 0) sh_q = atomicAdd(t.counter, 1u);
-    __syncthreads();
-    const uint32_t q = sh_q;
-    __syncthreads();
-    if (q >= t.n_tiles) return;
-    const uint32_t tile = t.order ? t.order[q] : q;
-    const uint32_t ncyc = t.tile_cycles ? t.tile_cycles[tile] : s.uniform;
-#define RT_SPACE make_space<V>(t.tpo, tile * t.tile_lanes, threadIdx.x, blockDim.x)
-    for (uint32_t c = 0; c < ncyc; c++) {
-      stim_items<V>(d, s, RT_SPACE, c);
-      __syncthreads();
-      for (uint32_t L = 0; L < d.n_layers; L++) {
-        eval_layer<V, U>(d, s, L, RT_SPACE, c);
-        __syncthreads();
-      }
-      commit_items<V>(d, s, RT_SPACE, c);
-      __syncthreads();
-      if (s.n_probe) {
-        probe_items<V>(s, RT_SPACE, c);
-        __syncthreads();
-      }
-    }
-#undef RT_SPACE
-  }
-}
-
-struct GridArgs {
-  uint32_t* count;        // scratch: arrivals at the current barrier
-  uint32_t* gen;          // scratch: barrier generation
-  uint32_t expected;      // arrivals that complete a barrier (= gridDim.x)
-  uint64_t timeout_ns;    // bounded wait per barrier
-  uint32_t ncyc;
-  FastDiv tpo;            // n_pad / V
-};
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Software grid barrier (sense by generation counter).  Every wait is bounded:
-// after timeout_ns the block sets *err and returns false; blocks that see *err
-// leave at their next barrier, so the kernel always ends.
-__device__ __forceinline__ bool grid_sync(const GridArgs& g, uint32_t* err, int* sh_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const uint32_t my = ld_acquire(g.gen);
-    __threadfence();
-    if (atomicAdd(g.count, 1u) == g.expected - 1u) {
-      atomicExch(g.count, 0u);
-      __threadfence();
-      atomicAdd(g.gen, 1u);
-    } else {
-      const uint64_t t0 = globaltimer();
-      while (ld_acquire(g.gen) == my) {
-        if (ld_acquire(err) != 0u) { ok = 0; break; }
-        if (globaltimer() - t0 > g.timeout_ns) { atomicOr(err, 1u); ok = 0; break; }
-        __nanosleep(100);
-      }
-    }
-    if (ld_acquire(err) != 0u) ok = 0;
-    __threadfence();
-    *sh_ok = ok;
-  }
-  __syncthreads();
-  return *sh_ok != 0;
-}
-
-template <int V, int U, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs g) {
-  __shared__ int sh_ok;
-  // the work mapping is recomputed per phase (a few integer ops) instead of
-  // being held in registers across every barrier
-#define RT_SPACE make_space<V>(g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x)
-  for (uint32_t c = 0; c < g.ncyc; c++) {
-    stim_items<V>(d, s, RT_SPACE, c);
-    if (!grid_sync(g, s.err, &sh_ok)) return;
-    for (uint32_t L = 0; L < d.n_layers; L++) {
-      eval_layer<V, U>(d, s, L, RT_SPACE, c);
-      if (!grid_sync(g, s.err, &sh_ok)) return;
-    }
-    commit_items<V>(d, s, RT_SPACE, c);
-    if (!grid_sync(g, s.err, &sh_ok)) return;
-    if (s.n_probe) {
-      probe_items<V>(s, RT_SPACE, c);
-      if (!grid_sync(g, s.err, &sh_ok)) return;
-    }
-  }
-#undef RT_SPACE
-}
-
-// GRID form with activity-aware evaluation (ops whose operands did not change
-// in a 128-lane chunk are skipped there); counts evaluated / skipped items.
-template <int V, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_grid_act(DDesign d, DSim s, GridArgs g) {
-  __shared__ int sh_ok;
-  uint32_t n_eval = 0, n_skip = 0;
-#define RT_SPACE make_space<V>(g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x)
-  for (uint32_t c = 0; c < g.ncyc; c++) {
-    stim_items<V>(d, s, RT_SPACE, c);
-    if (!grid_sync(g, s.err, &sh_ok)) return;
-    for (uint32_t L = 0; L < d.n_layers; L++) {
-      eval_layer_act<V>(d, s, L, RT_SPACE, c, n_eval, n_skip);
-      if (!grid_sync(g, s.err, &sh_ok)) return;
-    }
-    commit_items<V>(d, s, RT_SPACE, c);
-    if (!grid_sync(g, s.err, &sh_ok)) return;
-    if (s.n_probe) {
-      probe_items<V>(s, RT_SPACE, c);
-      if (!grid_sync(g, s.err, &sh_ok)) return;
-    }
-  }
-#undef RT_SPACE
-  for (int o = 16; o > 0; o >>= 1) {
-    n_eval += __shfl_xor_sync(0xFFFFFFFFu, n_eval, o);
-    n_skip += __shfl_xor_sync(0xFFFFFFFFu, n_skip, o);
-  }
-  if ((threadIdx.x & 31u) == 0 && (n_eval | n_skip)) {
-    atomicAdd(&s.act_count[0], (unsigned long long)n_eval);
-    atomicAdd(&s.act_count[1], (unsigned long long)n_skip);
-  }
-}
 
 }  // namespace rteaal
 #include "stream.cuh"
@@ -555,45 +411,30 @@ void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32
     k_layer_probe<V><<<blocks_for((uint64_t)ds.n_probe * tpo.d, 1), threads, 0, st>>>(ds, tpo, c, cyc_dev);
 }
 
-// Compiled variants of the persistent kernels: lanes per thread V, items in
-// flight per thread U, launch bounds (MAXT threads per CTA, MINB CTAs per SM;
-// MAXT * MINB = 2048 keeps every variant at full occupancy within 65,536
-// registers per SM, except U = 4 which trades occupancy for in-flight items).
-struct Variant {
-  int V, U, maxt, minb;
-  const void* tile;
-  const void* grid;
-};
-#define RT_VARIANT(V, U, T, B) {V, U, T, B, (const void*)k_tile<V, U, T, B>, (const void*)k_grid<V, U, T, B>}
-const Variant kVariants[] = {
-    RT_VARIANT(8, 1, 256, 2), RT_VARIANT(8, 1, 512, 1), RT_VARIANT(8, 1, 384, 2), RT_VARIANT(8, 1, 256, 4),
-    RT_VARIANT(8, 1, 384, 3), RT_VARIANT(8, 1, 512, 2), RT_VARIANT(8, 1, 128, 8),
-    RT_VARIANT(4, 1, 256, 4), RT_VARIANT(4, 1, 512, 2), RT_VARIANT(4, 1, 1024, 1),
-    RT_VARIANT(4, 1, 384, 4), RT_VARIANT(4, 1, 256, 6), RT_VARIANT(4, 1, 256, 8),
-    RT_VARIANT(4, 1, 640, 3), RT_VARIANT(4, 1, 448, 4),
-    RT_VARIANT(4, 2, 512, 1),
-    RT_VARIANT(2, 1, 256, 8), RT_VARIANT(2, 1, 512, 4), RT_VARIANT(2, 1, 1024, 2),
-    RT_VARIANT(2, 2, 512, 2), RT_VARIANT(2, 4, 512, 1),
-    RT_VARIANT(1, 1, 512, 4), RT_VARIANT(1, 2, 512, 2), RT_VARIANT(1, 4, 512, 1),
-};
-#undef RT_VARIANT
+// All compiled variants (tables in variants_*.cu, one translation unit each so
+// that they compile in parallel).
+const std::vector<Variant>& all_variants() {
+  static const std::vector<Variant> all = [] {
+    std::vector<Variant> v;
+    for (const VariantTable& t : {variants_v8(), variants_v4(), variants_v2_v1()}) v.insert(v.end(), t.v, t.v + t.n);
+    return v;
+  }();
+  return all;
+}
 
-struct ActVariant {
-  int V, maxt, minb;
-  const void* grid;
-};
-#define RT_ACT_VARIANT(V, T, B) {V, T, B, (const void*)k_grid_act<V, T, B>}
-const ActVariant kActVariants[] = {
-    RT_ACT_VARIANT(4, 384, 4), RT_ACT_VARIANT(4, 256, 8), RT_ACT_VARIANT(4, 512, 2),
-    RT_ACT_VARIANT(2, 512, 4), RT_ACT_VARIANT(8, 256, 2), RT_ACT_VARIANT(1, 512, 4), RT_ACT_VARIANT(8, 512, 2),
-};
-#undef RT_ACT_VARIANT
+const std::vector<ActVariant>& all_act_variants() {
+  static const std::vector<ActVariant> all = [] {
+    const ActVariantTable t = act_variants();
+    return std::vector<ActVariant>(t.v, t.v + t.n);
+  }();
+  return all;
+}
 
 const ActVariant* find_act_variant(int V, uint32_t threads, uint32_t minb = 0) {
   const ActVariant* best = nullptr;
-  for (const ActVariant& v : kActVariants)
+  for (const ActVariant& v : all_act_variants())
     if (v.V == V && (uint32_t)v.maxt == threads && (!minb || (uint32_t)v.minb == minb)) return &v;
-  for (const ActVariant& v : kActVariants)
+  for (const ActVariant& v : all_act_variants())
     if (v.V == V && (uint32_t)v.maxt >= threads && (!best || v.maxt < best->maxt)) best = &v;
   return best;
 }
@@ -603,12 +444,12 @@ const ActVariant* find_act_variant(int V, uint32_t threads, uint32_t minb = 0) {
 // the smallest launch bound above `threads`.
 const Variant* find_variant(int V, uint32_t U, uint32_t threads, uint32_t minb = 0) {
   const Variant* best = nullptr;
-  for (const Variant& v : kVariants)
+  for (const Variant& v : all_variants())
     if (v.V == V && (uint32_t)v.U == U && (uint32_t)v.maxt == threads && (!minb || (uint32_t)v.minb == minb) &&
         (!best || v.minb > best->minb))
       best = &v;
   if (best) return best;
-  for (const Variant& v : kVariants)
+  for (const Variant& v : all_variants())
     if (v.V == V && (uint32_t)v.U == U && (uint32_t)v.maxt >= threads && (!best || v.maxt < best->maxt))
       best = &v;
   return best;
@@ -845,7 +686,7 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     if (!lanes_per_thread && !find_act_variant(V, threads)) V = 4;
     const ActVariant* v = find_act_variant(V, threads, ctas_per_sm);
     if (!v)  // no variant for these threads: the first one compiled for this V, at its block size
-      for (const ActVariant& c : kActVariants)
+      for (const ActVariant& c : all_act_variants())
         if (c.V == V) {
           v = &c;
           threads = (uint32_t)c.maxt;
@@ -1090,11 +931,11 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     if (kernel_mask & (1u << RTEAAL_KERNEL_TILE))
       for (uint32_t T : {8u, 16u, 32u, 64u})
         if (T <= np && np % T == 0)
-          for (const Variant& v : kVariants)
+          for (const Variant& v : all_variants())
             if (v.V >= 2 && T % (uint32_t)v.V == 0)
               candx.push_back({RTEAAL_KERNEL_TILE, T, (uint32_t)v.maxt, (uint32_t)v.U, (uint32_t)v.V, (uint32_t)v.minb});
     if (kernel_mask & (1u << RTEAAL_KERNEL_GRID))
-      for (const Variant& v : kVariants)
+      for (const Variant& v : all_variants())
         if (v.V >= 2 && np % (uint32_t)v.V == 0)
           candx.push_back({RTEAAL_KERNEL_GRID, 0, (uint32_t)v.maxt, (uint32_t)v.U, (uint32_t)v.V, (uint32_t)v.minb});
     if (kernel_mask & (1u << RTEAAL_KERNEL_LAYER))
