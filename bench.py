@@ -398,6 +398,24 @@ def run_ours(args) -> None:
                "h2d_bytes_per_step": int(C * nl.n_inputs * n * 8 + n * 4),
                "d2h_bytes_per_step": int(probes.size * n * 8)}
 
+    # the plain single-instance form on the same design (the batching baseline):
+    # one instance, one launch sequence per cycle replayed as a CUDA graph
+    plain = None
+    if rank == 0 and world == 1 and args.plain_cycles > 0:
+        p_sim = rt.Sim(design, 1, kernel="layer_graph", xorshift_seed=np.ascontiguousarray(xs[:, :1]))
+        p_sim.step(1, stimulus="xorshift", reset=True)
+        p_sim.step(2, stimulus="xorshift")                   # warm-up (graph capture)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        p_sim.step(args.plain_cycles, stimulus="xorshift", stream=stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        p_rate = args.plain_cycles * nl.n_ops / (p0.elapsed_time(p1) / 1e3)
+        plain = {"form": "layer_graph, 1 instance", "value": p_rate, "unit": "op-evals/s",
+                 "cycles": args.plain_cycles, "batched_over_plain": value / p_rate}
+        p_sim.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         si, sc = cpu_sample_size(args.workload)
@@ -436,6 +454,7 @@ def run_ours(args) -> None:
                                   "kernel is bound by instruction issue"}),
             "gpu_launches": 1 * args.steps,
             "activity": activity,
+            "plain_single_instance": plain,
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -520,6 +539,8 @@ def main():
     ap.add_argument("--quantum", type=int, default=2000)
     ap.add_argument("--cycles-cap", type=int, default=0)
     ap.add_argument("--kernel", default="tile")
+    ap.add_argument("--plain-cycles", type=int, default=20,
+                    help="cycles of the plain single-instance form timed for comparison (0: skip)")
     ap.add_argument("--activity", action="store_true",
                     help="activity-aware evaluation (grid kernel): skip ops whose operands did not change")
     ap.add_argument("--fuse-mux-chains", action="store_true",
