@@ -4,10 +4,11 @@
   and the whole configuration -- reset + 100,000 cycles -- in the CUDA-graph
   plain form, every signal checked (the oracle runs alongside on the host);
 * batch-1M: 1M ops, 4,096 instances with uneven cycle budgets, in the launch
-  configuration the benchmark times (autotuned), three sampled instances
-  (first, middle, last lane) checked signal by signal;
+  configuration the benchmark times (autotuned), five sampled instances
+  (first, middle, last lane, shortest and longest budget) checked signal by signal;
 * soc-5M: 5M ops, 256k registers, 64 register files (2 read, 1 write port
-  each), 1,024 instances, two sampled instances, every signal and memory word.
+  each), 1,024 instances, reset + 200 cycles, two sampled instances, every
+  signal and memory word.
 """
 import numpy as np
 import pytest
@@ -59,9 +60,10 @@ def test_batch_1m_bench_configuration():
     nl = synth.generate(synth.spec_batch())
     n = 4096
     budgets = synth.cycle_budgets(5, n, 3, 12)
-    sample = [0, n // 2, n - 1]
+    # first / middle / last lane, and the instances with the shortest and longest budgets
+    sample = sorted({0, n // 2, n - 1, int(np.argmin(budgets)), int(np.argmax(budgets))})
     p = Pair(nl, n, kernel="grid", seed=5, expected_cycles=budgets, oracle_instances=sample,
-             threads=384, ctas_per_sm=4, lanes_per_thread=4, unroll=1)
+             threads=512, ctas_per_sm=2, lanes_per_thread=8, unroll=1)
     p.step(1, reset=True)
     p.sim.autotune(cycles_per_trial=1, kernels=["grid", "stream"])   # as the benchmark does
     p.step(budgets, threads=3)
@@ -77,6 +79,6 @@ def test_soc_5m_with_memories():
     n = 1024
     p = Pair(nl, n, kernel="grid", seed=3, oracle_instances=[1, n - 2])
     p.step(1, reset=True, threads=2)
-    p.step(3, threads=2)
+    p.step(200, threads=2)
     p.compare()
     p.close()
