@@ -477,7 +477,8 @@ def run_serving(args) -> None:
     sizes = {"d50k": 50_000, "d500k": 500_000, "d5M": 5_000_000}
     nls = {k: synth.generate(synth.spec_serving(v, seed=40 + i)) for i, (k, v) in enumerate(sizes.items())}
     capacity = {"d50k": 512, "d500k": 512, "d5M": 256}
-    srv = build_server({k: v.to_bytes() for k, v in nls.items()}, capacity, quantum=args.quantum)
+    srv = build_server({k: v.to_bytes() for k, v in nls.items()}, capacity, quantum=args.quantum,
+                       autotune=args.serve_autotune)
     warm = [Job(10_000 + i, k, 1, 10, seed=1, arrival=0.0) for i, k in enumerate(sizes)]
     srv.run(warm)
     srv.done.clear()
@@ -497,7 +498,8 @@ def run_serving(args) -> None:
             "config": {"workload": "serving", "designs_ops": list(sizes.values()), "jobs": len(done),
                        "rate_hz": args.serve_rate, "cycles": "lognormal(ln 10k, 1)" +
                        (" capped at %d" % args.cycles_cap if args.cycles_cap else ""),
-                       "instances": "U{1..64}", "capacity_lanes": capacity, "quantum": args.quantum},
+                       "instances": "U{1..64}", "capacity_lanes": capacity, "quantum": args.quantum,
+                       "pool_autotune": bool(args.serve_autotune)},
             "latency": st, "offered_op_evals_per_s": work / max(span, 1e-9),
             "served_op_evals_per_s": work / wall, "wall_s": wall, "rounds": srv.rounds,
             "clocks": clk.summary()}
@@ -537,6 +539,8 @@ def main():
     ap.add_argument("--serve-load", type=float, default=0.0,
                     help="serving: also replay a trace offering this fraction of the measured capacity")
     ap.add_argument("--quantum", type=int, default=2000)
+    ap.add_argument("--serve-autotune", action="store_true",
+                    help="serving: autotune each pool's launch configuration when it is created")
     ap.add_argument("--cycles-cap", type=int, default=0)
     ap.add_argument("--kernel", default="tile")
     ap.add_argument("--plain-cycles", type=int, default=20,
