@@ -379,6 +379,8 @@ def run_ours(args) -> None:
         out_host = torch.empty((1, probes.size, n), dtype=torch.int64).pin_memory()
         e2e_evals = 0
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             per = np.minimum(remaining, C).astype(np.uint32)
@@ -394,9 +396,12 @@ def run_ours(args) -> None:
             e2e_evals += int(per.astype(np.int64).sum()) * nl.n_ops
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
+        if world > 1:   # whole job: the slowest rank's time, every rank's work
+            e2e_ms, e2e_evals = reduce_over_ranks(e2e_s * 1e3, float(e2e_evals), dev)
+            e2e_s = e2e_ms / 1e3
         e2e = {"value": e2e_evals / e2e_s, "unit": "op-evals/s",
-               "h2d_bytes_per_step": int(C * nl.n_inputs * n * 8 + n * 4),
-               "d2h_bytes_per_step": int(probes.size * n * 8)}
+               "h2d_bytes_per_step": int(C * nl.n_inputs * n_total * 8 + n_total * 4),   # all ranks
+               "d2h_bytes_per_step": int(probes.size * n_total * 8)}
 
     # the plain single-instance form on the same design (the batching baseline):
     # one instance, one launch sequence per cycle replayed as a CUDA graph
