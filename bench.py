@@ -88,13 +88,15 @@ def measured_peaks() -> dict:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the device and lowering sources: DRAM counters taken on another
-    version of the kernel do not describe this one."""
+    """Hash of the sources that decide the persistent kernels' memory traffic: their
+    device code (kernels.cuh, persistent.cuh, the variant tables) and the state
+    layout (lower.*).  DRAM counters taken on another version do not describe this one."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2601_18140_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".cpp", ".hpp")):
+        if f in ("kernels.cuh", "persistent.cuh", "lower.cpp", "lower.hpp") or (
+                f.startswith("variants_") and f.endswith(".cu")):
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:12]
