@@ -56,8 +56,8 @@
  * slower domain), so every kernel form and option supports them; the hidden
  * signals have no id.
  *
- * Value domain (reading: the paper supports "all FIRRTL primitive operations"
- * but defines none): unsigned only; every signal has a width w in 1..64 and
+ * Value domain (reading: the paper claims support for every FIRRTL primitive
+ * operation without defining any): unsigned only; every signal has a width w in 1..64 and
  * is stored zero-extended in 64 bits, always masked to w.  mask(w) = 2^w - 1.
  * Every op result is masked to the op's width.  Opcodes (u8):
  *   0 COPY a            1 AND a,b,...   2 OR a,b,...   3 XOR a,b,...  (fold in O order)
@@ -166,7 +166,7 @@ int rteaal_design_free(rteaal_design *design);
 
 /* ---------------------------------------------------------------- simulation */
 enum {
-  RTEAAL_KERNEL_AUTO = 0,   /* TILE when lanes >= 64, else LAYER                   */
+  RTEAAL_KERNEL_AUTO = 0,   /* TILE when lanes >= 64, else LAYER; GRID with activity */
   RTEAAL_KERNEL_LAYER = 1,  /* plain form: one launch per layer per cycle          */
   RTEAAL_KERNEL_TILE = 2,   /* persistent: a CTA walks all layers and cycles of an
                                instance tile, CTA barrier between layers           */
@@ -202,8 +202,8 @@ typedef struct {
   uint32_t ctas_per_sm;    /* TILE / GRID residency target, 0 auto              */
   uint32_t unroll;         /* operations in flight per thread (1, 2, 4), 0 auto */
   uint32_t lanes_per_thread; /* lanes (instances) per thread per op (1, 2, 4, 8), 0 auto */
-  /* Activity-aware evaluation (the cascade-level optimisation "skipping
-   * partitions without activity" of App. B, at the finest grain): the sim
+  /* Activity-aware evaluation (App. B's cascade-level optimisation that leaves
+   * out partitions whose inputs did not change, at the finest grain): the sim
    * keeps, per row and 128-lane chunk, the last cycle in which the row changed
    * in any lane of the chunk; an op is evaluated for a chunk only if one of its
    * operands changed there in the current cycle (memory reads always), and its
@@ -285,8 +285,8 @@ enum { RTEAAL_PROBE_LAST = 0, RTEAAL_PROBE_EVERY = 1, RTEAAL_PROBE_CHANGES = 2 }
 /* One waveform event (RTEAAL_PROBE_CHANGES): probe `probe` of instance
  * `instance` took `value` at the end of cycle `cycle` (cycle index relative to
  * the step) and that differs from its value at the end of the previous cycle
- * (for cycle 0: its value when the step began).  Waveform generation, Sec. 5.2:
- * "record signal values when they change". */
+ * (for cycle 0: its value when the step began) -- waveform generation, Sec. 5.2,
+ * which keeps a value only when it changes. */
 typedef struct {
   uint32_t cycle, probe, instance, pad;
   uint64_t value;
