@@ -143,6 +143,43 @@ def test_no_inputs_no_registers():
     p.close()
 
 
+@pytest.mark.parametrize("kernel", KERNELS + ["specialized"])
+def test_designs_without_operations(kernel):
+    """Degenerate designs: registers fed straight from inputs, constants and other
+    registers (no combinational op at all: the edge reads copies the lowering
+    inserts), and a design with nothing but one input."""
+    b = Builder()
+    i0 = b.input(8)
+    i1 = b.input(64)
+    k = b.const(16, 0xBEEF)
+    r0 = b.reg(8, init=3)
+    r1 = b.reg(64)
+    r2 = b.reg(16)
+    r3 = b.reg(8)
+    b.connect(r0, i0)           # input -> register
+    b.connect(r1, i1)
+    b.connect(r2, k)            # constant -> register
+    b.connect(r3, r0)           # register -> register (a 2-stage delay line)
+    nl = b.build()
+    assert nl.n_ops == 0
+    n = 130
+    p = Pair(nl, n, kernel=kernel, seed=9)
+    p.step(1, reset=True)
+    p.step(5)
+    p.compare()
+    rng = np.random.default_rng(9)
+    budgets = rng.integers(0, 4, n).astype(np.uint32)
+    p.step(budgets)
+    p.compare()
+    p.close()
+    b = Builder()
+    b.input(1)
+    p = Pair(b.build(), 7 if kernel != "stream" else 128, kernel=kernel, seed=10)   # stream: 128-lane multiples
+    p.step(3)
+    p.compare()
+    p.close()
+
+
 def test_state_write_restore_checkpoint():
     """Run N cycles, snapshot, run M more; restore the snapshot and rerun M: same result."""
     nl = small_design(8, n_mems=2)
