@@ -85,9 +85,11 @@ def test_buffer_stimulus_and_probes(kernel):
     p.close()
 
 
-@pytest.mark.parametrize("kernel", ["layer", "tile", "grid", "stream"])
-def test_wide_ops_and_memories(kernel):
-    """Variadic folds (> 3 operands), long mux chains, two write ports per memory."""
+@pytest.mark.parametrize("kernel,lanes", [("layer", 0), ("tile", 0), ("grid", 0), ("grid", 8), ("stream", 0),
+                                          ("specialized", 0)])
+def test_wide_ops_and_memories(kernel, lanes):
+    """Variadic folds (> 3 operands), long mux chains, two write ports per memory;
+    the grid form also at 8 lanes per thread (the benchmark's configuration)."""
     b = Builder()
     ins = [b.input(w) for w in (64, 32, 8, 1, 1, 5)]
     m = b.mem(16, width=40)
@@ -106,7 +108,7 @@ def test_wide_ops_and_memories(kernel):
     b.connect(regs[2], ops[3])
     b.connect(regs[3], ops[4])
     nl = b.build()
-    p = Pair(nl, 200, kernel=kernel, seed=9)
+    p = Pair(nl, 200, kernel=kernel, seed=9, lanes_per_thread=lanes)
     p.step(1, reset=True)
     p.step(50)
     p.compare()
