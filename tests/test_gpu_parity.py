@@ -70,12 +70,15 @@ def test_tile_shapes(kernel, tile_lanes, unroll, threads):
     p.close()
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_buffer_stimulus_and_probes(kernel):
+@pytest.mark.parametrize("kernel,lanes", [(k, 0) for k in KERNELS] + [("grid", 8), ("tile", 8)])
+def test_buffer_stimulus_and_probes(kernel, lanes):
+    """Stimulus from a device buffer and held inputs; probes every cycle and at the
+    last cycle (also at 8 lanes per thread, the benchmark's configuration)."""
     nl = small_design(21)
     n, c = 200, 12
     vals = synth.stimulus_values(21, c, nl.n_inputs, n)
-    p = Pair(nl, n, kernel=kernel, seed=21)
+    p = Pair(nl, n, kernel=kernel, seed=21, lanes_per_thread=lanes,
+             tile_lanes=64 if (kernel == "tile" and lanes) else 0)
     p.step(1, reset=True, stimulus="hold")
     probes = [0, 1, nl.reg_base, nl.reg_base + 3, nl.op_base + 7, nl.n_signals - 1]
     p.step(c, stimulus="buffer", values=vals, probes=probes, probe_mode="every")
@@ -252,15 +255,15 @@ def test_stream_chunks(n):
     p.close()
 
 
-@pytest.mark.parametrize("kernel", ["layer", "tile", "grid", "stream"])
-def test_waveform_changes(kernel):
+@pytest.mark.parametrize("kernel,lanes", [("layer", 0), ("tile", 0), ("grid", 0), ("grid", 8), ("stream", 0)])
+def test_waveform_changes(kernel, lanes):
     """Device-side change records equal the changes derived from the oracle's trace."""
     from oracle.waveform import changes
     nl = small_design(51, n_mems=2)
     n = 130
     rng = np.random.default_rng(51)
     budgets = rng.integers(0, 17, n).astype(np.uint32)
-    p = Pair(nl, n, kernel=kernel, seed=51)
+    p = Pair(nl, n, kernel=kernel, seed=51, lanes_per_thread=lanes)
     p.step(1, reset=True)
     p.step(5)
     probes = [0, 3, nl.reg_base, nl.reg_base + 7, nl.op_base + 11, nl.op_base + 400, nl.n_signals - 1]
