@@ -714,6 +714,17 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     ctas_per_sm = ctas_per_sm ? std::min<uint32_t>(ctas_per_sm, (uint32_t)occ) : (uint32_t)occ;
     grid = ctas_per_sm * (uint32_t)s->design->n_sms;
     if (kernel == RTEAAL_KERNEL_TILE) grid = std::min<uint32_t>(grid, s->n_pad / tile_lanes);
+    if (kernel == RTEAAL_KERNEL_GRID) {
+      // CTAs beyond what the widest phase (a layer, or the register commit) can
+      // occupy only add arrivals to every grid barrier: few lanes (one instance)
+      // then run on a grid sized to the work
+      const Lowered& L = s->design->L;
+      uint64_t widest = L.reg_src.size() + (L.mem_info.size() / 4 - 1);
+      for (size_t l = 0; l + 1 < L.layer_off.size(); l++)
+        widest = std::max<uint64_t>(widest, L.layer_off[l + 1] - L.layer_off[l]);
+      const uint64_t items = std::max<uint64_t>(widest, 1) * (s->n_pad / V);
+      grid = (uint32_t)std::min<uint64_t>(grid, (items + threads - 1) / threads);
+    }
   } else {
     ctas_per_sm = 0;
   }
