@@ -150,6 +150,18 @@ typedef struct {
 int rteaal_design_load(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
                        rteaal_design **out);
 int rteaal_design_info(const rteaal_design *design, rteaal_design_stats *out);
+/* The lowering alone, on the host (no device is touched, nothing is kept):
+ * parse, lower clock domains, fuse (opts->fuse_mux_chains), levelise (Sec. 4.2:
+ * an op's layer is one more than the deepest of its operands; inputs,
+ * registers and constants are layer 0) and group, exactly as
+ * rteaal_design_load does.  *out receives the figures rteaal_design_info would
+ * report for the loaded design, except metadata_bytes = 0 (nothing uploaded).
+ * layer_ops (nullable, caller-owned host array of max_layers entries) receives
+ * the lowered op count of layers 1, 2, ... (first max_layers of them).
+ * opts nullable; its allocator and device are ignored.
+ * Errors: E_INVALID (null netlist or out), E_FORMAT (as rteaal_design_load). */
+int rteaal_design_lower(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
+                        rteaal_design_stats *out, uint32_t *layer_ops, uint32_t max_layers);
 /* Which signals hold a row of the state: present[i] = 1 for signal i that can
  * be read, written and probed, 0 for a mux absorbed by operator fusion.
  * present: host array of n_signals bytes (caller-owned); n_signals must equal

@@ -106,7 +106,8 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_sync", "rteaal_state_read", "rteaal_state_write", "rteaal_mem_read",
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
            "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
-           "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize"]
+           "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize",
+           "rteaal_design_lower"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -124,6 +125,8 @@ def lib() -> ctypes.CDLL:
         L.rteaal_design_load.argtypes = [ctypes.c_char_p, ctypes.c_size_t,
                                          ctypes.POINTER(rteaal_load_opts), ctypes.POINTER(_P)]
         L.rteaal_design_info.argtypes = [_P, ctypes.POINTER(rteaal_design_stats)]
+        L.rteaal_design_lower.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
+                                          ctypes.POINTER(rteaal_design_stats), _P, _U32]
         L.rteaal_design_free.argtypes = [_P]
         L.rteaal_design_specialize.argtypes = [_P, ctypes.POINTER(_U64)]
         L.rteaal_design_signals.argtypes = [_P, _P, _U64]
@@ -231,6 +234,20 @@ def rteaal_design_info(design: int) -> dict:
     st = rteaal_design_stats()
     _check(lib().rteaal_design_info(design, ctypes.byref(st)))
     return {n: getattr(st, n) for n, _ in st._fields_}
+
+
+def rteaal_design_lower(netlist: bytes, fuse_mux_chains: bool = False) -> tuple[dict, np.ndarray]:
+    """The lowering on the host (no device): the design figures and the lowered
+    op count of every layer."""
+    opts = rteaal_load_opts()
+    opts.device = -1
+    opts.fuse_mux_chains = int(bool(fuse_mux_chains))
+    st = rteaal_design_stats()
+    _check(lib().rteaal_design_lower(netlist, len(netlist), ctypes.byref(opts), ctypes.byref(st), None, 0))
+    layer_ops = np.zeros(max(st.n_layers, 1), np.uint32)
+    _check(lib().rteaal_design_lower(netlist, len(netlist), ctypes.byref(opts), ctypes.byref(st),
+                                     layer_ops.ctypes.data, st.n_layers))
+    return {n: getattr(st, n) for n, _ in st._fields_}, layer_ops[:st.n_layers]
 
 
 def rteaal_design_signals(design: int, n_signals: int) -> np.ndarray:

@@ -539,27 +539,53 @@ RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaa
   });
 }
 
+namespace {
+
+// Figures of a netlist (as the caller wrote it) and of its lowering.
+void fill_stats(const Netlist& nl, const Lowered& L, uint64_t metadata_bytes, rteaal_design_stats* o) {
+  o->n_signals = nl.n_signals();
+  o->n_inputs = nl.ni;
+  o->n_regs = nl.nr;
+  o->n_consts = nl.nc;
+  o->n_ops = nl.no;
+  o->n_mems = nl.nm;
+  o->n_wports = nl.nw;
+  o->n_layers = (uint32_t)L.layer_off.size() - 1;
+  o->n_groups = (uint32_t)L.group_off.size() - 1;
+  o->n_slots = L.n_slots;
+  o->n_lowered_ops = (uint32_t)L.meta.size();
+  o->max_layer_ops = L.max_layer_ops;
+  o->op_operands = L.op_operands;
+  o->mem_words_total = L.mem_words_total;
+  o->metadata_bytes = metadata_bytes;
+  o->state_bytes_per_lane = L.lane_bytes;
+  o->n_fused = L.n_fused;
+}
+
+}  // namespace
+
 RT_EXPORT int rteaal_design_info(const rteaal_design* d, rteaal_design_stats* o) {
   return guarded([&] {
     require(d && o, "rteaal_design_info: null argument");
-    const Lowered& L = d->L;
-    o->n_signals = d->nl.n_signals();
-    o->n_inputs = d->nl.ni;
-    o->n_regs = d->nl.nr;
-    o->n_consts = d->nl.nc;
-    o->n_ops = d->nl.no;
-    o->n_mems = d->nl.nm;
-    o->n_wports = d->nl.nw;
-    o->n_layers = (uint32_t)L.layer_off.size() - 1;
-    o->n_groups = (uint32_t)L.group_off.size() - 1;
-    o->n_slots = L.n_slots;
-    o->n_lowered_ops = (uint32_t)L.meta.size();
-    o->max_layer_ops = L.max_layer_ops;
-    o->op_operands = L.op_operands;
-    o->mem_words_total = L.mem_words_total;
-    o->metadata_bytes = d->metadata_bytes;
-    o->state_bytes_per_lane = L.lane_bytes;
-    o->n_fused = L.n_fused;
+    fill_stats(d->nl, d->L, d->metadata_bytes, o);
+  });
+}
+
+RT_EXPORT int rteaal_design_lower(const void* netlist, size_t nbytes, const rteaal_load_opts* opts,
+                                  rteaal_design_stats* o, uint32_t* layer_ops, uint32_t max_layers) {
+  return guarded([&] {
+    require(netlist && o, "rteaal_design_lower: null argument");
+    Netlist nl;
+    std::string err;
+    if (!parse_netlist(netlist, nbytes, nl, err)) throw Error(RTEAAL_E_FORMAT, err);
+    std::vector<uint32_t> user2x;
+    const Netlist nlx = lower_clock_domains(nl, user2x);
+    Lowered L;
+    lower_netlist(nlx, L, opts && opts->fuse_mux_chains);
+    fill_stats(nl, L, 0, o);
+    if (layer_ops)
+      for (uint32_t l = 0; l + 1 < L.layer_off.size() && l < max_layers; l++)
+        layer_ops[l] = L.layer_off[l + 1] - L.layer_off[l];
   });
 }
 
@@ -719,9 +745,7 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
       // occupy only add arrivals to every grid barrier: few lanes (one instance)
       // then run on a grid sized to the work
       const Lowered& L = s->design->L;
-      uint64_t widest = L.reg_src.size() + (L.mem_info.size() / 4 - 1);
-      for (size_t l = 0; l + 1 < L.layer_off.size(); l++)
-        widest = std::max<uint64_t>(widest, L.layer_off[l + 1] - L.layer_off[l]);
+      const uint64_t widest = std::max<uint64_t>(L.max_layer_ops, L.reg_src.size() + (L.mem_info.size() / 4 - 1));
       const uint64_t items = std::max<uint64_t>(widest, 1) * (s->n_pad / V);
       grid = (uint32_t)std::min<uint64_t>(grid, (items + threads - 1) / threads);
     }

@@ -8,31 +8,9 @@ import oracle
 import paper_2601_18140_gb300 as rt
 import synth
 from synth import OP, DesignSpec
+from tests.netlist_rules import fused_away
 
 pytestmark = pytest.mark.gpu
-
-
-def fused_away(nl: synth.Netlist) -> set:
-    """The muxes the fusion rule absorbs (single-fanout false operand, at least as wide)."""
-    fan = np.zeros(nl.n_signals, np.int64)
-    np.add.at(fan, nl.args.astype(np.int64), 1)
-    np.add.at(fan, nl.reg_d.astype(np.int64), 1)
-    if nl.n_wports:
-        np.add.at(fan, nl.wport[:, 1:].reshape(-1).astype(np.int64), 1)
-    gone = set()
-    for k in range(nl.n_ops - 1, -1, -1):
-        if k in gone or nl.op_code[k] != OP["MUX"]:
-            continue
-        w0 = int(nl.op_width[k])
-        cur = k
-        while True:
-            x = int(nl.op_args(cur)[2])
-            j = x - nl.op_base
-            if x < nl.op_base or nl.op_code[j] != OP["MUX"] or fan[x] != 1 or nl.op_width[j] < w0:
-                break
-            gone.add(j)
-            cur = j
-    return {nl.op_base + j for j in gone}
 
 
 @pytest.mark.parametrize("kernel", ["layer", "grid", "stream"])
