@@ -149,6 +149,9 @@ typedef struct {
  * rteaal_design_free.  Errors: E_INVALID, E_FORMAT, E_NOMEM, E_CUDA. */
 int rteaal_design_load(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
                        rteaal_design **out);
+/* Figures of a loaded design (the netlist's counts and its lowering: layers
+ * of Sec. 4.2, (layer, opcode, width) groups, compact state size, device bytes
+ * of the lowered operand lists).  out: caller-owned.  Errors: E_INVALID. */
 int rteaal_design_info(const rteaal_design *design, rteaal_design_stats *out);
 /* The lowering alone, on the host (no device is touched, nothing is kept):
  * parse, lower clock domains, fuse (opts->fuse_mux_chains), levelise (Sec. 4.2:
@@ -239,7 +242,10 @@ typedef struct {
  * design must outlive the sim.  Errors: E_INVALID, E_NOMEM, E_CUDA. */
 int rteaal_sim_create(const rteaal_design *design, uint32_t n_instances,
                       const rteaal_sim_opts *opts, rteaal_sim **out);
+/* Instance / lane counts, device bytes and the launch configuration in use.
+ * out: caller-owned.  Errors: E_INVALID. */
 int rteaal_sim_info(const rteaal_sim *sim, rteaal_sim_stats *out);
+/* Waits for the device, then frees the sim's device memory (NULL: no-op). */
 void rteaal_sim_destroy(rteaal_sim *sim);
 
 /* Change the launch configuration (kernel, tile_lanes, threads, ctas_per_sm,
@@ -342,18 +348,27 @@ int rteaal_sim_reset_lanes(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst
 int rteaal_sync(rteaal_sim *sim, void *stream);
 
 /* Copy signal values of instances [inst_begin, inst_begin + n_inst) to / from
- * host memory laid out [n][n_inst].  Synchronises stream.  Writing a constant
- * changes it for the rest of the simulation (checkpoint restore). */
+ * host memory laid out [n][n_inst] (caller-owned, any host memory; values
+ * zero-extended, writes masked to each signal's width).  signals: host array of
+ * n signal ids (caller-owned).  Synchronises stream.  Writing a constant
+ * changes it for the rest of the simulation (checkpoint restore).  Errors:
+ * E_INVALID (null sim or buffer, instance range beyond n_instances, signal id
+ * out of range or fused away), E_NOMEM (device staging buffer), E_CUDA. */
 int rteaal_state_read(rteaal_sim *sim, const uint32_t *signals, uint32_t n, uint32_t inst_begin,
                       uint32_t n_inst, uint64_t *host_out, void *stream);
 int rteaal_state_write(rteaal_sim *sim, const uint32_t *signals, uint32_t n, uint32_t inst_begin,
                        uint32_t n_inst, const uint64_t *host_in, void *stream);
-/* Memory words of all memories (memory-major, word order), [words_total][n_inst]. */
+/* Memory words of all memories (memory-major, word order): host buffer
+ * [mem_words_total][n_inst] uint64 (caller-owned); written words are stored
+ * as given (the caller keeps them within mem_width).  Synchronises stream.
+ * Errors as rteaal_state_read. */
 int rteaal_mem_read(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst, uint64_t *host_out,
                     void *stream);
 int rteaal_mem_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst, const uint64_t *host_in,
                      void *stream);
-/* xorshift64 states, [n_inputs][n_inst]. */
+/* xorshift64 stimulus states (Sec. 5.2 testbench; Marsaglia 2003): host buffer
+ * [n_inputs][n_inst] uint64 (caller-owned); writing them replays a stimulus
+ * from a checkpoint.  Synchronises stream.  Errors as rteaal_state_read. */
 int rteaal_stim_state_read(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst,
                            uint64_t *host_out, void *stream);
 int rteaal_stim_state_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst,
