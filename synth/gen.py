@@ -133,7 +133,8 @@ class DesignSpec:
     mem_read_ports: int = 2
     mem_write_ports: int = 1
     input_widths: tuple | None = None  # explicit primary-input widths (overrides the draw)
-    mux_chain_frac: float = 0.0       # P(a MUX's false operand is a MUX of the previous layer)
+    mux_chain_frac: float = 0.0       # P(a MUX takes a previous-layer MUX nothing else reads as its
+                                      # false operand), capped by how many such MUXes are left
 
 
 # Named workloads: the sizes the parity tests and the benchmark use.
