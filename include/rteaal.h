@@ -176,6 +176,15 @@ int rteaal_design_signals(const rteaal_design *design, uint8_t *present, uint64_
  * kernel is kept with the design).  Errors: E_UNSUPPORTED (too many ops),
  * E_CUDA (compile or load failure; the message holds the compiler log). */
 int rteaal_design_specialize(rteaal_design *design, uint64_t *compile_us);
+/* The design-specialised kernel's generation and NVRTC compile for sm_103a
+ * alone, on the host (no device is touched, nothing is kept): checks that a
+ * netlist's straight-line kernel (Sec. 4.4, unrolled S rank and inlined
+ * tensors) compiles.  cubin_bytes / compile_us (nullable) receive the size of
+ * the compiled image and the generation + compile time.  opts nullable (only
+ * fuse_mux_chains is read).  Errors: E_INVALID, E_FORMAT, E_UNSUPPORTED (too
+ * many ops), E_CUDA (compile failure; the message holds the compiler log). */
+int rteaal_design_specialize_host(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
+                                  uint64_t *cubin_bytes, uint64_t *compile_us);
 /* Returns E_BUSY (and frees nothing) while sims created from it are alive. */
 int rteaal_design_free(rteaal_design *design);
 

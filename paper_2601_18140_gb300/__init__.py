@@ -107,7 +107,7 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
            "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
            "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize",
-           "rteaal_design_lower"]
+           "rteaal_design_lower", "rteaal_design_specialize_host"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -125,6 +125,9 @@ def lib() -> ctypes.CDLL:
         L.rteaal_design_load.argtypes = [ctypes.c_char_p, ctypes.c_size_t,
                                          ctypes.POINTER(rteaal_load_opts), ctypes.POINTER(_P)]
         L.rteaal_design_info.argtypes = [_P, ctypes.POINTER(rteaal_design_stats)]
+        L.rteaal_design_specialize_host.argtypes = [ctypes.c_char_p, ctypes.c_size_t,
+                                                    ctypes.POINTER(rteaal_load_opts), ctypes.POINTER(_U64),
+                                                    ctypes.POINTER(_U64)]
         L.rteaal_design_lower.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
                                           ctypes.POINTER(rteaal_design_stats), _P, _U32]
         L.rteaal_design_free.argtypes = [_P]
@@ -248,6 +251,18 @@ def rteaal_design_lower(netlist: bytes, fuse_mux_chains: bool = False) -> tuple[
     _check(lib().rteaal_design_lower(netlist, len(netlist), ctypes.byref(opts), ctypes.byref(st),
                                      layer_ops.ctypes.data, st.n_layers))
     return {n: getattr(st, n) for n, _ in st._fields_}, layer_ops[:st.n_layers]
+
+
+def rteaal_design_specialize_host(netlist: bytes, fuse_mux_chains: bool = False) -> dict:
+    """Generate and compile the design-specialised kernel on the host (no device):
+    the compiled image's size and the generation + compile time."""
+    opts = rteaal_load_opts()
+    opts.device = -1
+    opts.fuse_mux_chains = int(bool(fuse_mux_chains))
+    nbytes, us = _U64(), _U64()
+    _check(lib().rteaal_design_specialize_host(netlist, len(netlist), ctypes.byref(opts), ctypes.byref(nbytes),
+                                               ctypes.byref(us)))
+    return {"cubin_bytes": nbytes.value, "compile_us": us.value}
 
 
 def rteaal_design_signals(design: int, n_signals: int) -> np.ndarray:

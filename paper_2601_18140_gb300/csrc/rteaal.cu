@@ -628,17 +628,24 @@ constexpr uint32_t kSpecThreads = 128;
 constexpr uint32_t kSpecOptimizeOps = 4096;  // NVVM optimiser on up to this many ops
 
 // Generate, compile (NVRTC, sm_103a) and load the design-specialised kernel once.
+// Generate and compile (NVRTC, sm_103a) the design-specialised kernel of a
+// lowered netlist; host only.
+std::vector<char> build_specialized(const Netlist& nlx, const Lowered& L) {
+  if (nlx.no > kSpecMaxOps)
+    throw Error(RTEAAL_E_UNSUPPORTED, "design-specialised kernel: more than 16,384 ops (compile time grows superlinearly)");
+  const std::string src = specialized_source(nlx, L);
+  std::vector<char> cubin;
+  std::string log;
+  if (!compile_specialized(src, "sm_103a", nlx.no <= kSpecOptimizeOps, cubin, log))
+    throw Error(RTEAAL_E_CUDA, "design-specialised kernel: compile failed: " + log.substr(0, 2000));
+  return cubin;
+}
+
 void ensure_specialized(rteaal_design* d) {
   std::lock_guard<std::mutex> g(d->spec_mu);
   if (d->spec_kernel) return;
-  if (d->nlx.no > kSpecMaxOps)
-    throw Error(RTEAAL_E_UNSUPPORTED, "design-specialised kernel: more than 16,384 ops (compile time grows superlinearly)");
   const auto t0 = std::chrono::steady_clock::now();
-  const std::string src = specialized_source(d->nlx, d->L);
-  std::vector<char> cubin;
-  std::string log;
-  if (!compile_specialized(src, "sm_103a", d->nlx.no <= kSpecOptimizeOps, cubin, log))
-    throw Error(RTEAAL_E_CUDA, "design-specialised kernel: compile failed: " + log.substr(0, 2000));
+  const std::vector<char> cubin = build_specialized(d->nlx, d->L);
   CK(cudaSetDevice(d->device));
   CK(cudaLibraryLoadData(&d->spec_lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
   CK(cudaLibraryGetKernel(&d->spec_kernel, d->spec_lib, "rteaal_spec"));
@@ -770,6 +777,26 @@ RT_EXPORT int rteaal_design_specialize(rteaal_design* d, uint64_t* compile_us) {
     require(d, "rteaal_design_specialize: null design");
     ensure_specialized(d);
     if (compile_us) *compile_us = d->spec_compile_us;
+  });
+}
+
+RT_EXPORT int rteaal_design_specialize_host(const void* netlist, size_t nbytes, const rteaal_load_opts* opts,
+                                            uint64_t* cubin_bytes, uint64_t* compile_us) {
+  return guarded([&] {
+    require(netlist, "rteaal_design_specialize_host: null netlist");
+    Netlist nl;
+    std::string err;
+    if (!parse_netlist(netlist, nbytes, nl, err)) throw Error(RTEAAL_E_FORMAT, err);
+    std::vector<uint32_t> user2x;
+    const Netlist nlx = lower_clock_domains(nl, user2x);
+    Lowered L;
+    lower_netlist(nlx, L, opts && opts->fuse_mux_chains);
+    const auto t0 = std::chrono::steady_clock::now();
+    const std::vector<char> cubin = build_specialized(nlx, L);
+    if (cubin_bytes) *cubin_bytes = cubin.size();
+    if (compile_us)
+      *compile_us = (uint64_t)std::chrono::duration_cast<std::chrono::microseconds>(
+                        std::chrono::steady_clock::now() - t0).count();
   });
 }
 
