@@ -67,6 +67,36 @@ def test_bruteforce_12bit_inputs_multicycle(seed):
         assert [int(x) for x in sim.vals[i]] == ps.v, i
 
 
+@pytest.mark.parametrize("seed", [19, 25])     # seeds whose write ports write and reads vary
+def test_bruteforce_memories_multicycle(seed):
+    """Every 12-bit input assignment held for 4 cycles after reset with two
+    register files (two read ports each, one or two write ports): values and
+    every memory word against the pure-Python evaluator, so that a write is seen
+    by the reads of the next cycle and not of its own."""
+    nl = synth.generate(DesignSpec(n_ops=40, n_regs=6, depth=5, n_inputs=2, n_consts=4, seed=seed,
+                                   input_widths=(4, 8), n_mems=2, mem_words=4, mem_read_ports=2,
+                                   mem_write_ports=1 + seed % 2,
+                                   widths={1: 0.3, 4: 0.2, 8: 0.2, 16: 0.1, 32: 0.1, 64: 0.1}))
+    assert nl.n_mems == 2 and nl.n_wports >= 2
+    n = 1 << 12
+    vals = np.stack([np.arange(n) & 15, np.arange(n) >> 4]).astype(np.uint64)
+    buf = np.broadcast_to(vals, (4, 2, n)).copy()
+    sim = oracle.OracleSim(nl.to_bytes(), n)
+    sim.step(1, reset=True)
+    sim.step(4, mode=oracle.STIM_BUFFER, buf=buf)
+    assert (nl.op_code == OP["MEMRD"]).sum() == 4
+    assert (sim.mems != 0).mean() > 0.2                       # the write ports do write
+    mr = np.flatnonzero(nl.op_code == OP["MEMRD"]) + nl.op_base
+    assert max(np.unique(sim.vals[:, x]).size for x in mr) > 1  # and the reads see it
+    for i in range(0, n, 5):
+        ps = PySim(nl)
+        ps.cycle([0, 0], reset=True)
+        for _ in range(4):
+            ps.cycle([i & 15, i >> 4])
+        assert [int(x) for x in sim.vals[i]] == ps.v, i
+        assert [int(x) for x in sim.mems[i, :sum(len(m) for m in ps.mem)]] == [w for m in ps.mem for w in m], i
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
 def test_cascade_matches_oracle(seed):
     nl = tiny(seed, n_ops=80, depth=6, n_regs=10, input_widths=(8, 16, 1, 64), n_mems=2)
