@@ -348,7 +348,8 @@ def rteaal_state_read(sim: int, signals, inst_begin: int, n_inst: int, stream=No
 def rteaal_state_write(sim: int, signals, inst_begin: int, values: np.ndarray, stream=None):
     sig = np.ascontiguousarray(np.asarray(signals, np.uint32).reshape(-1))
     v = np.ascontiguousarray(values, np.uint64)
-    assert v.shape[0] == sig.size
+    if v.ndim != 2 or v.shape[0] != sig.size:
+        raise ValueError("values must be [n_signals][n_instances]")
     _check(lib().rteaal_state_write(sim, _np_ptr(sig, _U32), sig.size, inst_begin, v.shape[1],
                                     v.ctypes.data, _stream_ptr(stream)))
 
@@ -456,11 +457,14 @@ class Sim:
             o.allocator = ctypes.pointer(self._alloc)
         if xorshift_seed is not None:
             xs = np.ascontiguousarray(xorshift_seed, np.uint64)
-            assert xs.shape == (design.info["n_inputs"], n_instances)
+            if xs.shape != (design.info["n_inputs"], n_instances):
+                raise ValueError("xorshift_seed must be [n_inputs][n_instances]")
             keep.append(xs)
             o.xorshift_seed = _np_ptr(xs, _U64)
         if expected_cycles is not None:
             ec = np.ascontiguousarray(expected_cycles, np.uint32)
+            if ec.size != n_instances:
+                raise ValueError("expected_cycles must have one entry per instance")
             keep.append(ec)
             o.expected_cycles = _np_ptr(ec, _U32)
         self.handle = rteaal_sim_create(design.handle, n_instances, o)
@@ -478,12 +482,14 @@ class Sim:
             cyc.uniform = int(cycles)
         else:
             pc = np.ascontiguousarray(cycles, np.uint32)
-            assert pc.size == self.n
+            if pc.size != self.n:
+                raise ValueError("per-instance cycles must have one entry per instance")
             keep.append(pc)
             cyc.per_instance = _np_ptr(pc, _U32)
         if reset_per_instance is not None:
             rp = np.ascontiguousarray(reset_per_instance, np.uint32)
-            assert rp.size == self.n
+            if rp.size != self.n:
+                raise ValueError("reset_per_instance must have one entry per instance")
             keep.append(rp)
             cyc.reset_per_instance = _np_ptr(rp, _U32)
         st = rteaal_stimulus()
@@ -491,6 +497,9 @@ class Sim:
         if values is not None:
             if isinstance(values, np.ndarray):
                 v = np.ascontiguousarray(values, np.uint64)
+                ncyc = int(np.max(cycles)) if not np.isscalar(cycles) else int(cycles)
+                if v.size < ncyc * int(self.design.info["n_inputs"]) * self.n:
+                    raise ValueError("stimulus values must be [cycles][n_inputs][n_instances]")
                 keep.append(v)
                 st.values, st.values_on_host = int(v.ctypes.data), 1
             else:
@@ -563,9 +572,13 @@ class Sim:
                                int(self.design.info["mem_words_total"]), stream)
 
     def write_mem(self, values: np.ndarray, inst_begin: int = 0, stream=None):
+        if np.ndim(values) != 2 or np.shape(values)[0] != int(self.design.info["mem_words_total"]):
+            raise ValueError("memory words must be [mem_words_total][n_instances]")
         rteaal_mem_write(self.handle, inst_begin, values, stream)
 
     def reset_lanes(self, inst_begin: int, n_inst: int, xorshift_seed=None, stream=None):
+        if xorshift_seed is not None and np.shape(xorshift_seed) != (int(self.design.info["n_inputs"]), n_inst):
+            raise ValueError("xorshift_seed must be [n_inputs][n_inst]")
         rteaal_sim_reset_lanes(self.handle, inst_begin, n_inst, xorshift_seed, stream)
 
     def read_stim_state(self, inst_begin: int = 0, n_inst: int | None = None, stream=None):
@@ -574,6 +587,8 @@ class Sim:
                                       int(self.design.info["n_inputs"]), stream)
 
     def write_stim_state(self, values: np.ndarray, inst_begin: int = 0, stream=None):
+        if np.ndim(values) != 2 or np.shape(values)[0] != int(self.design.info["n_inputs"]):
+            raise ValueError("xorshift states must be [n_inputs][n_instances]")
         rteaal_stim_state_write(self.handle, inst_begin, values, stream)
 
     def close(self):
