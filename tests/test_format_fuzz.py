@@ -1,0 +1,66 @@
+"""Malformed netlists on the host: seeded corruptions of valid RTLN netlists
+(flipped bytes, header counts set to edge values, truncation, trailing bytes,
+corrupted operand ids) never crash either parser, the library reports every
+rejection as E_FORMAT, and the library's parser (with its lowering) and the
+oracle's independent one accept exactly the same inputs."""
+import struct
+
+import numpy as np
+
+import oracle
+import paper_2601_18140_gb300 as rt
+import synth
+from paper_2601_18140_gb300 import build as rtbuild
+from synth import Builder, DesignSpec
+
+
+def _bases() -> list[bytes]:
+    out = [synth.generate(DesignSpec(n_ops=60, n_regs=5, depth=4, seed=s, n_mems=s % 2, mem_words=4)).to_bytes()
+           for s in range(3)]
+    b = Builder()
+    i0 = b.input(8)
+    r = b.reg(8)
+    b.connect(r, b.op("ADD", 8, r, i0))
+    b.clock(r, b.domain(4, 1))
+    out.append(b.build().to_bytes())
+    return out
+
+
+def _corrupt(b: bytearray, rng) -> bytes:
+    kind = rng.integers(0, 4)
+    if kind == 0:                                   # flipped bytes
+        for _ in range(rng.integers(1, 6)):
+            b[rng.integers(0, len(b))] = rng.integers(0, 256)
+    elif kind == 1:                                 # a header count set to an edge value
+        i = rng.integers(2, 10)
+        v = int(rng.choice([0, 1, 2, 255, 65535, 2**31, 2**32 - 1, rng.integers(0, 1000)]))
+        b[4 * i:4 * i + 4] = struct.pack("<I", v)
+    elif kind == 2:                                 # truncated or extended
+        b = b[:rng.integers(0, len(b))] if rng.random() < 0.5 else b + bytes(int(rng.integers(1, 64)))
+    else:                                           # a u32 of the body (ids, offsets, sizes)
+        j = int(rng.integers(40, max(41, len(b) - 4))) & ~3
+        b[j:j + 4] = struct.pack("<I", int(rng.choice([0xFFFFFFFF, 0x7FFFFFFF, rng.integers(0, 5000)])))
+    return bytes(b)
+
+
+def test_corrupted_netlists():
+    rtbuild.build()
+    bases = _bases()
+    rng = np.random.default_rng(2024)
+    accepted = 0
+    for it in range(1500):
+        b = _corrupt(bytearray(bases[it % len(bases)]), rng)
+        try:
+            rt.rteaal_design_lower(b)
+            lib_ok = True
+        except rt.RteaalError as e:
+            assert e.code == rt.RTEAAL_E_FORMAT, (it, str(e))
+            lib_ok = False
+        try:
+            oracle.OracleSim(b, 1)
+            orc_ok = True
+        except ValueError:                          # the oracle's format error
+            orc_ok = False
+        assert lib_ok == orc_ok, it
+        accepted += lib_ok
+    assert 0 < accepted < 1500          # both outcomes occur
