@@ -2,7 +2,8 @@
 (flipped bytes, header counts set to edge values, truncation, trailing bytes,
 corrupted operand ids) never crash either parser, the library reports every
 rejection as E_FORMAT, and the library's parser (with its lowering) and the
-oracle's independent one accept exactly the same inputs."""
+oracle's independent one accept exactly the same inputs; an accepted one-clock
+netlist is lowered as the levelisation restated from it predicts."""
 import struct
 
 import numpy as np
@@ -12,6 +13,7 @@ import paper_2601_18140_gb300 as rt
 import synth
 from paper_2601_18140_gb300 import build as rtbuild
 from synth import Builder, DesignSpec
+from tests.test_lowering_host import check
 
 
 def _bases() -> list[bytes]:
@@ -63,4 +65,8 @@ def test_corrupted_netlists():
             orc_ok = False
         assert lib_ok == orc_ok, it
         accepted += lib_ok
+        if lib_ok:
+            nl = synth.Netlist.from_bytes(b)
+            if not nl.n_domains:                    # the restatement has no clock domains
+                check(nl)
     assert 0 < accepted < 1500          # both outcomes occur
