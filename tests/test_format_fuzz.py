@@ -3,7 +3,8 @@
 corrupted operand ids) never crash either parser, the library reports every
 rejection as E_FORMAT, and the library's parser (with its lowering) and the
 oracle's independent one accept exactly the same inputs; an accepted one-clock
-netlist is lowered as the levelisation restated from it predicts."""
+netlist is lowered as the levelisation restated from it predicts, and the
+oracle simulates it as the pure-Python evaluator does."""
 import struct
 
 import numpy as np
@@ -13,6 +14,7 @@ import paper_2601_18140_gb300 as rt
 import synth
 from paper_2601_18140_gb300 import build as rtbuild
 from synth import Builder, DesignSpec
+from oracle.pyeval import PySim
 from tests.test_lowering_host import check
 
 
@@ -45,11 +47,25 @@ def _corrupt(b: bytearray, rng) -> bytes:
     return bytes(b)
 
 
+def _same_as_pyeval(b: bytes, nl: synth.Netlist, rng, n_inst: int = 2, cycles: int = 4):
+    ni = nl.n_inputs
+    vals = rng.integers(0, 2**63, size=(cycles, ni, n_inst), dtype=np.uint64)
+    sim = oracle.OracleSim(b, n_inst)
+    sim.step(1, reset=True)
+    sim.step(cycles, mode=oracle.STIM_BUFFER, buf=vals)
+    for i in range(n_inst):
+        ps = PySim(nl)
+        ps.cycle([0] * ni, reset=True)
+        for c in range(cycles):
+            ps.cycle([int(x) for x in vals[c, :, i]])
+        assert [int(x) for x in sim.vals[i]] == ps.v
+
+
 def test_corrupted_netlists():
     rtbuild.build()
     bases = _bases()
     rng = np.random.default_rng(2024)
-    accepted = 0
+    accepted = simulated = 0
     for it in range(1500):
         b = _corrupt(bytearray(bases[it % len(bases)]), rng)
         try:
@@ -67,6 +83,9 @@ def test_corrupted_netlists():
         accepted += lib_ok
         if lib_ok:
             nl = synth.Netlist.from_bytes(b)
-            if not nl.n_domains:                    # the restatement has no clock domains
+            if not nl.n_domains:                    # the restatements have no clock domains
                 check(nl)
+                _same_as_pyeval(b, nl, rng)
+                simulated += 1
     assert 0 < accepted < 1500          # both outcomes occur
+    assert simulated >= 50
