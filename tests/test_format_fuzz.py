@@ -4,7 +4,7 @@ corrupted operand ids) never crash either parser, the library reports every
 rejection as E_FORMAT, and the library's parser (with its lowering) and the
 oracle's independent one accept exactly the same inputs; an accepted one-clock
 netlist is lowered as the levelisation restated from it predicts, and the
-oracle simulates it as the pure-Python evaluator does."""
+oracle simulates it as the pure-Python evaluator and the Einsum cascade do."""
 import struct
 
 import numpy as np
@@ -14,6 +14,7 @@ import paper_2601_18140_gb300 as rt
 import synth
 from paper_2601_18140_gb300 import build as rtbuild
 from synth import Builder, DesignSpec
+from oracle.cascade import CascadeSim
 from oracle.pyeval import PySim
 from tests.test_lowering_host import check
 
@@ -59,6 +60,11 @@ def _same_as_pyeval(b: bytes, nl: synth.Netlist, rng, n_inst: int = 2, cycles: i
         for c in range(cycles):
             ps.cycle([int(x) for x in vals[c, :, i]])
         assert [int(x) for x in sim.vals[i]] == ps.v
+    cs = CascadeSim(nl)
+    cs.cycle(np.zeros(ni, np.uint64), reset=True)
+    for c in range(cycles):
+        cs.cycle(vals[c, :, 0])
+    assert [int(x) for x in sim.vals[0]] == cs.v
 
 
 def test_corrupted_netlists():
