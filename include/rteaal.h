@@ -165,6 +165,19 @@ int rteaal_design_info(const rteaal_design *design, rteaal_design_stats *out);
  * Errors: E_INVALID (null netlist or out), E_FORMAT (as rteaal_design_load). */
 int rteaal_design_lower(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
                         rteaal_design_stats *out, uint32_t *layer_ops, uint32_t max_layers);
+/* The one-clock netlist the library simulates for a netlist with clock domains
+ * (Sec. 5.2 "Multiple Clock Domains", reading in the format notes above): a
+ * hidden 32-bit cycle counter t (a register after the caller's registers), per
+ * slower domain an enable (t + phase) & (period - 1) == 0, and per register of
+ * such a domain a hold mux; without domains, the netlist itself.  Host only.
+ * out (nullable, caller-owned, capacity bytes) receives its RTLN bytes and
+ * *out_bytes their count (call with out = NULL to size the buffer).  user2x
+ * (nullable, caller-owned, n_user = the netlist's signal count) receives, for
+ * every caller signal, its id in the one-clock netlist.
+ * Errors: E_INVALID (null netlist or out_bytes, capacity or n_user too small or
+ * wrong), E_FORMAT (as rteaal_design_load). */
+int rteaal_design_single_clock(const void *netlist, size_t nbytes, void *out, size_t capacity,
+                               size_t *out_bytes, uint32_t *user2x, uint64_t n_user);
 /* Which signals hold a row of the state: present[i] = 1 for signal i that can
  * be read, written and probed, 0 for a mux absorbed by operator fusion.
  * present: host array of n_signals bytes (caller-owned); n_signals must equal

@@ -107,7 +107,7 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
            "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
            "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize",
-           "rteaal_design_lower", "rteaal_design_specialize_host"]
+           "rteaal_design_lower", "rteaal_design_specialize_host", "rteaal_design_single_clock"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -128,6 +128,8 @@ def lib() -> ctypes.CDLL:
         L.rteaal_design_specialize_host.argtypes = [ctypes.c_char_p, ctypes.c_size_t,
                                                     ctypes.POINTER(rteaal_load_opts), ctypes.POINTER(_U64),
                                                     ctypes.POINTER(_U64)]
+        L.rteaal_design_single_clock.argtypes = [ctypes.c_char_p, ctypes.c_size_t, _P, ctypes.c_size_t,
+                                                 ctypes.POINTER(ctypes.c_size_t), _P, _U64]
         L.rteaal_design_lower.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
                                           ctypes.POINTER(rteaal_design_stats), _P, _U32]
         L.rteaal_design_free.argtypes = [_P]
@@ -251,6 +253,18 @@ def rteaal_design_lower(netlist: bytes, fuse_mux_chains: bool = False) -> tuple[
     _check(lib().rteaal_design_lower(netlist, len(netlist), ctypes.byref(opts), ctypes.byref(st),
                                      layer_ops.ctypes.data, st.n_layers))
     return {n: getattr(st, n) for n, _ in st._fields_}, layer_ops[:st.n_layers]
+
+
+def rteaal_design_single_clock(netlist: bytes, n_signals: int) -> tuple[bytes, np.ndarray]:
+    """The one-clock netlist the library simulates (hidden cycle counter, enables
+    and hold muxes for clock domains) and, per caller signal, its id there."""
+    n = ctypes.c_size_t()
+    _check(lib().rteaal_design_single_clock(netlist, len(netlist), None, 0, ctypes.byref(n), None, 0))
+    out = ctypes.create_string_buffer(n.value)
+    user2x = np.zeros(n_signals, np.uint32)
+    _check(lib().rteaal_design_single_clock(netlist, len(netlist), out, n.value, ctypes.byref(n),
+                                            user2x.ctypes.data, n_signals))
+    return out.raw[:n.value], user2x
 
 
 def rteaal_design_specialize_host(netlist: bytes, fuse_mux_chains: bool = False) -> dict:

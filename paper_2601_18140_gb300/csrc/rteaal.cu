@@ -571,6 +571,64 @@ RT_EXPORT int rteaal_design_info(const rteaal_design* d, rteaal_design_stats* o)
   });
 }
 
+namespace {
+
+// RTLN bytes of a netlist (the inverse of parse_netlist; layout in rteaal.h).
+std::vector<uint8_t> serialize_netlist(const Netlist& nl) {
+  std::vector<uint8_t> out;
+  auto put = [&](const void* p, size_t n) {
+    const uint8_t* b = static_cast<const uint8_t*>(p);
+    out.insert(out.end(), b, b + n);
+  };
+  auto vec = [&](const auto& v) { put(v.data(), v.size() * sizeof(v[0])); };
+  const uint32_t hdr[10] = {0x4E4C5452u, 1u, nl.ni, nl.nr, nl.nc, nl.no, nl.nm, nl.nw, nl.na, nl.nd};
+  put(hdr, sizeof(hdr));
+  vec(nl.reg_init);
+  vec(nl.const_value);
+  vec(nl.reg_d);
+  vec(nl.argoff);
+  vec(nl.args);
+  vec(nl.mem_words);
+  vec(nl.wport);
+  if (nl.nd) {
+    vec(nl.dom_period);
+    vec(nl.dom_phase);
+  }
+  vec(nl.in_w);
+  vec(nl.reg_w);
+  vec(nl.const_w);
+  vec(nl.code);
+  vec(nl.width);
+  vec(nl.p0);
+  vec(nl.p1);
+  vec(nl.mem_w);
+  if (nl.nd) vec(nl.reg_dom);
+  return out;
+}
+
+}  // namespace
+
+RT_EXPORT int rteaal_design_single_clock(const void* netlist, size_t nbytes, void* out, size_t capacity,
+                                         size_t* out_bytes, uint32_t* user2x, uint64_t n_user) {
+  return guarded([&] {
+    require(netlist && out_bytes, "rteaal_design_single_clock: null argument");
+    Netlist nl;
+    std::string err;
+    if (!parse_netlist(netlist, nbytes, nl, err)) throw Error(RTEAAL_E_FORMAT, err);
+    std::vector<uint32_t> map;
+    const std::vector<uint8_t> bytes = serialize_netlist(lower_clock_domains(nl, map));
+    *out_bytes = bytes.size();
+    if (out) {
+      require(capacity >= bytes.size(), "rteaal_design_single_clock: output buffer too small");
+      std::memcpy(out, bytes.data(), bytes.size());
+    }
+    if (user2x) {
+      require(n_user == map.size(), "rteaal_design_single_clock: n_user differs from the netlist's signal count");
+      std::copy(map.begin(), map.end(), user2x);
+    }
+  });
+}
+
 RT_EXPORT int rteaal_design_lower(const void* netlist, size_t nbytes, const rteaal_load_opts* opts,
                                   rteaal_design_stats* o, uint32_t* layer_ops, uint32_t max_layers) {
   return guarded([&] {
