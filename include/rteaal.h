@@ -178,6 +178,20 @@ int rteaal_design_lower(const void *netlist, size_t nbytes, const rteaal_load_op
  * wrong), E_FORMAT (as rteaal_design_load). */
 int rteaal_design_single_clock(const void *netlist, size_t nbytes, void *out, size_t capacity,
                                size_t *out_bytes, uint32_t *user2x, uint64_t n_user);
+/* The lowered design as the kernels execute it, written back as a netlist
+ * (host only): one signal per state row -- inputs, registers (with the hidden
+ * cycle counter of clock domains), constants, then one op per descriptor in
+ * the lowered order (layer by layer, Sec. 4.2; grouped by opcode and width),
+ * each decoded from its descriptor: fused mux chains as MUXCHAIN, the copies
+ * the clock edge reads as COPY; registers and write ports from the edge
+ * tables.  Simulating it gives every surviving signal the value the design
+ * gives it.  out / capacity / out_bytes as rteaal_design_single_clock;
+ * user2sig (nullable, caller-owned, n_user = the netlist's signal count)
+ * receives each caller signal's id there, 0xFFFFFFFF for a mux absorbed by
+ * fusion.  opts nullable (only fuse_mux_chains is read).
+ * Errors: E_INVALID, E_FORMAT (as rteaal_design_load). */
+int rteaal_design_lowered_netlist(const void *netlist, size_t nbytes, const rteaal_load_opts *opts, void *out,
+                                  size_t capacity, size_t *out_bytes, uint32_t *user2sig, uint64_t n_user);
 /* Which signals hold a row of the state: present[i] = 1 for signal i that can
  * be read, written and probed, 0 for a mux absorbed by operator fusion.
  * present: host array of n_signals bytes (caller-owned); n_signals must equal

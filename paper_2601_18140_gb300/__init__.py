@@ -107,7 +107,8 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_mem_write", "rteaal_stim_state_read", "rteaal_stim_state_write",
            "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
            "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize",
-           "rteaal_design_lower", "rteaal_design_specialize_host", "rteaal_design_single_clock"]
+           "rteaal_design_lower", "rteaal_design_specialize_host", "rteaal_design_single_clock",
+           "rteaal_design_lowered_netlist"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -128,6 +129,8 @@ def lib() -> ctypes.CDLL:
         L.rteaal_design_specialize_host.argtypes = [ctypes.c_char_p, ctypes.c_size_t,
                                                     ctypes.POINTER(rteaal_load_opts), ctypes.POINTER(_U64),
                                                     ctypes.POINTER(_U64)]
+        L.rteaal_design_lowered_netlist.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
+                                                    _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _P, _U64]
         L.rteaal_design_single_clock.argtypes = [ctypes.c_char_p, ctypes.c_size_t, _P, ctypes.c_size_t,
                                                  ctypes.POINTER(ctypes.c_size_t), _P, _U64]
         L.rteaal_design_lower.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
@@ -265,6 +268,23 @@ def rteaal_design_single_clock(netlist: bytes, n_signals: int) -> tuple[bytes, n
     _check(lib().rteaal_design_single_clock(netlist, len(netlist), out, n.value, ctypes.byref(n),
                                             user2x.ctypes.data, n_signals))
     return out.raw[:n.value], user2x
+
+
+def rteaal_design_lowered_netlist(netlist: bytes, n_signals: int,
+                                  fuse_mux_chains: bool = False) -> tuple[bytes, np.ndarray]:
+    """The lowered design written back as a netlist (one signal per state row, one
+    op per descriptor) and, per caller signal, its id there (0xFFFFFFFF: fused away)."""
+    opts = rteaal_load_opts()
+    opts.device = -1
+    opts.fuse_mux_chains = int(bool(fuse_mux_chains))
+    n = ctypes.c_size_t()
+    _check(lib().rteaal_design_lowered_netlist(netlist, len(netlist), ctypes.byref(opts), None, 0,
+                                               ctypes.byref(n), None, 0))
+    out = ctypes.create_string_buffer(n.value)
+    user2sig = np.zeros(n_signals, np.uint32)
+    _check(lib().rteaal_design_lowered_netlist(netlist, len(netlist), ctypes.byref(opts), out, n.value,
+                                               ctypes.byref(n), user2sig.ctypes.data, n_signals))
+    return out.raw[:n.value], user2sig
 
 
 def rteaal_design_specialize_host(netlist: bytes, fuse_mux_chains: bool = False) -> dict:

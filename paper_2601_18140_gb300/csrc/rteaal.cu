@@ -18,6 +18,7 @@
 #include <numeric>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <chrono>
@@ -606,7 +607,86 @@ std::vector<uint8_t> serialize_netlist(const Netlist& nl) {
   return out;
 }
 
+// The lowered design as a netlist: one signal per state row (the pool rows keep
+// their ids, op rows follow in lowered order), every op decoded back from its
+// descriptor (ctl word and operand row references, or its side-array operand
+// list), registers and write ports from the clock-edge tables.
+Netlist netlist_of_lowering(const Netlist& nlx, const Lowered& L) {
+  std::unordered_map<uint32_t, uint32_t> slot_of_ref;
+  for (uint32_t sl = 0; sl < L.n_slots; sl++) slot_of_ref[L.slot_ref[sl]] = sl;
+  auto slot = [&](uint32_t ref) {
+    auto it = slot_of_ref.find(ref);
+    if (it == slot_of_ref.end()) throw Error(RTEAAL_E_FORMAT, "lowering: operand row without a slot");
+    return it->second;
+  };
+  Netlist x;
+  x.ni = nlx.ni;
+  x.nc = nlx.nc;
+  x.nr = (uint32_t)L.reg_src.size();
+  x.in_w = nlx.in_w;
+  x.const_w = nlx.const_w;
+  x.const_value = L.const_value;
+  for (uint32_t r = 0; r < x.nr; r++) {
+    x.reg_w.push_back((uint8_t)L.reg_width[r]);
+    x.reg_init.push_back(L.reg_init[r]);
+    x.reg_d.push_back(slot(L.reg_src[r]));
+  }
+  x.argoff.push_back(0);
+  for (const OpMeta& m : L.meta) {
+    const uint32_t ctl = m.ctl;
+    x.code.push_back((uint8_t)(ctl & 31u));
+    x.width.push_back((uint8_t)((ctl >> 8) & 127u));
+    x.p0.push_back((uint8_t)((ctl >> 16) & 255u));
+    x.p1.push_back((uint8_t)(ctl >> 24));
+    if (ctl & CTL_EXT) {
+      for (uint32_t j = 0; j < m.b; j++) x.args.push_back(slot(L.ext_args[m.a + j]));
+    } else {
+      const uint32_t refs[3] = {m.a, m.b, m.c}, ar = (ctl >> 5) & 3u;
+      for (uint32_t j = 0; j < ar; j++) x.args.push_back(slot(refs[j]));
+    }
+    x.argoff.push_back((uint32_t)x.args.size());
+  }
+  x.no = (uint32_t)L.meta.size();
+  x.na = (uint32_t)x.args.size();
+  x.nm = (uint32_t)(L.mem_info.size() / 4 - 1);
+  for (uint32_t m = 0; m < x.nm; m++) {
+    x.mem_words.push_back(L.mem_info[4ull * m + 1] + 1u);
+    x.mem_w.push_back((uint8_t)L.mem_info[4ull * m + 2]);
+  }
+  x.nw = (uint32_t)(L.wport.size() / 4);
+  for (uint32_t q = 0; q < x.nw; q++) {
+    x.wport.push_back(L.wport[4ull * q]);
+    for (int t = 1; t < 4; t++) x.wport.push_back(slot(L.wport[4ull * q + t]));
+  }
+  return x;
+}
+
 }  // namespace
+
+RT_EXPORT int rteaal_design_lowered_netlist(const void* netlist, size_t nbytes, const rteaal_load_opts* opts,
+                                            void* out, size_t capacity, size_t* out_bytes, uint32_t* user2sig,
+                                            uint64_t n_user) {
+  return guarded([&] {
+    require(netlist && out_bytes, "rteaal_design_lowered_netlist: null argument");
+    Netlist nl;
+    std::string err;
+    if (!parse_netlist(netlist, nbytes, nl, err)) throw Error(RTEAAL_E_FORMAT, err);
+    std::vector<uint32_t> user2x;
+    const Netlist nlx = lower_clock_domains(nl, user2x);
+    Lowered L;
+    lower_netlist(nlx, L, opts && opts->fuse_mux_chains);
+    const std::vector<uint8_t> bytes = serialize_netlist(netlist_of_lowering(nlx, L));
+    *out_bytes = bytes.size();
+    if (out) {
+      require(capacity >= bytes.size(), "rteaal_design_lowered_netlist: output buffer too small");
+      std::memcpy(out, bytes.data(), bytes.size());
+    }
+    if (user2sig) {
+      require(n_user == user2x.size(), "rteaal_design_lowered_netlist: n_user differs from the netlist's signal count");
+      for (size_t i = 0; i < user2x.size(); i++) user2sig[i] = L.sig2slot[user2x[i]];
+    }
+  });
+}
 
 RT_EXPORT int rteaal_design_single_clock(const void* netlist, size_t nbytes, void* out, size_t capacity,
                                          size_t* out_bytes, uint32_t* user2x, uint64_t n_user) {
