@@ -4,7 +4,9 @@ corrupted operand ids) never crash either parser, the library reports every
 rejection as E_FORMAT, and the library's parser (with its lowering) and the
 oracle's independent one accept exactly the same inputs; an accepted one-clock
 netlist is lowered as the levelisation restated from it predicts, and the
-oracle simulates it as the pure-Python evaluator and the Einsum cascade do."""
+oracle simulates it as the pure-Python evaluator and the Einsum cascade do; and
+every accepted netlist's lowering, decoded back into a netlist, simulates like
+it (with and without operator fusion)."""
 import struct
 
 import numpy as np
@@ -67,6 +69,19 @@ def _same_as_pyeval(b: bytes, nl: synth.Netlist, rng, n_inst: int = 2, cycles: i
     assert [int(x) for x in sim.vals[0]] == cs.v
 
 
+def _lowering_simulates_alike(b: bytes, nl: synth.Netlist, fuse: bool, seed: int, n_inst: int = 2):
+    low, user2sig = rt.rteaal_design_lowered_netlist(b, nl.n_signals, fuse)
+    keep = user2sig != 0xFFFFFFFF
+    native, lowered = oracle.OracleSim(b, n_inst), oracle.OracleSim(low, n_inst)
+    xs = synth.xorshift_seeds(seed, nl.n_inputs, n_inst)
+    xa, xb = xs.copy(), xs.copy()
+    for cycles, reset in [(1, True), (5, False), (1, True), (3, False)]:
+        native.step(cycles, reset=reset, mode=oracle.STIM_XORSHIFT, xs=xa)
+        lowered.step(cycles, reset=reset, mode=oracle.STIM_XORSHIFT, xs=xb)
+        assert np.array_equal(native.vals[:, keep], lowered.vals[:, user2sig[keep]])
+        assert np.array_equal(native.mems[:, :native.mem_total], lowered.mems[:, :native.mem_total])
+
+
 def test_corrupted_netlists():
     rtbuild.build()
     bases = _bases()
@@ -89,6 +104,8 @@ def test_corrupted_netlists():
         accepted += lib_ok
         if lib_ok:
             nl = synth.Netlist.from_bytes(b)
+            for fuse in (False, True):
+                _lowering_simulates_alike(b, nl, fuse, it)
             if not nl.n_domains:                    # the restatements have no clock domains
                 check(nl)
                 _same_as_pyeval(b, nl, rng)
