@@ -192,6 +192,14 @@ int rteaal_design_single_clock(const void *netlist, size_t nbytes, void *out, si
  * Errors: E_INVALID, E_FORMAT (as rteaal_design_load). */
 int rteaal_design_lowered_netlist(const void *netlist, size_t nbytes, const rteaal_load_opts *opts, void *out,
                                   size_t capacity, size_t *out_bytes, uint32_t *user2sig, uint64_t n_user);
+/* The compact layout of the lowered design (host only): refs (caller-owned,
+ * n_rows = the lowered design's row count, i.e. the signal count of
+ * rteaal_design_lowered_netlist, whose signal ids index it) receives every
+ * row's reference, width class k << 30 | per-lane byte offset (layout in the
+ * notes at the top of this file).  opts nullable (only fuse_mux_chains is
+ * read).  Errors: E_INVALID (null argument, wrong n_rows), E_FORMAT. */
+int rteaal_design_rows(const void *netlist, size_t nbytes, const rteaal_load_opts *opts, uint32_t *refs,
+                       uint64_t n_rows);
 /* Which signals hold a row of the state: present[i] = 1 for signal i that can
  * be read, written and probed, 0 for a mux absorbed by operator fusion.
  * present: host array of n_signals bytes (caller-owned); n_signals must equal

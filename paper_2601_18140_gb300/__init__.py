@@ -108,7 +108,7 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
            "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize",
            "rteaal_design_lower", "rteaal_design_specialize_host", "rteaal_design_single_clock",
-           "rteaal_design_lowered_netlist"]
+           "rteaal_design_lowered_netlist", "rteaal_design_rows"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -131,6 +131,7 @@ def lib() -> ctypes.CDLL:
                                                     ctypes.POINTER(_U64)]
         L.rteaal_design_lowered_netlist.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
                                                     _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _P, _U64]
+        L.rteaal_design_rows.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts), _P, _U64]
         L.rteaal_design_single_clock.argtypes = [ctypes.c_char_p, ctypes.c_size_t, _P, ctypes.c_size_t,
                                                  ctypes.POINTER(ctypes.c_size_t), _P, _U64]
         L.rteaal_design_lower.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
@@ -285,6 +286,17 @@ def rteaal_design_lowered_netlist(netlist: bytes, n_signals: int,
     _check(lib().rteaal_design_lowered_netlist(netlist, len(netlist), ctypes.byref(opts), out, n.value,
                                                ctypes.byref(n), user2sig.ctypes.data, n_signals))
     return out.raw[:n.value], user2sig
+
+
+def rteaal_design_rows(netlist: bytes, n_rows: int, fuse_mux_chains: bool = False) -> np.ndarray:
+    """Row reference (width class << 30 | per-lane byte offset) of every row of the
+    lowered design, indexed like the signals of rteaal_design_lowered_netlist."""
+    opts = rteaal_load_opts()
+    opts.device = -1
+    opts.fuse_mux_chains = int(bool(fuse_mux_chains))
+    refs = np.zeros(n_rows, np.uint32)
+    _check(lib().rteaal_design_rows(netlist, len(netlist), ctypes.byref(opts), refs.ctypes.data, n_rows))
+    return refs
 
 
 def rteaal_design_specialize_host(netlist: bytes, fuse_mux_chains: bool = False) -> dict:

@@ -688,6 +688,22 @@ RT_EXPORT int rteaal_design_lowered_netlist(const void* netlist, size_t nbytes, 
   });
 }
 
+RT_EXPORT int rteaal_design_rows(const void* netlist, size_t nbytes, const rteaal_load_opts* opts, uint32_t* refs,
+                                 uint64_t n_rows) {
+  return guarded([&] {
+    require(netlist && refs, "rteaal_design_rows: null argument");
+    Netlist nl;
+    std::string err;
+    if (!parse_netlist(netlist, nbytes, nl, err)) throw Error(RTEAAL_E_FORMAT, err);
+    std::vector<uint32_t> user2x;
+    const Netlist nlx = lower_clock_domains(nl, user2x);
+    Lowered L;
+    lower_netlist(nlx, L, opts && opts->fuse_mux_chains);
+    require(n_rows == L.n_slots, "rteaal_design_rows: n_rows differs from the lowered design's row count");
+    std::copy(L.slot_ref.begin(), L.slot_ref.end(), refs);
+  });
+}
+
 RT_EXPORT int rteaal_design_single_clock(const void* netlist, size_t nbytes, void* out, size_t capacity,
                                          size_t* out_bytes, uint32_t* user2x, uint64_t n_user) {
   return guarded([&] {

@@ -135,3 +135,27 @@ def test_edge_copies_and_degenerate_designs():
     b = Builder()
     b.input(1)
     roundtrip(b.build(), n=3)
+
+
+@pytest.mark.parametrize("fuse", [False, True])
+def test_compact_layout(fuse):
+    """Every row is stored at its width class (1, 2, 4 or 8 bytes per lane for
+    widths up to 8, 16, 32, 64); the class-3 rows come first, then 2, 1, 0; inside
+    a class the rows follow their ids (pool rows before op rows) with no gap, so
+    the rows tile [0, state bytes per lane) exactly."""
+    nl = synth.generate(DesignSpec(n_ops=4000, n_regs=150, depth=16, n_inputs=4, seed=72,
+                                   input_widths=(8, 32, 1, 64), mux_chain_frac=0.7, n_mems=2, mem_words=8))
+    low, _ = rt.rteaal_design_lowered_netlist(nl.to_bytes(), nl.n_signals, fuse_mux_chains=fuse)
+    x = synth.Netlist.from_bytes(low)
+    refs = rt.rteaal_design_rows(nl.to_bytes(), x.n_signals, fuse_mux_chains=fuse).astype(np.int64)
+    k, off = refs >> 30, refs & ((1 << 30) - 1)
+    w = x.signal_widths().astype(np.int64)
+    assert np.array_equal(k, np.select([w <= 8, w <= 16, w <= 32], [0, 1, 2], 3))
+    size = np.int64(1) << k
+    end = 0
+    for cls in (3, 2, 1, 0):
+        ids = np.flatnonzero(k == cls)                       # in id order
+        assert np.array_equal(off[ids], end + size[ids].cumsum() - size[ids])
+        end += int(size[ids].sum())
+    info, _ = rt.rteaal_design_lower(nl.to_bytes(), fuse_mux_chains=fuse)
+    assert end == info["state_bytes_per_lane"]
