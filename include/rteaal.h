@@ -153,6 +153,21 @@ int rteaal_design_load(const void *netlist, size_t nbytes, const rteaal_load_opt
  * of Sec. 4.2, (layer, opcode, width) groups, compact state size, device bytes
  * of the lowered operand lists).  out: caller-owned.  Errors: E_INVALID. */
 int rteaal_design_info(const rteaal_design *design, rteaal_design_stats *out);
+/* Which signals hold a row of the state: present[i] = 1 for signal i that can
+ * be read, written and probed, 0 for a mux absorbed by operator fusion.
+ * present: host array of n_signals bytes (caller-owned); n_signals must equal
+ * the design's signal count.  Errors: E_INVALID. */
+int rteaal_design_signals(const rteaal_design *design, uint8_t *present, uint64_t n_signals);
+/* Generate and compile the design-specialised kernel (RTEAAL_KERNEL_SPECIALIZED)
+ * now instead of at the first configure that asks for it; *compile_us
+ * (nullable) receives the generation + compile time of the first call (the
+ * kernel is kept with the design).  Errors: E_UNSUPPORTED (too many ops),
+ * E_CUDA (compile or load failure; the message holds the compiler log). */
+int rteaal_design_specialize(rteaal_design *design, uint64_t *compile_us);
+/* ---------------------------------------------------------------- host-only inspection
+ * The calls below (up to rteaal_design_specialize_host) parse and lower a netlist
+ * on the host, touch no device and keep nothing: they expose what the kernels will
+ * execute so that it can be checked without a GPU. */
 /* The lowering alone, on the host (no device is touched, nothing is kept):
  * parse, lower clock domains, fuse (opts->fuse_mux_chains), levelise (Sec. 4.2:
  * an op's layer is one more than the deepest of its operands; inputs,
@@ -200,17 +215,6 @@ int rteaal_design_lowered_netlist(const void *netlist, size_t nbytes, const rtea
  * read).  Errors: E_INVALID (null argument, wrong n_rows), E_FORMAT. */
 int rteaal_design_rows(const void *netlist, size_t nbytes, const rteaal_load_opts *opts, uint32_t *refs,
                        uint64_t n_rows);
-/* Which signals hold a row of the state: present[i] = 1 for signal i that can
- * be read, written and probed, 0 for a mux absorbed by operator fusion.
- * present: host array of n_signals bytes (caller-owned); n_signals must equal
- * the design's signal count.  Errors: E_INVALID. */
-int rteaal_design_signals(const rteaal_design *design, uint8_t *present, uint64_t n_signals);
-/* Generate and compile the design-specialised kernel (RTEAAL_KERNEL_SPECIALIZED)
- * now instead of at the first configure that asks for it; *compile_us
- * (nullable) receives the generation + compile time of the first call (the
- * kernel is kept with the design).  Errors: E_UNSUPPORTED (too many ops),
- * E_CUDA (compile or load failure; the message holds the compiler log). */
-int rteaal_design_specialize(rteaal_design *design, uint64_t *compile_us);
 /* The design-specialised kernel's generation and NVRTC compile for sm_103a
  * alone, on the host (no device is touched, nothing is kept): checks that a
  * netlist's straight-line kernel (Sec. 4.4, unrolled S rank and inlined
