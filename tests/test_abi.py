@@ -1,6 +1,6 @@
 """Host-side checks of the C ABI (no GPU needed): the library loads, exports
-every function include/rteaal.h declares, and rejects malformed netlists
-before touching the device."""
+every function include/rteaal.h declares, rejects malformed netlists before
+touching the device, and a plain C program can include the header and link."""
 import ctypes
 import os
 import re
@@ -70,3 +70,28 @@ def test_fast_division_formula():
         assert m < 2**32
         q = ((((ns.astype(object) * m) >> 32) + ns.astype(object)) >> l)
         assert (q == ns.astype(object) // d).all(), d
+
+
+def test_header_is_plain_c_and_links(L, tmp_path):
+    """A C11 program includes the header (no C++ constructs, no warnings under
+    -pedantic), links against the library and calls a host-only entry point."""
+    import subprocess
+    src = tmp_path / "consumer.c"
+    src.write_text(
+        '#include "rteaal.h"\n'
+        '#include <stdio.h>\n'
+        'int main(void) {\n'
+        '  rteaal_design_stats st;\n'
+        '  const char bad[4] = {0, 0, 0, 0};\n'
+        '  int rc = rteaal_design_lower(bad, sizeof bad, NULL, &st, NULL, 0);\n'
+        '  printf("%d %s\\n", rc, rteaal_last_error());\n'
+        '  return rc == RTEAAL_E_FORMAT ? 0 : 1;\n'
+        '}\n')
+    libdir = os.path.dirname(rt.LIB_PATH)
+    exe = tmp_path / "consumer"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), "-o", str(exe), str(src), "-L", libdir, "-lrteaal",
+                    "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.startswith("%d " % rt.RTEAAL_E_FORMAT)
