@@ -45,7 +45,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     # the persistent-kernel variants are instantiated in their own units so that
     # they compile in parallel with the runtime
     for f in ["rteaal.cu", "variants_v8.cu", "variants_v4.cu", "variants_v2_v1.cu", "variants_act.cu",
-              "lower.cpp", "specialize.cpp"]:
+              "lower.cpp", "inspect.cpp", "specialize.cpp"]:
         src = os.path.join(CSRC, f)
         obj = os.path.join(BUILD, f + ".o")
         cmd = [nvcc] + ARCH + common + ["-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
