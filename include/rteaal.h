@@ -165,7 +165,7 @@ int rteaal_design_signals(const rteaal_design *design, uint8_t *present, uint64_
  * E_CUDA (compile or load failure; the message holds the compiler log). */
 int rteaal_design_specialize(rteaal_design *design, uint64_t *compile_us);
 /* ---------------------------------------------------------------- host-only inspection
- * The calls below (up to rteaal_design_specialize_host) parse and lower a netlist
+ * The calls below (up to rteaal_design_specialized_source) parse and lower a netlist
  * on the host, touch no device and keep nothing: they expose what the kernels will
  * execute so that it can be checked without a GPU. */
 /* The lowering alone, on the host (no device is touched, nothing is kept):
@@ -224,6 +224,14 @@ int rteaal_design_rows(const void *netlist, size_t nbytes, const rteaal_load_opt
  * many ops), E_CUDA (compile failure; the message holds the compiler log). */
 int rteaal_design_specialize_host(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
                                   uint64_t *cubin_bytes, uint64_t *compile_us);
+/* The design-specialised kernel's CUDA source text (the kernel rteaal_spec:
+ * one thread per lane, every signal a local, one statement per op), as
+ * generated for the lowered design; host only.  out (nullable, caller-owned,
+ * capacity bytes, not NUL-terminated) receives the text and *out_bytes its
+ * length (call with out = NULL to size the buffer).  opts nullable (only
+ * fuse_mux_chains is read).  Errors: E_INVALID, E_FORMAT. */
+int rteaal_design_specialized_source(const void *netlist, size_t nbytes, const rteaal_load_opts *opts, char *out,
+                                     size_t capacity, size_t *out_bytes);
 /* Returns E_BUSY (and frees nothing) while sims created from it are alive. */
 int rteaal_design_free(rteaal_design *design);
 

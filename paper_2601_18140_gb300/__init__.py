@@ -108,7 +108,8 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
            "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize",
            "rteaal_design_lower", "rteaal_design_specialize_host", "rteaal_design_single_clock",
-           "rteaal_design_lowered_netlist", "rteaal_design_rows"]
+           "rteaal_design_lowered_netlist", "rteaal_design_rows",
+           "rteaal_design_specialized_source"]
 STATIC_MAX_LANES = 65536
 
 _lib = None
@@ -131,6 +132,9 @@ def lib() -> ctypes.CDLL:
                                                     ctypes.POINTER(_U64)]
         L.rteaal_design_lowered_netlist.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
                                                     _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _P, _U64]
+        L.rteaal_design_specialized_source.argtypes = [ctypes.c_char_p, ctypes.c_size_t,
+                                                       ctypes.POINTER(rteaal_load_opts), _P, ctypes.c_size_t,
+                                                       ctypes.POINTER(ctypes.c_size_t)]
         L.rteaal_design_rows.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts), _P, _U64]
         L.rteaal_design_single_clock.argtypes = [ctypes.c_char_p, ctypes.c_size_t, _P, ctypes.c_size_t,
                                                  ctypes.POINTER(ctypes.c_size_t), _P, _U64]
@@ -297,6 +301,20 @@ def rteaal_design_rows(netlist: bytes, n_rows: int, fuse_mux_chains: bool = Fals
     refs = np.zeros(n_rows, np.uint32)
     _check(lib().rteaal_design_rows(netlist, len(netlist), ctypes.byref(opts), refs.ctypes.data, n_rows))
     return refs
+
+
+def rteaal_design_specialized_source(netlist: bytes, fuse_mux_chains: bool = False) -> str:
+    """The design-specialised kernel's generated CUDA source (host only)."""
+    opts = rteaal_load_opts()
+    opts.device = -1
+    opts.fuse_mux_chains = int(bool(fuse_mux_chains))
+    n = ctypes.c_size_t()
+    _check(lib().rteaal_design_specialized_source(netlist, len(netlist), ctypes.byref(opts), None, 0,
+                                                  ctypes.byref(n)))
+    out = ctypes.create_string_buffer(max(n.value, 1))
+    _check(lib().rteaal_design_specialized_source(netlist, len(netlist), ctypes.byref(opts), out, n.value,
+                                                  ctypes.byref(n)))
+    return out.raw[:n.value].decode()
 
 
 def rteaal_design_specialize_host(netlist: bytes, fuse_mux_chains: bool = False) -> dict:

@@ -707,6 +707,26 @@ RT_EXPORT int rteaal_design_specialize(rteaal_design* d, uint64_t* compile_us) {
   });
 }
 
+RT_EXPORT int rteaal_design_specialized_source(const void* netlist, size_t nbytes, const rteaal_load_opts* opts,
+                                               char* out, size_t capacity, size_t* out_bytes) {
+  return guarded([&] {
+    require(netlist && out_bytes, "rteaal_design_specialized_source: null argument");
+    Netlist nl;
+    std::string err;
+    if (!parse_netlist(netlist, nbytes, nl, err)) throw Error(RTEAAL_E_FORMAT, err);
+    std::vector<uint32_t> user2x;
+    const Netlist nlx = lower_clock_domains(nl, user2x);
+    Lowered L;
+    lower_netlist(nlx, L, opts && opts->fuse_mux_chains);
+    const std::string src = specialized_source(nlx, L);
+    *out_bytes = src.size();
+    if (out) {
+      require(capacity >= src.size(), "rteaal_design_specialized_source: output buffer too small");
+      std::memcpy(out, src.data(), src.size());
+    }
+  });
+}
+
 RT_EXPORT int rteaal_design_specialize_host(const void* netlist, size_t nbytes, const rteaal_load_opts* opts,
                                             uint64_t* cubin_bytes, uint64_t* compile_us) {
   return guarded([&] {
