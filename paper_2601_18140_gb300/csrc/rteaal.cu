@@ -549,12 +549,10 @@ namespace {
 
 constexpr int kStreamConsumerWarps = 16;
 
-
 constexpr uint32_t kSpecMaxOps = 16384;
 constexpr uint32_t kSpecThreads = 128;
 constexpr uint32_t kSpecOptimizeOps = 4096;  // NVVM optimiser on up to this many ops
 
-// Generate, compile (NVRTC, sm_103a) and load the design-specialised kernel once.
 // Generate and compile (NVRTC, sm_103a) the design-specialised kernel of a
 // lowered netlist; host only.
 std::vector<char> build_specialized(const Netlist& nlx, const Lowered& L) {
@@ -568,6 +566,7 @@ std::vector<char> build_specialized(const Netlist& nlx, const Lowered& L) {
   return cubin;
 }
 
+// Generate, compile and load the design-specialised kernel once per design.
 void ensure_specialized(rteaal_design* d) {
   std::lock_guard<std::mutex> g(d->spec_mu);
   if (d->spec_kernel) return;
