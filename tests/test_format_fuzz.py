@@ -6,7 +6,8 @@ oracle's independent one accept exactly the same inputs; an accepted one-clock
 netlist is lowered as the levelisation restated from it predicts, and the
 oracle simulates it as the pure-Python evaluator and the Einsum cascade do; and
 every accepted netlist's lowering, decoded back into a netlist, simulates like
-it (with and without operator fusion)."""
+it (with and without operator fusion); the other host-only calls accept and
+refuse the same inputs, never crashing."""
 import struct
 
 import numpy as np
@@ -102,8 +103,20 @@ def test_corrupted_netlists():
             orc_ok = False
         assert lib_ok == orc_ok, it
         accepted += lib_ok
+        if not lib_ok:                              # every host-only call refuses it alike
+            for call in (lambda: rt.rteaal_design_single_clock(b, 1), lambda: rt.rteaal_design_rows(b, 1),
+                         lambda: rt.rteaal_design_specialized_source(b)):
+                try:
+                    call()
+                    raise AssertionError("accepted by one host-only call only: %d" % it)
+                except rt.RteaalError as e:
+                    assert e.code == rt.RTEAAL_E_FORMAT, (it, str(e))
         if lib_ok:
             nl = synth.Netlist.from_bytes(b)
+            low, _ = rt.rteaal_design_lowered_netlist(b, nl.n_signals)
+            rt.rteaal_design_rows(b, synth.Netlist.from_bytes(low).n_signals)
+            assert "rteaal_spec" in rt.rteaal_design_specialized_source(b)
+            rt.rteaal_design_single_clock(b, nl.n_signals)
             for fuse in (False, True):
                 _lowering_simulates_alike(b, nl, fuse, it)
             if not nl.n_domains:                    # the restatements have no clock domains
