@@ -41,7 +41,6 @@ void fill_stats(const Netlist& nl, const Lowered& L, uint64_t metadata_bytes, rt
   o->n_fused = L.n_fused;
 }
 
-
 }  // namespace rteaal
 
 using namespace rteaal;
