@@ -1,0 +1,177 @@
+// Test-only host harness for the LAYER form: the library's own device functions
+// (kernels.cuh: stim_items, eval_layer, commit_items) and lowering (lower.cpp),
+// compiled with the host compiler, run phase by phase -- stimulus, every layer,
+// clock edge -- with each phase called once per thread index.  Within a phase
+// no item reads what another item writes (ops of one layer read lower layers
+// only; the edge reads op rows and writes register rows), so running the
+// thread indices one after another gives the result of any GPU interleaving.
+// The CUDA built-ins those functions use are stood in for below; the warp
+// votes and shuffles belong to activity-aware evaluation only, never used here.
+#include <cuda_runtime.h>  // vector types (uint4, ...) and qualifiers for a host compile
+
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#ifndef __noinline__
+#define __noinline__
+#endif
+
+static uint3 threadIdx, blockIdx, blockDim, gridDim;
+
+template <typename T>
+static inline T __ldg(const T* p) {
+  return *p;
+}
+// byte n of the result = byte (selector nibble n & 7) of the 8-byte value {y, x}
+static inline unsigned __byte_perm(unsigned x, unsigned y, unsigned s) {
+  const unsigned long long v = ((unsigned long long)y << 32) | x;
+  unsigned r = 0;
+  for (int n = 0; n < 4; n++) r |= (unsigned)((v >> (8 * ((s >> (4 * n)) & 7u))) & 0xFFu) << (8 * n);
+  return r;
+}
+static inline int __popc(unsigned x) { return __builtin_popcount(x); }
+static inline int __popcll(unsigned long long x) { return __builtin_popcountll(x); }
+static inline int __ffs(int x) { return __builtin_ffs(x); }
+static inline unsigned __ballot_sync(unsigned, int) { abort(); }
+template <typename T>
+static inline T __shfl_sync(unsigned, T, int, int = 32) {
+  abort();
+}
+static inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
+  const unsigned long long o = *p;
+  *p += v;
+  return o;
+}
+
+#include "kernels.cuh"
+#include "lower.hpp"
+
+using namespace rteaal;
+
+namespace {
+
+struct Emu {
+  Netlist nl, nlx;
+  Lowered L;
+  std::vector<uint32_t> user2x;
+  DDesign d{};
+  DSim s{};
+  uint8_t* state = nullptr;
+  std::vector<uint64_t> mem, xs;
+  uint32_t np = 0, err = 0;
+};
+
+template <class T>
+const T* ptr(const std::vector<T>& v) {
+  static const uint64_t zero[4] = {0, 0, 0, 0};
+  return v.empty() ? reinterpret_cast<const T*>(zero) : v.data();
+}
+
+// Granlund & Montgomery, PLDI 1994, Fig. 4.1 (the kernels' division by a constant)
+FastDiv fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) l++;
+  return FastDiv{d, (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1), l};
+}
+
+template <int V>
+void cycles(Emu& e, uint32_t nthreads, uint32_t ncyc) {
+  const FastDiv tpo = fastdiv(e.np / V);
+  for (uint32_t c = 0; c < ncyc; c++) {
+    if (e.s.stim_mode)
+      for (uint32_t t = 0; t < nthreads; t++) stim_items<V>(e.d, e.s, make_space<V>(tpo, 0u, t, nthreads), c);
+    for (uint32_t l = 0; l < e.d.n_layers; l++)
+      for (uint32_t t = 0; t < nthreads; t++) eval_layer<V, 1>(e.d, e.s, l, make_space<V>(tpo, 0u, t, nthreads), c);
+    if (e.d.n_regs + e.d.n_mems)
+      for (uint32_t t = 0; t < nthreads; t++) commit_items<V>(e.d, e.s, make_space<V>(tpo, 0u, t, nthreads), c);
+  }
+}
+
+}  // namespace
+
+// np: lanes (a power of two, every lane an instance); xs_init: [n_inputs][np].
+extern "C" void* emu_create(const void* bytes, size_t nbytes, int fuse, uint32_t np, const uint64_t* xs_init) {
+  Emu* e = new Emu();
+  std::string err;
+  if (!parse_netlist(bytes, nbytes, e->nl, err)) {
+    delete e;
+    return nullptr;
+  }
+  e->nlx = lower_clock_domains(e->nl, e->user2x);
+  lower_netlist(e->nlx, e->L, fuse != 0);
+  const Lowered& L = e->L;
+  e->np = np;
+  const size_t sbytes = (L.lane_bytes * np + 63) / 64 * 64 + 64;
+  e->state = static_cast<uint8_t*>(aligned_alloc(64, sbytes));
+  std::memset(e->state, 0, sbytes);
+  e->mem.assign(L.mem_words_total * np + 1, 0);
+  e->xs.assign(xs_init, xs_init + (size_t)L.in_width.size() * np);
+  DDesign& d = e->d;
+  d.meta = reinterpret_cast<const uint4*>(ptr(L.meta));
+  d.dst = ptr(L.dst_ref);
+  d.ext = ptr(L.ext_args);
+  d.layer_off = ptr(L.layer_off);
+  d.layer_ext = ptr(L.layer_ext);
+  d.reg_src = ptr(L.reg_src);
+  d.reg_ref = ptr(L.reg_ref);
+  d.reg_w = ptr(L.reg_width);
+  d.reg_init = ptr(L.reg_init);
+  d.wport = reinterpret_cast<const uint4*>(ptr(L.wport));
+  d.mem_info = reinterpret_cast<const uint4*>(ptr(L.mem_info));
+  d.in_w = ptr(L.in_width);
+  d.in_ref = ptr(L.in_ref);
+  d.n_layers = (uint32_t)L.layer_off.size() - 1;
+  d.n_regs = (uint32_t)L.reg_src.size();
+  d.n_inputs = (uint32_t)L.in_width.size();
+  d.n_mems = (uint32_t)(L.mem_info.size() / 4 - 1);
+  d.op_base = L.op_base;
+  d.reg_base = L.reg_base;
+  for (size_t c = 0; c < L.const_value.size(); c++)      // constants, as at sim creation
+    for (uint32_t lane = 0; lane < np; lane++) st1(e->state, L.const_ref[c], np, lane, L.const_value[c]);
+  DSim& s = e->s;
+  s.state = e->state;
+  s.mem = e->mem.data();
+  s.xs = e->xs.empty() ? nullptr : e->xs.data();
+  s.n_pad = np;
+  s.n_user = np;
+  s.err = &e->err;
+  return e;
+}
+
+// One step of ncyc cycles at V lanes per item with nthreads thread indices per
+// phase; budget: [np] cycles per lane (nullable: every lane runs ncyc).
+extern "C" int emu_step(void* p, uint32_t V, uint32_t nthreads, uint32_t ncyc, const uint32_t* budget, int reset) {
+  Emu& e = *static_cast<Emu*>(p);
+  e.s.budget = budget;
+  e.s.uniform = ncyc;
+  e.s.reset = reset;
+  e.s.stim_mode = e.L.in_width.empty() ? 0 : 1;   // xorshift64 stimulus
+  switch (V) {
+    case 1: cycles<1>(e, nthreads, ncyc); break;
+    case 2: cycles<2>(e, nthreads, ncyc); break;
+    case 4: cycles<4>(e, nthreads, ncyc); break;
+    case 8: cycles<8>(e, nthreads, ncyc); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+// Values of a caller signal in every lane (-1: fused away).
+extern "C" int emu_read(void* p, uint32_t sig, uint64_t* out) {
+  Emu& e = *static_cast<Emu*>(p);
+  const uint32_t slot = e.L.sig2slot[e.user2x[sig]];
+  if (slot == 0xFFFFFFFFu) return -1;
+  for (uint32_t lane = 0; lane < e.np; lane++) out[lane] = ld1(e.state, e.L.slot_ref[slot], e.np, lane);
+  return 0;
+}
+
+extern "C" const uint64_t* emu_mem(void* p) { return static_cast<Emu*>(p)->mem.data(); }
+extern "C" const uint64_t* emu_xs(void* p) { return static_cast<Emu*>(p)->xs.data(); }
+
+extern "C" void emu_free(void* p) {
+  Emu* e = static_cast<Emu*>(p);
+  free(e->state);
+  delete e;
+}

@@ -1,0 +1,186 @@
+"""The data-driven kernels' device code checked on the host (no GPU): the
+library's own kernels.cuh (operand gathers of 1, 2, 4 or 8 packed lanes per
+row class, the 32-bit narrow path, side-array operand lists, stimulus, clock
+edge and write ports) and lower.cpp are compiled with the host compiler into
+tests/layer_form_harness.cpp, which runs the LAYER form phase by phase with
+every thread index of a phase called in turn.  Signals, memory words and
+stimulus states must equal the oracle's for every lanes-per-thread width and
+for thread counts equal to, above and below the number of lane chunks (the
+fixed and the generic work mapping).  Planted mistakes in a temporary copy of
+kernels.cuh must fail it.  The library runs these functions only on the GPU;
+this checks their arithmetic and indexing without one."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2601_18140_gb300 as rt
+import synth
+from synth import Builder, DesignSpec
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(rt.__file__), "csrc")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+CUDA_INCLUDE = "/usr/local/cuda/include"
+NP = 32                     # lanes (a power of two, as the library pads small batches)
+P = ctypes.c_void_p
+
+
+def build_harness(csrc: str, out_dir) -> ctypes.CDLL:
+    so = os.path.join(str(out_dir), "harness.so")
+    subprocess.run(["g++", "-std=c++17", "-O1", "-w", "-shared", "-fPIC", "-I", CUDA_INCLUDE, "-I", INCLUDE,
+                    "-I", csrc, "-o", so, os.path.join(HERE, "layer_form_harness.cpp"),
+                    os.path.join(csrc, "lower.cpp")], check=True)
+    lib = ctypes.CDLL(so)
+    lib.emu_create.restype = P
+    lib.emu_create.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, P]
+    lib.emu_step.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int]
+    lib.emu_read.argtypes = [P, ctypes.c_uint32, P]
+    lib.emu_mem.restype = P
+    lib.emu_mem.argtypes = [P]
+    lib.emu_xs.restype = P
+    lib.emu_xs.argtypes = [P]
+    lib.emu_free.argtypes = [P]
+    return lib
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    if not os.path.isdir(CUDA_INCLUDE):
+        pytest.skip("CUDA headers not found")
+    return build_harness(CSRC, tmp_path_factory.mktemp("harness"))
+
+
+def designs() -> dict:
+    out = {}
+    out["random+mem"] = (synth.generate(DesignSpec(n_ops=400, n_regs=30, depth=7, n_inputs=4, seed=3, n_mems=2,
+                                                   mem_words=8, mem_write_ports=2,
+                                                   input_widths=(8, 32, 1, 64))), False)
+    chains = synth.generate(DesignSpec(n_ops=500, n_regs=30, depth=8, n_inputs=4, seed=71,
+                                       input_widths=(8, 32, 1, 64), mux_chain_frac=0.7))
+    out["chains"] = (chains, False)
+    out["chains-fused"] = (chains, True)
+    b = Builder()                                            # variadic folds, MUXCHAIN, ports
+    ins = [b.input(w) for w in (64, 32, 8, 1, 1, 5)]
+    m = b.mem(16, width=40)
+    regs = [b.reg(w) for w in (64, 32, 40, 8)]
+    ops = [b.op("ADD", 64, ins[0], ins[1], ins[2], regs[0], regs[1]),
+           b.op("XOR", 32, ins[1], ins[2], regs[1], regs[3]),
+           b.op("MUL", 64, ins[2], ins[5], regs[3], ins[2]),
+           b.op("MUXCHAIN", 64, ins[3], ins[0], ins[4], regs[0], regs[3], ins[1], regs[2]),
+           b.op("XORR", 1, regs[0]),
+           b.op("MEMRD", 40, ins[5], p0=m)]
+    t = b.op("CAT", 64, ops[5], b.op("BITS", 24, ops[0], p0=30, p1=7), p0=24)
+    b.write_port(m, ins[3], ins[2], ops[0])
+    b.write_port(m, ops[4], ins[5], ops[2])
+    b.connect(regs[0], t)
+    b.connect(regs[1], b.op("DSHR", 32, ops[1], ins[5]))
+    b.connect(regs[2], ops[3])
+    b.connect(regs[3], b.op("SUB", 8, ins[2], regs[3]))
+    b.clock(regs[1], b.domain(4, 1))                         # and two clock domains
+    b.clock(regs[3], b.domain(2, 0))
+    out["wide+domains"] = (b.build(), False)
+    out["counter+lfsr"] = (synth.generate(synth.spec_tiny(0)), False)
+    b = Builder()                                            # no ops: edge copies only
+    i0, k = b.input(8), b.const(16, 0xBEEF)
+    r0, r1, r2 = b.reg(8, init=3), b.reg(16), b.reg(8)
+    b.connect(r0, i0)
+    b.connect(r1, k)
+    b.connect(r2, r0)
+    out["copies-only"] = (b.build(), False)
+    return out
+
+
+DESIGNS = designs()
+
+
+def run_and_compare(lib, nl: synth.Netlist, fuse: bool, V: int, nthreads: int, seed: int = 1) -> None:
+    nb = nl.to_bytes()
+    xs = np.ascontiguousarray(synth.xorshift_seeds(seed, nl.n_inputs, NP))
+    e = lib.emu_create(nb, len(nb), int(fuse), NP, xs.ctypes.data if nl.n_inputs else None)
+    assert e
+    orc = oracle.OracleSim(nb, NP)
+    xo = xs.copy()
+    rng = np.random.default_rng(seed)
+    out = np.zeros(NP, np.uint64)
+    try:
+        for cycles, reset in [(1, True), (20, False), (None, False), (1, True), (7, False)]:
+            budget = rng.integers(0, 12, NP).astype(np.uint32) if cycles is None else None
+            ncyc = int(budget.max()) if budget is not None else cycles
+            lib.emu_step(e, V, nthreads, ncyc, None if budget is None else budget.ctypes.data, int(reset))
+            orc.step(budget if budget is not None else cycles, reset=reset, mode=oracle.STIM_XORSHIFT, xs=xo)
+            for sig in range(nl.n_signals):
+                if lib.emu_read(e, sig, out.ctypes.data) == 0:
+                    assert np.array_equal(out, orc.vals[:, sig]), (sig, V, nthreads)
+            words = orc.mem_total
+            mem = np.ctypeslib.as_array(ctypes.cast(lib.emu_mem(e), ctypes.POINTER(ctypes.c_uint64)),
+                                        (max(words, 1) * NP,))
+            assert np.array_equal(mem[:words * NP].reshape(words, NP).T, orc.mems[:, :words])
+            if nl.n_inputs:
+                xk = np.ctypeslib.as_array(ctypes.cast(lib.emu_xs(e), ctypes.POINTER(ctypes.c_uint64)),
+                                           (nl.n_inputs * NP,))
+                assert np.array_equal(xk.reshape(nl.n_inputs, NP), xo)
+    finally:
+        lib.emu_free(e)
+
+
+@pytest.mark.parametrize("mapping", ["one thread per chunk", "more threads", "fewer threads"])
+@pytest.mark.parametrize("V", [1, 2, 4, 8])
+@pytest.mark.parametrize("name", list(DESIGNS))
+def test_layer_form_matches_oracle(harness, name, V, mapping):
+    nl, fuse = DESIGNS[name]
+    chunks = NP // V
+    nthreads = {"one thread per chunk": chunks, "more threads": 3 * chunks + 5,
+                "fewer threads": max(1, chunks // 3)}[mapping]
+    run_and_compare(harness, nl, fuse, V, nthreads)
+
+
+KERNEL_MUTANTS = [
+    ("narrow SUB operands swapped",
+     "case OP_SUB: RT_LANES(a.x[v] - b.x[v]); break;\n    case OP_MUL: RT_LANES(a.x[v] * b.x[v] * (ar == 3 ? c.x[v] : 1u)); break;",
+     "case OP_SUB: RT_LANES(b.x[v] - a.x[v]); break;\n    case OP_MUL: RT_LANES(a.x[v] * b.x[v] * (ar == 3 ? c.x[v] : 1u)); break;"),
+    ("8-lane 1-byte gather: upper lanes from the lower word",
+     "r.x[4 + v] = __byte_perm(t.y, 0u, 0x4440u + v);", "r.x[4 + v] = __byte_perm(t.x, 0u, 0x4440u + v);"),
+    ("4-lane 2-byte store: lanes swapped within a word",
+     "(uint32_t)(r.x[0] | (r.x[1] << 16)), (uint32_t)(r.x[2] | (r.x[3] << 16))",
+     "(uint32_t)(r.x[1] | (r.x[0] << 16)), (uint32_t)(r.x[2] | (r.x[3] << 16))"),
+    ("per-lane cycle budgets ignored",
+     "return s.budget ? cyc < __ldg(&s.budget[lane]) : (lane < s.n_user && cyc < s.uniform);",
+     "return lane < s.n_user && cyc < s.uniform;"),
+    ("mux chain: the last set selector wins",
+     "const bool take = (sel.x[v] & 1u) && !((done >> v) & 1u);", "const bool take = (sel.x[v] & 1u);"),
+    ("reset ignores init values",
+     "if (s.reset) {\n        const uint64_t init = __ldg(&d.reg_init[r]) & mk;",
+     "if (s.reset) {\n        const uint64_t init = 0;"),
+]
+
+
+def test_planted_kernel_mistakes_are_caught(tmp_path):
+    if not os.path.isdir(CUDA_INCLUDE):
+        pytest.skip("CUDA headers not found")
+    with open(os.path.join(CSRC, "kernels.cuh")) as f:
+        src = f.read()
+    for k, (name, old, new) in enumerate(KERNEL_MUTANTS):
+        assert src.count(old) == 1, "mutation site not found exactly once: " + name
+        d = tmp_path / ("m%d" % k)
+        d.mkdir()
+        for f in ["lower.hpp", "lower.cpp"]:
+            shutil.copy(os.path.join(CSRC, f), str(d / f))
+        (d / "kernels.cuh").write_text(src.replace(old, new))
+        lib = build_harness(str(d), d)
+        caught = False
+        for name_d in ["random+mem", "wide+domains", "chains-fused", "copies-only"]:
+            nl, fuse = DESIGNS[name_d]
+            for V in (4, 8):
+                try:
+                    run_and_compare(lib, nl, fuse, V, NP // V)
+                except AssertionError:
+                    caught = True
+                    break
+            if caught:
+                break
+        assert caught, "no design catches: " + name
