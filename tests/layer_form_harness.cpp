@@ -1,4 +1,4 @@
-// Test-only host harness for the LAYER form: the library's own device functions
+// Test-only host harness for the LAYER and TILE forms: the library's own device functions
 // (kernels.cuh: stim_items, eval_layer, commit_items) and lowering (lower.cpp),
 // compiled with the host compiler, run phase by phase -- stimulus, every layer,
 // clock edge -- with each phase called once per thread index.  Within a phase
@@ -76,16 +76,33 @@ FastDiv fastdiv(uint32_t d) {
   return FastDiv{d, (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1), l};
 }
 
+// tile_lanes = 0: the LAYER form (every phase spans all lanes); otherwise the
+// TILE form's mapping (each tile of lanes runs every phase with its own lane
+// base; tiles are independent, so one after another).  U: rows in flight per
+// thread (the unrolled variants).
+template <int V, int U>
+void cycles(Emu& e, uint32_t tile_lanes, uint32_t nthreads, uint32_t ncyc) {
+  const uint32_t span = tile_lanes ? tile_lanes : e.np;
+  const FastDiv tpo = fastdiv(span / V);
+  for (uint32_t base = 0; base < e.np; base += span)
+    for (uint32_t c = 0; c < ncyc; c++) {
+      if (e.s.stim_mode)
+        for (uint32_t t = 0; t < nthreads; t++) stim_items<V>(e.d, e.s, make_space<V>(tpo, base, t, nthreads), c);
+      for (uint32_t l = 0; l < e.d.n_layers; l++)
+        for (uint32_t t = 0; t < nthreads; t++)
+          eval_layer<V, U>(e.d, e.s, l, make_space<V>(tpo, base, t, nthreads), c);
+      if (e.d.n_regs + e.d.n_mems)
+        for (uint32_t t = 0; t < nthreads; t++) commit_items<V>(e.d, e.s, make_space<V>(tpo, base, t, nthreads), c);
+    }
+}
+
 template <int V>
-void cycles(Emu& e, uint32_t nthreads, uint32_t ncyc) {
-  const FastDiv tpo = fastdiv(e.np / V);
-  for (uint32_t c = 0; c < ncyc; c++) {
-    if (e.s.stim_mode)
-      for (uint32_t t = 0; t < nthreads; t++) stim_items<V>(e.d, e.s, make_space<V>(tpo, 0u, t, nthreads), c);
-    for (uint32_t l = 0; l < e.d.n_layers; l++)
-      for (uint32_t t = 0; t < nthreads; t++) eval_layer<V, 1>(e.d, e.s, l, make_space<V>(tpo, 0u, t, nthreads), c);
-    if (e.d.n_regs + e.d.n_mems)
-      for (uint32_t t = 0; t < nthreads; t++) commit_items<V>(e.d, e.s, make_space<V>(tpo, 0u, t, nthreads), c);
+int cycles_u(Emu& e, uint32_t U, uint32_t tile_lanes, uint32_t nthreads, uint32_t ncyc) {
+  switch (U) {
+    case 1: cycles<V, 1>(e, tile_lanes, nthreads, ncyc); return 0;
+    case 2: cycles<V, 2>(e, tile_lanes, nthreads, ncyc); return 0;
+    case 4: cycles<V, 4>(e, tile_lanes, nthreads, ncyc); return 0;
+    default: return -1;
   }
 }
 
@@ -140,22 +157,24 @@ extern "C" void* emu_create(const void* bytes, size_t nbytes, int fuse, uint32_t
   return e;
 }
 
-// One step of ncyc cycles at V lanes per item with nthreads thread indices per
-// phase; budget: [np] cycles per lane (nullable: every lane runs ncyc).
-extern "C" int emu_step(void* p, uint32_t V, uint32_t nthreads, uint32_t ncyc, const uint32_t* budget, int reset) {
+// One step of ncyc cycles at V lanes per item, U rows in flight, with nthreads
+// thread indices per phase over all lanes (tile_lanes = 0) or per tile of
+// tile_lanes lanes; budget: [np] cycles per lane (nullable: every lane runs ncyc).
+extern "C" int emu_step(void* p, uint32_t V, uint32_t U, uint32_t tile_lanes, uint32_t nthreads, uint32_t ncyc,
+                        const uint32_t* budget, int reset) {
   Emu& e = *static_cast<Emu*>(p);
   e.s.budget = budget;
   e.s.uniform = ncyc;
   e.s.reset = reset;
   e.s.stim_mode = e.L.in_width.empty() ? 0 : 1;   // xorshift64 stimulus
+  if (tile_lanes && (e.np % tile_lanes || tile_lanes % V)) return -1;
   switch (V) {
-    case 1: cycles<1>(e, nthreads, ncyc); break;
-    case 2: cycles<2>(e, nthreads, ncyc); break;
-    case 4: cycles<4>(e, nthreads, ncyc); break;
-    case 8: cycles<8>(e, nthreads, ncyc); break;
+    case 1: return cycles_u<1>(e, U, tile_lanes, nthreads, ncyc);
+    case 2: return cycles_u<2>(e, U, tile_lanes, nthreads, ncyc);
+    case 4: return cycles_u<4>(e, U, tile_lanes, nthreads, ncyc);
+    case 8: return cycles_u<8>(e, U, tile_lanes, nthreads, ncyc);
     default: return -1;
   }
-  return 0;
 }
 
 // Values of a caller signal in every lane (-1: fused away).

@@ -2,11 +2,12 @@
 library's own kernels.cuh (operand gathers of 1, 2, 4 or 8 packed lanes per
 row class, the 32-bit narrow path, side-array operand lists, stimulus, clock
 edge and write ports) and lower.cpp are compiled with the host compiler into
-tests/layer_form_harness.cpp, which runs the LAYER form phase by phase with
-every thread index of a phase called in turn.  Signals, memory words and
+tests/layer_form_harness.cpp, which runs the LAYER form (and the TILE form's
+lane tiles) phase by phase with every thread index of a phase called in turn.  Signals, memory words and
 stimulus states must equal the oracle's for every lanes-per-thread width and
 for thread counts equal to, above and below the number of lane chunks (the
-fixed and the generic work mapping).  Planted mistakes in a temporary copy of
+fixed and the generic work mapping), over all lanes or tiles of lanes, with one,
+two or four rows in flight per thread.  Planted mistakes in a temporary copy of
 kernels.cuh must fail it.  The library runs these functions only on the GPU;
 this checks their arithmetic and indexing without one."""
 import ctypes
@@ -38,7 +39,7 @@ def build_harness(csrc: str, out_dir) -> ctypes.CDLL:
     lib = ctypes.CDLL(so)
     lib.emu_create.restype = P
     lib.emu_create.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, P]
-    lib.emu_step.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int]
+    lib.emu_step.argtypes = [P] + [ctypes.c_uint32] * 5 + [P, ctypes.c_int]
     lib.emu_read.argtypes = [P, ctypes.c_uint32, P]
     lib.emu_mem.restype = P
     lib.emu_mem.argtypes = [P]
@@ -98,7 +99,8 @@ def designs() -> dict:
 DESIGNS = designs()
 
 
-def run_and_compare(lib, nl: synth.Netlist, fuse: bool, V: int, nthreads: int, seed: int = 1) -> None:
+def run_and_compare(lib, nl: synth.Netlist, fuse: bool, V: int, nthreads: int, U: int = 1, tile_lanes: int = 0,
+                    seed: int = 1) -> None:
     nb = nl.to_bytes()
     xs = np.ascontiguousarray(synth.xorshift_seeds(seed, nl.n_inputs, NP))
     e = lib.emu_create(nb, len(nb), int(fuse), NP, xs.ctypes.data if nl.n_inputs else None)
@@ -111,7 +113,8 @@ def run_and_compare(lib, nl: synth.Netlist, fuse: bool, V: int, nthreads: int, s
         for cycles, reset in [(1, True), (20, False), (None, False), (1, True), (7, False)]:
             budget = rng.integers(0, 12, NP).astype(np.uint32) if cycles is None else None
             ncyc = int(budget.max()) if budget is not None else cycles
-            lib.emu_step(e, V, nthreads, ncyc, None if budget is None else budget.ctypes.data, int(reset))
+            assert lib.emu_step(e, V, U, tile_lanes, nthreads, ncyc,
+                                None if budget is None else budget.ctypes.data, int(reset)) == 0
             orc.step(budget if budget is not None else cycles, reset=reset, mode=oracle.STIM_XORSHIFT, xs=xo)
             for sig in range(nl.n_signals):
                 if lib.emu_read(e, sig, out.ctypes.data) == 0:
@@ -128,15 +131,25 @@ def run_and_compare(lib, nl: synth.Netlist, fuse: bool, V: int, nthreads: int, s
         lib.emu_free(e)
 
 
-@pytest.mark.parametrize("mapping", ["one thread per chunk", "more threads", "fewer threads"])
+# (tile lanes (0: all lanes, the LAYER form), threads per phase as a function of
+# the lane chunks of a span, rows in flight per thread)
+MAPPINGS = {
+    "one thread per chunk": (0, lambda ch: ch, 1),
+    "more threads": (0, lambda ch: 3 * ch + 5, 1),
+    "fewer threads": (0, lambda ch: max(1, ch // 3), 1),
+    "all lanes, 4 rows in flight": (0, lambda ch: 2 * ch, 4),
+    "tiles of 16 lanes, 2 rows in flight": (16, lambda ch: 5, 2),
+    "tiles of 8 lanes, 4 rows in flight": (8, lambda ch: 3, 4),
+}
+
+
+@pytest.mark.parametrize("mapping", list(MAPPINGS))
 @pytest.mark.parametrize("V", [1, 2, 4, 8])
 @pytest.mark.parametrize("name", list(DESIGNS))
-def test_layer_form_matches_oracle(harness, name, V, mapping):
+def test_layer_and_tile_forms_match_oracle(harness, name, V, mapping):
     nl, fuse = DESIGNS[name]
-    chunks = NP // V
-    nthreads = {"one thread per chunk": chunks, "more threads": 3 * chunks + 5,
-                "fewer threads": max(1, chunks // 3)}[mapping]
-    run_and_compare(harness, nl, fuse, V, nthreads)
+    tile, threads, U = MAPPINGS[mapping]
+    run_and_compare(harness, nl, fuse, V, threads((tile or NP) // V), U=U, tile_lanes=tile)
 
 
 KERNEL_MUTANTS = [
