@@ -60,6 +60,8 @@ struct Emu {
   DSim s{};
   uint8_t* state = nullptr;
   std::vector<uint64_t> mem, xs;
+  std::vector<uint32_t> probe_refs;
+  std::vector<uint64_t> probe_prev;
   uint32_t np = 0, err = 0;
 };
 
@@ -93,6 +95,8 @@ void cycles(Emu& e, uint32_t tile_lanes, uint32_t nthreads, uint32_t ncyc) {
           eval_layer<V, U>(e.d, e.s, l, make_space<V>(tpo, base, t, nthreads), c);
       if (e.d.n_regs + e.d.n_mems)
         for (uint32_t t = 0; t < nthreads; t++) commit_items<V>(e.d, e.s, make_space<V>(tpo, base, t, nthreads), c);
+      if (e.s.n_probe)
+        for (uint32_t t = 0; t < nthreads; t++) probe_items<V>(e.s, make_space<V>(tpo, base, t, nthreads), c);
     }
 }
 
@@ -175,6 +179,36 @@ extern "C" int emu_step(void* p, uint32_t V, uint32_t U, uint32_t tile_lanes, ui
     case 8: return cycles_u<8>(e, U, tile_lanes, nthreads, ncyc);
     default: return -1;
   }
+}
+
+// Probes for the following steps (n = 0: none): mode 1 writes every cycle's
+// values to out [cycles][n][np]; mode 2 appends change records {cycle | probe
+// << 32, instance, value} to out (capacity records, *count = records found),
+// against the probes' values as the next step begins.  -1: a signal fused away.
+extern "C" int emu_probe(void* p, const uint32_t* sigs, uint32_t n, int mode, uint64_t* out, uint64_t capacity,
+                         unsigned long long* count) {
+  Emu& e = *static_cast<Emu*>(p);
+  e.probe_refs.assign(n, 0);
+  for (uint32_t i = 0; i < n; i++) {
+    const uint32_t slot = e.L.sig2slot[e.user2x[sigs[i]]];
+    if (slot == 0xFFFFFFFFu) return -1;
+    e.probe_refs[i] = e.L.slot_ref[slot];
+  }
+  e.s.n_probe = n;
+  e.s.probe_slot = ptr(e.probe_refs);
+  e.s.probe_out = out;
+  e.s.probe_changes = mode == 2;
+  if (mode == 2) {
+    e.probe_prev.assign((size_t)n * e.np, 0);
+    for (uint32_t i = 0; i < n; i++)
+      for (uint32_t lane = 0; lane < e.np; lane++)
+        e.probe_prev[(size_t)i * e.np + lane] = ld1(e.state, e.probe_refs[i], e.np, lane);
+    e.s.probe_prev = e.probe_prev.data();
+    e.s.change_count = count;
+    e.s.change_cap = capacity;
+    *count = 0;
+  }
+  return 0;
 }
 
 // Values of a caller signal in every lane (-1: fused away).

@@ -46,6 +46,7 @@ def build_harness(csrc: str, out_dir) -> ctypes.CDLL:
     lib.emu_xs.restype = P
     lib.emu_xs.argtypes = [P]
     lib.emu_free.argtypes = [P]
+    lib.emu_probe.argtypes = [P, P, ctypes.c_uint32, ctypes.c_int, P, ctypes.c_uint64, P]
     return lib
 
 
@@ -150,6 +151,52 @@ def test_layer_and_tile_forms_match_oracle(harness, name, V, mapping):
     nl, fuse = DESIGNS[name]
     tile, threads, U = MAPPINGS[mapping]
     run_and_compare(harness, nl, fuse, V, threads((tile or NP) // V), U=U, tile_lanes=tile)
+
+
+@pytest.mark.parametrize("mapping", ["one thread per chunk", "fewer threads", "tiles of 8 lanes, 4 rows in flight"])
+@pytest.mark.parametrize("V", [1, 4, 8])
+def test_probes_every_cycle_and_change_records(harness, V, mapping):
+    """Probes (Sec. 5.2 waveform generation): every cycle's values, and change
+    records against the values at the start of the step, as the oracle's trace
+    gives them."""
+    from oracle.waveform import changes
+    nl, fuse = DESIGNS["random+mem"]
+    tile, threads, U = MAPPINGS[mapping]
+    nthreads = threads((tile or NP) // V)
+    nb = nl.to_bytes()
+    xs = np.ascontiguousarray(synth.xorshift_seeds(5, nl.n_inputs, NP))
+    e = harness.emu_create(nb, len(nb), 0, NP, xs.ctypes.data)
+    orc, xo = oracle.OracleSim(nb, NP), xs.copy()
+    probes = np.array([0, 3, nl.reg_base, nl.reg_base + 7, nl.op_base + 11, nl.op_base + 200, nl.n_signals - 1],
+                      np.uint32)
+    try:
+        assert harness.emu_step(e, V, U, tile, nthreads, 1, None, 1) == 0
+        orc.step(1, reset=True, mode=oracle.STIM_XORSHIFT, xs=xo)
+        budgets = np.random.default_rng(V).integers(0, 15, NP).astype(np.uint32)
+        ncyc = int(budgets.max())
+        every = np.zeros((ncyc, probes.size, NP), np.uint64)
+        assert harness.emu_probe(e, probes.ctypes.data, probes.size, 1, every.ctypes.data, 0, None) == 0
+        assert harness.emu_step(e, V, U, tile, nthreads, ncyc, budgets.ctypes.data, 0) == 0
+        tr = orc.step(budgets, mode=oracle.STIM_XORSHIFT, xs=xo, probes=probes, probe_cycles=ncyc)
+        for i in range(NP):
+            assert np.array_equal(every[:budgets[i], :, i], tr[:budgets[i], :, i]), i
+        cap = 4096
+        recs = np.zeros(3 * cap, np.uint64)
+        count = np.zeros(1, np.uint64)
+        assert harness.emu_probe(e, probes.ctypes.data, probes.size, 2, recs.ctypes.data, cap,
+                                 count.ctypes.data) == 0
+        before = orc.read(probes)
+        assert harness.emu_step(e, V, U, tile, nthreads, 9, None, 0) == 0
+        tr = orc.step(9, mode=oracle.STIM_XORSHIFT, xs=xo, probes=probes, probe_cycles=9)
+        exp = changes(before, tr, 9)
+        n = int(count[0])
+        assert 0 < n == len(exp) <= cap
+        r = recs[:3 * n].reshape(n, 3)
+        got = np.stack([r[:, 0] & 0xFFFFFFFF, r[:, 0] >> 32, r[:, 1], r[:, 2]], axis=1).astype(np.uint64)
+        got = got[np.lexsort(got.T[::-1])]
+        assert np.array_equal(got, np.asarray(exp, np.uint64))
+    finally:
+        harness.emu_free(e)
 
 
 KERNEL_MUTANTS = [
