@@ -62,6 +62,10 @@ struct Emu {
   std::vector<uint64_t> mem, xs;
   std::vector<uint32_t> probe_refs;
   std::vector<uint64_t> probe_prev;
+  std::vector<uint8_t> act;          // activity stamps [rows][128-lane chunks]
+  uint64_t act_g = 1;                // cycle number of the next step's first cycle
+  bool act_force = true;             // next step's first cycle evaluates every op
+  unsigned long long act_count[2] = {0, 0};
   uint32_t np = 0, err = 0;
 };
 
@@ -98,6 +102,27 @@ void cycles(Emu& e, uint32_t tile_lanes, uint32_t nthreads, uint32_t ncyc) {
       if (e.s.n_probe)
         for (uint32_t t = 0; t < nthreads; t++) probe_items<V>(e.s, make_space<V>(tpo, base, t, nthreads), c);
     }
+}
+
+// Activity-aware evaluation over all lanes (the GRID form's activity phases;
+// with fewer than 32 lane chunks per row each thread checks and evaluates its
+// own rows, no warp votes).
+template <int V>
+void cycles_act(Emu& e, uint32_t nthreads, uint32_t ncyc) {
+  const FastDiv tpo = fastdiv(e.np / V);
+  for (uint32_t c = 0; c < ncyc; c++) {
+    if (e.s.stim_mode)
+      for (uint32_t t = 0; t < nthreads; t++) stim_items<V>(e.d, e.s, make_space<V>(tpo, 0u, t, nthreads), c);
+    for (uint32_t l = 0; l < e.d.n_layers; l++)
+      for (uint32_t t = 0; t < nthreads; t++) {
+        uint32_t n_eval = 0, n_skip = 0;
+        eval_layer_act<V>(e.d, e.s, l, make_space<V>(tpo, 0u, t, nthreads), c, n_eval, n_skip);
+        e.act_count[0] += n_eval;
+        e.act_count[1] += n_skip;
+      }
+    if (e.d.n_regs + e.d.n_mems)
+      for (uint32_t t = 0; t < nthreads; t++) commit_items<V>(e.d, e.s, make_space<V>(tpo, 0u, t, nthreads), c);
+  }
 }
 
 template <int V>
@@ -149,6 +174,11 @@ extern "C" void* emu_create(const void* bytes, size_t nbytes, int fuse, uint32_t
   d.n_mems = (uint32_t)(L.mem_info.size() / 4 - 1);
   d.op_base = L.op_base;
   d.reg_base = L.reg_base;
+  {  // class regions of the compact layout: class 3 first, then 2, 1, 0
+    const uint32_t c3 = L.class_rows[3], c2 = L.class_rows[2], c1 = L.class_rows[1];
+    d.cls_off = make_uint4(8 * c3 + 4 * c2 + 2 * c1, 8 * c3 + 4 * c2, 8 * c3, 0u);
+    d.cls_idx = make_uint4(c3 + c2 + c1, c3 + c2, c3, 0u);
+  }
   for (size_t c = 0; c < L.const_value.size(); c++)      // constants, as at sim creation
     for (uint32_t lane = 0; lane < np; lane++) st1(e->state, L.const_ref[c], np, lane, L.const_value[c]);
   DSim& s = e->s;
@@ -208,6 +238,41 @@ extern "C" int emu_probe(void* p, const uint32_t* sigs, uint32_t n, int mode, ui
     e.s.change_cap = capacity;
     *count = 0;
   }
+  return 0;
+}
+
+// A step with activity-aware evaluation (stamps kept across steps as the
+// library keeps them); stim_mode 0 holds the inputs, 1 draws xorshift64.  Needs np / V lane chunks per row below 32 and a thread
+// per chunk.  counts: [2] items evaluated and skipped so far.
+extern "C" int emu_step_act(void* p, uint32_t V, uint32_t ncyc, const uint32_t* budget, int reset, int stim_mode,
+                            unsigned long long* counts) {
+  Emu& e = *static_cast<Emu*>(p);
+  const uint32_t chunks = e.np / V;
+  if (chunks % 32u == 0u) return -1;
+  const uint32_t act_chunks = (e.np + 127) / 128;
+  if (e.act.empty()) e.act.assign((size_t)e.L.n_slots * act_chunks, 0);
+  e.s.budget = budget;
+  e.s.uniform = ncyc;
+  e.s.reset = reset;
+  e.s.stim_mode = e.L.in_width.empty() ? 0 : stim_mode;   // 0: inputs held, 1: xorshift64
+  e.s.act = e.act.data();
+  e.s.act_chunks = act_chunks;
+  e.s.act_g0 = (uint32_t)(e.act_g & 255u);
+  e.s.act_force = e.act_force ? 1 : 0;
+  switch (V) {
+    case 2: cycles_act<2>(e, chunks, ncyc); break;
+    case 4: cycles_act<4>(e, chunks, ncyc); break;
+    case 8: cycles_act<8>(e, chunks, ncyc); break;
+    default: return -1;
+  }
+  bool uneven = false;  // a lane that stopped early has an edge the next step's first cycle has not seen
+  if (budget)
+    for (uint32_t lane = 0; lane < e.np && !uneven; lane++) uneven = budget[lane] != ncyc;
+  e.act_g += ncyc;
+  e.act_force = uneven;
+  e.s.act = nullptr;
+  counts[0] = e.act_count[0];
+  counts[1] = e.act_count[1];
   return 0;
 }
 

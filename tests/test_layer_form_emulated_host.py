@@ -47,6 +47,7 @@ def build_harness(csrc: str, out_dir) -> ctypes.CDLL:
     lib.emu_xs.argtypes = [P]
     lib.emu_free.argtypes = [P]
     lib.emu_probe.argtypes = [P, P, ctypes.c_uint32, ctypes.c_int, P, ctypes.c_uint64, P]
+    lib.emu_step_act.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int, ctypes.c_int, P]
     return lib
 
 
@@ -244,3 +245,69 @@ def test_planted_kernel_mistakes_are_caught(tmp_path):
             if caught:
                 break
         assert caught, "no design catches: " + name
+
+
+def run_activity(lib, V: int, hold: bool) -> tuple[int, int]:
+    """Activity-aware evaluation on enable-gated modules against the oracle after
+    every step (reset, quiet stretches, uneven budgets -- the next step's first
+    cycle then evaluates everything -- and a second reset); returns the items
+    evaluated and skipped."""
+    nl = synth.generate_modular(synth.ModularSpec(n_modules=4, ops_per_module=150, regs_per_module=12, depth=6,
+                                                  seed=9, inputs_per_module=4))
+    nb = nl.to_bytes()
+    xs = np.ascontiguousarray(synth.xorshift_seeds(9, nl.n_inputs, NP))
+    e = lib.emu_create(nb, len(nb), 0, NP, xs.ctypes.data)
+    orc, xo = oracle.OracleSim(nb, NP), xs.copy()
+    counts = np.zeros(2, np.uint64)
+    out = np.zeros(NP, np.uint64)
+    rng = np.random.default_rng(V)
+    try:
+        for cycles, reset in [(1, True), (40, False), (None, False), (13, False), (1, True), (30, False)]:
+            budget = rng.integers(0, 25, NP).astype(np.uint32) if cycles is None else None
+            ncyc = int(budget.max()) if budget is not None else cycles
+            mode = oracle.STIM_HOLD if hold and not reset else oracle.STIM_XORSHIFT
+            assert lib.emu_step_act(e, V, ncyc, None if budget is None else budget.ctypes.data, int(reset),
+                                    0 if mode == oracle.STIM_HOLD else 1, counts.ctypes.data) == 0
+            orc.step(budget if budget is not None else cycles, reset=reset, mode=mode, xs=xo)
+            for sig in range(nl.n_signals):
+                if lib.emu_read(e, sig, out.ctypes.data) == 0:
+                    assert np.array_equal(out, orc.vals[:, sig]), sig
+    finally:
+        lib.emu_free(e)
+    return int(counts[0]), int(counts[1])
+
+
+@pytest.mark.parametrize("V", [2, 4, 8])
+@pytest.mark.parametrize("stimulus", ["held inputs", "random inputs"])
+def test_activity_aware_evaluation(harness, V, stimulus):
+    """Activity-aware evaluation (ops whose operands did not change in a 128-lane
+    chunk are skipped there) equals the oracle; with held inputs most items are
+    skipped."""
+    evaluated, skipped = run_activity(harness, V, stimulus == "held inputs")
+    assert evaluated > 0 and skipped > 0
+    if stimulus == "held inputs":
+        assert skipped > evaluated
+
+
+ACTIVITY_MUTANTS = [
+    ("a row's third operand never makes it hot", "  if (ar >= 3) h |= hot_ref(m.z);\n", "\n"),
+    ("a register change left unstamped",
+     "        *act_at(d, s, qref, lane) = (uint8_t)(s.act_g0 + cyc + 1u);\n", "\n"),
+]
+
+
+def test_planted_activity_mistakes_are_caught(tmp_path):
+    if not os.path.isdir(CUDA_INCLUDE):
+        pytest.skip("CUDA headers not found")
+    with open(os.path.join(CSRC, "kernels.cuh")) as f:
+        src = f.read()
+    for k, (name, old, new) in enumerate(ACTIVITY_MUTANTS):
+        assert src.count(old) == 1, "mutation site not found exactly once: " + name
+        d = tmp_path / ("a%d" % k)
+        d.mkdir()
+        for f in ["lower.hpp", "lower.cpp"]:
+            shutil.copy(os.path.join(CSRC, f), str(d / f))
+        (d / "kernels.cuh").write_text(src.replace(old, new))
+        lib = build_harness(str(d), d)
+        with pytest.raises(AssertionError):
+            run_activity(lib, 4, True)
