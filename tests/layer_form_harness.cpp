@@ -9,16 +9,40 @@
 // votes and shuffles belong to activity-aware evaluation only, never used here.
 #include <cuda_runtime.h>  // vector types (uint4, ...) and qualifiers for a host compile
 
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #ifndef __noinline__
 #define __noinline__
 #endif
 
-static uint3 threadIdx, blockIdx, blockDim, gridDim;
+static thread_local uint3 threadIdx;
+static uint3 blockIdx, blockDim, gridDim;
+
+// A warp of 32 host threads: ballots and shuffles exchange their values through
+// one slot per lane between two barrier rounds.  Every caller reaches the same
+// sequence of collectives (each branch that leads to one is warp-uniform).
+struct Warp {
+  std::atomic<unsigned> arrived{0}, generation{0};
+  unsigned long long slot[32];
+  void wait() {  // yields while waiting; a wait that never ends aborts instead of hanging
+    const unsigned gen = generation.load();
+    if (arrived.fetch_add(1) + 1 == 32) {
+      arrived.store(0);
+      generation.fetch_add(1);
+      return;
+    }
+    for (unsigned long long spins = 0; generation.load() == gen; spins++) {
+      if (spins > 2000000000ull) abort();
+      std::this_thread::yield();
+    }
+  }
+};
+static thread_local Warp* warp = nullptr;
 
 template <typename T>
 static inline T __ldg(const T* p) {
@@ -34,10 +58,24 @@ static inline unsigned __byte_perm(unsigned x, unsigned y, unsigned s) {
 static inline int __popc(unsigned x) { return __builtin_popcount(x); }
 static inline int __popcll(unsigned long long x) { return __builtin_popcountll(x); }
 static inline int __ffs(int x) { return __builtin_ffs(x); }
-static inline unsigned __ballot_sync(unsigned, int) { abort(); }
+static inline unsigned __ballot_sync(unsigned, int pred) {
+  if (!warp) abort();
+  const unsigned lid = threadIdx.x & 31u;
+  warp->slot[lid] = pred ? 1u : 0u;
+  warp->wait();
+  unsigned r = 0;
+  for (unsigned i = 0; i < 32; i++) r |= (unsigned)warp->slot[i] << i;
+  warp->wait();
+  return r;
+}
 template <typename T>
-static inline T __shfl_sync(unsigned, T, int, int = 32) {
-  abort();
+static inline T __shfl_sync(unsigned, T v, int src, int = 32) {
+  if (!warp) abort();
+  warp->slot[threadIdx.x & 31u] = (unsigned long long)v;
+  warp->wait();
+  const T r = (T)warp->slot[src & 31];
+  warp->wait();
+  return r;
 }
 static inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
   const unsigned long long o = *p;
@@ -104,24 +142,64 @@ void cycles(Emu& e, uint32_t tile_lanes, uint32_t nthreads, uint32_t ncyc) {
     }
 }
 
-// Activity-aware evaluation over all lanes (the GRID form's activity phases;
-// with fewer than 32 lane chunks per row each thread checks and evaluates its
-// own rows, no warp votes).
+// Activity-aware evaluation over all lanes (the GRID form's activity phases).
+// With a multiple of 32 lane chunks per row the warps vote on hot rows
+// (warp-cooperative branch: 32 host threads per warp); otherwise each thread
+// checks and evaluates its own rows.
 template <int V>
 void cycles_act(Emu& e, uint32_t nthreads, uint32_t ncyc) {
   const FastDiv tpo = fastdiv(e.np / V);
-  for (uint32_t c = 0; c < ncyc; c++) {
+  auto stim = [&](uint32_t c) {
     if (e.s.stim_mode)
       for (uint32_t t = 0; t < nthreads; t++) stim_items<V>(e.d, e.s, make_space<V>(tpo, 0u, t, nthreads), c);
-    for (uint32_t l = 0; l < e.d.n_layers; l++)
-      for (uint32_t t = 0; t < nthreads; t++) {
-        uint32_t n_eval = 0, n_skip = 0;
-        eval_layer_act<V>(e.d, e.s, l, make_space<V>(tpo, 0u, t, nthreads), c, n_eval, n_skip);
-        e.act_count[0] += n_eval;
-        e.act_count[1] += n_skip;
-      }
+  };
+  auto edge = [&](uint32_t c) {
     if (e.d.n_regs + e.d.n_mems)
       for (uint32_t t = 0; t < nthreads; t++) commit_items<V>(e.d, e.s, make_space<V>(tpo, 0u, t, nthreads), c);
+  };
+  if (tpo.d % 32u != 0u) {  // each thread checks and evaluates its own rows
+    for (uint32_t c = 0; c < ncyc; c++) {
+      stim(c);
+      for (uint32_t l = 0; l < e.d.n_layers; l++)
+        for (uint32_t t = 0; t < nthreads; t++) {
+          uint32_t n_eval = 0, n_skip = 0;
+          threadIdx.x = t;
+          eval_layer_act<V>(e.d, e.s, l, make_space<V>(tpo, 0u, t, nthreads), c, n_eval, n_skip);
+          e.act_count[0] += n_eval;
+          e.act_count[1] += n_skip;
+        }
+      edge(c);
+    }
+    return;
+  }
+  // warp-cooperative branch: 32 host threads act as the 32 lanes of a warp and
+  // take the warps one after another (warps of a layer are independent); lane 0
+  // runs the stimulus and clock-edge phases while the others wait
+  Warp wp;
+  uint32_t ev[32] = {0}, sk[32] = {0};
+  std::vector<std::thread> lanes;
+  for (uint32_t i = 0; i < 32; i++)
+    lanes.emplace_back([&, i] {
+      warp = &wp;
+      for (uint32_t c = 0; c < ncyc; c++) {
+        if (i == 0) stim(c);
+        wp.wait();
+        for (uint32_t l = 0; l < e.d.n_layers; l++) {
+          for (uint32_t w0 = 0; w0 < nthreads; w0 += 32) {
+            threadIdx.x = w0 + i;
+            eval_layer_act<V>(e.d, e.s, l, make_space<V>(tpo, 0u, w0 + i, nthreads), c, ev[i], sk[i]);
+          }
+          wp.wait();
+        }
+        if (i == 0) edge(c);
+        wp.wait();
+      }
+      warp = nullptr;
+    });
+  for (auto& th : lanes) th.join();
+  for (uint32_t i = 0; i < 32; i++) {
+    e.act_count[0] += ev[i];
+    e.act_count[1] += sk[i];
   }
 }
 
@@ -242,13 +320,12 @@ extern "C" int emu_probe(void* p, const uint32_t* sigs, uint32_t n, int mode, ui
 }
 
 // A step with activity-aware evaluation (stamps kept across steps as the
-// library keeps them); stim_mode 0 holds the inputs, 1 draws xorshift64.  Needs np / V lane chunks per row below 32 and a thread
-// per chunk.  counts: [2] items evaluated and skipped so far.
+// library keeps them); stim_mode 0 holds the inputs, 1 draws xorshift64; one
+// thread per lane chunk.  counts: [2] items evaluated and skipped so far.
 extern "C" int emu_step_act(void* p, uint32_t V, uint32_t ncyc, const uint32_t* budget, int reset, int stim_mode,
                             unsigned long long* counts) {
   Emu& e = *static_cast<Emu*>(p);
-  const uint32_t chunks = e.np / V;
-  if (chunks % 32u == 0u) return -1;
+  const uint32_t chunks = e.np / V;   // one thread per lane chunk (whole warps when 32 divide it)
   const uint32_t act_chunks = (e.np + 127) / 128;
   if (e.act.empty()) e.act.assign((size_t)e.L.n_slots * act_chunks, 0);
   e.s.budget = budget;
@@ -260,6 +337,7 @@ extern "C" int emu_step_act(void* p, uint32_t V, uint32_t ncyc, const uint32_t* 
   e.s.act_g0 = (uint32_t)(e.act_g & 255u);
   e.s.act_force = e.act_force ? 1 : 0;
   switch (V) {
+    case 1: cycles_act<1>(e, chunks, ncyc); break;
     case 2: cycles_act<2>(e, chunks, ncyc); break;
     case 4: cycles_act<4>(e, chunks, ncyc); break;
     case 8: cycles_act<8>(e, chunks, ncyc); break;

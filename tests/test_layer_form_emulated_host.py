@@ -33,7 +33,7 @@ P = ctypes.c_void_p
 
 def build_harness(csrc: str, out_dir) -> ctypes.CDLL:
     so = os.path.join(str(out_dir), "harness.so")
-    subprocess.run(["g++", "-std=c++17", "-O1", "-w", "-shared", "-fPIC", "-I", CUDA_INCLUDE, "-I", INCLUDE,
+    subprocess.run(["g++", "-std=c++17", "-O1", "-w", "-pthread", "-shared", "-fPIC", "-I", CUDA_INCLUDE, "-I", INCLUDE,
                     "-I", csrc, "-o", so, os.path.join(HERE, "layer_form_harness.cpp"),
                     os.path.join(csrc, "lower.cpp")], check=True)
     lib = ctypes.CDLL(so)
@@ -247,7 +247,7 @@ def test_planted_kernel_mistakes_are_caught(tmp_path):
         assert caught, "no design catches: " + name
 
 
-def run_activity(lib, V: int, hold: bool) -> tuple[int, int]:
+def run_activity(lib, V: int, hold: bool, np_: int = NP) -> tuple[int, int]:
     """Activity-aware evaluation on enable-gated modules against the oracle after
     every step (reset, quiet stretches, uneven budgets -- the next step's first
     cycle then evaluates everything -- and a second reset); returns the items
@@ -255,15 +255,15 @@ def run_activity(lib, V: int, hold: bool) -> tuple[int, int]:
     nl = synth.generate_modular(synth.ModularSpec(n_modules=4, ops_per_module=150, regs_per_module=12, depth=6,
                                                   seed=9, inputs_per_module=4))
     nb = nl.to_bytes()
-    xs = np.ascontiguousarray(synth.xorshift_seeds(9, nl.n_inputs, NP))
-    e = lib.emu_create(nb, len(nb), 0, NP, xs.ctypes.data)
-    orc, xo = oracle.OracleSim(nb, NP), xs.copy()
+    xs = np.ascontiguousarray(synth.xorshift_seeds(9, nl.n_inputs, np_))
+    e = lib.emu_create(nb, len(nb), 0, np_, xs.ctypes.data)
+    orc, xo = oracle.OracleSim(nb, np_), xs.copy()
     counts = np.zeros(2, np.uint64)
-    out = np.zeros(NP, np.uint64)
+    out = np.zeros(np_, np.uint64)
     rng = np.random.default_rng(V)
     try:
         for cycles, reset in [(1, True), (40, False), (None, False), (13, False), (1, True), (30, False)]:
-            budget = rng.integers(0, 25, NP).astype(np.uint32) if cycles is None else None
+            budget = rng.integers(0, 25, np_).astype(np.uint32) if cycles is None else None
             ncyc = int(budget.max()) if budget is not None else cycles
             mode = oracle.STIM_HOLD if hold and not reset else oracle.STIM_XORSHIFT
             assert lib.emu_step_act(e, V, ncyc, None if budget is None else budget.ctypes.data, int(reset),
@@ -289,10 +289,24 @@ def test_activity_aware_evaluation(harness, V, stimulus):
         assert skipped > evaluated
 
 
+@pytest.mark.parametrize("V", [1, 2, 8])
+def test_activity_aware_evaluation_warp_cooperative(harness, V):
+    """The warp-cooperative branch (a multiple of 32 lane chunks per row: 256
+    lanes, two 128-lane stamp chunks): each warp's 32 threads run together,
+    vote on hot rows and evaluate only those; equal to the oracle."""
+    evaluated, skipped = run_activity(harness, V, True, np_=256)
+    assert evaluated > 0 and skipped > evaluated
+
+
+# (name, text, replacement, lanes per thread, lanes): 256 lanes at 8 per thread
+# take the warp-cooperative branch with warps spanning two 128-lane stamp chunks
 ACTIVITY_MUTANTS = [
-    ("a row's third operand never makes it hot", "  if (ar >= 3) h |= hot_ref(m.z);\n", "\n"),
+    ("a row's third operand never makes it hot", "  if (ar >= 3) h |= hot_ref(m.z);\n", "\n", 4, NP),
     ("a register change left unstamped",
-     "        *act_at(d, s, qref, lane) = (uint8_t)(s.act_g0 + cyc + 1u);\n", "\n"),
+     "        *act_at(d, s, qref, lane) = (uint8_t)(s.act_g0 + cyc + 1u);\n", "\n", 4, NP),
+    ("a warp checks only the first stamp chunk of its lanes",
+     "const uint32_t ch_lo = first >> 7, ch_hi = (first + 32u * V - 1u) >> 7;",
+     "const uint32_t ch_lo = first >> 7, ch_hi = ch_lo;", 8, 256),
 ]
 
 
@@ -301,7 +315,7 @@ def test_planted_activity_mistakes_are_caught(tmp_path):
         pytest.skip("CUDA headers not found")
     with open(os.path.join(CSRC, "kernels.cuh")) as f:
         src = f.read()
-    for k, (name, old, new) in enumerate(ACTIVITY_MUTANTS):
+    for k, (name, old, new, V, lanes) in enumerate(ACTIVITY_MUTANTS):
         assert src.count(old) == 1, "mutation site not found exactly once: " + name
         d = tmp_path / ("a%d" % k)
         d.mkdir()
@@ -310,4 +324,4 @@ def test_planted_activity_mistakes_are_caught(tmp_path):
         (d / "kernels.cuh").write_text(src.replace(old, new))
         lib = build_harness(str(d), d)
         with pytest.raises(AssertionError):
-            run_activity(lib, 4, True)
+            run_activity(lib, V, True, np_=lanes)
