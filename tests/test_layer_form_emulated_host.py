@@ -31,9 +31,9 @@ NP = 32                     # lanes (a power of two, as the library pads small b
 P = ctypes.c_void_p
 
 
-def build_harness(csrc: str, out_dir) -> ctypes.CDLL:
+def build_harness(csrc: str, out_dir, opt: str = "-O1") -> ctypes.CDLL:
     so = os.path.join(str(out_dir), "harness.so")
-    subprocess.run(["g++", "-std=c++17", "-O1", "-w", "-pthread", "-shared", "-fPIC", "-I", CUDA_INCLUDE, "-I", INCLUDE,
+    subprocess.run(["g++", "-std=c++17", opt, "-w", "-pthread", "-shared", "-fPIC", "-I", CUDA_INCLUDE, "-I", INCLUDE,
                     "-I", csrc, "-o", so, os.path.join(HERE, "layer_form_harness.cpp"),
                     os.path.join(csrc, "lower.cpp")], check=True)
     lib = ctypes.CDLL(so)
@@ -232,7 +232,7 @@ def test_planted_kernel_mistakes_are_caught(tmp_path):
         for f in ["lower.hpp", "lower.cpp"]:
             shutil.copy(os.path.join(CSRC, f), str(d / f))
         (d / "kernels.cuh").write_text(src.replace(old, new))
-        lib = build_harness(str(d), d)
+        lib = build_harness(str(d), d, opt="-O0")   # quick to build; the runs are short
         caught = False
         for name_d in ["random+mem", "wide+domains", "chains-fused", "copies-only"]:
             nl, fuse = DESIGNS[name_d]
@@ -322,6 +322,6 @@ def test_planted_activity_mistakes_are_caught(tmp_path):
         for f in ["lower.hpp", "lower.cpp"]:
             shutil.copy(os.path.join(CSRC, f), str(d / f))
         (d / "kernels.cuh").write_text(src.replace(old, new))
-        lib = build_harness(str(d), d)
+        lib = build_harness(str(d), d, opt="-O0")   # quick to build; the runs are short
         with pytest.raises(AssertionError):
             run_activity(lib, V, True, np_=lanes)
