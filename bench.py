@@ -3,17 +3,18 @@
 Default workload ("batch-1M"): random layered DAG of 1,000,000 ops, 65,536
 registers, depth 80, 32 primary inputs, 4,096 stimulus instances with per-
 instance cycle budgets uniform in [1k, 100k], per-instance xorshift64
-stimulus, persistent tile kernel.  One step = one pass of the whole hot path
-(stimulus, every layer, clock edge) for a chunk of `--chunk` cycles over every
-instance that still has cycles left.  The timed window covers cycles
-[W*chunk, (W+K)*chunk) of the job; instances never finish inside it (budgets
->= 1,000 cycles), so every instance-cycle in the window is active.
+stimulus, the persistent grid kernel (launch configuration autotuned).  One
+step = one pass of the whole hot path (stimulus, every layer, clock edge) for
+a chunk of `--chunk` cycles over every instance that still has cycles left.
+The timed window covers cycles [W*chunk, (W+K)*chunk) of the job; instances
+never finish inside it (budgets >= 1,000 cycles), so every instance-cycle in
+the window is active.
 
 value       op-evals/s (active instance-cycles x ops / device time), inputs resident
 e2e         same metric through the public API with host buffers: explicit
             per-cycle stimulus copied from pinned host memory each step and
             64 probed register values per instance copied back each step
-roofline    dominant kernel (k_tile): algorithmic bytes per launch / launch time
+roofline    dominant kernel (k_grid): algorithmic bytes per launch / launch time
 cpu_baseline  the oracle on this host's cores, on a bounded sample
 
 --impl reference  times the oracle (gate-by-gate C interpreter) as the
@@ -35,6 +36,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
+
+# the metric both arms report (op-evaluations = netlist ops x instances x cycles)
+METRIC = "op-evaluations/sec (ops\u00d7instances\u00d7cycles) on 1 GB300, bit-exact, % mem roofline"
 
 WORKLOADS = {
     # name: (spec factory, instances, cycle budget range, tile lanes)
@@ -223,7 +227,7 @@ def run_reference(args) -> None:
     ms = float(np.mean([x["seconds"] for x in vals])) * 1e3
     cb = dict(vals[0])
     cb["value"] = v
-    line = {"impl": "reference", "metric": "op-evaluations/sec (ops x instances x cycles), bit-exact",
+    line = {"impl": "reference", "metric": METRIC,
             "value": v, "unit": "op-evals/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -405,6 +409,46 @@ def run_ours(args) -> None:
                "h2d_bytes_per_step": int(C * nl.n_inputs * n_total * 8 + n_total * 4),   # all ranks
                "d2h_bytes_per_step": int(probes.size * n_total * 8)}
 
+    # ---- the whole job: with uneven budgets instances retire as the job goes on
+    # and each step visits only the live lanes, so the device time per cycle
+    # falls with the live count.  Measure it at points t of the job (instances
+    # with budget > t run a window of C cycles from their state; the others are
+    # done), integrate over t, and divide the job's op-evaluations by it.
+    job = None
+    if args.job_points > 0:
+        tmax = int(budgets_all.max())
+        pts = [int(round(tmax * i / args.job_points)) for i in range(args.job_points)]
+        samples = []
+        for t in pts:
+            per = np.clip(budgets.astype(np.int64) - t, 0, C).astype(np.uint32)
+            if per.max() == 0:
+                samples.append({"t": t, "live": 0, "ms_per_cycle": 0.0})
+                continue
+            sim.step(per, stimulus=run_stim)                     # warm-up at this span
+            j0, j1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            j0.record(stream)
+            for _ in range(2):
+                sim.step(per, stimulus=run_stim)
+            j1.record(stream)
+            torch.cuda.synchronize()
+            ms = j0.elapsed_time(j1) / (2 * C)
+            samples.append({"t": t, "live": int((per > 0).sum()), "ms_per_cycle": ms,
+                            "span": int(sim.info["last_span"]),
+                            "op_evals_per_s": float(per.astype(np.int64).sum()) * nl.n_ops / (ms * C / 1e3)})
+        ts = np.array([x["t"] for x in samples] + [tmax], np.float64)
+        ys = np.array([x["ms_per_cycle"] for x in samples] + [0.0], np.float64)
+        job_ms = float(np.sum((ys[1:] + ys[:-1]) * np.diff(ts)) / 2.0)     # trapezoid over t
+        job_evals = float(budgets.astype(np.int64).sum()) * nl.n_ops
+        if world > 1:
+            job_ms, job_evals = reduce_over_ranks(job_ms, job_evals, dev)
+        job = {"value": job_evals / (job_ms / 1e3), "unit": "op-evals/s",
+               "job_seconds": job_ms / 1e3, "op_evals": job_evals,
+               "over_value": (job_evals / (job_ms / 1e3)) / value,
+               "method": "device time per cycle measured at %d points of the job (window of %d cycles "
+                         "for the instances still running), integrated over the job's %d cycles"
+                         % (len(pts), C, tmax),
+               "points": samples}
+
     # the plain single-instance form on the same design (the batching baseline):
     # one instance, one launch sequence per cycle replayed as a CUDA graph
     plain = None
@@ -433,7 +477,7 @@ def run_ours(args) -> None:
 
     if rank == 0:
         line = {
-            "metric": "op-evaluations/sec (ops x instances x cycles) on 1 GB300, bit-exact, % mem roofline",
+            "metric": METRIC,
             "value": value, "unit": "op-evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -462,6 +506,7 @@ def run_ours(args) -> None:
             "gpu_launches": 1 * args.steps,
             "activity": activity,
             "plain_single_instance": plain,
+            "job": job,
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -564,6 +609,8 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--lanes-per-thread", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--job-points", type=int, default=12,
+                    help="points of the job at which the per-cycle time is measured (0: skip the job leg)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--tune-kernels", default="tile,grid,stream")
     ap.add_argument("--tune-log", default="")

@@ -10,7 +10,7 @@
  *     LI_{i+1} = LO_i | LO_sel_i
  *   then every register commits its next state at the clock edge (Sec. 2.1,
  *   Fig. 1), and the testbench drives the primary inputs at the cycle boundary
- *   (Sec. 5.2, "Host-DUT Communication").
+ *   (Sec. 6.2, "Host-DUT Communication").
  *
  * Device form.  Identity operations are elided by giving every signal one
  * global row (Sec. 4.3): LI / LO of every layer are views of one state array,
@@ -23,9 +23,9 @@
  * per lane of all rows before it; element (row, lane) of an n-lane state is the
  * little-endian integer of 1 << k bytes at byte o * n + (lane << k).  OIM is lowered
  * to per-layer operand lists whose operations are grouped by (opcode, width)
- * -- the swizzled [I, N, S, O, R] order of the NU kernel (Sec. 4.4) -- with the
+ * -- the swizzled [I, N, S, O, R] order of the NU kernel (Sec. 5.2) -- with the
  * S coordinates implicit (the outputs of a layer occupy consecutive slots) and
- * the N / O payloads implied by the opcode (Sec. 4.3, "Compressing the OIM").
+ * the N / O payloads implied by the opcode (Sec. 5.1, "Compressing the OIM").
  *
  * ------------------------------------------------------------------------
  * Netlist format "RTLN" version 1 (input of rteaal_design_load)
@@ -45,7 +45,7 @@
  * then op outputs in topological order (every operand id < the op's own id).
  * Op k's operands are args[op_argoff[k] .. op_argoff[k+1]) in O order.
  *
- * Clock domains (Sec. 5.2 "Multiple Clock Domains"; the rule is a reading):
+ * Clock domains (Sec. 6.2 "Multiple Clock Domains"; the rule is a reading):
  * domain d has a period p (a power of two <= 2^31, in base-clock cycles) and a
  * phase f < p; every register names its domain (at most 256).  Each instance
  * counts t, the non-reset cycles since its last reset cycle; at the edge of a
@@ -181,7 +181,7 @@ int rteaal_design_specialize(rteaal_design *design, uint64_t *compile_us);
 int rteaal_design_lower(const void *netlist, size_t nbytes, const rteaal_load_opts *opts,
                         rteaal_design_stats *out, uint32_t *layer_ops, uint32_t max_layers);
 /* The one-clock netlist the library simulates for a netlist with clock domains
- * (Sec. 5.2 "Multiple Clock Domains", reading in the format notes above): a
+ * (Sec. 6.2 "Multiple Clock Domains", reading in the format notes above): a
  * hidden 32-bit cycle counter t (a register after the caller's registers), per
  * slower domain an enable (t + phase) & (period - 1) == 0, and per register of
  * such a domain a hold mux; without domains, the netlist itself.  Host only.
@@ -217,7 +217,7 @@ int rteaal_design_rows(const void *netlist, size_t nbytes, const rteaal_load_opt
                        uint64_t n_rows);
 /* The design-specialised kernel's generation and NVRTC compile for sm_103a
  * alone, on the host (no device is touched, nothing is kept): checks that a
- * netlist's straight-line kernel (Sec. 4.4, unrolled S rank and inlined
+ * netlist's straight-line kernel (Sec. 5.2, unrolled S rank and inlined
  * tensors) compiles.  cubin_bytes / compile_us (nullable) receive the size of
  * the compiled image and the generation + compile time.  opts nullable (only
  * fuse_mux_chains is read).  Errors: E_INVALID, E_FORMAT, E_UNSUPPORTED (too
@@ -249,7 +249,7 @@ enum {
                                shared-memory ring with bulk copies (TMA engine,
                                mbarriers), consumer warps compute from it; needs a
                                multiple of 128 lanes                              */
-  RTEAAL_KERNEL_SPECIALIZED = 6 /* design-specialised (Sec. 4.4 SU / TI on the GPU):
+  RTEAAL_KERNEL_SPECIALIZED = 6 /* design-specialised (Sec. 5.2 SU / TI on the GPU):
                                the op list unrolled into straight-line code compiled
                                at run time (NVRTC), every signal a local variable,
                                one thread per instance for all cycles of a step;
@@ -291,10 +291,13 @@ typedef struct {
   uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid;
   uint32_t lanes_per_thread;
   int activity;                  /* activity-aware evaluation on                  */
+  uint32_t last_span;            /* lanes the last rteaal_step visited (live prefix) */
+  uint32_t last_grid;            /* CTAs of the last GRID launch (0: none yet)    */
 } rteaal_sim_stats;
 
 /* Allocates and zero-initialises the state of n_instances (>= 1) independent
- * instances, writes the constants.  Registers are 0 until a reset cycle.
+ * instances -- LI / LO of every layer as one global row per signal (identity
+ * elision, Sec. 4.3), one lane per stimulus instance -- and writes the constants.  Registers are 0 until a reset cycle.
  * design must outlive the sim.  Errors: E_INVALID, E_NOMEM, E_CUDA. */
 int rteaal_sim_create(const rteaal_design *design, uint32_t n_instances,
                       const rteaal_sim_opts *opts, rteaal_sim **out);
@@ -359,7 +362,7 @@ enum { RTEAAL_PROBE_LAST = 0, RTEAAL_PROBE_EVERY = 1, RTEAAL_PROBE_CHANGES = 2 }
 /* One waveform event (RTEAAL_PROBE_CHANGES): probe `probe` of instance
  * `instance` took `value` at the end of cycle `cycle` (cycle index relative to
  * the step) and that differs from its value at the end of the previous cycle
- * (for cycle 0: its value when the step began) -- waveform generation, Sec. 5.2,
+ * (for cycle 0: its value when the step began) -- waveform generation, Sec. 6.2,
  * which keeps a value only when it changes. */
 typedef struct {
   uint32_t cycle, probe, instance, pad;
@@ -383,7 +386,13 @@ typedef struct {
 
 enum { RTEAAL_STEP_RESET = 1 };
 
-/* Advance every instance by its cycle count (0 allowed).  flags & RESET makes
+/* Advance every instance by its cycle count (0 allowed): per cycle, inputs
+ * (Sec. 6.2 "Host--DUT Communication"), every layer of Cascade 1 in order
+ * (Sec. 4.2, Alg. 3 / Alg. 4), then the register commit (Sec. 2.1, Fig. 1);
+ * uneven counts are the iterative rank of Alg. 1 applied per instance.
+ * Only lanes up to the last one with a nonzero count are visited (lanes are
+ * ordered by expected_cycles, so finished instances cost nothing; a frozen
+ * instance is never written).  flags & RESET makes
  * every cycle of the call a reset cycle.  Work is enqueued on stream (a
  * cudaStream_t; NULL = legacy default stream) and is asynchronous unless a
  * host buffer is involved.  Caller-owned device buffers must stay valid until
@@ -403,8 +412,8 @@ int rteaal_sim_reset_lanes(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst
 /* Blocks until the sim's work on stream is done; returns any pending error. */
 int rteaal_sync(rteaal_sim *sim, void *stream);
 
-/* Copy signal values of instances [inst_begin, inst_begin + n_inst) to / from
- * host memory laid out [n][n_inst] (caller-owned, any host memory; values
+/* Copy signal values (rows of LI / LO, Sec. 4.1; register Q values, Sec. 2.1)
+ * of instances [inst_begin, inst_begin + n_inst) to / from host memory laid out [n][n_inst] (caller-owned, any host memory; values
  * zero-extended, writes masked to each signal's width).  signals: host array of
  * n signal ids (caller-owned).  Synchronises stream.  Writing a constant
  * changes it for the rest of the simulation (checkpoint restore).  Errors:
@@ -422,7 +431,7 @@ int rteaal_mem_read(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst, uint6
                     void *stream);
 int rteaal_mem_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst, const uint64_t *host_in,
                      void *stream);
-/* xorshift64 stimulus states (Sec. 5.2 testbench; Marsaglia 2003): host buffer
+/* xorshift64 stimulus states (Sec. 6.2 testbench; Marsaglia 2003): host buffer
  * [n_inputs][n_inst] uint64 (caller-owned); writing them replays a stimulus
  * from a checkpoint.  Synchronises stream.  Errors as rteaal_state_read. */
 int rteaal_stim_state_read(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_inst,
@@ -446,10 +455,18 @@ int rteaal_stim_state_write(rteaal_sim *sim, uint32_t inst_begin, uint32_t n_ins
  *         (constants' rows must hold their values)
  *   mem   [mem_words_total][n_lanes] uint64 (nullable without memories)
  *   xs    [n_inputs][n_lanes] uint64 xorshift64 states (nullable unless XORSHIFT)
- * Slot order of op rows: by level, then (opcode, width), then netlist order;
- * a register D or write-port signal that is not an op output gets a COPY op
- * on level 1, ordered after the netlist's own ops of the same key.  16-byte aligned buffers with an even n_lanes
- * use two lanes per thread.
+ * Slot order of op rows (the layout's row order; rteaal_design_rows and
+ * rteaal_design_lowered_netlist report it for a given netlist): by level;
+ * inside a level, ops with at most three operands before the others; among
+ * those, narrow ops before wide ones (narrow: the result and every operand at
+ * most 32 bits wide, and the op is not MEMRD, not BITS with hi >= 32, not ANDR
+ * over more than 32 bits); then (opcode, width); then netlist order.  A
+ * register D or write-port signal that is not an op output gets a COPY op on
+ * level 1, ordered after the netlist's own ops of the same key.  16-byte
+ * aligned buffers with an even n_lanes use two lanes per thread, otherwise one.
+ * The bound of every device wait and the test hook that withholds barrier
+ * arrivals are read from the environment at each call, as rteaal_sim_create
+ * reads them (RTEAAL_BARRIER_TIMEOUT_NS, RTEAAL_TEST_WITHHOLD_ARRIVAL).
  * cycles: host [n_lanes] per-lane cycle counts, or NULL to run uniform_cycles.
  * stim_mode: RTEAAL_STIM_HOLD or RTEAAL_STIM_XORSHIFT.  flags: RTEAAL_STEP_RESET.
  * Sizes beyond RTEAAL_STATIC_MAX_LANES lanes are rejected (E_INVALID).

@@ -8,13 +8,13 @@
  * by operation type and no operation-input-mask tensors.  Each cycle, for each
  * instance:
  *   1. drive the primary inputs (the testbench writes the layer input at the
- *      cycle boundary, Sec. 5.2 "Host-DUT Communication");
+ *      cycle boundary, Sec. 6.2 "Host-DUT Communication");
  *   2. evaluate every operation in the netlist's topological order,
  *      v = f_op(v[operands], params) masked to the op's width;
  *   3. at the edge: every register takes reset ? init : v[D] (masked to its
  *      width); memory write ports apply in port order;
  *   4. the next cycle reads the new register values.
- * Clock domains (optional; the paper's multi-clock reading, Sec. 5.2 "Multiple
+ * Clock domains (optional; the paper's multi-clock reading, Sec. 6.2 "Multiple
  * Clock Domains"): each instance counts t, the non-reset cycles completed since
  * its last reset cycle; at the edge of a non-reset cycle a register of domain
  * (period p, phase f) takes v[D] only if (t + f) mod p == 0, else it keeps its

@@ -1,6 +1,6 @@
 """Waveform events from per-cycle traces -- TEST INFRASTRUCTURE ONLY.
 
-Sec. 5.2 ("Waveform Generation"): record a signal's value when it changes,
+Sec. 6.2 ("Waveform Generation"): record a signal's value when it changes,
 detected by comparing each signal's value with its value in the previous
 cycle.  Given the probed values before a step and the end-of-cycle trace of
 the step, this lists every (cycle, probe, instance, value) whose value differs

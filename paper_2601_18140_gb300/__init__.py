@@ -73,7 +73,7 @@ class rteaal_sim_stats(ctypes.Structure):
     _fields_ = [("n_instances", _U32), ("n_lanes", _U32), ("device_bytes", _U64),
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
                 ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("lanes_per_thread", _U32),
-                ("activity", ctypes.c_int)]
+                ("activity", ctypes.c_int), ("last_span", _U32), ("last_grid", _U32)]
 
 
 class rteaal_tune_trial(ctypes.Structure):

@@ -44,8 +44,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     objs = []
     # the persistent-kernel variants are instantiated in their own units so that
     # they compile in parallel with the runtime
-    for f in ["rteaal.cu", "variants_v8.cu", "variants_v4.cu", "variants_v2_v1.cu", "variants_act.cu",
-              "lower.cpp", "inspect.cpp", "specialize.cpp"]:
+    units = ["rteaal.cu"] + sorted(f for f in os.listdir(CSRC) if f.startswith("variants_") and f.endswith(".cu")) + [
+        "lower.cpp", "inspect.cpp", "specialize.cpp"]
+    for f in units:
         src = os.path.join(CSRC, f)
         obj = os.path.join(BUILD, f + ".o")
         cmd = [nvcc] + ARCH + common + ["-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",

@@ -24,6 +24,7 @@ struct DDesign {
   const uint32_t* ext;        // operand row references of ops with > 3 operands
   const uint32_t* layer_off;  // [n_layers + 1]
   const uint32_t* layer_ext;  // [n_layers] first op with > 3 operands (they close each layer)
+  const uint32_t* layer_wide; // [n_layers] first op with <= 3 operands that is not narrow
   const uint32_t* reg_src;    // [n_regs] row reference of D
   const uint32_t* reg_ref;    // [n_regs] row reference of Q
   const uint32_t* reg_w;      // [n_regs]
@@ -233,13 +234,13 @@ __device__ __forceinline__ Lanes<V> alu_v(uint32_t ctl, const Lanes<V>& a, const
 #define RT_LANES(expr) _Pragma("unroll") for (int v = 0; v < V; v++) r.x[v] = (expr)
   switch (op) {
     case OP_COPY: RT_LANES(a.x[v]); break;
-    case OP_AND: RT_LANES(a.x[v] & b.x[v] & (ar == 3 ? c.x[v] : ~0ull)); break;
-    case OP_OR: RT_LANES(a.x[v] | b.x[v] | (ar == 3 ? c.x[v] : 0ull)); break;
-    case OP_XOR: RT_LANES(a.x[v] ^ b.x[v] ^ (ar == 3 ? c.x[v] : 0ull)); break;
+    case OP_AND: RT_LANES(a.x[v] & b.x[v]); if (ar == 3) RT_LANES(r.x[v] & c.x[v]); break;
+    case OP_OR: RT_LANES(a.x[v] | b.x[v]); if (ar == 3) RT_LANES(r.x[v] | c.x[v]); break;
+    case OP_XOR: RT_LANES(a.x[v] ^ b.x[v]); if (ar == 3) RT_LANES(r.x[v] ^ c.x[v]); break;
     case OP_NOT: RT_LANES(~a.x[v]); break;
-    case OP_ADD: RT_LANES(a.x[v] + b.x[v] + (ar == 3 ? c.x[v] : 0ull)); break;
+    case OP_ADD: RT_LANES(a.x[v] + b.x[v]); if (ar == 3) RT_LANES(r.x[v] + c.x[v]); break;
     case OP_SUB: RT_LANES(a.x[v] - b.x[v]); break;
-    case OP_MUL: RT_LANES(a.x[v] * b.x[v] * (ar == 3 ? c.x[v] : 1ull)); break;
+    case OP_MUL: RT_LANES(a.x[v] * b.x[v]); if (ar == 3) RT_LANES(r.x[v] * c.x[v]); break;
     case OP_SHL: RT_LANES(p0 >= 64u ? 0ull : a.x[v] << p0); break;
     case OP_SHR: RT_LANES(p0 >= 64u ? 0ull : a.x[v] >> p0); break;
     case OP_DSHL: RT_LANES(b.x[v] >= 64ull ? 0ull : a.x[v] << (uint32_t)b.x[v]); break;
@@ -498,13 +499,13 @@ __device__ __forceinline__ Lanes32<V> alu32_v(uint32_t ctl, const Lanes32<V>& a,
 #define RT_LANES(expr) _Pragma("unroll") for (int v = 0; v < V; v++) r.x[v] = (expr)
   switch (op) {
     case OP_COPY: RT_LANES(a.x[v]); break;
-    case OP_AND: RT_LANES(a.x[v] & b.x[v] & (ar == 3 ? c.x[v] : ~0u)); break;
-    case OP_OR: RT_LANES(a.x[v] | b.x[v] | (ar == 3 ? c.x[v] : 0u)); break;
-    case OP_XOR: RT_LANES(a.x[v] ^ b.x[v] ^ (ar == 3 ? c.x[v] : 0u)); break;
+    case OP_AND: RT_LANES(a.x[v] & b.x[v]); if (ar == 3) RT_LANES(r.x[v] & c.x[v]); break;
+    case OP_OR: RT_LANES(a.x[v] | b.x[v]); if (ar == 3) RT_LANES(r.x[v] | c.x[v]); break;
+    case OP_XOR: RT_LANES(a.x[v] ^ b.x[v]); if (ar == 3) RT_LANES(r.x[v] ^ c.x[v]); break;
     case OP_NOT: RT_LANES(~a.x[v]); break;
-    case OP_ADD: RT_LANES(a.x[v] + b.x[v] + (ar == 3 ? c.x[v] : 0u)); break;
+    case OP_ADD: RT_LANES(a.x[v] + b.x[v]); if (ar == 3) RT_LANES(r.x[v] + c.x[v]); break;
     case OP_SUB: RT_LANES(a.x[v] - b.x[v]); break;
-    case OP_MUL: RT_LANES(a.x[v] * b.x[v] * (ar == 3 ? c.x[v] : 1u)); break;
+    case OP_MUL: RT_LANES(a.x[v] * b.x[v]); if (ar == 3) RT_LANES(r.x[v] * c.x[v]); break;
     case OP_SHL: RT_LANES(p0 >= 32u ? 0u : a.x[v] << p0); break;
     case OP_SHR: RT_LANES(p0 >= 32u ? 0u : a.x[v] >> p0); break;
     case OP_DSHL: RT_LANES(b.x[v] >= 32u ? 0u : a.x[v] << b.x[v]); break;
@@ -739,6 +740,255 @@ __device__ __forceinline__ Lanes<V> apply(const DDesign& d, const DSim& s, const
   return r;
 }
 
+// ---- loads-first item bodies.  Every operand byte of an item is requested
+// before any of them is used, so a thread keeps the op's whole gather (OI =
+// LI . OIM for this s coordinate) in flight at once: the dependent chain of an
+// item is one memory round trip instead of one per operand.  Loads are issued
+// into packed words (Raw) and unpacked to lanes only afterwards.
+
+// Packed bytes of V consecutive lanes of one row: V << k bytes for class k.
+template <int V>
+struct Raw {
+  uint32_t w[2 * V];
+};
+
+// Issue the loads of V lanes of a row (lane is a multiple of V, so the packed
+// bytes are naturally aligned).  NARROW: the row's class is at most 2.
+template <int V, bool NARROW>
+__device__ __forceinline__ void raw_load(Raw<V>& r, const uint8_t* st, uint32_t ref, size_t np, uint32_t lane) {
+  const uint8_t* p = elem(st, ref, np, lane);
+  const uint32_t k = ref >> 30;
+  if constexpr (V == 8) {
+    if (k == 0) {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+      r.w[0] = t.x; r.w[1] = t.y;
+    } else if (k == 1) {
+      const uint4 t = *reinterpret_cast<const uint4*>(p);
+      r.w[0] = t.x; r.w[1] = t.y; r.w[2] = t.z; r.w[3] = t.w;
+    } else if (NARROW || k == 2) {
+      const uint4 t0 = reinterpret_cast<const uint4*>(p)[0];
+      const uint4 t1 = reinterpret_cast<const uint4*>(p)[1];
+      r.w[0] = t0.x; r.w[1] = t0.y; r.w[2] = t0.z; r.w[3] = t0.w;
+      r.w[4] = t1.x; r.w[5] = t1.y; r.w[6] = t1.z; r.w[7] = t1.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const uint4 t = reinterpret_cast<const uint4*>(p)[q];
+        r.w[4 * q] = t.x; r.w[4 * q + 1] = t.y; r.w[4 * q + 2] = t.z; r.w[4 * q + 3] = t.w;
+      }
+    }
+  } else if constexpr (V == 4) {
+    if (k == 0) {
+      r.w[0] = *reinterpret_cast<const uint32_t*>(p);
+    } else if (k == 1) {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+      r.w[0] = t.x; r.w[1] = t.y;
+    } else if (NARROW || k == 2) {
+      const uint4 t = *reinterpret_cast<const uint4*>(p);
+      r.w[0] = t.x; r.w[1] = t.y; r.w[2] = t.z; r.w[3] = t.w;
+    } else {
+      const uint4 t0 = reinterpret_cast<const uint4*>(p)[0];
+      const uint4 t1 = reinterpret_cast<const uint4*>(p)[1];
+      r.w[0] = t0.x; r.w[1] = t0.y; r.w[2] = t0.z; r.w[3] = t0.w;
+      r.w[4] = t1.x; r.w[5] = t1.y; r.w[6] = t1.z; r.w[7] = t1.w;
+    }
+  } else if constexpr (V == 2) {
+    if (k == 0) {
+      r.w[0] = *reinterpret_cast<const uint16_t*>(p);
+    } else if (k == 1) {
+      r.w[0] = *reinterpret_cast<const uint32_t*>(p);
+    } else if (NARROW || k == 2) {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+      r.w[0] = t.x; r.w[1] = t.y;
+    } else {
+      const uint4 t = *reinterpret_cast<const uint4*>(p);
+      r.w[0] = t.x; r.w[1] = t.y; r.w[2] = t.z; r.w[3] = t.w;
+    }
+  } else {
+    static_assert(V == 1, "lanes per thread: 1, 2, 4 or 8");
+    if (k == 0) {
+      r.w[0] = *p;
+    } else if (k == 1) {
+      r.w[0] = *reinterpret_cast<const uint16_t*>(p);
+    } else if (NARROW || k == 2) {
+      r.w[0] = *reinterpret_cast<const uint32_t*>(p);
+    } else {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+      r.w[0] = t.x; r.w[1] = t.y;
+    }
+  }
+}
+
+// Lanes of packed words of class k <= 2, zero-extended to 32 bits (byte v,
+// half v or word v of the packed bytes).
+template <int V>
+__device__ __forceinline__ Lanes32<V> unpack32(const Raw<V>& r, uint32_t k) {
+  Lanes32<V> x;
+  if (k == 0) {
+#pragma unroll
+    for (int v = 0; v < V; v++) x.x[v] = __byte_perm(r.w[v >> 2], 0u, 0x4440u + (v & 3));
+  } else if (k == 1) {
+#pragma unroll
+    for (int v = 0; v < V; v++) x.x[v] = (v & 1) ? r.w[v >> 1] >> 16 : r.w[v >> 1] & 0xFFFFu;
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; v++) x.x[v] = r.w[v];
+  }
+  return x;
+}
+
+// Lanes of packed words of any class, zero-extended to 64 bits.
+template <int V>
+__device__ __forceinline__ Lanes<V> unpack64(const Raw<V>& r, uint32_t k) {
+  Lanes<V> x;
+  if (k == 3) {
+#pragma unroll
+    for (int v = 0; v < V; v++) x.x[v] = (uint64_t)r.w[2 * v] | ((uint64_t)r.w[2 * v + 1] << 32);
+  } else {
+    const Lanes32<V> y = unpack32<V>(r, k);
+#pragma unroll
+    for (int v = 0; v < V; v++) x.x[v] = y.x[v];
+  }
+  return x;
+}
+
+// One narrow op (operands and result of at most 32 bits, <= 3 operands) for V lanes.
+template <int V>
+__device__ __forceinline__ void item_narrow(uint8_t* st, size_t np, uint32_t lane, const uint4& m, uint32_t dref,
+                                            uint32_t am) {
+  const uint32_t ar = (m.w >> 5) & 3u;
+  Raw<V> ra, rb, rc;
+  raw_load<V, true>(ra, st, m.x, np, lane);
+  if (ar >= 2) raw_load<V, true>(rb, st, m.y, np, lane);
+  if (ar >= 3) raw_load<V, true>(rc, st, m.z, np, lane);
+  const Lanes32<V> a = unpack32<V>(ra, m.x >> 30);
+  Lanes32<V> b, c;
+#pragma unroll
+  for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0u;
+  if (ar >= 2) b = unpack32<V>(rb, m.y >> 30);
+  if (ar >= 3) c = unpack32<V>(rc, m.z >> 30);
+  str32<V>(st, dref, np, lane, alu32_v<V>(m.w, a, b, c), am);
+}
+
+// One wide op (a result or operand above 32 bits, or MEMRD; <= 3 operands).
+template <int V>
+__device__ __forceinline__ void item_wide(const DDesign& d, const DSim& s, uint32_t lane, const uint4& m,
+                                          uint32_t dref, uint32_t am) {
+  const uint32_t ar = (m.w >> 5) & 3u;
+  Raw<V> ra, rb, rc;
+  raw_load<V, false>(ra, s.state, m.x, s.n_pad, lane);
+  if (ar >= 2) raw_load<V, false>(rb, s.state, m.y, s.n_pad, lane);
+  if (ar >= 3) raw_load<V, false>(rc, s.state, m.z, s.n_pad, lane);
+  const Lanes<V> a = unpack64<V>(ra, m.x >> 30);
+  Lanes<V> b, c;
+#pragma unroll
+  for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0ull;
+  if (ar >= 2) b = unpack64<V>(rb, m.y >> 30);
+  if (ar >= 3) c = unpack64<V>(rc, m.z >> 30);
+  str<V>(s.state, dref, s.n_pad, lane, apply<V>(d, s, m, a, b, c, lane), am);
+}
+
+// Row kinds of a layer, in their order: narrow (<= 3 operands), wide (<= 3
+// operands), extended (> 3 operands in the side array).
+enum : int { ROW_NARROW = 0, ROW_WIDE = 1, ROW_EXT = 2 };
+
+template <int V, int KIND>
+__device__ __forceinline__ void item_of_kind(const DDesign& d, const DSim& s, uint32_t lane, const uint4& m,
+                                             uint32_t dref, uint32_t am) {
+  if constexpr (KIND == ROW_NARROW) {
+    item_narrow<V>(s.state, s.n_pad, lane, m, dref, am);
+  } else if constexpr (KIND == ROW_WIDE) {
+    item_wide<V>(d, s, lane, m, dref, am);
+  } else {
+    if (m.w & CTL_NARROW)
+      str32<V>(s.state, dref, s.n_pad, lane, eval_ext32_v<V>(d, s, m, lane), am);
+    else
+      str<V>(s.state, dref, s.n_pad, lane, eval_ext_v<V>(d, s, m, lane), am);
+  }
+}
+
+// This thread's rows r, r + stride, ... below r_end of one kind (fixed lane
+// chunk), descriptors read from global memory one row ahead; returns the
+// thread's first row at or past r_end (where the next kind continues).
+template <int V, int KIND>
+__device__ __forceinline__ uint32_t walk_rows(const DDesign& d, const DSim& s, uint32_t op0, uint32_t r,
+                                              uint32_t r_end, uint32_t stride, uint32_t lane, uint32_t am) {
+  if (r >= r_end) return r;
+  uint4 m = __ldg(&d.meta[op0 + r]);
+  uint32_t dref = __ldg(&d.dst[op0 + r]);
+  for (;;) {
+    const uint32_t rn = r + stride;
+    uint4 mn = make_uint4(0, 0, 0, 0);
+    uint32_t dn = 0;
+    if (rn < r_end) {
+      mn = __ldg(&d.meta[op0 + rn]);
+      dn = __ldg(&d.dst[op0 + rn]);
+    }
+    item_of_kind<V, KIND>(d, s, lane, m, dref, am);
+    if (rn >= r_end) return rn;
+    r = rn;
+    m = mn;
+    dref = dn;
+  }
+}
+
+// The same with U rows in flight per thread: the U rows' descriptors, then
+// all their operand loads, then their results (more memory-level parallelism
+// per thread at the price of registers).
+template <int V, int KIND, int U>
+__device__ __forceinline__ uint32_t walk_rows_u(const DDesign& d, const DSim& s, uint32_t op0, uint32_t r,
+                                                uint32_t r_end, uint32_t stride, uint32_t lane, uint32_t am) {
+  if constexpr (U == 1 || KIND == ROW_EXT) {
+    return walk_rows<V, KIND>(d, s, op0, r, r_end, stride, lane, am);
+  } else {
+    if (r >= r_end) return r;
+    // the thread's first row at or past r_end: the next kind starts there
+    const uint32_t next = r + (r_end - r + stride - 1u) / stride * stride;
+    for (; r < r_end; r += U * stride) {
+      uint4 m[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        ok[u] = r + u * stride < r_end;
+        m[u] = ok[u] ? __ldg(&d.meta[op0 + r + u * stride]) : make_uint4(0, 0, 0, 0);
+      }
+      Raw<V> ra[U], rb[U], rc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (!ok[u]) continue;
+        const uint32_t ar = (m[u].w >> 5) & 3u;
+        raw_load<V, KIND == ROW_NARROW>(ra[u], s.state, m[u].x, s.n_pad, lane);
+        if (ar >= 2) raw_load<V, KIND == ROW_NARROW>(rb[u], s.state, m[u].y, s.n_pad, lane);
+        if (ar >= 3) raw_load<V, KIND == ROW_NARROW>(rc[u], s.state, m[u].z, s.n_pad, lane);
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (!ok[u]) continue;
+        const uint32_t ar = (m[u].w >> 5) & 3u;
+        const uint32_t dref = __ldg(&d.dst[op0 + r + u * stride]);
+        if constexpr (KIND == ROW_NARROW) {
+          const Lanes32<V> a = unpack32<V>(ra[u], m[u].x >> 30);
+          Lanes32<V> b, c;
+#pragma unroll
+          for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0u;
+          if (ar >= 2) b = unpack32<V>(rb[u], m[u].y >> 30);
+          if (ar >= 3) c = unpack32<V>(rc[u], m[u].z >> 30);
+          str32<V>(s.state, dref, s.n_pad, lane, alu32_v<V>(m[u].w, a, b, c), am);
+        } else {
+          const Lanes<V> a = unpack64<V>(ra[u], m[u].x >> 30);
+          Lanes<V> b, c;
+#pragma unroll
+          for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0ull;
+          if (ar >= 2) b = unpack64<V>(rb[u], m[u].y >> 30);
+          if (ar >= 3) c = unpack64<V>(rc[u], m[u].z >> 30);
+          str<V>(s.state, dref, s.n_pad, lane, apply<V>(d, s, m[u], a, b, c, lane), am);
+        }
+      }
+    }
+    return next;
+  }
+}
+
 // Generic mapping (more lane chunks than threads): kept out of line so that it
 // does not cost the fixed-mapping hot loop any registers.
 template <int V, int U>
@@ -898,8 +1148,19 @@ __device__ __forceinline__ void eval_layer(const DDesign& d, const DSim& s, uint
                                            const ItemSpace& is, uint32_t cyc) {
   const uint32_t o0 = __ldg(&d.layer_off[L]), e = __ldg(&d.layer_ext[L]);
   const uint32_t o1 = __ldg(&d.layer_off[L + 1]);
-  eval_ops<V, U>(d, s, o0, e - o0, is, cyc);
-  if (e < o1) eval_ext_rows<V>(d, s, e, o1 - e, is, cyc);
+  if (!is.row_stride) {  // generic mapping
+    eval_ops<V, U>(d, s, o0, e - o0, is, cyc);
+    if (e < o1) eval_ext_rows<V>(d, s, e, o1 - e, is, cyc);
+    return;
+  }
+  // fixed lane chunk: one row sequence over the layer, kind by kind
+  if (is.row0 == NO_ROW || is.row0 >= o1 - o0) return;
+  const uint32_t am = act_mask<V>(s, is.lane, cyc);
+  if (!am) return;
+  const uint32_t nw = __ldg(&d.layer_wide[L]) - o0;
+  uint32_t r = walk_rows_u<V, ROW_NARROW, U>(d, s, o0, is.row0, nw, is.row_stride, is.lane, am);
+  r = walk_rows_u<V, ROW_WIDE, U>(d, s, o0, r, e - o0, is.row_stride, is.lane, am);
+  walk_rows<V, ROW_EXT>(d, s, o0, r, o1 - o0, is.row_stride, is.lane, am);
 }
 
 // ---- activity-aware evaluation (the cascade-level "skip what did not change"

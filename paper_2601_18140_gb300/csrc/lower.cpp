@@ -280,6 +280,7 @@ void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
     uint32_t level, code, width, p0, p1, src_sig;  // src_sig: netlist op index, or copy source
     bool is_copy;
     bool is_ext;  // more than three operands: operand rows in the side array
+    bool wide;    // result or an operand wider than 32 bits, or MEMRD (see CTL_NARROW)
   };
   std::vector<LOp> ops;
   ops.reserve(nl.no + 16);
@@ -293,7 +294,7 @@ void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
     lop_of[k] = (uint32_t)ops.size();
     const uint32_t code = head_of[k] != NONE ? (uint32_t)OP_MUXCHAIN : nl.code[k];
     op_args(k, tmp);
-    ops.push_back({level[opb + k], code, nl.width[k], nl.p0[k], nl.p1[k], k, false, tmp.size() > 3});
+    ops.push_back({level[opb + k], code, nl.width[k], nl.p0[k], nl.p1[k], k, false, tmp.size() > 3, false});
   }
   std::unordered_map<uint32_t, uint32_t> copy_of;  // pool signal -> lowered op index
   std::vector<uint8_t> sig_w(nsig);
@@ -306,7 +307,7 @@ void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
     auto it = copy_of.find(sig);
     if (it != copy_of.end()) return it->second;
     const uint32_t idx = (uint32_t)ops.size();
-    ops.push_back({1u, OP_COPY, sig_w[sig], 0u, 0u, sig, true, false});
+    ops.push_back({1u, OP_COPY, sig_w[sig], 0u, 0u, sig, true, false, false});
     copy_of[sig] = idx;
     return idx;
   };
@@ -316,17 +317,31 @@ void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
   for (uint32_t q = 0; q < nl.nw; q++)
     for (int t = 0; t < 3; t++) wp_lop[3ull * q + t] = edge_src(nl.wport[4ull * q + 1 + t]);
   L.n_copies = (uint32_t)copy_of.size();
+  // narrow ops (CTL_NARROW): the result and every operand fit 32 bits
+  for (LOp& o : ops) {
+    bool narrow = o.width <= 32 && o.code != OP_MEMRD && (o.code != OP_BITS || o.p0 < 32) &&
+                  (o.code != OP_ANDR || o.p0 <= 32);
+    if (o.is_copy) {
+      narrow = narrow && sig_w[o.src_sig] <= 32;
+    } else {
+      op_args(o.src_sig, tmp);
+      for (uint32_t x : tmp) narrow = narrow && sig_w[x] <= 32;
+    }
+    o.wide = !narrow;
+  }
 
-  // 3. order: by level, then ops with at most three operands before the others
-  //    (so kernels walk each kind with its own loop), then (opcode, width) --
-  //    the N rank swizzled above S -- then original order.  Position = slot
-  //    offset (S coordinates implicit).
+  // 3. order: by level, then ops with at most three operands before the others,
+  //    and among those the narrow ones before the wide ones (so kernels walk
+  //    each kind with its own loop), then (opcode, width) -- the N rank
+  //    swizzled above S -- then original order.  Position = slot offset (S
+  //    coordinates implicit).
   std::vector<uint32_t> order(ops.size());
   std::iota(order.begin(), order.end(), 0u);
   std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
     const LOp &a = ops[x], &b = ops[y];
     if (a.level != b.level) return a.level < b.level;
     if (a.is_ext != b.is_ext) return b.is_ext;
+    if (!a.is_ext && a.wide != b.wide) return b.wide;
     if (a.code != b.code) return a.code < b.code;
     return a.width < b.width;
   });
@@ -376,6 +391,7 @@ void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
   for (const LOp& o : ops) n_layers = std::max(n_layers, o.level);
   L.layer_off.assign(n_layers + 1, 0);
   L.layer_ext.assign(n_layers, NONE);
+  L.layer_wide.assign(n_layers, NONE);
   L.group_off.clear();
   for (uint32_t i = 0; i < order.size(); i++) {
     const LOp& o = ops[order[i]];
@@ -391,10 +407,7 @@ void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
     L.lowered_operands += a.size();
     OpMeta m{};
     uint32_t ctl = code | (o.width << 8) | (o.p0 << 16) | (o.p1 << 24);
-    bool narrow = o.width <= 32 && code != OP_MEMRD &&
-                  (code != OP_BITS || o.p0 < 32) && (code != OP_ANDR || o.p0 <= 32);
-    for (uint32_t r : a) narrow = narrow && (r >> 30) <= 2u;  // operand rows of at most 32 bits
-    if (narrow) ctl |= CTL_NARROW;
+    if (!o.wide) ctl |= CTL_NARROW;
     if (a.size() <= 3) {
       m.a = a[0];
       m.b = a.size() > 1 ? a[1] : a[0];
@@ -410,6 +423,7 @@ void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
     m.ctl = ctl;
     L.meta[i] = m;
     if ((ctl & CTL_EXT) && L.layer_ext[o.level - 1] == NONE) L.layer_ext[o.level - 1] = i;
+    if (!(ctl & CTL_EXT) && o.wide && L.layer_wide[o.level - 1] == NONE) L.layer_wide[o.level - 1] = i;
     L.layer_off[o.level] = i + 1;  // running end of the layer
     if (i == 0 || ops[order[i - 1]].level != o.level || ops[order[i - 1]].code != o.code ||
         ops[order[i - 1]].width != o.width)
@@ -422,8 +436,10 @@ void lower_netlist(const Netlist& nl, Lowered& L, bool fuse_mux_chains) {
   std::vector<uint32_t> ends(L.layer_off.begin() + 1, L.layer_off.end());
   L.layer_off[0] = 0;
   for (uint32_t l = 0; l < n_layers; l++) L.layer_off[l + 1] = ends[l];
-  for (uint32_t l = 0; l < n_layers; l++)
+  for (uint32_t l = 0; l < n_layers; l++) {
     if (L.layer_ext[l] == NONE) L.layer_ext[l] = L.layer_off[l + 1];
+    if (L.layer_wide[l] == NONE) L.layer_wide[l] = L.layer_ext[l];
+  }
   L.max_layer_ops = 0;
   for (uint32_t l = 0; l < n_layers; l++)
     L.max_layer_ops = std::max(L.max_layer_ops, L.layer_off[l + 1] - L.layer_off[l]);

@@ -1,10 +1,10 @@
 // lower.hpp -- netlist parsing and the netlist -> device-tensor lowering.
 //
-// The lowering realises the paper's compile flow (Sec. 5.1, Fig. "compiler"):
+// The lowering realises the paper's compile flow (Sec. 6.1, Fig. "compiler"):
 // levelisation by topological sort (Sec. 4.2), the OIM built per layer with
 // operations of one type grouped together (the swizzled [I, N, S, O, R] format
-// of the NU kernel, Sec. 4.4 / Fig. "opt-space:format"c), and identity
-// elision by assigning every signal one global slot (Sec. 4.3, Sec. 5.1).
+// of the NU kernel, Sec. 5.2 / Fig. "opt-space:format"c), and identity
+// elision by assigning every signal one global slot (Sec. 4.3, Sec. 6.1).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -73,6 +73,8 @@ struct Lowered {
   std::vector<uint32_t> layer_off;       // [n_layers + 1] into meta
   std::vector<uint32_t> layer_ext;       // [n_layers] first op of the layer with > 3 operands
                                          //   (they close the layer), or the layer's end
+  std::vector<uint32_t> layer_wide;      // [n_layers] first op of the layer with <= 3 operands
+                                         //   that is not narrow (narrow ones come first), or layer_ext
   std::vector<uint32_t> group_off;       // [n_groups + 1] into meta ((layer, opcode, width) runs)
   std::vector<uint32_t> reg_src;         // [n_regs] row reference of D (always an op row)
   std::vector<uint32_t> reg_width;       // [n_regs]

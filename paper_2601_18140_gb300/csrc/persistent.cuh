@@ -58,7 +58,8 @@ struct GridArgs {
   uint32_t expected;      // arrivals that complete a barrier (= gridDim.x)
   uint64_t timeout_ns;    // bounded wait per barrier
   uint32_t ncyc;
-  FastDiv tpo;            // n_pad / V
+  FastDiv tpo;            // lane span / V
+  uint32_t stage_cap;     // descriptors a CTA can stage in shared memory (0: none)
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
@@ -102,19 +103,155 @@ __device__ __forceinline__ bool grid_sync(const GridArgs& g, uint32_t* err, int*
   return *sh_ok != 0;
 }
 
+// ---- op descriptors staged in shared memory (the OIM of one layer for the
+// rows this CTA evaluates), copied with cp.async while the CTA waits at the
+// grid barrier before the layer, so that an item reads its descriptor from
+// shared memory instead of carrying a global load in its chain.
+//
+// In the fixed mapping thread t keeps lane chunk t mod tpo and walks rows
+// row0 = t / tpo, row0 + per, row0 + 2 per, ... (per = threads / tpo).  The
+// CTA's threads have row0 in [R0, R0 + span), so at step i they need the
+// contiguous rows [R0 + i per, R0 + i per + span): entry i * span + (row0 - R0).
+struct Stage {
+  uint32_t R0, span, per;  // span = 0: the CTA stages nothing (no rows, generic mapping)
+};
+
+__device__ __forceinline__ Stage stage_of_cta(const FastDiv& tpo) {
+  Stage st{0, 0, 0};
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  if (nthreads < tpo.d) return st;  // generic mapping
+  const uint32_t per = fdiv(tpo, nthreads), valid = per * tpo.d;
+  const uint32_t t0 = blockIdx.x * blockDim.x;
+  if (t0 >= valid) return st;
+  const uint32_t t1 = min(t0 + blockDim.x, valid) - 1u;
+  st.R0 = fdiv(tpo, t0);
+  st.span = fdiv(tpo, t1) - st.R0 + 1u;
+  st.per = per;
+  return st;
+}
+
+// Descriptors the CTA needs for a layer of n rows (0 if it has none).
+__device__ __forceinline__ uint32_t stage_rows(const Stage& st, uint32_t n) {
+  if (!st.span || n <= st.R0) return 0;
+  return (n - st.R0 + st.per - 1u) / st.per * st.span;
+}
+
+__device__ __forceinline__ void cp_async16(void* sm, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sm)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sm, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(sm)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Issue the copies of layer L's descriptors for this CTA (every thread takes a share).
+__device__ __forceinline__ void stage_layer(const DDesign& d, uint32_t L, const Stage& st, uint32_t cap,
+                                            uint4* sm_meta, uint32_t* sm_dst) {
+  const uint32_t o0 = __ldg(&d.layer_off[L]), n = __ldg(&d.layer_off[L + 1]) - o0;
+  const uint32_t total = stage_rows(st, n);
+  if (total > cap) return;  // does not fit: the layer reads its descriptors from global memory
+  for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const uint32_t i = idx / st.span, j = idx - i * st.span;
+    const uint32_t r = st.R0 + i * st.per + j;
+    if (r < n) {
+      cp_async16(&sm_meta[idx], &d.meta[o0 + r]);
+      cp_async4(&sm_dst[idx], &d.dst[o0 + r]);
+    }
+  }
+}
+
+// Grid barrier that stages the next phase's descriptors while it waits: the
+// copies start once every thread of the CTA is done with the current ones.
+template <typename F>
+__device__ __forceinline__ bool grid_sync_staging(const GridArgs& g, uint32_t* err, int* sh_ok, F&& stage) {
+  __syncthreads();
+  stage();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const uint32_t my = ld_acquire(g.gen);
+    __threadfence();
+    if (atomicAdd(g.count, 1u) == g.expected - 1u) {
+      atomicExch(g.count, 0u);
+      __threadfence();
+      atomicAdd(g.gen, 1u);
+    } else {
+      const uint64_t t0 = globaltimer();
+      while (ld_acquire(g.gen) == my) {
+        if (ld_acquire(err) != 0u) { ok = 0; break; }
+        if (globaltimer() - t0 > g.timeout_ns) { atomicOr(err, 1u); ok = 0; break; }
+        __nanosleep(100);
+      }
+    }
+    if (ld_acquire(err) != 0u) ok = 0;
+    __threadfence();
+    *sh_ok = ok;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  return *sh_ok != 0;
+}
+
+// This thread's rows of one kind with descriptors from shared memory (entry
+// i * span + j of row row0 + i * per); returns the next (i, row).
+template <int V, int KIND>
+__device__ __forceinline__ void walk_staged(const DDesign& d, const DSim& s, uint32_t& i, uint32_t& r,
+                                            uint32_t r_end, const Stage& st, uint32_t j, uint32_t lane,
+                                            uint32_t am, const uint4* sm_meta, const uint32_t* sm_dst) {
+  for (; r < r_end; r += st.per, i++) {
+    const uint32_t idx = i * st.span + j;
+    item_of_kind<V, KIND>(d, s, lane, sm_meta[idx], sm_dst[idx], am);
+  }
+}
+
+// (a2) one layer with staged descriptors; falls back to eval_layer where the
+// CTA could not stage them.
+template <int V, int U>
+__device__ __forceinline__ void eval_layer_staged(const DDesign& d, const DSim& s, uint32_t L, const ItemSpace& is,
+                                                  uint32_t cyc, const Stage& st, uint32_t cap,
+                                                  const uint4* sm_meta, const uint32_t* sm_dst) {
+  const uint32_t o0 = __ldg(&d.layer_off[L]), n = __ldg(&d.layer_off[L + 1]) - o0;
+  const uint32_t total = stage_rows(st, n);
+  if (!is.row_stride || total == 0 || total > cap || U > 1) {
+    eval_layer<V, U>(d, s, L, is, cyc);
+    return;
+  }
+  if (is.row0 == NO_ROW || is.row0 >= n) return;
+  const uint32_t am = act_mask<V>(s, is.lane, cyc);
+  if (!am) return;
+  const uint32_t nw = __ldg(&d.layer_wide[L]) - o0, ne = __ldg(&d.layer_ext[L]) - o0;
+  const uint32_t j = is.row0 - st.R0;
+  uint32_t i = 0, r = is.row0;
+  walk_staged<V, ROW_NARROW>(d, s, i, r, nw, st, j, is.lane, am, sm_meta, sm_dst);
+  walk_staged<V, ROW_WIDE>(d, s, i, r, ne, st, j, is.lane, am, sm_meta, sm_dst);
+  walk_staged<V, ROW_EXT>(d, s, i, r, n, st, j, is.lane, am, sm_meta, sm_dst);
+}
+
 template <int V, int U, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs g) {
   __shared__ int sh_ok;
+  extern __shared__ __align__(16) uint4 sm_stage[];  // [stage_cap] descriptors, then [stage_cap] output rows
+  uint4* sm_meta = sm_stage;
+  uint32_t* sm_dst = reinterpret_cast<uint32_t*>(sm_stage + g.stage_cap);
   // the work mapping is recomputed per phase (a few integer ops) instead of
   // being held in registers across every barrier
 #define RT_SPACE make_space<V>(g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x)
+#define RT_STAGE(L)                                                                            \
+  [&] {                                                                                       \
+    if (g.stage_cap && (L) < d.n_layers) stage_layer(d, (L), stage_of_cta(g.tpo), g.stage_cap, sm_meta, sm_dst); \
+  }
   for (uint32_t c = 0; c < g.ncyc; c++) {
     stim_items<V>(d, s, RT_SPACE, c);
-    if (!grid_sync(g, s.err, &sh_ok)) return;
+    if (!grid_sync_staging(g, s.err, &sh_ok, RT_STAGE(0u))) return;
     for (uint32_t L = 0; L < d.n_layers; L++) {
-      eval_layer<V, U>(d, s, L, RT_SPACE, c);
-      if (!grid_sync(g, s.err, &sh_ok)) return;
+      if (g.stage_cap)
+        eval_layer_staged<V, U>(d, s, L, RT_SPACE, c, stage_of_cta(g.tpo), g.stage_cap, sm_meta, sm_dst);
+      else
+        eval_layer<V, U>(d, s, L, RT_SPACE, c);
+      if (!grid_sync_staging(g, s.err, &sh_ok, RT_STAGE(L + 1u))) return;
     }
+#undef RT_STAGE
     commit_items<V>(d, s, RT_SPACE, c);
     if (!grid_sync(g, s.err, &sh_ok)) return;
     if (s.n_probe) {
@@ -180,9 +317,16 @@ struct ActVariantTable {
 #define RT_VARIANT(V, U, T, B) {V, U, T, B, (const void*)k_tile<V, U, T, B>, (const void*)k_grid<V, U, T, B>}
 #define RT_ACT_VARIANT(V, T, B) {V, T, B, (const void*)k_grid_act<V, T, B>}
 
-VariantTable variants_v8();     // variants_v8.cu
-VariantTable variants_v4();     // variants_v4.cu
-VariantTable variants_v2_v1();  // variants_v2_v1.cu
-ActVariantTable act_variants(); // variants_act.cu
+// one translation unit per table (variants_<name>.cu), compiled in parallel
+VariantTable variants_v8a();
+VariantTable variants_v8b();
+VariantTable variants_v8c();
+VariantTable variants_v4a();
+VariantTable variants_v4b();
+VariantTable variants_v4c();
+VariantTable variants_v2();
+VariantTable variants_v1();
+ActVariantTable variants_act_a();
+ActVariantTable variants_act_b();
 
 }  // namespace rteaal

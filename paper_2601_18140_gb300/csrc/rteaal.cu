@@ -273,6 +273,9 @@ struct rteaal_sim {
   uint64_t barrier_timeout_ns = 2000000000ull;
   uint32_t barrier_extra = 0;        // test hook: arrivals withheld from every grid barrier
   uint32_t stream_chunk = 0;         // STREAM: lanes per item
+  uint32_t stage_cap = 0;            // GRID: descriptors a CTA stages in shared memory
+  uint32_t last_span = 0;            // lanes the last step visited
+  uint32_t last_grid = 0;            // CTAs of the last GRID launch
   // activity-aware evaluation (GRID only)
   bool activity = false;
   uint8_t* act = nullptr;            // [n_slots][act_chunks] 8-bit change stamps
@@ -328,15 +331,25 @@ DSim dsim(const rteaal_sim* s) {
   return x;
 }
 
+// Which bounded device waits gave up (error word bits): 1 grid barrier,
+// 2 stream ring barrier, 4 stream drain of its own copies after a timeout.
+std::string wait_kind(uint32_t e) {
+  std::string k;
+  if (e & 1u) k += "grid barrier";
+  if (e & 2u) k += k.empty() ? "stream ring barrier" : ", stream ring barrier";
+  if (e & 4u) k += k.empty() ? "stream drain of copies in flight" : ", stream drain of copies in flight";
+  return k.empty() ? "unknown wait" : k;
+}
+
 void check_pending(rteaal_sim* s) {
   if (!s->pending) return;
   cudaError_t q = cudaEventQuery(s->done);
   if (q == cudaErrorNotReady) return;
   if (q != cudaSuccess) throw Error(RTEAAL_E_CUDA, std::string("previous step: ") + cudaGetErrorString(q));
   s->pending = false;
-  if (*s->err_host) {
+  if (const uint32_t e = *s->err_host) {
     *s->err_host = 0;
-    throw Error(RTEAAL_E_TIMEOUT, "a grid barrier wait timed out in a previous step");
+    throw Error(RTEAAL_E_TIMEOUT, std::string("a device wait timed out in a previous step (") + wait_kind(e) + ")");
   }
 }
 
@@ -345,17 +358,17 @@ void sync_sim(rteaal_sim* s, cudaStream_t st) {
   if (s->pending) {
     CK(cudaEventSynchronize(s->done));
     s->pending = false;
-    if (*s->err_host) {
+    if (const uint32_t e = *s->err_host) {
       *s->err_host = 0;
-      throw Error(RTEAAL_E_TIMEOUT, "a grid barrier wait timed out");
+      throw Error(RTEAAL_E_TIMEOUT, std::string("a device wait timed out (") + wait_kind(e) + ")");
     }
   }
 }
 
 template <int V>
 void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32_t c,
-                        const uint32_t* cyc_dev, cudaStream_t st, int n_sms) {
-  const FastDiv tpo = make_fastdiv(s->n_pad / V);
+                        const uint32_t* cyc_dev, cudaStream_t st, int n_sms, uint32_t span) {
+  const FastDiv tpo = make_fastdiv(span / V);
   const uint32_t threads = 256;
   auto blocks_for = [&](uint64_t items, uint32_t per_thread) {
     uint64_t b = (items + (uint64_t)threads * per_thread - 1) / ((uint64_t)threads * per_thread);
@@ -388,7 +401,9 @@ void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32
 const std::vector<Variant>& all_variants() {
   static const std::vector<Variant> all = [] {
     std::vector<Variant> v;
-    for (const VariantTable& t : {variants_v8(), variants_v4(), variants_v2_v1()}) v.insert(v.end(), t.v, t.v + t.n);
+    for (const VariantTable& t : {variants_v8a(), variants_v8b(), variants_v8c(), variants_v4a(), variants_v4b(),
+                                  variants_v4c(), variants_v2(), variants_v1()})
+      v.insert(v.end(), t.v, t.v + t.n);
     return v;
   }();
   return all;
@@ -396,8 +411,9 @@ const std::vector<Variant>& all_variants() {
 
 const std::vector<ActVariant>& all_act_variants() {
   static const std::vector<ActVariant> all = [] {
-    const ActVariantTable t = act_variants();
-    return std::vector<ActVariant>(t.v, t.v + t.n);
+    std::vector<ActVariant> v;
+    for (const ActVariantTable& t : {variants_act_a(), variants_act_b()}) v.insert(v.end(), t.v, t.v + t.n);
+    return v;
   }();
   return all;
 }
@@ -425,6 +441,36 @@ const Variant* find_variant(int V, uint32_t U, uint32_t threads, uint32_t minb =
     if (v.V == V && (uint32_t)v.U == U && (uint32_t)v.maxt >= threads && (!best || v.maxt < best->maxt))
       best = &v;
   return best;
+}
+
+// Lanes a launch visits: every lane up to the last one with cycles left in this
+// step, rounded up to `gran` lanes (whole warps of V-lane chunks) and at most
+// n_pad.  Lanes are ordered by expected cycles, so finished instances gather at
+// the end and leave the span: the work per cycle follows the live instances
+// (Alg. 1's iterative rank over cycles, per instance).  Lanes beyond the span
+// have no cycle this step, so leaving them out changes no result.
+uint32_t live_span(const rteaal_sim* s, const std::vector<uint32_t>& lane_budget, uint32_t gran) {
+  uint64_t live = s->n_user;
+  if (!lane_budget.empty()) {
+    live = 0;
+    for (size_t l = lane_budget.size(); l > 0; l--)
+      if (lane_budget[l - 1]) {
+        live = l;
+        break;
+      }
+  }
+  const uint64_t span = (live + gran - 1) / gran * gran;
+  return (uint32_t)std::max<uint64_t>(std::min<uint64_t>(span, s->n_pad), std::min<uint64_t>(gran, s->n_pad));
+}
+
+// Persistent grid for a lane span: the configured grid, capped at what the
+// widest phase over the span can occupy.
+uint32_t grid_for_span(const rteaal_sim* s, uint32_t span, uint32_t V) {
+  const Lowered& L = s->design->L;
+  const uint64_t widest = std::max<uint64_t>(
+      {(uint64_t)L.max_layer_ops, L.reg_src.size() + (L.mem_info.size() / 4 - 1), (uint64_t)L.in_width.size(), 1});
+  const uint64_t items = widest * (span / V);
+  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(s->grid, (items + s->threads - 1) / s->threads));
 }
 
 void ensure_staging(rteaal_sim* s, size_t bytes) {
@@ -481,6 +527,7 @@ RT_EXPORT int rteaal_design_load(const void* netlist, size_t nbytes, const rteaa
       dd.ext = d->upload(L.ext_args);
       dd.layer_off = d->upload(L.layer_off);
       dd.layer_ext = d->upload(L.layer_ext);
+      dd.layer_wide = d->upload(L.layer_wide);
       dd.reg_src = d->upload(L.reg_src);
       dd.reg_w = d->upload(L.reg_width);
       dd.reg_init = d->upload(L.reg_init);
@@ -579,6 +626,25 @@ void ensure_specialized(rteaal_design* d) {
                            std::chrono::steady_clock::now() - t0).count();
 }
 
+// Shared-memory descriptor staging of the GRID form (persistent.cuh): a CTA
+// stages, per layer, the descriptors of the rows its threads evaluate --
+// at most ceil(layer rows / per) steps of span rows, per = threads / lane
+// chunks and span <= ceil(CTA threads / lane chunks) + 1.  Capped so that the
+// CTAs of an SM share at most ~200 KB; layers beyond the cap read their
+// descriptors from global memory.
+constexpr uint32_t kStageBytes = 20;       // 16-byte descriptor + 4-byte output row
+constexpr uint32_t kStageMax = 2304;       // at most 46 KB per CTA (no opt-in needed)
+uint32_t stage_capacity(uint32_t chunks, uint32_t grid, uint32_t threads, uint32_t max_layer_ops,
+                        uint32_t ctas_per_sm) {
+  const uint64_t nthreads = (uint64_t)grid * threads;
+  if (chunks == 0 || nthreads < chunks || max_layer_ops == 0) return 0;
+  const uint64_t per = nthreads / chunks;
+  const uint64_t span = (threads + chunks - 1) / chunks + 1;
+  const uint64_t rows = (max_layer_ops + per - 1) / per * span;
+  const uint64_t budget = 200ull * 1024 / std::max<uint32_t>(ctas_per_sm, 1) / kStageBytes;
+  return (uint32_t)std::min<uint64_t>({rows, kStageMax, budget});
+}
+
 // Validate and apply a launch configuration (never changes results).
 void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
                uint32_t unroll, uint32_t lanes_per_thread) {
@@ -615,7 +681,7 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     if (!V) V = 1;
   }
   require(span % (uint32_t)V == 0, "lanes_per_thread must divide the lanes of a tile / the padded lane count");
-  uint32_t grid = 0;
+  uint32_t grid = 0, stage = 0;
   if (kernel == RTEAAL_KERNEL_LAYER || kernel == RTEAAL_KERNEL_LAYER_GRAPH) threads = 256;
   if (kernel == RTEAAL_KERNEL_SPECIALIZED) {
     ensure_specialized(s->design_mut);
@@ -681,11 +747,18 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
       const uint64_t widest = std::max<uint64_t>(L.max_layer_ops, L.reg_src.size() + (L.mem_info.size() / 4 - 1));
       const uint64_t items = std::max<uint64_t>(widest, 1) * (s->n_pad / V);
       grid = (uint32_t)std::min<uint64_t>(grid, (items + threads - 1) / threads);
+      stage = stage_capacity(s->n_pad / (uint32_t)V, grid, threads, L.max_layer_ops, ctas_per_sm);
+      if (stage) {  // the staged descriptors must not lower the residency the grid counts on
+        int occ2 = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, v->grid, (int)threads, stage * kStageBytes));
+        if ((uint32_t)occ2 < ctas_per_sm) stage = 0;
+      }
     }
   } else {
     ctas_per_sm = 0;
   }
   s->kernel = kernel;
+  s->stage_cap = stage;
   s->tile_lanes = tile_lanes;
   s->threads = threads;
   s->ctas_per_sm = ctas_per_sm;
@@ -875,6 +948,8 @@ RT_EXPORT int rteaal_sim_info(const rteaal_sim* s, rteaal_sim_stats* o) {
     o->grid = s->grid;
     o->lanes_per_thread = (uint32_t)s->V;
     o->activity = s->activity ? 1 : 0;
+    o->last_span = s->last_span;
+    o->last_grid = s->last_grid;
   });
 }
 
@@ -1111,11 +1186,16 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
     }
 
     const uint32_t U = s->unroll;
+    // lanes this step visits (STREAM: whole chunks; the others: whole warps)
+    const uint32_t span = live_span(s, hb, s->kernel == RTEAAL_KERNEL_STREAM ? s->stream_chunk
+                                           : s->kernel == RTEAAL_KERNEL_SPECIALIZED ? kSpecThreads
+                                           : 32u * (uint32_t)s->V);
+    s->last_span = span;
     if (s->kernel == RTEAAL_KERNEL_LAYER) {
       for (uint64_t c = 0; c < max_cyc; c++) {
-        if (s->V == 4) launch_layer_cycle<4>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
-        else if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
-        else launch_layer_cycle<1>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms);
+        if (s->V == 4) launch_layer_cycle<4>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms, span);
+        else if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms, span);
+        else launch_layer_cycle<1>(s, D->dd, ds, (uint32_t)c, nullptr, st, D->n_sms, span);
       }
       CK(cudaGetLastError());
     } else if (s->kernel == RTEAAL_KERNEL_LAYER_GRAPH) {
@@ -1127,9 +1207,9 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       cudaGraphExec_t ge = nullptr;
       try {
         CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        if (s->V == 4) launch_layer_cycle<4>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
-        else if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
-        else launch_layer_cycle<1>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms);
+        if (s->V == 4) launch_layer_cycle<4>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms, span);
+        else if (s->V == 2) launch_layer_cycle<2>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms, span);
+        else launch_layer_cycle<1>(s, D->dd, ds, 0u, cyc_dev, cap, D->n_sms, span);
         k_tick<<<1, 1, 0, cap>>>(cyc_dev);
         CK(cudaStreamEndCapture(cap, &g));
         CK(cudaGraphInstantiate(&ge, g, 0));
@@ -1158,7 +1238,8 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       uint32_t a_np = s->n_pad, a_nu = s->n_user, a_uni = ds.uniform;
       int a_mode = ds.stim_mode, a_reset = ds.reset;
       void* args[] = {&a_st, &a_mem, &a_xs, &a_stim, &a_budget, &a_rl, &a_uol, &a_np, &a_nu, &a_uni, &a_mode, &a_reset};
-      CK(cudaLaunchKernel((const void*)D->spec_kernel, dim3(s->grid), dim3(kSpecThreads), args, 0, st));
+      CK(cudaLaunchKernel((const void*)D->spec_kernel, dim3((span + kSpecThreads - 1) / kSpecThreads),
+                          dim3(kSpecThreads), args, 0, st));
       CK(cudaGetLastError());
     } else if (s->kernel == RTEAAL_KERNEL_TILE) {
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
@@ -1195,8 +1276,8 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       ga.expected = s->grid + s->barrier_extra;
       ga.timeout_ns = s->barrier_timeout_ns;
       ga.ncyc = (uint32_t)max_cyc;
-      ga.tpo = make_fastdiv((uint32_t)(np / STREAM_V));
-      StreamArgs sa{s->stream_chunk, (uint32_t)(np / s->stream_chunk)};
+      ga.tpo = make_fastdiv(span / STREAM_V);
+      StreamArgs sa{s->stream_chunk, span / s->stream_chunk};
       CK(cudaMemsetAsync(s->scratch, 0, 16, st));
       void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ga, (void*)&sa};
       cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_stream<kStreamConsumerWarps>, dim3(s->grid),
@@ -1209,13 +1290,15 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       s->pending = true;
     } else {  // GRID
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
+      const uint32_t grid = grid_for_span(s, span, (uint32_t)s->V);
       GridArgs ga{};
       ga.count = s->scratch + 2;
       ga.gen = s->scratch + 3;
-      ga.expected = s->grid + s->barrier_extra;
+      ga.expected = grid + s->barrier_extra;
       ga.timeout_ns = s->barrier_timeout_ns;
       ga.ncyc = (uint32_t)max_cyc;
-      ga.tpo = make_fastdiv((uint32_t)(np / s->V));
+      ga.tpo = make_fastdiv(span / (uint32_t)s->V);
+      ga.stage_cap = s->activity ? 0u : s->stage_cap;
       CK(cudaMemsetAsync(s->scratch, 0, 16, st));
       const void* fn = nullptr;
       if (s->activity) {
@@ -1235,7 +1318,9 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
         fn = v->grid;
       }
       void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ga};
-      cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(s->grid), dim3(s->threads), args, 0, st);
+      s->last_grid = grid;
+      cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(s->threads), args,
+                                                  (size_t)ga.stage_cap * kStageBytes, st);
       if (e == cudaErrorCooperativeLaunchTooLarge)
         throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
       CK(e);
@@ -1501,6 +1586,9 @@ RT_EXPORT int rteaal_step_static(const rteaal_design* d, void* state, uint64_t* 
     ga.gen = scratch + 2;
     ga.expected = grid;
     ga.timeout_ns = 2000000000ull;
+    // the same wait bound and test hook as the regular grid launch
+    if (const char* e = getenv("RTEAAL_BARRIER_TIMEOUT_NS")) ga.timeout_ns = strtoull(e, nullptr, 10);
+    if (const char* e = getenv("RTEAAL_TEST_WITHHOLD_ARRIVAL")) ga.expected += (uint32_t)atoi(e);
     ga.ncyc = max_cyc;
     ga.tpo = make_fastdiv(n_lanes / V);
     void* args[] = {(void*)&d->dd, (void*)&ds, (void*)&ga};

@@ -1,5 +1,5 @@
 // specialize.cpp -- the design-specialised form: the paper's S-rank unrolling
-// and tensor inlining (Sec. 4.4, kernels SU and TI) carried to the GPU.
+// and tensor inlining (Sec. 5.2, kernels SU and TI) carried to the GPU.
 //
 // The lowered operation list is unrolled into straight-line CUDA source in
 // which every signal is a local variable (the OIM is encoded in the code, no

@@ -191,7 +191,9 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s,
   const uint32_t* act = act_words <= STREAM_ACT_WORDS ? act_bits : nullptr;
   __shared__ int sh_ok;
   __shared__ int sh_bad_store;
+  __shared__ uint32_t sh_issued_store;  // items whose copies the producer issued (monotonic)
   volatile int* sh_bad = &sh_bad_store;
+  volatile uint32_t* sh_issued = &sh_issued_store;
   const uint32_t warp = threadIdx.x / 32, lane_id = threadIdx.x % 32;
   const bool producer = warp == (uint32_t)NCW;
   if (threadIdx.x == 0) {
@@ -201,6 +203,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s,
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sh_bad = 0;
+    *sh_issued = 0;
   }
   __syncthreads();
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
@@ -275,6 +278,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s,
                 bulk_g2s(ring + si.off[o], elem(s.state, refs[o], s.n_pad, lane0), sa.chunk << (refs[o] >> 30),
                          &full[slot]);
             }
+            *sh_issued = k + 1u;
             (void)par;
           }
         }
@@ -299,12 +303,18 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s,
       kk += n_items;
       __syncthreads();
       if (*sh_bad) {
-        // drain: wait (bounded) for this CTA's copies still in flight, then leave
+        // drain: wait (bounded) for the copies this CTA actually issued and that
+        // may still be in flight (the last NS items up to the producer's count),
+        // then leave; a drain wait that gives up is reported as its own bit
         __syncthreads();
         if (threadIdx.x == 0) {
-          const uint32_t first = kk > STREAM_NS ? kk - STREAM_NS : 0;
-          for (uint32_t k = first; k < kk; k++)
-            mbar_wait(&full[k % STREAM_NS], (k / STREAM_NS) & 1u, g.timeout_ns);
+          const uint32_t issued = *sh_issued;
+          const uint32_t first = issued > STREAM_NS ? issued - STREAM_NS : 0;
+          for (uint32_t k = first; k < issued; k++)
+            if (!mbar_wait(&full[k % STREAM_NS], (k / STREAM_NS) & 1u, g.timeout_ns)) {
+              atomicOr(s.err, 4u);
+              break;
+            }
         }
         __syncthreads();
         grid_sync(g, s.err, &sh_ok);

@@ -1,0 +1,15 @@
+// variants_v8b.cu -- persistent-kernel variants with 8 lanes per thread (own translation
+// unit: the variant units compile in parallel).
+#include "persistent.cuh"
+
+namespace rteaal {
+
+static const Variant kTable[] = {
+    RT_VARIANT(8, 1, 384, 2),
+    RT_VARIANT(8, 1, 256, 4),
+    RT_VARIANT(8, 1, 384, 3),
+};
+
+VariantTable variants_v8b() { return {kTable, sizeof(kTable) / sizeof(kTable[0])}; }
+
+}  // namespace rteaal

@@ -1,7 +1,7 @@
 """Seeded synthetic circuits and stimulus seeds.
 
 Stands in for the paper's Chipyard designs (RocketChip, BOOM, Gemmini, SHA3;
-Sec. 6.1, Table 1), which are not available: random layered dataflow graphs
+Sec. 7.1; Table 1), which are not available: random layered dataflow graphs
 whose scale matches or exceeds Table 1's effectual-operation counts.  This
 module only *builds* netlists and draws random seeds; it evaluates nothing.
 

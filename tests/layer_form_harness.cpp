@@ -238,6 +238,7 @@ extern "C" void* emu_create(const void* bytes, size_t nbytes, int fuse, uint32_t
   d.ext = ptr(L.ext_args);
   d.layer_off = ptr(L.layer_off);
   d.layer_ext = ptr(L.layer_ext);
+  d.layer_wide = ptr(L.layer_wide);
   d.reg_src = ptr(L.reg_src);
   d.reg_ref = ptr(L.reg_ref);
   d.reg_w = ptr(L.reg_width);

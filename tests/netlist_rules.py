@@ -75,3 +75,12 @@ def edge_copies(nl: synth.Netlist) -> list[int]:
 def class_bytes(width: int) -> int:
     """Bytes per lane of a row holding a signal of this width (1, 2, 4 or 8)."""
     return 1 if width <= 8 else 2 if width <= 16 else 4 if width <= 32 else 8
+
+
+def is_wide(nl: synth.Netlist, k: int, args: list[int], w: np.ndarray) -> bool:
+    """Op k is evaluated in 64-bit arithmetic (not narrow): its result or an
+    operand is wider than 32 bits, it reads a memory, or it is a BITS reaching
+    bit 32 or an ANDR over more than 32 bits.  w: the netlist's signal widths."""
+    code = int(nl.op_code[k])
+    return (int(nl.op_width[k]) > 32 or code == OP["MEMRD"] or (code == OP["BITS"] and nl.op_p0[k] >= 32)
+            or (code == OP["ANDR"] and nl.op_p0[k] > 32) or any(int(w[x]) > 32 for x in args))

@@ -2,7 +2,7 @@
 one-clock netlist it builds (a hidden cycle counter, per slower domain an
 enable, per register of such a domain a hold mux) is simulated by the oracle
 as a plain one-clock design and must equal, signal for signal and memory word
-for memory word, the oracle applying the domain rule (Sec. 5.2, "Multiple
+for memory word, the oracle applying the domain rule (Sec. 6.2, "Multiple
 Clock Domains") to the original netlist -- across uneven cycle counts and a
 second reset that restarts every domain's phase."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""Multiple clock domains (Sec. 5.2): registers of slower domains load only on
+"""Multiple clock domains (Sec. 6.2): registers of slower domains load only on
 their ticks.  The library lowers the domains to one clock (a hidden cycle
 counter and hold muxes); every kernel form must match the oracle, which
 implements the domain rule directly."""

@@ -6,8 +6,12 @@
 * batch-1M: 1M ops, 4,096 instances with uneven cycle budgets, in the launch
   configuration the benchmark times (autotuned), five sampled instances
   (first, middle, last lane, shortest and longest budget) checked signal by signal;
+  and the configuration's own budgets (uniform in [1k, 100k]) run for the
+  first 2,000 cycles of the job: the shortest-budget instance (it finishes
+  inside the run), one whose budget ends between 1k and 2k cycles and two
+  still running, every signal;
 * soc-5M: 5M ops, 256k registers, 64 register files (2 read, 1 write port
-  each), 1,024 instances, reset + 200 cycles, two sampled instances, every
+  each), 1,024 instances, reset + 2,000 cycles, two sampled instances, every
   signal and memory word.
 """
 import numpy as np
@@ -72,6 +76,29 @@ def test_batch_1m_bench_configuration():
     p.close()
 
 
+def test_batch_1m_job_budgets_first_2000_cycles():
+    nl = synth.generate(synth.spec_batch())
+    n = 4096
+    budgets = synth.cycle_budgets(5, n, 1000, 100_000)
+    order = np.argsort(budgets, kind="stable")
+    mid = [int(i) for i in order if 1000 < budgets[i] < 2000]
+    assert mid, "no budget between 1k and 2k cycles"
+    running = [int(i) for i in order[-2:]] + [int(order[n // 2])]
+    sample = sorted({int(order[0]), mid[len(mid) // 2], *running})
+    p = Pair(nl, n, kernel="grid", seed=5, expected_cycles=budgets, oracle_instances=sample,
+             threads=224, ctas_per_sm=4, lanes_per_thread=8, unroll=1)
+    p.step(1, reset=True, threads=len(sample))
+    run = np.minimum(budgets, 2000).astype(np.uint32)
+    done = np.zeros(n, np.uint32)
+    for _ in range(4):   # four steps of up to 500 cycles: the live span shrinks as instances finish
+        per = np.minimum(run - done, 500).astype(np.uint32)
+        p.step(per, threads=len(sample))
+        done += per
+    assert np.array_equal(done, run)
+    p.compare()
+    p.close()
+
+
 def test_soc_5m_with_memories():
     nl = synth.generate(synth.spec_soc())
     assert nl.n_mems == 64 and nl.n_wports == 64
@@ -79,6 +106,7 @@ def test_soc_5m_with_memories():
     n = 1024
     p = Pair(nl, n, kernel="grid", seed=3, oracle_instances=[1, n - 2])
     p.step(1, reset=True, threads=2)
-    p.step(200, threads=2)
+    for _ in range(4):   # 2,000 cycles, in four steps
+        p.step(500, threads=2)
     p.compare()
     p.close()

@@ -1,4 +1,4 @@
-"""Design-specialised form (Sec. 4.4 SU / TI on the GPU: the op list unrolled
+"""Design-specialised form (Sec. 5.2 SU / TI on the GPU: the op list unrolled
 into run-time-compiled straight-line code, one thread per instance): bit-exact
 with the oracle, and its state is the data-driven kernels' state."""
 import numpy as np

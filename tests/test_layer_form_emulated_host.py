@@ -157,7 +157,7 @@ def test_layer_and_tile_forms_match_oracle(harness, name, V, mapping):
 @pytest.mark.parametrize("mapping", ["one thread per chunk", "fewer threads", "tiles of 8 lanes, 4 rows in flight"])
 @pytest.mark.parametrize("V", [1, 4, 8])
 def test_probes_every_cycle_and_change_records(harness, V, mapping):
-    """Probes (Sec. 5.2 waveform generation): every cycle's values, and change
+    """Probes (Sec. 6.2 waveform generation): every cycle's values, and change
     records against the values at the start of the step, as the oracle's trace
     gives them."""
     from oracle.waveform import changes
@@ -202,10 +202,12 @@ def test_probes_every_cycle_and_change_records(harness, V, mapping):
 
 KERNEL_MUTANTS = [
     ("narrow SUB operands swapped",
-     "case OP_SUB: RT_LANES(a.x[v] - b.x[v]); break;\n    case OP_MUL: RT_LANES(a.x[v] * b.x[v] * (ar == 3 ? c.x[v] : 1u)); break;",
-     "case OP_SUB: RT_LANES(b.x[v] - a.x[v]); break;\n    case OP_MUL: RT_LANES(a.x[v] * b.x[v] * (ar == 3 ? c.x[v] : 1u)); break;"),
-    ("8-lane 1-byte gather: upper lanes from the lower word",
-     "r.x[4 + v] = __byte_perm(t.y, 0u, 0x4440u + v);", "r.x[4 + v] = __byte_perm(t.x, 0u, 0x4440u + v);"),
+     "case OP_SUB: RT_LANES(a.x[v] - b.x[v]); break;\n    case OP_MUL: RT_LANES(a.x[v] * b.x[v]); if (ar == 3) RT_LANES(r.x[v] * c.x[v]); break;\n    case OP_SHL: RT_LANES(p0 >= 32u",
+     "case OP_SUB: RT_LANES(b.x[v] - a.x[v]); break;\n    case OP_MUL: RT_LANES(a.x[v] * b.x[v]); if (ar == 3) RT_LANES(r.x[v] * c.x[v]); break;\n    case OP_SHL: RT_LANES(p0 >= 32u"),
+    ("packed 1-byte lanes: upper lanes from the first word",
+     "x.x[v] = __byte_perm(r.w[v >> 2], 0u, 0x4440u + (v & 3));", "x.x[v] = __byte_perm(r.w[0], 0u, 0x4440u + (v & 3));"),
+    ("rows in flight: the next kind skips the rows past the boundary",
+     "    return next;\n  }\n}", "    return r;\n  }\n}"),
     ("4-lane 2-byte store: lanes swapped within a word",
      "(uint32_t)(r.x[0] | (r.x[1] << 16)), (uint32_t)(r.x[2] | (r.x[3] << 16))",
      "(uint32_t)(r.x[1] | (r.x[0] << 16)), (uint32_t)(r.x[2] | (r.x[3] << 16))"),
@@ -238,7 +240,8 @@ def test_planted_kernel_mistakes_are_caught(tmp_path):
             nl, fuse = DESIGNS[name_d]
             for V in (4, 8):
                 try:
-                    run_and_compare(lib, nl, fuse, V, NP // V)
+                    # rows in flight per thread: 4 for the mutant of that path
+                    run_and_compare(lib, nl, fuse, V, NP // V, U=4 if "rows in flight" in name else 1)
                 except AssertionError:
                     caught = True
                     break

@@ -11,7 +11,7 @@ import paper_2601_18140_gb300 as rt
 import synth
 from paper_2601_18140_gb300 import build as rtbuild
 from synth import OP, Builder, DesignSpec
-from tests.netlist_rules import class_bytes, edge_copies, effective_args, fused_away, levels
+from tests.netlist_rules import class_bytes, edge_copies, effective_args, fused_away, is_wide, levels
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,15 +35,16 @@ def expected(nl: synth.Netlist, fuse: bool) -> dict:
     state = sum(class_bytes(int(w)) for w in widths[:nl.op_base])
     state += sum(class_bytes(int(nl.op_width[k])) for k in range(nl.n_ops) if lv[k] > 0)
     state += sum(class_bytes(int(widths[x])) for x in copies)
-    # grouping keys: (layer, operand list wider than three, opcode, width)
+    # grouping keys: (layer, operand list wider than three, wide (ops with at
+    # most three operands only), opcode, width)
     keys = set()
     for k in range(nl.n_ops):
         if lv[k] > 0:
             a = effective_args(nl, k, gone)
             code = OP["MUXCHAIN"] if (nl.op_code[k] == OP["MUX"] and len(a) > 3) else int(nl.op_code[k])
-            keys.add((int(lv[k]), len(a) > 3, code, int(nl.op_width[k])))
+            keys.add((int(lv[k]), len(a) > 3, len(a) <= 3 and is_wide(nl, k, a, widths), code, int(nl.op_width[k])))
     for x in copies:
-        keys.add((1, False, OP["COPY"], int(widths[x])))
+        keys.add((1, False, int(widths[x]) > 32, OP["COPY"], int(widths[x])))
     return dict(n_layers=n_layers, layer_ops=layer_ops, n_lowered_ops=n_lowered,
                 n_slots=nl.op_base + n_lowered, state_bytes_per_lane=state, n_fused=len(gone),
                 keys=keys, n_copies=len(copies))
@@ -67,7 +68,7 @@ def check(nl: synth.Netlist, fuse: bool = False) -> dict:
     assert info["metadata_bytes"] == 0
     # a group is a run of one (layer, opcode, width) in the sorted op list; the
     # ops with more than three operands of a layer follow the others
-    distinct_lcw = {(l, c, w) for (l, _x, c, w) in e["keys"]}
+    distinct_lcw = {(l, c, w) for (l, _x, _wd, c, w) in e["keys"]}
     assert len(distinct_lcw) <= info["n_groups"] <= len(e["keys"])
     return info
 
