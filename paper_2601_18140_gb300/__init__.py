@@ -532,7 +532,11 @@ class Sim:
             keep.append(ec)
             o.expected_cycles = _np_ptr(ec, _U32)
         self.handle = rteaal_sim_create(design.handle, n_instances, o)
-        self.info = rteaal_sim_info(self.handle)
+
+    @property
+    def info(self) -> dict:
+        """Instance / lane counts, launch configuration and the last step's span (live)."""
+        return rteaal_sim_info(self.handle)
 
     def step(self, cycles, stimulus: str = "hold", values=None, reset: bool = False,
              probes=None, probe_mode: str = "last", probe_out=None, stream=None,
@@ -611,16 +615,13 @@ class Sim:
         o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
         o.lanes_per_thread = lanes_per_thread
         rteaal_sim_configure(self.handle, o)
-        self.info = rteaal_sim_info(self.handle)
 
     def autotune(self, cycles_per_trial: int = 1, kernels=None, stream=None) -> list[dict]:
         """Time candidate launch configurations; keep the fastest; state is restored."""
         mask = 0
         for k in kernels or []:
             mask |= 1 << (KERNELS[k] if isinstance(k, str) else int(k))
-        trials = rteaal_sim_autotune(self.handle, cycles_per_trial, mask, stream=stream)
-        self.info = rteaal_sim_info(self.handle)
-        return trials
+        return rteaal_sim_autotune(self.handle, cycles_per_trial, mask, stream=stream)
 
     def read(self, signals=None, inst_begin: int = 0, n_inst: int | None = None, stream=None):
         if signals is None:

@@ -740,154 +740,6 @@ __device__ __forceinline__ Lanes<V> apply(const DDesign& d, const DSim& s, const
   return r;
 }
 
-// ---- loads-first item bodies.  Every operand byte of an item is requested
-// before any of them is used, so a thread keeps the op's whole gather (OI =
-// LI . OIM for this s coordinate) in flight at once: the dependent chain of an
-// item is one memory round trip instead of one per operand.  Loads are issued
-// into packed words (Raw) and unpacked to lanes only afterwards.
-
-// Packed bytes of V consecutive lanes of one row: V << k bytes for class k.
-template <int V>
-struct Raw {
-  uint32_t w[2 * V];
-};
-
-// Issue the loads of V lanes of a row (lane is a multiple of V, so the packed
-// bytes are naturally aligned).  NARROW: the row's class is at most 2.
-template <int V, bool NARROW>
-__device__ __forceinline__ void raw_load(Raw<V>& r, const uint8_t* st, uint32_t ref, size_t np, uint32_t lane) {
-  const uint8_t* p = elem(st, ref, np, lane);
-  const uint32_t k = ref >> 30;
-  if constexpr (V == 8) {
-    if (k == 0) {
-      const uint2 t = *reinterpret_cast<const uint2*>(p);
-      r.w[0] = t.x; r.w[1] = t.y;
-    } else if (k == 1) {
-      const uint4 t = *reinterpret_cast<const uint4*>(p);
-      r.w[0] = t.x; r.w[1] = t.y; r.w[2] = t.z; r.w[3] = t.w;
-    } else if (NARROW || k == 2) {
-      const uint4 t0 = reinterpret_cast<const uint4*>(p)[0];
-      const uint4 t1 = reinterpret_cast<const uint4*>(p)[1];
-      r.w[0] = t0.x; r.w[1] = t0.y; r.w[2] = t0.z; r.w[3] = t0.w;
-      r.w[4] = t1.x; r.w[5] = t1.y; r.w[6] = t1.z; r.w[7] = t1.w;
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const uint4 t = reinterpret_cast<const uint4*>(p)[q];
-        r.w[4 * q] = t.x; r.w[4 * q + 1] = t.y; r.w[4 * q + 2] = t.z; r.w[4 * q + 3] = t.w;
-      }
-    }
-  } else if constexpr (V == 4) {
-    if (k == 0) {
-      r.w[0] = *reinterpret_cast<const uint32_t*>(p);
-    } else if (k == 1) {
-      const uint2 t = *reinterpret_cast<const uint2*>(p);
-      r.w[0] = t.x; r.w[1] = t.y;
-    } else if (NARROW || k == 2) {
-      const uint4 t = *reinterpret_cast<const uint4*>(p);
-      r.w[0] = t.x; r.w[1] = t.y; r.w[2] = t.z; r.w[3] = t.w;
-    } else {
-      const uint4 t0 = reinterpret_cast<const uint4*>(p)[0];
-      const uint4 t1 = reinterpret_cast<const uint4*>(p)[1];
-      r.w[0] = t0.x; r.w[1] = t0.y; r.w[2] = t0.z; r.w[3] = t0.w;
-      r.w[4] = t1.x; r.w[5] = t1.y; r.w[6] = t1.z; r.w[7] = t1.w;
-    }
-  } else if constexpr (V == 2) {
-    if (k == 0) {
-      r.w[0] = *reinterpret_cast<const uint16_t*>(p);
-    } else if (k == 1) {
-      r.w[0] = *reinterpret_cast<const uint32_t*>(p);
-    } else if (NARROW || k == 2) {
-      const uint2 t = *reinterpret_cast<const uint2*>(p);
-      r.w[0] = t.x; r.w[1] = t.y;
-    } else {
-      const uint4 t = *reinterpret_cast<const uint4*>(p);
-      r.w[0] = t.x; r.w[1] = t.y; r.w[2] = t.z; r.w[3] = t.w;
-    }
-  } else {
-    static_assert(V == 1, "lanes per thread: 1, 2, 4 or 8");
-    if (k == 0) {
-      r.w[0] = *p;
-    } else if (k == 1) {
-      r.w[0] = *reinterpret_cast<const uint16_t*>(p);
-    } else if (NARROW || k == 2) {
-      r.w[0] = *reinterpret_cast<const uint32_t*>(p);
-    } else {
-      const uint2 t = *reinterpret_cast<const uint2*>(p);
-      r.w[0] = t.x; r.w[1] = t.y;
-    }
-  }
-}
-
-// Lanes of packed words of class k <= 2, zero-extended to 32 bits (byte v,
-// half v or word v of the packed bytes).
-template <int V>
-__device__ __forceinline__ Lanes32<V> unpack32(const Raw<V>& r, uint32_t k) {
-  Lanes32<V> x;
-  if (k == 0) {
-#pragma unroll
-    for (int v = 0; v < V; v++) x.x[v] = __byte_perm(r.w[v >> 2], 0u, 0x4440u + (v & 3));
-  } else if (k == 1) {
-#pragma unroll
-    for (int v = 0; v < V; v++) x.x[v] = (v & 1) ? r.w[v >> 1] >> 16 : r.w[v >> 1] & 0xFFFFu;
-  } else {
-#pragma unroll
-    for (int v = 0; v < V; v++) x.x[v] = r.w[v];
-  }
-  return x;
-}
-
-// Lanes of packed words of any class, zero-extended to 64 bits.
-template <int V>
-__device__ __forceinline__ Lanes<V> unpack64(const Raw<V>& r, uint32_t k) {
-  Lanes<V> x;
-  if (k == 3) {
-#pragma unroll
-    for (int v = 0; v < V; v++) x.x[v] = (uint64_t)r.w[2 * v] | ((uint64_t)r.w[2 * v + 1] << 32);
-  } else {
-    const Lanes32<V> y = unpack32<V>(r, k);
-#pragma unroll
-    for (int v = 0; v < V; v++) x.x[v] = y.x[v];
-  }
-  return x;
-}
-
-// One narrow op (operands and result of at most 32 bits, <= 3 operands) for V lanes.
-template <int V>
-__device__ __forceinline__ void item_narrow(uint8_t* st, size_t np, uint32_t lane, const uint4& m, uint32_t dref,
-                                            uint32_t am) {
-  const uint32_t ar = (m.w >> 5) & 3u;
-  Raw<V> ra, rb, rc;
-  raw_load<V, true>(ra, st, m.x, np, lane);
-  if (ar >= 2) raw_load<V, true>(rb, st, m.y, np, lane);
-  if (ar >= 3) raw_load<V, true>(rc, st, m.z, np, lane);
-  const Lanes32<V> a = unpack32<V>(ra, m.x >> 30);
-  Lanes32<V> b, c;
-#pragma unroll
-  for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0u;
-  if (ar >= 2) b = unpack32<V>(rb, m.y >> 30);
-  if (ar >= 3) c = unpack32<V>(rc, m.z >> 30);
-  str32<V>(st, dref, np, lane, alu32_v<V>(m.w, a, b, c), am);
-}
-
-// One wide op (a result or operand above 32 bits, or MEMRD; <= 3 operands).
-template <int V>
-__device__ __forceinline__ void item_wide(const DDesign& d, const DSim& s, uint32_t lane, const uint4& m,
-                                          uint32_t dref, uint32_t am) {
-  const uint32_t ar = (m.w >> 5) & 3u;
-  Raw<V> ra, rb, rc;
-  raw_load<V, false>(ra, s.state, m.x, s.n_pad, lane);
-  if (ar >= 2) raw_load<V, false>(rb, s.state, m.y, s.n_pad, lane);
-  if (ar >= 3) raw_load<V, false>(rc, s.state, m.z, s.n_pad, lane);
-  const Lanes<V> a = unpack64<V>(ra, m.x >> 30);
-  Lanes<V> b, c;
-#pragma unroll
-  for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0ull;
-  if (ar >= 2) b = unpack64<V>(rb, m.y >> 30);
-  if (ar >= 3) c = unpack64<V>(rc, m.z >> 30);
-  str<V>(s.state, dref, s.n_pad, lane, apply<V>(d, s, m, a, b, c, lane), am);
-}
-
 // Row kinds of a layer, in their order: narrow (<= 3 operands), wide (<= 3
 // operands), extended (> 3 operands in the side array).
 enum : int { ROW_NARROW = 0, ROW_WIDE = 1, ROW_EXT = 2 };
@@ -896,9 +748,11 @@ template <int V, int KIND>
 __device__ __forceinline__ void item_of_kind(const DDesign& d, const DSim& s, uint32_t lane, const uint4& m,
                                              uint32_t dref, uint32_t am) {
   if constexpr (KIND == ROW_NARROW) {
-    item_narrow<V>(s.state, s.n_pad, lane, m, dref, am);
+    item32<V>(s.state, s.n_pad, lane, m, dref, am);
   } else if constexpr (KIND == ROW_WIDE) {
-    item_wide<V>(d, s, lane, m, dref, am);
+    Lanes<V> va, vb, vc;
+    gather<V>(s.state, s.n_pad, lane, m, va, vb, vc);
+    str<V>(s.state, dref, s.n_pad, lane, apply<V>(d, s, m, va, vb, vc, lane), am);
   } else {
     if (m.w & CTL_NARROW)
       str32<V>(s.state, dref, s.n_pad, lane, eval_ext32_v<V>(d, s, m, lane), am);
@@ -933,8 +787,8 @@ __device__ __forceinline__ uint32_t walk_rows(const DDesign& d, const DSim& s, u
 }
 
 // The same with U rows in flight per thread: the U rows' descriptors, then
-// all their operand loads, then their results (more memory-level parallelism
-// per thread at the price of registers).
+// all their operand gathers, then their results (more memory-level
+// parallelism per thread at the price of registers; 64-bit lanes throughout).
 template <int V, int KIND, int U>
 __device__ __forceinline__ uint32_t walk_rows_u(const DDesign& d, const DSim& s, uint32_t op0, uint32_t r,
                                                 uint32_t r_end, uint32_t stride, uint32_t lane, uint32_t am) {
@@ -952,37 +806,15 @@ __device__ __forceinline__ uint32_t walk_rows_u(const DDesign& d, const DSim& s,
         ok[u] = r + u * stride < r_end;
         m[u] = ok[u] ? __ldg(&d.meta[op0 + r + u * stride]) : make_uint4(0, 0, 0, 0);
       }
-      Raw<V> ra[U], rb[U], rc[U];
+      Lanes<V> va[U], vb[U], vc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (ok[u]) gather<V>(s.state, s.n_pad, lane, m[u], va[u], vb[u], vc[u]);
 #pragma unroll
       for (int u = 0; u < U; u++) {
         if (!ok[u]) continue;
-        const uint32_t ar = (m[u].w >> 5) & 3u;
-        raw_load<V, KIND == ROW_NARROW>(ra[u], s.state, m[u].x, s.n_pad, lane);
-        if (ar >= 2) raw_load<V, KIND == ROW_NARROW>(rb[u], s.state, m[u].y, s.n_pad, lane);
-        if (ar >= 3) raw_load<V, KIND == ROW_NARROW>(rc[u], s.state, m[u].z, s.n_pad, lane);
-      }
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        if (!ok[u]) continue;
-        const uint32_t ar = (m[u].w >> 5) & 3u;
-        const uint32_t dref = __ldg(&d.dst[op0 + r + u * stride]);
-        if constexpr (KIND == ROW_NARROW) {
-          const Lanes32<V> a = unpack32<V>(ra[u], m[u].x >> 30);
-          Lanes32<V> b, c;
-#pragma unroll
-          for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0u;
-          if (ar >= 2) b = unpack32<V>(rb[u], m[u].y >> 30);
-          if (ar >= 3) c = unpack32<V>(rc[u], m[u].z >> 30);
-          str32<V>(s.state, dref, s.n_pad, lane, alu32_v<V>(m[u].w, a, b, c), am);
-        } else {
-          const Lanes<V> a = unpack64<V>(ra[u], m[u].x >> 30);
-          Lanes<V> b, c;
-#pragma unroll
-          for (int v = 0; v < V; v++) b.x[v] = c.x[v] = 0ull;
-          if (ar >= 2) b = unpack64<V>(rb[u], m[u].y >> 30);
-          if (ar >= 3) c = unpack64<V>(rc[u], m[u].z >> 30);
-          str<V>(s.state, dref, s.n_pad, lane, apply<V>(d, s, m[u], a, b, c, lane), am);
-        }
+        const Lanes<V> res = apply<V>(d, s, m[u], va[u], vb[u], vc[u], lane);
+        str<V>(s.state, __ldg(&d.dst[op0 + r + u * stride]), s.n_pad, lane, res, am);
       }
     }
     return next;

@@ -594,7 +594,6 @@ RT_EXPORT uint64_t rteaal_sim_footprint(const rteaal_design* d, uint32_t n) {
 
 namespace {
 
-constexpr int kStreamConsumerWarps = 16;
 
 constexpr uint32_t kSpecMaxOps = 16384;
 constexpr uint32_t kSpecThreads = 128;
@@ -691,16 +690,18 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     ctas_per_sm = 0;
     grid = (uint32_t)((s->n_pad + kSpecThreads - 1) / kSpecThreads);
   } else if (kernel == RTEAAL_KERNEL_STREAM) {
-    // producer warp + consumer warps, one CTA per SM, chunks of up to 512 lanes
+    // one CTA of STREAM_WARPS warps per SM; items of 256 lanes (128 when the
+    // lane count is an odd multiple of 128); every warp keeps one chunk
     if (s->n_pad % 128 != 0)
       throw Error(RTEAAL_E_UNSUPPORTED, "stream kernel needs a multiple of 128 lanes");
-    uint32_t chunk = STREAM_CHUNK_MAX;
-    while (s->n_pad % chunk) chunk >>= 1;
-    s->stream_chunk = chunk;
+    const uint32_t half = s->n_pad % 256 == 0 ? 2u : 1u;
+    s->stream_chunk = 128u * half;
+    if ((uint64_t)s->design->n_sms * STREAM_WARPS < s->n_pad / s->stream_chunk)
+      throw Error(RTEAAL_E_UNSUPPORTED, "stream kernel: more lane chunks than warps");
     V = (int)STREAM_V;
-    threads = 32 * (kStreamConsumerWarps + 1);
+    threads = 32 * STREAM_WARPS;
     unroll = 1;
-    const void* fn = (const void*)k_stream<kStreamConsumerWarps>;
+    const void* fn = half == 2 ? (const void*)k_stream<2> : (const void*)k_stream<1>;
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stream_smem_bytes()));
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, (int)threads, stream_smem_bytes()));
@@ -1277,11 +1278,12 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       ga.timeout_ns = s->barrier_timeout_ns;
       ga.ncyc = (uint32_t)max_cyc;
       ga.tpo = make_fastdiv(span / STREAM_V);
-      StreamArgs sa{s->stream_chunk, span / s->stream_chunk};
+      const uint32_t half = s->stream_chunk / 128u;
+      StreamArgs sa{half, span / s->stream_chunk};
       CK(cudaMemsetAsync(s->scratch, 0, 16, st));
       void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ga, (void*)&sa};
-      cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_stream<kStreamConsumerWarps>, dim3(s->grid),
-                                                  dim3(s->threads), args, stream_smem_bytes(), st);
+      cudaError_t e = cudaLaunchCooperativeKernel(half == 2 ? (const void*)k_stream<2> : (const void*)k_stream<1>,
+                                                  dim3(s->grid), dim3(s->threads), args, stream_smem_bytes(), st);
       if (e == cudaErrorCooperativeLaunchTooLarge)
         throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
       CK(e);

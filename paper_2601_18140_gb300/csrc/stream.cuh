@@ -1,53 +1,67 @@
-// stream.cuh -- the streaming form: operand gathers through the bulk-copy (TMA)
-// engine into a shared-memory ring, computation from shared memory.
+// stream.cuh -- the streaming form: every warp feeds its own shared-memory ring
+// with bulk copies (TMA engine) of its items' operand row segments and
+// evaluates them from shared memory.
 //
-// One CTA per SM walks every layer of every cycle over all lanes (grid barrier
-// between layers, as in the grid form).  An item is one op for a chunk of
-// CHUNK consecutive lanes.  CTA b owns a contiguous range of the layer's ops
-// (all their chunks, op-major).  Per item:
-//   producer (one thread): wait until the ring slot is free (empty barrier),
-//     write the op's descriptor into the slot, announce the byte count on the
-//     slot's full barrier and issue one cp.async.bulk per operand row segment
-//     (CHUNK << class bytes, contiguous in the compact layout);
-//   consumer warp (items round-robin over NCW warps): wait on the full
-//     barrier, evaluate the CHUNK lanes from shared memory (4 packed lanes per
-//     thread per step), store the results to global memory, release the slot.
-// The ring keeps NS items of operand bytes in flight per SM without holding
-// registers, which is what the gather needs: it is latency-bound, not
-// instruction-bound, when every thread keeps one dependent load chain alive.
-// Every mbarrier wait is bounded (%globaltimer); on a timeout the CTA records
-// the error, drains its own copies in flight (bounded) and leaves at the next
-// grid barrier.
+// One CTA per SM walks every layer of every cycle over the live lanes (grid
+// barrier between layers, as in the grid form).  An item is one op for a chunk
+// of CH = 128 H consecutive lanes (H = 1 or 2); thread t of a warp owns lanes
+// {4t .. 4t+3} of each 128-lane half of the chunk, so that its operand bytes
+// are one conflict-free shared-memory access per half and its results one
+// coalesced store per half.  Warp w keeps one chunk for the whole launch
+// (w mod chunks) and walks the rows w / chunks, + W / chunks, ... of every
+// layer (W warps in all).  Per item, lane 0
+//   * reads the op's descriptor (staged in shared memory during the grid
+//     barrier before the layer),
+//   * reserves the operand bytes in the warp's ring (a FIFO of monotonic byte
+//     positions), writes the item's slot record, announces the byte count on
+//     the slot's mbarrier and issues one cp.async.bulk per operand segment
+//     (CH << class bytes, contiguous in the compact layout);
+// and the whole warp later waits on that mbarrier, evaluates the CH lanes from
+// shared memory and stores the results to global memory.  Up to SLOTS items
+// (at most RING bytes) are in flight per warp, with no registers held for
+// them: the gather's latency is covered by the copy engine, and the threads
+// only compute.  Ops with more than three operands read them from global
+// memory instead (their slot carries no bytes).
+//
+// Every mbarrier wait is bounded (%globaltimer); on a timeout the warp records
+// the error, waits (bounded) for the copies it issued and leaves at the next
+// grid barrier with the rest of the grid.
 #pragma once
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "persistent.cuh"
 
 namespace rteaal {
 
-constexpr uint32_t STREAM_NS = 64;                     // item (descriptor) slots
-constexpr uint32_t STREAM_CHUNK_MAX = 2048;            // lanes per item
-constexpr uint32_t STREAM_RING = 160 * 1024;           // operand bytes in flight per SM
-constexpr uint32_t STREAM_V = 4;                       // lanes per consumer thread per step
-constexpr uint32_t STREAM_ACT_WORDS = 2048;            // activity bitmap: up to 65,536 lanes
+constexpr uint32_t STREAM_WARPS = 16;     // warps per CTA (one CTA per SM)
+constexpr uint32_t STREAM_RING = 8192;    // operand bytes per warp
+constexpr uint32_t STREAM_SLOTS = 8;      // items in flight per warp
+constexpr uint32_t STREAM_DESC = 128;     // descriptors staged per warp and layer
+constexpr uint32_t STREAM_V = 4;          // lanes per thread in the stimulus / edge / probe phases
+static_assert(3u * (256u << 3) <= STREAM_RING, "the largest item must fit the ring");
 
 struct StreamArgs {
-  uint32_t chunk;       // lanes per item (divides n_pad, multiple of 32 * STREAM_V, <= STREAM_CHUNK_MAX)
-  uint32_t n_chunks;    // n_pad / chunk
+  uint32_t half;       // H: items of 128 H lanes
+  uint32_t n_chunks;   // items per row over the lane span (span / (128 H))
 };
 
 struct __align__(16) SlotInfo {
   uint4 meta;
-  uint32_t dst, lane0;
-  uint32_t off[3];               // ring byte offset of each operand segment
-  uint32_t pad;
-  unsigned long long start;      // monotonic ring position of the item's first byte
+  uint32_t dst;
+  uint32_t off[2];      // ring byte offsets of operands 0, 1 (operand 2 follows operand 1)
+  uint32_t end;         // monotonic ring position just past the item's bytes
 };
 
-constexpr uint32_t stream_smem_bytes() {
-  return STREAM_RING + STREAM_NS * (uint32_t)sizeof(SlotInfo) + 2 * STREAM_NS * 8 +
-         STREAM_ACT_WORDS * 4 + 64;
-}
+struct __align__(16) WarpArea {
+  uint8_t ring[STREAM_RING];
+  uint4 dmeta[STREAM_DESC];
+  uint32_t ddst[STREAM_DESC];
+  SlotInfo slot[STREAM_SLOTS];
+  uint64_t full[STREAM_SLOTS];
+};
+
+constexpr uint32_t stream_smem_bytes() { return STREAM_WARPS * (uint32_t)sizeof(WarpArea); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -76,19 +90,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ uint64_t stream_clock() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Bounded wait for the phase with the given parity; false after timeout_ns.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
   if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = stream_clock();
+  const uint64_t t0 = globaltimer();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (stream_clock() - t0 > timeout_ns) return false;
+    if (globaltimer() - t0 > timeout_ns) return false;
   }
 }
 
@@ -100,227 +108,245 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Order this thread's later bulk-copy (async proxy) reads after the generic
-// writes that the preceding barrier made visible.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// Order the warp's earlier generic-proxy reads of a consumed item before later
+// bulk copies (async proxy) into the same bytes.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// STREAM_V lanes of an operand segment in shared memory (class k, lane offset sub).
-__device__ __forceinline__ Lanes<STREAM_V> lds4(const uint8_t* seg, uint32_t k, uint32_t sub) {
-  Lanes<STREAM_V> r;
+// 4 lanes of an operand segment in shared memory (class k <= 2), from lane
+// offset sub (a multiple of 4): zero-extended to 32 bits.
+__device__ __forceinline__ void lds32x4(const uint8_t* seg, uint32_t k, uint32_t sub, uint32_t* x) {
   const uint8_t* p = seg + (sub << k);
-  switch (k) {
-    case 0: {
-      const uint32_t t = *reinterpret_cast<const uint32_t*>(p);
-      r.x[0] = t & 0xFFu;
-      r.x[1] = (t >> 8) & 0xFFu;
-      r.x[2] = (t >> 16) & 0xFFu;
-      r.x[3] = t >> 24;
-    } break;
-    case 1: {
-      const uint2 t = *reinterpret_cast<const uint2*>(p);
-      r.x[0] = t.x & 0xFFFFu;
-      r.x[1] = t.x >> 16;
-      r.x[2] = t.y & 0xFFFFu;
-      r.x[3] = t.y >> 16;
-    } break;
-    case 2: {
-      const uint4 t = *reinterpret_cast<const uint4*>(p);
-      r.x[0] = t.x;
-      r.x[1] = t.y;
-      r.x[2] = t.z;
-      r.x[3] = t.w;
-    } break;
-    default: {
-      const ulonglong2 t0 = reinterpret_cast<const ulonglong2*>(p)[0];
-      const ulonglong2 t1 = reinterpret_cast<const ulonglong2*>(p)[1];
-      r.x[0] = t0.x;
-      r.x[1] = t0.y;
-      r.x[2] = t1.x;
-      r.x[3] = t1.y;
-    } break;
+  if (k == 0) {
+    const uint32_t t = *reinterpret_cast<const uint32_t*>(p);
+#pragma unroll
+    for (int v = 0; v < 4; v++) x[v] = __byte_perm(t, 0u, 0x4440u + v);
+  } else if (k == 1) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    x[0] = t.x & 0xFFFFu; x[1] = t.x >> 16;
+    x[2] = t.y & 0xFFFFu; x[3] = t.y >> 16;
+  } else {
+    const uint4 t = *reinterpret_cast<const uint4*>(p);
+    x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+  }
+}
+
+// The same for any class, zero-extended to 64 bits.
+__device__ __forceinline__ Lanes<4> lds64x4(const uint8_t* seg, uint32_t k, uint32_t sub) {
+  Lanes<4> r;
+  if (k == 3) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(seg + (sub << 3));
+    const ulonglong2 t0 = p[0], t1 = p[1];
+    r.x[0] = t0.x; r.x[1] = t0.y; r.x[2] = t1.x; r.x[3] = t1.y;
+  } else {
+    uint32_t x[4];
+    lds32x4(seg, k, sub, x);
+#pragma unroll
+    for (int v = 0; v < 4; v++) r.x[v] = x[v];
   }
   return r;
 }
 
-// Evaluate one item from its ring slot (one consumer warp).
-__device__ __forceinline__ void stream_consume(const DDesign& d, const DSim& s, const SlotInfo& si,
-                                               const uint8_t* ring, uint32_t chunk, uint32_t cyc,
-                                               uint32_t lane_id, const uint32_t* act) {
+// Evaluate one item from its slot: thread lane_id owns lanes {4 lane_id ..
+// + 3} of each 128-lane half of the chunk starting at lane0; am: bit 4h + v =
+// lane 128 h + 4 lane_id + v active.
+template <int H>
+__device__ __forceinline__ void stream_item(const DDesign& d, const DSim& s, const SlotInfo& si,
+                                            const uint8_t* ring, uint32_t lane0, uint32_t lane_id, uint32_t am) {
   const uint4 m = si.meta;
   const uint32_t ctl = m.w;
   const size_t np = s.n_pad;
+  const uint32_t sub = 4u * lane_id;
+  if (ctl & CTL_EXT) {  // operands from global memory
+#pragma unroll
+    for (int h = 0; h < H; h++) {
+      const uint32_t lane = lane0 + 128u * h + sub, mk = (am >> (4 * h)) & 15u;
+      if (!mk) continue;
+      if (ctl & CTL_NARROW)
+        str32<4>(s.state, si.dst, np, lane, eval_ext32_v<4>(d, s, m, lane), mk);
+      else
+        str<4>(s.state, si.dst, np, lane, eval_ext_v<4>(d, s, m, lane), mk);
+    }
+    return;
+  }
   const uint32_t ar = (ctl >> 5) & 3u;
   const uint32_t ka = m.x >> 30, kb = m.y >> 30, kc = m.z >> 30;
+  const uint32_t CH = 128u * H;
   const uint8_t* sa = ring + si.off[0];
   const uint8_t* sb = ring + si.off[1];
-  const uint8_t* sc = ring + si.off[2];
-  for (uint32_t sub = lane_id * STREAM_V; sub < chunk; sub += 32 * STREAM_V) {
-    const uint32_t lane = si.lane0 + sub;
-    const uint32_t am = act ? (act[lane >> 5] >> (lane & 31u)) & 0xFu : act_mask<STREAM_V>(s, lane, cyc);
-    if (!am) continue;
-    Lanes<STREAM_V> r;
-    if (ctl & CTL_EXT) {
-      r = eval_ext_v<STREAM_V>(d, s, m, lane);
-    } else {
-      Lanes<STREAM_V> a = lds4(sa, ka, sub), b, c;
+  const uint8_t* sc = sb + (CH << kb);
+  if (ctl & CTL_NARROW) {
+    Lanes32<4 * H> a, b, c;
 #pragma unroll
-      for (int v = 0; v < (int)STREAM_V; v++) b.x[v] = c.x[v] = 0;
-      if (ar >= 2) b = lds4(sb, kb, sub);
-      if (ar >= 3) c = lds4(sc, kc, sub);
-      if ((ctl & 31u) == OP_MEMRD) {
+    for (int h = 0; h < H; h++) {
+      lds32x4(sa + ((128u * h) << ka), ka, sub, &a.x[4 * h]);
 #pragma unroll
-        for (int v = 0; v < (int)STREAM_V; v++) r.x[v] = eval_memrd(d, s, ctl, a.x[v], lane + v);
-      } else {
-        r = alu_v<STREAM_V>(ctl, a, b, c);
-      }
+      for (int v = 0; v < 4; v++) b.x[4 * h + v] = c.x[4 * h + v] = 0u;
+      if (ar >= 2) lds32x4(sb + ((128u * h) << kb), kb, sub, &b.x[4 * h]);
+      if (ar >= 3) lds32x4(sc + ((128u * h) << kc), kc, sub, &c.x[4 * h]);
     }
-    str<STREAM_V>(s.state, si.dst, np, lane, r, am);
+    const Lanes32<4 * H> r = alu32_v<4 * H>(ctl, a, b, c);
+#pragma unroll
+    for (int h = 0; h < H; h++) {
+      const uint32_t mk = (am >> (4 * h)) & 15u;
+      if (!mk) continue;
+      Lanes32<4> q;
+#pragma unroll
+      for (int v = 0; v < 4; v++) q.x[v] = r.x[4 * h + v];
+      str32<4>(s.state, si.dst, np, lane0 + 128u * h + sub, q, mk);
+    }
+  } else {  // 64-bit lanes, one half at a time
+#pragma unroll
+    for (int h = 0; h < H; h++) {
+      const uint32_t mk = (am >> (4 * h)) & 15u;
+      if (!mk) continue;
+      const uint32_t lane = lane0 + 128u * h + sub;
+      const Lanes<4> a = lds64x4(sa + ((128u * h) << ka), ka, sub);
+      Lanes<4> b, c;
+#pragma unroll
+      for (int v = 0; v < 4; v++) b.x[v] = c.x[v] = 0ull;
+      if (ar >= 2) b = lds64x4(sb + ((128u * h) << kb), kb, sub);
+      if (ar >= 3) c = lds64x4(sc + ((128u * h) << kc), kc, sub);
+      str<4>(s.state, si.dst, np, lane, apply<4>(d, s, m, a, b, c, lane), mk);
+    }
   }
 }
 
-template <int NCW>
-__global__ void __launch_bounds__(32 * (NCW + 1), 1) k_stream(DDesign d, DSim s, GridArgs g, StreamArgs sa) {
+// Warp w's place in the item space of a layer: its chunk (fixed for the
+// launch), its first row and the stride between its rows (0: the warp has no
+// rows -- the warps beyond a multiple of the chunk count).
+struct WarpRows {
+  uint32_t chunk, row0, stride;
+};
+
+__device__ __forceinline__ WarpRows warp_rows(uint32_t w, uint32_t n_warps, uint32_t n_chunks) {
+  WarpRows wr;
+  wr.stride = n_warps / n_chunks;
+  wr.chunk = w % n_chunks;
+  wr.row0 = w / n_chunks;
+  if (wr.row0 >= wr.stride) wr.stride = 0;
+  return wr;
+}
+
+// Stage the descriptors of the warp's rows of layer L (its first STREAM_DESC
+// rows) into its area; every lane copies a share (cp.async, completed before
+// the grid barrier ends).
+__device__ __forceinline__ void stream_stage(const DDesign& d, uint32_t L, const WarpRows& wr, WarpArea* wa,
+                                             uint32_t lane_id) {
+  if (!wr.stride || L >= d.n_layers) return;
+  const uint32_t o0 = __ldg(&d.layer_off[L]), n = __ldg(&d.layer_off[L + 1]) - o0;
+  for (uint32_t i = lane_id; i < STREAM_DESC; i += 32u) {
+    const uint32_t r = wr.row0 + i * wr.stride;
+    if (r >= n) break;
+    cp_async16(&wa->dmeta[i], &d.meta[o0 + r]);
+    cp_async4(&wa->ddst[i], &d.dst[o0 + r]);
+  }
+}
+
+template <int H>
+__global__ void __launch_bounds__(32 * STREAM_WARPS, 1) k_stream(DDesign d, DSim s, GridArgs g, StreamArgs sa) {
   extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t* ring = smem;
-  SlotInfo* info = reinterpret_cast<SlotInfo*>(smem + STREAM_RING);
-  uint64_t* full = reinterpret_cast<uint64_t*>(info + STREAM_NS);
-  uint64_t* empty = full + STREAM_NS;
-  uint32_t* act_bits = reinterpret_cast<uint32_t*>(empty + STREAM_NS);
-  // per-cycle lane activity in shared memory (one bit per lane) when it fits
-  const uint32_t act_words = (s.n_pad + 31) / 32;
-  const uint32_t* act = act_words <= STREAM_ACT_WORDS ? act_bits : nullptr;
   __shared__ int sh_ok;
-  __shared__ int sh_bad_store;
-  __shared__ uint32_t sh_issued_store;  // items whose copies the producer issued (monotonic)
-  volatile int* sh_bad = &sh_bad_store;
-  volatile uint32_t* sh_issued = &sh_issued_store;
-  const uint32_t warp = threadIdx.x / 32, lane_id = threadIdx.x % 32;
-  const bool producer = warp == (uint32_t)NCW;
-  if (threadIdx.x == 0) {
-    for (uint32_t i = 0; i < STREAM_NS; i++) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
-    }
+  const uint32_t warp = threadIdx.x / 32u, lane_id = threadIdx.x % 32u;
+  WarpArea* wa = reinterpret_cast<WarpArea*>(smem) + warp;
+  if (lane_id == 0) {
+    for (uint32_t i = 0; i < STREAM_SLOTS; i++) mbar_init(&wa->full[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    *sh_bad = 0;
-    *sh_issued = 0;
   }
   __syncthreads();
-  const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
-  uint32_t kk = 0;      // items this CTA has passed through its ring (all warps agree)
-  unsigned long long pos = 0;  // producer: next free monotonic ring byte
-  uint32_t oldest = 0;         // producer: oldest item whose slot / bytes are not yet known free
-#define RT_SPACE make_space<STREAM_V>(g.tpo, 0u, gtid, nthreads)
+  const uint32_t n_warps = gridDim.x * STREAM_WARPS;
+  const WarpRows wr = warp_rows(blockIdx.x * STREAM_WARPS + warp, n_warps, sa.n_chunks);
+  const uint32_t CH = 128u * H, lane0 = wr.chunk * CH;
+  uint32_t uses = 0;  // items that went through this warp's slots since launch (slot and parity)
+  bool bad = false;
+#define RT_SPACE make_space<STREAM_V>(g.tpo, 0u, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x)
   for (uint32_t c = 0; c < g.ncyc; c++) {
-    if (act)
-      for (uint32_t w = threadIdx.x; w < act_words; w += blockDim.x) {
-        uint32_t bits = 0;
-        for (uint32_t b = 0; b < 32; b++)
-          if (lane_active(s, w * 32 + b, c)) bits |= 1u << b;
-        act_bits[w] = bits;
-      }
+    // lane activity of this thread's lanes in the cycle (the warp's chunk is fixed)
+    uint32_t am = 0;
+    if (wr.stride)
+#pragma unroll
+      for (int h = 0; h < H; h++) am |= act_mask<4>(s, lane0 + 128u * h + 4u * lane_id, c) << (4 * h);
+    const bool warp_live = __ballot_sync(0xFFFFFFFFu, am != 0u) != 0u;
     stim_items<STREAM_V>(d, s, RT_SPACE, c);
-    if (!grid_sync(g, s.err, &sh_ok)) return;
+    if (!grid_sync_staging(g, s.err, &sh_ok, [&] { stream_stage(d, 0u, wr, wa, lane_id); })) return;
     for (uint32_t L = 0; L < d.n_layers; L++) {
-      const uint32_t o0 = __ldg(&d.layer_off[L]), o1 = __ldg(&d.layer_off[L + 1]);
-      const uint32_t n_ops = o1 - o0;
-      const uint32_t r0 = (uint32_t)((uint64_t)n_ops * blockIdx.x / gridDim.x);
-      const uint32_t r1 = (uint32_t)((uint64_t)n_ops * (blockIdx.x + 1) / gridDim.x);
-      const uint32_t n_items = (r1 - r0) * sa.n_chunks;
-      if (producer) {
-        // one issuing lane; monotonic byte positions: the ring segment of item k
-        // is [start, end); space is reclaimed from the oldest item still in use
-        if (lane_id == 0) {
-          fence_proxy_async();
-          for (uint32_t j = 0; j < n_items; j++) {
-            if (*sh_bad) break;
-            const uint32_t k = kk + j, slot = k % STREAM_NS, par = (k / STREAM_NS) & 1u;
-            const uint32_t jr = j / sa.n_chunks;
-            const uint32_t op = o0 + r0 + jr;
-            const uint32_t lane0 = (j - jr * sa.n_chunks) * sa.chunk;
-            const uint4 m = __ldg(&d.meta[op]);
-            const uint32_t ar = (m.w & CTL_EXT) ? 0u : (m.w >> 5) & 3u;
-            const uint32_t refs[3] = {m.x, m.y, m.z};
-            uint32_t need = 0;
-            for (uint32_t o = 0; o < ar; o++) need += sa.chunk << (refs[o] >> 30);
-            // contiguous placement: skip to the next ring lap if the item would wrap
-            unsigned long long p0 = pos;
-            if ((p0 % STREAM_RING) + need > STREAM_RING) p0 = (p0 / STREAM_RING + 1) * STREAM_RING;
-            bool ok = true;
-            // free the descriptor slot (item k - NS) and the ring bytes up to p0 + need by
-            // waiting for the oldest items' release (item counters compared by difference)
-            while (ok && (k - oldest >= STREAM_NS ||
-                          (k != oldest && p0 + need > info[oldest % STREAM_NS].start + STREAM_RING))) {
-              ok = mbar_wait(&empty[oldest % STREAM_NS], (oldest / STREAM_NS) & 1u, g.timeout_ns);
-              oldest++;
-            }
-            if (!ok) {
-              atomicOr(s.err, 2u);
-              *sh_bad = 1;
-              break;
-            }
-            SlotInfo& si = info[slot];
-            si.meta = m;
-            si.dst = __ldg(&d.dst[op]);
-            si.lane0 = lane0;
-            si.start = p0;
-            unsigned long long q = p0;
-            for (uint32_t o = 0; o < 3; o++) {
-              si.off[o] = (uint32_t)(q % STREAM_RING);
-              if (o < ar) q += sa.chunk << (refs[o] >> 30);
-            }
-            pos = q;
-            if (ar == 0) {
-              mbar_arrive(&full[slot]);  // operands read from global by the consumer
-            } else {
-              mbar_arrive_expect_tx(&full[slot], need);
-              for (uint32_t o = 0; o < ar; o++)
-                bulk_g2s(ring + si.off[o], elem(s.state, refs[o], s.n_pad, lane0), sa.chunk << (refs[o] >> 30),
-                         &full[slot]);
-            }
-            *sh_issued = k + 1u;
-            (void)par;
+      const uint32_t o0 = __ldg(&d.layer_off[L]), n = __ldg(&d.layer_off[L + 1]) - o0;
+      const uint32_t ni = (wr.stride && warp_live && wr.row0 < n) ? (n - wr.row0 + wr.stride - 1u) / wr.stride : 0u;
+      uint32_t issued = 0, done = 0;
+      uint32_t head = 0, tail = 0;  // monotonic ring positions (the ring is empty between layers)
+      while (done < ni) {
+        // issue as many items as slots and ring bytes allow (warp-uniform decisions)
+        while (issued < ni && issued - done < STREAM_SLOTS) {
+          const uint32_t i = issued, r = wr.row0 + i * wr.stride;
+          uint4 m;
+          uint32_t dref;
+          if (i < STREAM_DESC) {
+            m = wa->dmeta[i];
+            dref = wa->ddst[i];
+          } else {
+            m = __ldg(&d.meta[o0 + r]);
+            dref = __ldg(&d.dst[o0 + r]);
           }
-        }
-      } else {
-        for (uint32_t j = warp; j < n_items; j += NCW) {
-          const uint32_t k = kk + j, slot = k % STREAM_NS, par = (k / STREAM_NS) & 1u;
-          int ok = 1;
+          const uint32_t ar = (m.w & CTL_EXT) ? 0u : (m.w >> 5) & 3u;
+          const uint32_t b0 = ar ? CH << (m.x >> 30) : 0u, b1 = ar >= 2 ? CH << (m.y >> 30) : 0u,
+                         b2 = ar >= 3 ? CH << (m.z >> 30) : 0u;
+          const uint32_t need = b0 + b1 + b2;
+          uint32_t p = head;
+          if ((p % STREAM_RING) + need > STREAM_RING) p = (p / STREAM_RING + 1u) * STREAM_RING;  // no wrap inside
+          if (p + need - tail > STREAM_RING) break;                                            // ring full
+          const uint32_t slot = (uses + i) % STREAM_SLOTS;
           if (lane_id == 0) {
-            ok = *sh_bad ? 0 : (mbar_wait(&full[slot], par, g.timeout_ns) ? 1 : 2);
-            if (ok == 2) {
-              atomicOr(s.err, 2u);
-              *sh_bad = 1;
+            SlotInfo& si = wa->slot[slot];
+            si.meta = m;
+            si.dst = dref;
+            si.off[0] = p % STREAM_RING;
+            si.off[1] = (p + b0) % STREAM_RING;
+            si.end = p + need;
+            if (!need) {
+              mbar_arrive(&wa->full[slot]);
+            } else {
+              mbar_arrive_expect_tx(&wa->full[slot], need);
+              bulk_g2s(wa->ring + si.off[0], elem(s.state, m.x, s.n_pad, lane0), b0, &wa->full[slot]);
+              if (b1) bulk_g2s(wa->ring + si.off[1], elem(s.state, m.y, s.n_pad, lane0), b1, &wa->full[slot]);
+              if (b2) bulk_g2s(wa->ring + si.off[1] + b1, elem(s.state, m.z, s.n_pad, lane0), b2, &wa->full[slot]);
             }
           }
-          ok = __shfl_sync(0xFFFFFFFFu, ok, 0);  // warp-uniform decision
-          if (ok != 1) break;
-          stream_consume(d, s, info[slot], ring, sa.chunk, c, lane_id, act);
-          __syncwarp();
-          if (lane_id == 0) mbar_arrive(&empty[slot]);
+          head = p + need;
+          issued++;
         }
+        // consume the oldest item
+        const uint32_t i = done, slot = (uses + i) % STREAM_SLOTS, par = ((uses + i) / STREAM_SLOTS) & 1u;
+        int ok = 1;
+        if (lane_id == 0) ok = mbar_wait(&wa->full[slot], par, g.timeout_ns) ? 1 : 0;
+        ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+        if (!ok) {
+          if (lane_id == 0) atomicOr(s.err, 2u);
+          bad = true;
+          break;
+        }
+        const SlotInfo& si = wa->slot[slot];
+        stream_item<H>(d, s, si, wa->ring, lane0, lane_id, am);
+        tail = si.end;
+        __syncwarp();
+        if (lane_id == 0) fence_proxy_async();  // the bytes just read may be overwritten by later copies
+        done++;
       }
-      kk += n_items;
-      __syncthreads();
-      if (*sh_bad) {
-        // drain: wait (bounded) for the copies this CTA actually issued and that
-        // may still be in flight (the last NS items up to the producer's count),
-        // then leave; a drain wait that gives up is reported as its own bit
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          const uint32_t issued = *sh_issued;
-          const uint32_t first = issued > STREAM_NS ? issued - STREAM_NS : 0;
-          for (uint32_t k = first; k < issued; k++)
-            if (!mbar_wait(&full[k % STREAM_NS], (k / STREAM_NS) & 1u, g.timeout_ns)) {
+      if (bad) {
+        // wait (bounded) for the copies this warp issued and has not consumed,
+        // the timed-out item's included
+        if (lane_id == 0)
+          for (uint32_t i = done; i < issued; i++) {
+            const uint32_t slot = (uses + i) % STREAM_SLOTS, par = ((uses + i) / STREAM_SLOTS) & 1u;
+            if (!mbar_wait(&wa->full[slot], par, g.timeout_ns)) {
               atomicOr(s.err, 4u);
               break;
             }
-        }
-        __syncthreads();
+          }
+        __syncwarp();
         grid_sync(g, s.err, &sh_ok);
         return;
       }
-      if (!grid_sync(g, s.err, &sh_ok)) return;
+      uses += ni;
+      if (!grid_sync_staging(g, s.err, &sh_ok, [&] { stream_stage(d, L + 1u, wr, wa, lane_id); })) return;
     }
     commit_items<STREAM_V>(d, s, RT_SPACE, c);
     if (!grid_sync(g, s.err, &sh_ok)) return;

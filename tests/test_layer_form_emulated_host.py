@@ -204,8 +204,8 @@ KERNEL_MUTANTS = [
     ("narrow SUB operands swapped",
      "case OP_SUB: RT_LANES(a.x[v] - b.x[v]); break;\n    case OP_MUL: RT_LANES(a.x[v] * b.x[v]); if (ar == 3) RT_LANES(r.x[v] * c.x[v]); break;\n    case OP_SHL: RT_LANES(p0 >= 32u",
      "case OP_SUB: RT_LANES(b.x[v] - a.x[v]); break;\n    case OP_MUL: RT_LANES(a.x[v] * b.x[v]); if (ar == 3) RT_LANES(r.x[v] * c.x[v]); break;\n    case OP_SHL: RT_LANES(p0 >= 32u"),
-    ("packed 1-byte lanes: upper lanes from the first word",
-     "x.x[v] = __byte_perm(r.w[v >> 2], 0u, 0x4440u + (v & 3));", "x.x[v] = __byte_perm(r.w[0], 0u, 0x4440u + (v & 3));"),
+    ("8-lane 1-byte gather: upper lanes from the lower word",
+     "r.x[4 + v] = __byte_perm(t.y, 0u, 0x4440u + v);", "r.x[4 + v] = __byte_perm(t.x, 0u, 0x4440u + v);"),
     ("rows in flight: the next kind skips the rows past the boundary",
      "    return next;\n  }\n}", "    return r;\n  }\n}"),
     ("4-lane 2-byte store: lanes swapped within a word",
