@@ -82,6 +82,24 @@ def algorithmic_bytes_per_instance_cycle(nl: synth.Netlist, lanes_sharing_meta: 
             "total": ops + regs + inputs + memw + meta}
 
 
+def live_ops(nl: synth.Netlist) -> int:
+    """Ops whose value can reach state that outlives the cycle: the transitive
+    fan-in cone of every register's next state and every write-port signal.
+    Code generated per design (the specialised form) may drop the others from
+    every cycle whose values are not stored, so a rate over all ops would count
+    evaluations that never happen."""
+    live = np.zeros(nl.n_signals, bool)
+    live[nl.reg_d.astype(np.int64)] = True
+    if nl.n_wports:
+        live[nl.wport[:, 1:].reshape(-1).astype(np.int64)] = True
+    args = nl.args.astype(np.int64)
+    off = nl.op_argoff.astype(np.int64)
+    for k in range(nl.n_ops - 1, -1, -1):        # operands precede their op
+        if live[nl.op_base + k]:
+            live[args[off[k]:off[k + 1]]] = True
+    return int(live[nl.op_base:].sum())
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -327,6 +345,7 @@ def run_ours(args) -> None:
     if world > 1:
         t_max, evals = reduce_over_ranks(t_ms, evals, dev)
     value = evals / (t_max / 1e3)
+    n_live = live_ops(nl) if info["kernel"] == 6 else None
 
     # ---- roofline of the dominant kernel (one k_tile launch per step)
     sharing = info["tile_lanes"] if info["kernel"] == 2 else n
@@ -338,6 +357,9 @@ def run_ours(args) -> None:
         ev, sk = ev1 - act0[0], sk1 - act0[1]
         frac_eval = ev / max(1, ev + sk)
         activity = {"items_evaluated": ev, "items_skipped": sk, "evaluated_fraction": frac_eval,
+                    "value_is": "equivalent rate: skipped op-evaluations (unchanged operands) are counted "
+                                "as evaluated; evaluated_op_evals_per_s counts only the evaluated ones",
+                    "evaluated_op_evals_per_s": value * frac_eval,
                     "item": "(op, lanes of one thread) with an active lane"}
         per_launch_bytes *= frac_eval
     avg_launch_s = float(np.mean(step_ms)) / 1e3
@@ -505,6 +527,12 @@ def run_ours(args) -> None:
                                   "kernel is bound by instruction issue"}),
             "gpu_launches": 1 * args.steps,
             "activity": activity,
+            "specialized": ({"live_ops": n_live, "ops": nl.n_ops,
+                             "value_counting_live_ops": value * ((n_live * (C - 1) + nl.n_ops) / (C * nl.n_ops)),
+                             "note": "straight-line code stores every row in the last cycle of a step only, so "
+                                     "ops outside the live cone may be dropped from the other cycles; this rate "
+                                     "counts the live ops every cycle and all ops in the last"}
+                            if info["kernel"] == 6 else None),
             "plain_single_instance": plain,
             "job": job,
             "clocks": clk.summary(),
@@ -528,9 +556,12 @@ def run_serving(args) -> None:
     torch.cuda.set_device(0)
     sizes = {"d50k": 50_000, "d500k": 500_000, "d5M": 5_000_000}
     nls = {k: synth.generate(synth.spec_serving(v, seed=40 + i)) for i, (k, v) in enumerate(sizes.items())}
-    capacity = {"d50k": 512, "d500k": 512, "d5M": 256}
+    # pools sized to hold a saturated queue of 1-64-instance jobs of each design
+    capacity = {"d50k": 2048, "d500k": 1024, "d5M": 512}
+    pool_kw = ({"kernel": "stream"} if args.kernel == "stream" else
+               {"kernel": "grid", "sim_kw": dict(threads=224, ctas_per_sm=4, lanes_per_thread=8)})
     srv = build_server({k: v.to_bytes() for k, v in nls.items()}, capacity, quantum=args.quantum,
-                       autotune=args.serve_autotune)
+                       autotune=args.serve_autotune, **pool_kw)
     warm = [Job(10_000 + i, k, 1, 10, seed=1, arrival=0.0) for i, k in enumerate(sizes)]
     srv.run(warm)
     srv.done.clear()
@@ -586,14 +617,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch-1M", choices=sorted(WORKLOADS) + ["serving"])
-    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-jobs", type=int, default=120)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-load", type=float, default=0.0,
                     help="serving: also replay a trace offering this fraction of the measured capacity")
     ap.add_argument("--quantum", type=int, default=2000)
     ap.add_argument("--serve-autotune", action="store_true",
                     help="serving: autotune each pool's launch configuration when it is created")
-    ap.add_argument("--cycles-cap", type=int, default=0)
+    ap.add_argument("--cycles-cap", type=int, default=10_000,
+                    help="serving: cap on the lognormal cycle counts (0: none); stated in the line")
     ap.add_argument("--kernel", default="tile")
     ap.add_argument("--plain-cycles", type=int, default=20,
                     help="cycles of the plain single-instance form timed for comparison (0: skip)")

@@ -249,6 +249,11 @@ enum {
                                shared-memory ring with bulk copies (TMA engine,
                                mbarriers), consumer warps compute from it; needs a
                                multiple of 128 lanes                              */
+  RTEAAL_KERNEL_CLUSTER = 7,  /* thread-block clusters (up to 16 CTAs, one per SM)
+                               each own a tile of tile_lanes lanes and walk every
+                               layer of every cycle of it with the hardware
+                               cluster barrier between layers (for few lanes:
+                               one instance, the tail of a job)                   */
   RTEAAL_KERNEL_SPECIALIZED = 6 /* design-specialised (Sec. 5.2 SU / TI on the GPU):
                                the op list unrolled into straight-line code compiled
                                at run time (NVRTC), every signal a local variable,
@@ -282,6 +287,7 @@ typedef struct {
    * GRID kernel only (configure refuses the others: E_UNSUPPORTED); costs one
    * byte of device memory per row and chunk.  Fixed at creation. */
   int activity;
+  uint32_t cluster_ctas;   /* CLUSTER: CTAs per cluster (2..16), 0 auto          */
 } rteaal_sim_opts;
 
 typedef struct {
@@ -293,6 +299,7 @@ typedef struct {
   int activity;                  /* activity-aware evaluation on                  */
   uint32_t last_span;            /* lanes the last rteaal_step visited (live prefix) */
   uint32_t last_grid;            /* CTAs of the last GRID launch (0: none yet)    */
+  uint32_t cluster_ctas;         /* CLUSTER: CTAs per cluster                     */
 } rteaal_sim_stats;
 
 /* Allocates and zero-initialises the state of n_instances (>= 1) independent
@@ -308,19 +315,20 @@ int rteaal_sim_info(const rteaal_sim *sim, rteaal_sim_stats *out);
 void rteaal_sim_destroy(rteaal_sim *sim);
 
 /* Change the launch configuration (kernel, tile_lanes, threads, ctas_per_sm,
- * unroll, lanes_per_thread of opts; the other fields are ignored).  Results never depend on it.
+ * unroll, lanes_per_thread, cluster_ctas of opts; the other fields are ignored).  Results never depend on it.
  * Errors: E_INVALID, E_UNSUPPORTED (no compiled variant). */
 int rteaal_sim_configure(rteaal_sim *sim, const rteaal_sim_opts *opts);
 
 typedef struct {
   int kernel;
-  uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid, lanes_per_thread;
+  uint32_t tile_lanes, threads, ctas_per_sm, unroll, grid, lanes_per_thread;  /* CLUSTER:
+                                    ctas_per_sm holds the CTAs per cluster */
   float ms;                      /* device time of one trial step                 */
 } rteaal_tune_trial;
 
 /* Autotuner: times every candidate launch configuration of the kernels in
- * kernel_mask (bit 1 << RTEAAL_KERNEL_*, 0 = TILE|GRID|STREAM, or LAYER|GRID for
- * fewer than 64 lanes) on this sim, one warm-up and one timed step of
+ * kernel_mask (bit 1 << RTEAAL_KERNEL_*, 0 = TILE|GRID|STREAM, or
+ * LAYER|GRID|CLUSTER for fewer than 64 lanes) on this sim, one warm-up and one timed step of
  * cycles_per_trial cycles each, keeps the fastest, and restores the state,
  * memories and stimulus states exactly (device-to-device snapshot: needs
  * free device memory equal to the sim's state).  trials (nullable) receives

@@ -27,7 +27,8 @@ RTEAAL_STIM_HOLD, RTEAAL_STIM_XORSHIFT, RTEAAL_STIM_BUFFER = 0, 1, 2
 RTEAAL_PROBE_LAST, RTEAAL_PROBE_EVERY, RTEAAL_PROBE_CHANGES = 0, 1, 2
 RTEAAL_STEP_RESET = 1
 
-KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4, "stream": 5, "specialized": 6}
+KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4, "stream": 5, "specialized": 6,
+           "cluster": 7}
 
 
 class RteaalError(RuntimeError):
@@ -66,14 +67,15 @@ class rteaal_sim_opts(ctypes.Structure):
                 ("xorshift_seed", ctypes.POINTER(_U64)),
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
                 ("ctas_per_sm", _U32), ("unroll", _U32), ("lanes_per_thread", _U32),
-                ("activity", ctypes.c_int)]
+                ("activity", ctypes.c_int), ("cluster_ctas", _U32)]
 
 
 class rteaal_sim_stats(ctypes.Structure):
     _fields_ = [("n_instances", _U32), ("n_lanes", _U32), ("device_bytes", _U64),
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
                 ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("lanes_per_thread", _U32),
-                ("activity", ctypes.c_int), ("last_span", _U32), ("last_grid", _U32)]
+                ("activity", ctypes.c_int), ("last_span", _U32), ("last_grid", _U32),
+                ("cluster_ctas", _U32)]
 
 
 class rteaal_tune_trial(ctypes.Structure):
@@ -507,7 +509,8 @@ class Sim:
     def __init__(self, design: Design, n_instances: int, kernel: str | int = "auto",
                  xorshift_seed: np.ndarray | None = None, expected_cycles=None,
                  tile_lanes: int = 0, threads: int = 0, ctas_per_sm: int = 0, unroll: int = 0,
-                 lanes_per_thread: int = 0, use_torch_allocator: bool = True, activity: bool = False):
+                 lanes_per_thread: int = 0, use_torch_allocator: bool = True, activity: bool = False,
+                 cluster_ctas: int = 0):
         self.design = design
         self.n = n_instances
         o = rteaal_sim_opts()
@@ -515,6 +518,7 @@ class Sim:
         o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
         o.lanes_per_thread = lanes_per_thread
         o.activity = int(activity)
+        o.cluster_ctas = cluster_ctas
         keep: list[Any] = []
         if use_torch_allocator:
             self._alloc = torch_allocator()
@@ -609,11 +613,12 @@ class Sim:
         return rteaal_sim_activity(self.handle, stream)
 
     def configure(self, kernel: str | int = "auto", tile_lanes: int = 0, threads: int = 0,
-                  ctas_per_sm: int = 0, unroll: int = 0, lanes_per_thread: int = 0):
+                  ctas_per_sm: int = 0, unroll: int = 0, lanes_per_thread: int = 0, cluster_ctas: int = 0):
         o = rteaal_sim_opts()
         o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
         o.lanes_per_thread = lanes_per_thread
+        o.cluster_ctas = cluster_ctas
         rteaal_sim_configure(self.handle, o)
 
     def autotune(self, cycles_per_trial: int = 1, kernels=None, stream=None) -> list[dict]:

@@ -26,6 +26,7 @@
 #include "kernels.cuh"
 #include "host_api.hpp"
 #include "lower.hpp"
+#include "cluster.cuh"
 #include "persistent.cuh"
 #include "rteaal.h"
 
@@ -273,7 +274,9 @@ struct rteaal_sim {
   uint64_t barrier_timeout_ns = 2000000000ull;
   uint32_t barrier_extra = 0;        // test hook: arrivals withheld from every grid barrier
   uint32_t stream_chunk = 0;         // STREAM: lanes per item
-  uint32_t stage_cap = 0;            // GRID: descriptors a CTA stages in shared memory
+  uint32_t stage_cap = 0;            // GRID, CLUSTER: descriptors a CTA stages in shared memory
+  uint32_t cluster_ctas = 0;         // CLUSTER: CTAs per cluster
+  uint32_t n_clusters = 0;           // CLUSTER: clusters resident at once
   uint32_t last_span = 0;            // lanes the last step visited
   uint32_t last_grid = 0;            // CTAs of the last GRID launch
   // activity-aware evaluation (GRID only)
@@ -416,6 +419,13 @@ const std::vector<ActVariant>& all_act_variants() {
     return v;
   }();
   return all;
+}
+
+const ClusterVariant* find_cluster_variant(int V) {
+  static const ClusterVariantTable t = variants_cluster();
+  for (size_t i = 0; i < t.n; i++)
+    if (t.v[i].V == V) return &t.v[i];
+  return nullptr;
 }
 
 const ActVariant* find_act_variant(int V, uint32_t threads, uint32_t minb = 0) {
@@ -646,14 +656,16 @@ uint32_t stage_capacity(uint32_t chunks, uint32_t grid, uint32_t threads, uint32
 
 // Validate and apply a launch configuration (never changes results).
 void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
-               uint32_t unroll, uint32_t lanes_per_thread) {
+               uint32_t unroll, uint32_t lanes_per_thread, uint32_t cluster_ctas = 0) {
   if (kernel == RTEAAL_KERNEL_AUTO)
     kernel = s->activity ? RTEAAL_KERNEL_GRID : s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
   if (s->activity && kernel != RTEAAL_KERNEL_GRID)
     throw Error(RTEAAL_E_UNSUPPORTED, "activity-aware evaluation runs with the GRID kernel only");
   if (s->activity && unroll > 1)
     throw Error(RTEAAL_E_UNSUPPORTED, "activity-aware evaluation has no unrolled variants");
-  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_SPECIALIZED, "unknown kernel");
+  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_CLUSTER, "unknown kernel");
+  if (kernel == RTEAAL_KERNEL_CLUSTER && !tile_lanes)  // a cluster tile: all lanes of a small sim, else 256 / 128
+    tile_lanes = s->n_pad <= 256 ? s->n_pad : s->n_pad % 256 == 0 ? 256u : 128u;
   if (!unroll) unroll = 1;
   require(unroll == 1 || unroll == 2 || unroll == 4, "unroll must be 1, 2 or 4");
   if (!threads) threads = 512;
@@ -663,6 +675,10 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
               lanes_per_thread == 8,
           "lanes_per_thread must be 1, 2, 4 or 8");
   uint32_t span = s->n_pad;  // lanes that one V-lane chunk must divide
+  if (kernel == RTEAAL_KERNEL_CLUSTER) {
+    require(tile_lanes >= 1 && s->n_pad % tile_lanes == 0, "cluster tile_lanes must divide the padded lane count");
+    span = tile_lanes;
+  }
   if (kernel == RTEAAL_KERNEL_TILE) {
     require(tile_lanes >= 1 && tile_lanes <= 64 && (tile_lanes & (tile_lanes - 1)) == 0,
             "tile_lanes must be a power of two <= 64");
@@ -672,11 +688,19 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
   int V = (int)lanes_per_thread;
   if (!V) {  // widest V that divides the span and (persistent forms) has a compiled variant
     const bool persistent = kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID;
-    for (int c : {4, 2, 1, 8})
-      if (span % (uint32_t)c == 0 && (!persistent || find_variant(c, unroll ? unroll : 1, threads ? threads : 512))) {
-        V = c;
-        break;
-      }
+    if (kernel == RTEAAL_KERNEL_CLUSTER) {
+      for (int c : {8, 4, 2, 1})
+        if (span % (uint32_t)c == 0 && find_cluster_variant(c)) {
+          V = c;
+          break;
+        }
+    } else {
+      for (int c : {4, 2, 1, 8})
+        if (span % (uint32_t)c == 0 && (!persistent || find_variant(c, unroll ? unroll : 1, threads ? threads : 512))) {
+          V = c;
+          break;
+        }
+    }
     if (!V) V = 1;
   }
   require(span % (uint32_t)V == 0, "lanes_per_thread must divide the lanes of a tile / the padded lane count");
@@ -689,6 +713,46 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     unroll = 1;
     ctas_per_sm = 0;
     grid = (uint32_t)((s->n_pad + kSpecThreads - 1) / kSpecThreads);
+  } else if (kernel == RTEAAL_KERNEL_CLUSTER) {
+    const ClusterVariant* cv = find_cluster_variant(V);
+    if (!cv) throw Error(RTEAAL_E_UNSUPPORTED, "no compiled cluster variant for V=" + std::to_string(V));
+    threads = (uint32_t)cv->maxt;
+    unroll = 1;
+    require(cluster_ctas == 0 || (cluster_ctas >= 1 && cluster_ctas <= 16), "cluster_ctas must be in 1..16");
+    CK(cudaFuncSetAttribute(cv->fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    const Lowered& L = s->design->L;
+    uint32_t best_cs = 0, best_ncl = 0;
+    for (uint32_t cs : {16u, 8u, 4u, 2u, 1u}) {
+      if (cluster_ctas && cs != cluster_ctas) continue;
+      stage = stage_capacity(tile_lanes / (uint32_t)V, cs, threads, L.max_layer_ops, 1);
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cs;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(threads);
+      cfg.dynamicSmemBytes = (size_t)stage * kStageBytes;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, cv->fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        ncl = 0;
+      }
+      if (ncl > 0) {
+        best_cs = cs;
+        best_ncl = (uint32_t)ncl;
+        break;
+      }
+    }
+    if (!best_cs) throw Error(RTEAAL_E_UNSUPPORTED, "cluster kernel cannot be resident");
+    stage = stage_capacity(tile_lanes / (uint32_t)V, best_cs, threads, L.max_layer_ops, 1);
+    s->cluster_ctas = best_cs;
+    s->n_clusters = std::min<uint32_t>(best_ncl, s->n_pad / tile_lanes);
+    ctas_per_sm = 1;
+    grid = s->n_clusters * best_cs;
   } else if (kernel == RTEAAL_KERNEL_STREAM) {
     // one CTA of STREAM_WARPS warps per SM; items of 256 lanes (128 when the
     // lane count is an odd multiple of 128); every warp keeps one chunk
@@ -838,7 +902,7 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       s->n_pad = pad_lanes(n_instances);
       s->activity = opts && opts->activity;
       configure(s, opts ? opts->kernel : 0, opts ? opts->tile_lanes : 0, opts ? opts->threads : 0,
-                opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0, opt_lanes(opts));
+                opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0, opt_lanes(opts), opts ? opts->cluster_ctas : 0);
       if (const char* e = getenv("RTEAAL_TEST_WITHHOLD_ARRIVAL")) s->barrier_extra = (uint32_t)atoi(e);
       if (const char* e = getenv("RTEAAL_BARRIER_TIMEOUT_NS")) s->barrier_timeout_ns = strtoull(e, nullptr, 10);
 
@@ -931,7 +995,8 @@ RT_EXPORT int rteaal_sim_configure(rteaal_sim* s, const rteaal_sim_opts* o) {
   return guarded([&] {
     require(s && o, "rteaal_sim_configure: null argument");
     CK(cudaSetDevice(s->design->device));
-    configure(s, o->kernel, o->tile_lanes, o->threads, o->ctas_per_sm, o->unroll, o->lanes_per_thread);
+    configure(s, o->kernel, o->tile_lanes, o->threads, o->ctas_per_sm, o->unroll, o->lanes_per_thread,
+              o->cluster_ctas);
   });
 }
 
@@ -951,6 +1016,7 @@ RT_EXPORT int rteaal_sim_info(const rteaal_sim* s, rteaal_sim_stats* o) {
     o->activity = s->activity ? 1 : 0;
     o->last_span = s->last_span;
     o->last_grid = s->last_grid;
+    o->cluster_ctas = s->kernel == RTEAAL_KERNEL_CLUSTER ? s->cluster_ctas : 0;
   });
 }
 
@@ -993,7 +1059,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     if (!kernel_mask)
       kernel_mask = s->n_pad >= 64 ? ((1u << RTEAAL_KERNEL_TILE) | (1u << RTEAAL_KERNEL_GRID) |
                                       (1u << RTEAAL_KERNEL_STREAM))
-                                   : ((1u << RTEAAL_KERNEL_LAYER) | (1u << RTEAAL_KERNEL_GRID));
+                                   : ((1u << RTEAAL_KERNEL_LAYER) | (1u << RTEAAL_KERNEL_GRID) |
+                                      (1u << RTEAAL_KERNEL_CLUSTER));
     const Lowered& L = s->design->L;
     const size_t np = s->n_pad;
     const size_t b_state = np * L.lane_bytes, b_mem = np * 8 * L.mem_words_total,
@@ -1029,6 +1096,12 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
       for (uint32_t U : {2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER_GRAPH, 0, 256, U, 0});
     if ((kernel_mask & (1u << RTEAAL_KERNEL_STREAM)) && np % 128 == 0)
       cands.push_back({RTEAAL_KERNEL_STREAM, 0, 0, 1, 0});
+    if (kernel_mask & (1u << RTEAAL_KERNEL_CLUSTER))  // ctas: CTAs per cluster
+      for (uint32_t T : {np <= 256 ? (uint32_t)np : 256u, np <= 128 ? (uint32_t)np : 128u})
+        if (np % T == 0)
+          for (uint32_t V : {1u, 2u, 4u, 8u})
+            if (T % V == 0 && find_cluster_variant((int)V))
+              for (uint32_t cs : {16u, 8u}) candx.push_back({RTEAAL_KERNEL_CLUSTER, T, 0, 1, V, cs});
     for (const Cand& c : cands) candx.push_back({c.kernel, c.T, c.threads, c.U, c.V, 0});
 
     const int saved[6] = {s->kernel, (int)s->tile_lanes, (int)s->threads, (int)s->ctas_per_sm, (int)s->unroll,
@@ -1045,7 +1118,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     uint32_t nt = 0;
     for (const CandX& c : candx) {
       try {
-        configure(s, c.kernel, c.T, c.threads, c.ctas, c.U, c.V);
+        const bool cl = c.kernel == RTEAAL_KERNEL_CLUSTER;
+        configure(s, c.kernel, c.T, c.threads, cl ? 0 : c.ctas, c.U, c.V, cl ? c.ctas : 0);
       } catch (const Error&) {
         continue;  // not compiled / not resident
       }
@@ -1058,19 +1132,23 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, e0, e1));
       if (trials && nt < max_trials)
-        trials[nt] = rteaal_tune_trial{s->kernel, s->tile_lanes, s->threads, s->ctas_per_sm, s->unroll, s->grid,
-                                       (uint32_t)s->V, ms};
+        trials[nt] = rteaal_tune_trial{s->kernel, s->tile_lanes, s->threads,
+                                       s->kernel == RTEAAL_KERNEL_CLUSTER ? s->cluster_ctas : s->ctas_per_sm,
+                                       s->unroll, s->grid, (uint32_t)s->V, ms};
       nt++;
       if (ms < best) {
         best = ms;
         best_c = c;
-        best_ctas = c.ctas ? c.ctas : s->ctas_per_sm;  // the variant's target selects it again
+        best_ctas = c.ctas ? c.ctas : s->kernel == RTEAAL_KERNEL_CLUSTER ? s->cluster_ctas
+                                                                        : s->ctas_per_sm;  // selects it again
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (n_trials) *n_trials = nt;
-    configure(s, best_c.kernel, best_c.T, best_c.threads, best_ctas, best_c.U, best_c.V);
+    const bool best_cl = best_c.kernel == RTEAAL_KERNEL_CLUSTER;
+    configure(s, best_c.kernel, best_c.T, best_c.threads, best_cl ? 0 : best_ctas, best_c.U, best_c.V,
+              best_cl ? best_ctas : 0);
     s->act_force = true;  // restored below; stamps of the trials are stale
     CK(cudaMemcpyAsync(s->state, snap, b_state, cudaMemcpyDeviceToDevice, st));
     if (b_mem) CK(cudaMemcpyAsync(s->mem, snap + b_state, b_mem, cudaMemcpyDeviceToDevice, st));
@@ -1190,6 +1268,7 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
     // lanes this step visits (STREAM: whole chunks; the others: whole warps)
     const uint32_t span = live_span(s, hb, s->kernel == RTEAAL_KERNEL_STREAM ? s->stream_chunk
                                            : s->kernel == RTEAAL_KERNEL_SPECIALIZED ? kSpecThreads
+                                           : s->kernel == RTEAAL_KERNEL_CLUSTER ? s->tile_lanes
                                            : 32u * (uint32_t)s->V);
     s->last_span = span;
     if (s->kernel == RTEAAL_KERNEL_LAYER) {
@@ -1241,6 +1320,41 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       void* args[] = {&a_st, &a_mem, &a_xs, &a_stim, &a_budget, &a_rl, &a_uol, &a_np, &a_nu, &a_uni, &a_mode, &a_reset};
       CK(cudaLaunchKernel((const void*)D->spec_kernel, dim3((span + kSpecThreads - 1) / kSpecThreads),
                           dim3(kSpecThreads), args, 0, st));
+      CK(cudaGetLastError());
+    } else if (s->kernel == RTEAAL_KERNEL_CLUSTER) {
+      require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
+      const uint32_t T = s->tile_lanes;
+      const uint32_t n_tiles = span / T;
+      ClusterArgs ca{};
+      ca.tile_lanes = T;
+      ca.n_tiles = n_tiles;
+      ca.tpo = make_fastdiv(T / (uint32_t)s->V);
+      ca.stage_cap = s->stage_cap;
+      if (cycles->per_instance) {
+        std::vector<uint32_t> tc(n_tiles, 0);
+        for (uint32_t t = 0; t < n_tiles; t++)
+          for (uint32_t l = 0; l < T; l++) tc[t] = std::max(tc[t], hb[(size_t)t * T + l]);
+        CK(cudaMemcpyAsync(s->tile_cycles, tc.data(), n_tiles * 4, cudaMemcpyHostToDevice, st));
+        ca.tile_cycles = s->tile_cycles;
+      }
+      const ClusterVariant* cv = find_cluster_variant(s->V);
+      require(cv != nullptr, "rteaal_step: no cluster variant for this configuration");
+      const uint32_t n_cl = std::max<uint32_t>(1, std::min(s->n_clusters, n_tiles));
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = s->cluster_ctas;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(n_cl * s->cluster_ctas);
+      cfg.blockDim = dim3(s->threads);
+      cfg.dynamicSmemBytes = (size_t)s->stage_cap * kStageBytes;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ca};
+      s->last_grid = n_cl * s->cluster_ctas;
+      CK(cudaLaunchKernelExC(&cfg, cv->fn, args));
       CK(cudaGetLastError());
     } else if (s->kernel == RTEAAL_KERNEL_TILE) {
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");

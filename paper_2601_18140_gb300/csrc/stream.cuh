@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(32 * STREAM_WARPS, 1) k_stream(DDesign d, DSim
           const uint32_t b0 = ar ? CH << (m.x >> 30) : 0u, b1 = ar >= 2 ? CH << (m.y >> 30) : 0u,
                          b2 = ar >= 3 ? CH << (m.z >> 30) : 0u;
           const uint32_t need = b0 + b1 + b2;
+          if (issued == done) head = tail = 0;  // nothing in flight: start the ring afresh (no wrap gap)
           uint32_t p = head;
           if ((p % STREAM_RING) + need > STREAM_RING) p = (p / STREAM_RING + 1u) * STREAM_RING;  // no wrap inside
           if (p + need - tail > STREAM_RING) break;                                            // ring full

@@ -22,9 +22,12 @@ occupies a contiguous range of free lanes of its design's pool:
               read back, its latency (completion - arrival) recorded and its
               lanes freed for the queue.
 
-Pools of different designs are stepped one after another on one stream:
-their grid-form kernels each occupy the whole device, so they cannot run side
-by side.  The policy is host logic only; every step of the simulation runs in
+Pools of different designs are stepped one after another on one stream (the
+grid forms synchronise their CTAs, which must all be resident at once).  A
+step visits only its pool's live lanes -- up to the last lane with cycles
+left, with a grid capped at that work -- and lanes are handed out first-fit
+from the bottom, so a partly filled pool costs in proportion to its live
+lanes.  The policy is host logic only; every step of the simulation runs in
 the library's kernels.
 """
 from __future__ import annotations
@@ -229,7 +232,7 @@ def poisson_trace(rng_seed: int, n_jobs: int, rate_hz: float, designs: list[str]
 
 
 def build_server(netlists: dict, capacity: dict, mem_budget: int | None = None, quantum: int = 1000,
-                 kernel: str = "grid", seed_fn=None, autotune: bool = False):
+                 kernel: str = "grid", seed_fn=None, autotune: bool = False, sim_kw: dict | None = None):
     """Server over the CUDA library: one Design per netlist, pools as Sims."""
     from . import Design, Sim
     import synth  # seeded stimulus (input generator module, no simulation arithmetic)
@@ -241,7 +244,7 @@ def build_server(netlists: dict, capacity: dict, mem_budget: int | None = None, 
         mem_budget = int(free * 0.8)
 
     def backend(name, cap):
-        sim = Sim(designs[name], cap, kernel=kernel)
+        sim = Sim(designs[name], cap, kernel=kernel, **(sim_kw or {}))
         if autotune:
             sim.autotune(cycles_per_trial=1, kernels=["grid", "tile"])
         return sim

@@ -75,3 +75,21 @@ def test_measured_peak_is_read_from_the_driver_file():
         assert p["source"] == "measured" and p["hbm_gbs"] > 1000
     else:
         assert p["source"] == "fallback"
+
+
+def test_live_ops_is_the_cone_of_state():
+    """Ops counted live: the fan-in cone of register next states and write-port
+    signals; an op read only by a dead op is dead too."""
+    b = Builder()
+    i = b.input(8)
+    r = b.reg(8)
+    m = b.mem(4, 8)
+    a = b.op("ADD", 8, r, i)            # live: feeds the register through x
+    x = b.op("XOR", 8, a, i)            # live: the register's D
+    b.op("NOT", 8, x)                   # dead: read by nothing ...
+    d2 = b.op("AND", 8, a, i)           # dead: read only by a dead op
+    b.op("OR", 8, d2, i)                # dead
+    en = b.op("ORR", 1, i)              # live: a write-port enable
+    b.connect(r, x)
+    b.write_port(m, en, i, r)
+    assert bench.live_ops(b.build()) == 3

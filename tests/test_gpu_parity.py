@@ -8,7 +8,7 @@ from tests.gpu_util import Pair
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = ["layer", "layer_graph", "tile", "grid", "stream"]
+KERNELS = ["layer", "layer_graph", "tile", "grid", "stream", "cluster"]
 
 
 def small_design(seed, n_ops=600, depth=10, n_regs=40, n_mems=0, inputs=(8, 32, 64, 1)):
@@ -89,7 +89,7 @@ def test_buffer_stimulus_and_probes(kernel, lanes):
 
 
 @pytest.mark.parametrize("kernel,lanes", [("layer", 0), ("tile", 0), ("grid", 0), ("grid", 8), ("stream", 0),
-                                          ("specialized", 0)])
+                                          ("specialized", 0), ("cluster", 0)])
 def test_wide_ops_and_memories(kernel, lanes):
     """Variadic folds (> 3 operands), long mux chains, two write ports per memory;
     the grid form also at 8 lanes per thread (the benchmark's configuration)."""
@@ -279,4 +279,21 @@ def test_waveform_changes(kernel, lanes):
     recs2, count2 = p.sim.step(3, stimulus="xorshift", probes=probes, probe_mode="changes",
                                change_capacity=5)
     assert len(recs2) == min(5, count2)                       # overflow: count kept, records capped
+    p.close()
+
+
+def test_stream_many_items_per_warp():
+    """Wide layers (15k ops each) over 512 lanes: every warp of the stream form
+    has about a dozen items per layer, so its ring wraps and its slots are
+    reused many times within a layer and across layers."""
+    nl = synth.generate(DesignSpec(n_ops=60_000, n_regs=1000, depth=4, n_inputs=4, seed=71,
+                                   input_widths=(8, 32, 64, 1), n_mems=1, mem_words=8))
+    n = 512
+    budgets = synth.cycle_budgets(71, n, 5, 30)
+    p = Pair(nl, n, kernel="stream", seed=71, expected_cycles=budgets,
+             oracle_instances=[0, 129, 255, 256, 400, n - 1])
+    p.step(1, reset=True)
+    p.step(budgets)
+    p.step(7)
+    p.compare()
     p.close()
