@@ -288,6 +288,10 @@ typedef struct {
    * byte of device memory per row and chunk.  Fixed at creation. */
   int activity;
   uint32_t cluster_ctas;   /* CLUSTER: CTAs per cluster (2..16), 0 auto          */
+  /* CLUSTER with one tile of at most 64 lanes: keep the whole state in the
+   * cluster's distributed shared memory for the length of a step (0: when it
+   * fits, 1: required -- E_UNSUPPORTED if it does not fit, -1: never). */
+  int cluster_resident;
 } rteaal_sim_opts;
 
 typedef struct {
@@ -300,6 +304,7 @@ typedef struct {
   uint32_t last_span;            /* lanes the last rteaal_step visited (live prefix) */
   uint32_t last_grid;            /* CTAs of the last GRID launch (0: none yet)    */
   uint32_t cluster_ctas;         /* CLUSTER: CTAs per cluster                     */
+  int cluster_resident;          /* CLUSTER: state kept in distributed shared memory */
 } rteaal_sim_stats;
 
 /* Allocates and zero-initialises the state of n_instances (>= 1) independent
@@ -315,7 +320,8 @@ int rteaal_sim_info(const rteaal_sim *sim, rteaal_sim_stats *out);
 void rteaal_sim_destroy(rteaal_sim *sim);
 
 /* Change the launch configuration (kernel, tile_lanes, threads, ctas_per_sm,
- * unroll, lanes_per_thread, cluster_ctas of opts; the other fields are ignored).  Results never depend on it.
+ * unroll, lanes_per_thread, cluster_ctas, cluster_resident of opts; the other
+ * fields are ignored).  Results never depend on it.
  * Errors: E_INVALID, E_UNSUPPORTED (no compiled variant). */
 int rteaal_sim_configure(rteaal_sim *sim, const rteaal_sim_opts *opts);
 

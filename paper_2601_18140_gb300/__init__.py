@@ -67,7 +67,7 @@ class rteaal_sim_opts(ctypes.Structure):
                 ("xorshift_seed", ctypes.POINTER(_U64)),
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
                 ("ctas_per_sm", _U32), ("unroll", _U32), ("lanes_per_thread", _U32),
-                ("activity", ctypes.c_int), ("cluster_ctas", _U32)]
+                ("activity", ctypes.c_int), ("cluster_ctas", _U32), ("cluster_resident", ctypes.c_int)]
 
 
 class rteaal_sim_stats(ctypes.Structure):
@@ -75,7 +75,7 @@ class rteaal_sim_stats(ctypes.Structure):
                 ("kernel", ctypes.c_int), ("tile_lanes", _U32), ("threads", _U32),
                 ("ctas_per_sm", _U32), ("unroll", _U32), ("grid", _U32), ("lanes_per_thread", _U32),
                 ("activity", ctypes.c_int), ("last_span", _U32), ("last_grid", _U32),
-                ("cluster_ctas", _U32)]
+                ("cluster_ctas", _U32), ("cluster_resident", ctypes.c_int)]
 
 
 class rteaal_tune_trial(ctypes.Structure):
@@ -510,7 +510,7 @@ class Sim:
                  xorshift_seed: np.ndarray | None = None, expected_cycles=None,
                  tile_lanes: int = 0, threads: int = 0, ctas_per_sm: int = 0, unroll: int = 0,
                  lanes_per_thread: int = 0, use_torch_allocator: bool = True, activity: bool = False,
-                 cluster_ctas: int = 0):
+                 cluster_ctas: int = 0, cluster_resident: int = 0):
         self.design = design
         self.n = n_instances
         o = rteaal_sim_opts()
@@ -519,6 +519,7 @@ class Sim:
         o.lanes_per_thread = lanes_per_thread
         o.activity = int(activity)
         o.cluster_ctas = cluster_ctas
+        o.cluster_resident = cluster_resident
         keep: list[Any] = []
         if use_torch_allocator:
             self._alloc = torch_allocator()
@@ -613,12 +614,14 @@ class Sim:
         return rteaal_sim_activity(self.handle, stream)
 
     def configure(self, kernel: str | int = "auto", tile_lanes: int = 0, threads: int = 0,
-                  ctas_per_sm: int = 0, unroll: int = 0, lanes_per_thread: int = 0, cluster_ctas: int = 0):
+                  ctas_per_sm: int = 0, unroll: int = 0, lanes_per_thread: int = 0, cluster_ctas: int = 0,
+                  cluster_resident: int = 0):
         o = rteaal_sim_opts()
         o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         o.tile_lanes, o.threads, o.ctas_per_sm, o.unroll = tile_lanes, threads, ctas_per_sm, unroll
         o.lanes_per_thread = lanes_per_thread
         o.cluster_ctas = cluster_ctas
+        o.cluster_resident = cluster_resident
         rteaal_sim_configure(self.handle, o)
 
     def autotune(self, cycles_per_trial: int = 1, kernels=None, stream=None) -> list[dict]:

@@ -118,6 +118,209 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(DDesign d, DSim s, ClusterA
   }
 }
 
+// ---- resident variant (few lanes): the whole compact state lives in the
+// cluster's distributed shared memory.  The state's bytes (lane_bytes x lanes)
+// are split into cluster-size slices of S bytes; CTA q keeps bytes
+// [q S, (q + 1) S) in its shared memory, loaded from global memory when the
+// launch starts and written back when it ends.  S is a multiple of 16 and
+// every element is naturally aligned at its size, so an element never straddles
+// two slices: it is one load or store at a generic address inside the
+// cluster's shared-memory window (mapa).  Memories, stimulus states and probes
+// stay in global memory.  One lane per thread; the cluster barrier orders the
+// shared::cluster accesses of one phase before the next.
+struct ResidentArgs {
+  uint32_t ncyc;       // cycles of this step (lanes stop at their own budgets)
+  uint32_t bytes;      // state bytes (lane_bytes x lanes)
+  FastDiv slice;       // S
+  FastDiv tpo;         // lanes (one lane per thread)
+  uint32_t stage_cap;  // descriptors a CTA can stage (0: none)
+};
+
+__device__ __forceinline__ uint8_t* dsmem_map(uint8_t* p, uint32_t rank) {
+  uint64_t r;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+  return reinterpret_cast<uint8_t*>(r);
+}
+
+// Element (row ref, lane) of the resident state.
+__device__ __forceinline__ uint8_t* res_elem(uint8_t* const* base, const ResidentArgs& ra, uint32_t ref,
+                                             uint32_t lane) {
+  const uint32_t o = (ref & REF_OFF_MASK) * ra.tpo.d + (lane << (ref >> 30));
+  const uint32_t q = fdiv(ra.slice, o);
+  return base[q] + (o - q * ra.slice.d);
+}
+
+__device__ __forceinline__ uint64_t res_ld(uint8_t* const* base, const ResidentArgs& ra, uint32_t ref,
+                                           uint32_t lane) {
+  const uint8_t* p = res_elem(base, ra, ref, lane);
+  switch (ref >> 30) {
+    case 0: return *p;
+    case 1: return *reinterpret_cast<const uint16_t*>(p);
+    case 2: return *reinterpret_cast<const uint32_t*>(p);
+    default: return *reinterpret_cast<const uint64_t*>(p);
+  }
+}
+
+__device__ __forceinline__ void res_st(uint8_t* const* base, const ResidentArgs& ra, uint32_t ref, uint32_t lane,
+                                       uint64_t v) {
+  uint8_t* p = res_elem(base, ra, ref, lane);
+  switch (ref >> 30) {
+    case 0: *p = (uint8_t)v; break;
+    case 1: *reinterpret_cast<uint16_t*>(p) = (uint16_t)v; break;
+    case 2: *reinterpret_cast<uint32_t*>(p) = (uint32_t)v; break;
+    default: *reinterpret_cast<uint64_t*>(p) = v; break;
+  }
+}
+
+// (a2) one op for one lane from the resident state.
+__device__ __forceinline__ void res_item(const DDesign& d, const DSim& s, uint8_t* const* base,
+                                         const ResidentArgs& ra, const uint4& m, uint32_t dref, uint32_t lane) {
+  uint64_t r;
+  if (m.w & CTL_EXT) {
+    const Lanes<1> x = ext_eval<1, Lanes<1>>(d.ext + m.x, m.w & 31u, m.y, [&](uint32_t ref) {
+      Lanes<1> y;
+      y.x[0] = res_ld(base, ra, ref, lane);
+      return y;
+    });
+    r = x.x[0] & wmask(ctl_width(m.w));
+  } else {
+    const uint32_t ar = (m.w >> 5) & 3u;
+    const uint64_t a = res_ld(base, ra, m.x, lane);
+    const uint64_t b = ar >= 2 ? res_ld(base, ra, m.y, lane) : 0ull;
+    const uint64_t c = ar >= 3 ? res_ld(base, ra, m.z, lane) : 0ull;
+    r = (m.w & 31u) == OP_MEMRD ? eval_memrd(d, s, m.w, a, lane) : alu(m.w, a, b, c);
+  }
+  res_st(base, ra, dref, lane, r);
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, ResidentArgs ra) {
+  extern __shared__ __align__(16) uint8_t sm_res[];  // [S] state slice, [stage_cap] descriptors, [stage_cap] rows
+  __shared__ uint8_t* base[16];
+  const uint32_t S = ra.slice.d;
+  uint8_t* slice = sm_res;
+  uint4* sm_meta = reinterpret_cast<uint4*>(sm_res + S);
+  uint32_t* sm_dst = reinterpret_cast<uint32_t*>(sm_meta + ra.stage_cap);
+  const uint32_t rank = cluster_rank(), cs = cluster_size(), nthreads = cs * blockDim.x;
+  const uint32_t ct = rank * blockDim.x + threadIdx.x;
+  if (threadIdx.x < cs) base[threadIdx.x] = dsmem_map(slice, threadIdx.x);
+  {  // this CTA's slice of the state from global memory
+    const uint32_t lo = rank * S, hi = min(lo + S, ra.bytes);
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) slice[i - lo] = s.state[i];
+  }
+  const Stage st = stage_of_cluster_cta(ra.tpo, rank, nthreads);
+  __syncthreads();
+  cluster_arrive();
+  cluster_wait();
+#define RT_SPACE make_space<1>(ra.tpo, 0u, ct, nthreads)
+#define RT_STAGE(L)                                                                                  \
+  [&] {                                                                                             \
+    if (ra.stage_cap && (L) < d.n_layers) stage_layer(d, (L), st, ra.stage_cap, sm_meta, sm_dst);   \
+  }
+  for (uint32_t c = 0; c < ra.ncyc; c++) {
+    // (a1) inputs
+    if (s.stim_mode)
+      for_rows<1>(RT_SPACE, d.n_inputs, [&](uint32_t j, uint32_t lane) {
+        if (!lane_active(s, lane, c)) return;
+        uint64_t x;
+        if (s.stim_mode == 1) {
+          x = s.xs[(size_t)j * s.n_pad + lane];
+          x ^= x << 13;
+          x ^= x >> 7;
+          x ^= x << 17;
+          s.xs[(size_t)j * s.n_pad + lane] = x;
+        } else {
+          x = __ldg(&s.stim[((size_t)c * d.n_inputs + j) * s.n_user + user_of(s, lane)]);
+        }
+        res_st(base, ra, __ldg(&d.in_ref[j]), lane, x & wmask(__ldg(&d.in_w[j])));
+      });
+    cluster_phase_sync(RT_STAGE(0u));
+    // (a2) layers
+    for (uint32_t L = 0; L < d.n_layers; L++) {
+      const ItemSpace is = RT_SPACE;
+      const uint32_t o0 = __ldg(&d.layer_off[L]), n = __ldg(&d.layer_off[L + 1]) - o0;
+      const uint32_t total = stage_rows(st, n);
+      if (is.row_stride && is.row0 != NO_ROW && lane_active(s, is.lane, c)) {
+        const bool staged = ra.stage_cap && total && total <= ra.stage_cap;
+        const uint32_t j = is.row0 - st.R0;
+        uint32_t i = 0;
+        for (uint32_t r = is.row0; r < n; r += is.row_stride, i++) {
+          uint4 m;
+          uint32_t dref;
+          if (staged) {
+            m = sm_meta[i * st.span + j];
+            dref = sm_dst[i * st.span + j];
+          } else {
+            m = __ldg(&d.meta[o0 + r]);
+            dref = __ldg(&d.dst[o0 + r]);
+          }
+          res_item(d, s, base, ra, m, dref, is.lane);
+        }
+      } else if (!is.row_stride) {  // more lanes than threads
+        for_rows<1>(is, n, [&](uint32_t r, uint32_t lane) {
+          if (lane_active(s, lane, c)) res_item(d, s, base, ra, __ldg(&d.meta[o0 + r]), __ldg(&d.dst[o0 + r]), lane);
+        });
+      }
+      cluster_phase_sync(RT_STAGE(L + 1u));
+    }
+    // (a5) clock edge: registers, then memory write ports
+    for_rows<1>(RT_SPACE, d.n_regs + d.n_mems, [&](uint32_t r, uint32_t lane) {
+      if (!lane_active(s, lane, c)) return;
+      if (r < d.n_regs) {
+        const uint64_t mk = wmask(__ldg(&d.reg_w[r]));
+        uint64_t v = res_ld(base, ra, __ldg(&d.reg_src[r]), lane) & mk;
+        if (s.reset || (s.reset_lane && c < __ldg(&s.reset_lane[lane]))) v = __ldg(&d.reg_init[r]) & mk;
+        res_st(base, ra, __ldg(&d.reg_ref[r]), lane, v);
+      } else {
+        const uint32_t mi = r - d.n_regs;
+        const uint4 info = __ldg(&d.mem_info[mi]);
+        const uint32_t p1 = __ldg(&d.mem_info[mi + 1]).w;
+        const uint64_t mk = wmask(info.z);
+        for (uint32_t p = info.w; p < p1; p++) {
+          const uint4 w = __ldg(&d.wport[p]);
+          if (res_ld(base, ra, w.y, lane) & 1ull) {
+            const uint64_t a = res_ld(base, ra, w.z, lane) & (uint64_t)info.y;
+            s.mem[((size_t)info.x + a) * s.n_pad + lane] = res_ld(base, ra, w.w, lane) & mk;
+          }
+        }
+      }
+    });
+    cluster_phase_sync([] {});
+    // (a7) probes
+    if (s.n_probe) {
+      for_rows<1>(RT_SPACE, s.n_probe, [&](uint32_t p, uint32_t lane) {
+        if (!lane_active(s, lane, c)) return;
+        const uint64_t v = res_ld(base, ra, __ldg(&s.probe_slot[p]), lane);
+        if (s.probe_changes) {
+          uint64_t* prev = s.probe_prev + (size_t)p * s.n_pad + lane;
+          if (*prev != v) {
+            *prev = v;
+            const unsigned long long k = atomicAdd(s.change_count, 1ull);
+            if (k < s.change_cap) {
+              uint64_t* rec = s.probe_out + 3 * k;
+              rec[0] = (uint64_t)c | ((uint64_t)p << 32);
+              rec[1] = (uint64_t)user_of(s, lane);
+              rec[2] = v;
+            }
+          }
+        } else {
+          s.probe_out[((size_t)c * s.n_probe + p) * s.n_user + user_of(s, lane)] = v;
+        }
+      });
+      cluster_phase_sync([] {});
+    }
+  }
+#undef RT_STAGE
+#undef RT_SPACE
+  {  // the slice back to global memory
+    const uint32_t lo = rank * S, hi = min(lo + S, ra.bytes);
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s.state[i] = slice[i - lo];
+  }
+  // no CTA may leave while another still reads its shared memory
+  cluster_arrive();
+  cluster_wait();
+}
+
 // Compiled variants: lanes per thread V, threads per CTA (one CTA per SM).
 struct ClusterVariant {
   int V, maxt;
@@ -129,5 +332,7 @@ struct ClusterVariantTable {
 };
 #define RT_CLUSTER_VARIANT(V, T) {V, T, (const void*)k_cluster<V, T>}
 ClusterVariantTable variants_cluster();  // variants_cluster.cu
+const void* cluster_resident_kernel();   // variants_cluster.cu: k_cluster_res, 1,024 threads per CTA
+constexpr uint32_t kResidentThreads = 1024;
 
 }  // namespace rteaal

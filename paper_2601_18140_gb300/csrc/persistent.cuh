@@ -194,11 +194,33 @@ __device__ __forceinline__ bool grid_sync_staging(const GridArgs& g, uint32_t* e
 }
 
 // This thread's rows of one kind with descriptors from shared memory (entry
-// i * span + j of row row0 + i * per); returns the next (i, row).
-template <int V, int KIND>
+// i * span + j of row row0 + i * per); advances (i, row) past the kind.
+// Narrow rows go two at a time when U >= 2: both rows' operand loads are
+// issued before either result is computed (two gathers in flight per thread;
+// 32-bit lanes keep the pair within the registers a wide row needs alone).
+template <int V, int KIND, int U>
 __device__ __forceinline__ void walk_staged(const DDesign& d, const DSim& s, uint32_t& i, uint32_t& r,
                                             uint32_t r_end, const Stage& st, uint32_t j, uint32_t lane,
                                             uint32_t am, const uint4* sm_meta, const uint32_t* sm_dst) {
+  if constexpr (KIND == ROW_NARROW && U >= 2) {
+    const size_t np = s.n_pad;
+    for (; r + st.per < r_end; r += 2u * st.per, i += 2u) {
+      const uint32_t i0 = i * st.span + j, i1 = i0 + st.span;
+      const uint4 m0 = sm_meta[i0], m1 = sm_meta[i1];
+      const uint32_t ar0 = (m0.w >> 5) & 3u, ar1 = (m1.w >> 5) & 3u;
+      Lanes32<V> a0, b0, c0, a1, b1, c1;
+#pragma unroll
+      for (int v = 0; v < V; v++) b0.x[v] = c0.x[v] = b1.x[v] = c1.x[v] = 0u;
+      a0 = ldr32<V>(s.state, m0.x, np, lane);
+      a1 = ldr32<V>(s.state, m1.x, np, lane);
+      if (ar0 >= 2) b0 = ldr32<V>(s.state, m0.y, np, lane);
+      if (ar1 >= 2) b1 = ldr32<V>(s.state, m1.y, np, lane);
+      if (ar0 >= 3) c0 = ldr32<V>(s.state, m0.z, np, lane);
+      if (ar1 >= 3) c1 = ldr32<V>(s.state, m1.z, np, lane);
+      str32<V>(s.state, sm_dst[i0], np, lane, alu32_v<V>(m0.w, a0, b0, c0), am);
+      str32<V>(s.state, sm_dst[i1], np, lane, alu32_v<V>(m1.w, a1, b1, c1), am);
+    }
+  }
   for (; r < r_end; r += st.per, i++) {
     const uint32_t idx = i * st.span + j;
     item_of_kind<V, KIND>(d, s, lane, sm_meta[idx], sm_dst[idx], am);
@@ -213,8 +235,8 @@ __device__ __forceinline__ void eval_layer_staged(const DDesign& d, const DSim& 
                                                   const uint4* sm_meta, const uint32_t* sm_dst) {
   const uint32_t o0 = __ldg(&d.layer_off[L]), n = __ldg(&d.layer_off[L + 1]) - o0;
   const uint32_t total = stage_rows(st, n);
-  if (!is.row_stride || total == 0 || total > cap || U > 1) {
-    eval_layer<V, U>(d, s, L, is, cyc);
+  if (!is.row_stride || total == 0 || total > cap) {  // rows in flight apply to staged narrow rows only
+    eval_layer<V, 1>(d, s, L, is, cyc);
     return;
   }
   if (is.row0 == NO_ROW || is.row0 >= n) return;
@@ -223,9 +245,9 @@ __device__ __forceinline__ void eval_layer_staged(const DDesign& d, const DSim& 
   const uint32_t nw = __ldg(&d.layer_wide[L]) - o0, ne = __ldg(&d.layer_ext[L]) - o0;
   const uint32_t j = is.row0 - st.R0;
   uint32_t i = 0, r = is.row0;
-  walk_staged<V, ROW_NARROW>(d, s, i, r, nw, st, j, is.lane, am, sm_meta, sm_dst);
-  walk_staged<V, ROW_WIDE>(d, s, i, r, ne, st, j, is.lane, am, sm_meta, sm_dst);
-  walk_staged<V, ROW_EXT>(d, s, i, r, n, st, j, is.lane, am, sm_meta, sm_dst);
+  walk_staged<V, ROW_NARROW, U>(d, s, i, r, nw, st, j, is.lane, am, sm_meta, sm_dst);
+  walk_staged<V, ROW_WIDE, 1>(d, s, i, r, ne, st, j, is.lane, am, sm_meta, sm_dst);
+  walk_staged<V, ROW_EXT, 1>(d, s, i, r, n, st, j, is.lane, am, sm_meta, sm_dst);
 }
 
 template <int V, int U, int MAXT, int MINB>
@@ -248,7 +270,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs
       if (g.stage_cap)
         eval_layer_staged<V, U>(d, s, L, RT_SPACE, c, stage_of_cta(g.tpo), g.stage_cap, sm_meta, sm_dst);
       else
-        eval_layer<V, U>(d, s, L, RT_SPACE, c);
+        eval_layer<V, 1>(d, s, L, RT_SPACE, c);
       if (!grid_sync_staging(g, s.err, &sh_ok, RT_STAGE(L + 1u))) return;
     }
 #undef RT_STAGE
@@ -321,6 +343,7 @@ struct ActVariantTable {
 VariantTable variants_v8a();
 VariantTable variants_v8b();
 VariantTable variants_v8c();
+VariantTable variants_v8d();
 VariantTable variants_v4a();
 VariantTable variants_v4b();
 VariantTable variants_v4c();

@@ -277,6 +277,9 @@ struct rteaal_sim {
   uint32_t stage_cap = 0;            // GRID, CLUSTER: descriptors a CTA stages in shared memory
   uint32_t cluster_ctas = 0;         // CLUSTER: CTAs per cluster
   uint32_t n_clusters = 0;           // CLUSTER: clusters resident at once
+  bool resident = false;             // CLUSTER: state kept in the cluster's shared memory
+  uint32_t res_slice = 0;            // CLUSTER resident: state bytes per CTA
+  uint32_t res_smem = 0;             // CLUSTER resident: dynamic shared memory per CTA
   uint32_t last_span = 0;            // lanes the last step visited
   uint32_t last_grid = 0;            // CTAs of the last GRID launch
   // activity-aware evaluation (GRID only)
@@ -404,7 +407,7 @@ void launch_layer_cycle(rteaal_sim* s, const DDesign& dd, const DSim& ds, uint32
 const std::vector<Variant>& all_variants() {
   static const std::vector<Variant> all = [] {
     std::vector<Variant> v;
-    for (const VariantTable& t : {variants_v8a(), variants_v8b(), variants_v8c(), variants_v4a(), variants_v4b(),
+    for (const VariantTable& t : {variants_v8a(), variants_v8b(), variants_v8c(), variants_v8d(), variants_v4a(), variants_v4b(),
                                   variants_v4c(), variants_v2(), variants_v1()})
       v.insert(v.end(), t.v, t.v + t.n);
     return v;
@@ -655,8 +658,55 @@ uint32_t stage_capacity(uint32_t chunks, uint32_t grid, uint32_t threads, uint32
 }
 
 // Validate and apply a launch configuration (never changes results).
+// Resident cluster form (cluster.cuh): the smallest slice layout that fits,
+// for the given cluster size (0: the first of 8, 16, 4, 2 that fits).  Returns
+// the cluster size, 0 if none fits; sets the slice, staging capacity and
+// shared memory per CTA.
+uint32_t plan_resident(rteaal_sim* s, uint32_t cluster_ctas, uint32_t& slice, uint32_t& stage, uint32_t& smem) {
+  const Lowered& L = s->design->L;
+  const uint64_t bytes = (uint64_t)s->n_pad * L.lane_bytes;
+  constexpr uint64_t kBudget = 220 * 1024;
+  const void* fn = cluster_resident_kernel();
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  for (uint32_t cs : {8u, 16u, 4u, 2u}) {
+    if (cluster_ctas && cs != cluster_ctas) continue;
+    const uint64_t S = ((bytes + cs - 1) / cs + 15) / 16 * 16;
+    if (S + 16 > kBudget) continue;
+    uint64_t st = stage_capacity(s->n_pad, cs, kResidentThreads, L.max_layer_ops, 1);
+    st = std::min<uint64_t>(st, (kBudget - S) / kStageBytes);
+    const uint64_t sm = S + st * kStageBytes;
+    // the opt-in maximum (a sim's launch asks for its own size, at most this)
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->design->device));
+    if (sm > (uint64_t)optin) continue;
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kResidentThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      ncl = 0;
+    }
+    if (ncl < 1) continue;
+    slice = (uint32_t)S;
+    stage = (uint32_t)st;
+    smem = (uint32_t)sm;
+    return cs;
+  }
+  return 0;
+}
+
 void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
-               uint32_t unroll, uint32_t lanes_per_thread, uint32_t cluster_ctas = 0) {
+               uint32_t unroll, uint32_t lanes_per_thread, uint32_t cluster_ctas = 0, int cluster_resident = 0) {
   if (kernel == RTEAAL_KERNEL_AUTO)
     kernel = s->activity ? RTEAAL_KERNEL_GRID : s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
   if (s->activity && kernel != RTEAAL_KERNEL_GRID)
@@ -713,7 +763,21 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     unroll = 1;
     ctas_per_sm = 0;
     grid = (uint32_t)((s->n_pad + kSpecThreads - 1) / kSpecThreads);
+  } else if (kernel == RTEAAL_KERNEL_CLUSTER && cluster_resident >= 0 && tile_lanes == s->n_pad && s->n_pad <= 64 &&
+             (plan_resident(s, cluster_ctas, s->res_slice, stage, s->res_smem) != 0 || cluster_resident > 0)) {
+    // the whole state in the cluster's distributed shared memory, one lane per thread
+    const uint32_t cs = plan_resident(s, cluster_ctas, s->res_slice, stage, s->res_smem);
+    if (!cs) throw Error(RTEAAL_E_UNSUPPORTED, "cluster form: the state does not fit the cluster's shared memory");
+    s->resident = true;
+    s->cluster_ctas = cs;
+    s->n_clusters = 1;
+    V = 1;
+    threads = kResidentThreads;
+    unroll = 1;
+    ctas_per_sm = 1;
+    grid = cs;
   } else if (kernel == RTEAAL_KERNEL_CLUSTER) {
+    s->resident = false;
     const ClusterVariant* cv = find_cluster_variant(V);
     if (!cv) throw Error(RTEAAL_E_UNSUPPORTED, "no compiled cluster variant for V=" + std::to_string(V));
     threads = (uint32_t)cv->maxt;
@@ -902,7 +966,8 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
       s->n_pad = pad_lanes(n_instances);
       s->activity = opts && opts->activity;
       configure(s, opts ? opts->kernel : 0, opts ? opts->tile_lanes : 0, opts ? opts->threads : 0,
-                opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0, opt_lanes(opts), opts ? opts->cluster_ctas : 0);
+                opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0, opt_lanes(opts), opts ? opts->cluster_ctas : 0,
+                opts ? opts->cluster_resident : 0);
       if (const char* e = getenv("RTEAAL_TEST_WITHHOLD_ARRIVAL")) s->barrier_extra = (uint32_t)atoi(e);
       if (const char* e = getenv("RTEAAL_BARRIER_TIMEOUT_NS")) s->barrier_timeout_ns = strtoull(e, nullptr, 10);
 
@@ -996,7 +1061,7 @@ RT_EXPORT int rteaal_sim_configure(rteaal_sim* s, const rteaal_sim_opts* o) {
     require(s && o, "rteaal_sim_configure: null argument");
     CK(cudaSetDevice(s->design->device));
     configure(s, o->kernel, o->tile_lanes, o->threads, o->ctas_per_sm, o->unroll, o->lanes_per_thread,
-              o->cluster_ctas);
+              o->cluster_ctas, o->cluster_resident);
   });
 }
 
@@ -1017,6 +1082,7 @@ RT_EXPORT int rteaal_sim_info(const rteaal_sim* s, rteaal_sim_stats* o) {
     o->last_span = s->last_span;
     o->last_grid = s->last_grid;
     o->cluster_ctas = s->kernel == RTEAAL_KERNEL_CLUSTER ? s->cluster_ctas : 0;
+    o->cluster_resident = s->kernel == RTEAAL_KERNEL_CLUSTER && s->resident ? 1 : 0;
   });
 }
 
@@ -1102,6 +1168,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
           for (uint32_t V : {1u, 2u, 4u, 8u})
             if (T % V == 0 && find_cluster_variant((int)V))
               for (uint32_t cs : {16u, 8u}) candx.push_back({RTEAAL_KERNEL_CLUSTER, T, 0, 1, V, cs});
+    if ((kernel_mask & (1u << RTEAAL_KERNEL_CLUSTER)) && np <= 64)  // resident state (U = 2 marks it)
+      for (uint32_t cs : {4u, 8u, 16u}) candx.push_back({RTEAAL_KERNEL_CLUSTER, (uint32_t)np, 0, 2, 1, cs});
     for (const Cand& c : cands) candx.push_back({c.kernel, c.T, c.threads, c.U, c.V, 0});
 
     const int saved[6] = {s->kernel, (int)s->tile_lanes, (int)s->threads, (int)s->ctas_per_sm, (int)s->unroll,
@@ -1119,7 +1187,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     for (const CandX& c : candx) {
       try {
         const bool cl = c.kernel == RTEAAL_KERNEL_CLUSTER;
-        configure(s, c.kernel, c.T, c.threads, cl ? 0 : c.ctas, c.U, c.V, cl ? c.ctas : 0);
+        configure(s, c.kernel, c.T, c.threads, cl ? 0 : c.ctas, cl ? 1 : c.U, c.V, cl ? c.ctas : 0,
+                  cl ? (c.U == 2 ? 1 : -1) : 0);
       } catch (const Error&) {
         continue;  // not compiled / not resident
       }
@@ -1147,8 +1216,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     cudaEventDestroy(e1);
     if (n_trials) *n_trials = nt;
     const bool best_cl = best_c.kernel == RTEAAL_KERNEL_CLUSTER;
-    configure(s, best_c.kernel, best_c.T, best_c.threads, best_cl ? 0 : best_ctas, best_c.U, best_c.V,
-              best_cl ? best_ctas : 0);
+    configure(s, best_c.kernel, best_c.T, best_c.threads, best_cl ? 0 : best_ctas, best_cl ? 1 : best_c.U,
+              best_c.V, best_cl ? best_ctas : 0, best_cl ? (best_c.U == 2 ? 1 : -1) : 0);
     s->act_force = true;  // restored below; stamps of the trials are stale
     CK(cudaMemcpyAsync(s->state, snap, b_state, cudaMemcpyDeviceToDevice, st));
     if (b_mem) CK(cudaMemcpyAsync(s->mem, snap + b_state, b_mem, cudaMemcpyDeviceToDevice, st));
@@ -1320,6 +1389,30 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       void* args[] = {&a_st, &a_mem, &a_xs, &a_stim, &a_budget, &a_rl, &a_uol, &a_np, &a_nu, &a_uni, &a_mode, &a_reset};
       CK(cudaLaunchKernel((const void*)D->spec_kernel, dim3((span + kSpecThreads - 1) / kSpecThreads),
                           dim3(kSpecThreads), args, 0, st));
+      CK(cudaGetLastError());
+    } else if (s->kernel == RTEAAL_KERNEL_CLUSTER && s->resident) {
+      require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
+      ResidentArgs ra{};
+      ra.ncyc = (uint32_t)max_cyc;
+      ra.bytes = (uint32_t)(np * L.lane_bytes);
+      ra.slice = make_fastdiv(s->res_slice);
+      ra.tpo = make_fastdiv((uint32_t)np);
+      ra.stage_cap = s->stage_cap;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = s->cluster_ctas;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(s->cluster_ctas);
+      cfg.blockDim = dim3(kResidentThreads);
+      cfg.dynamicSmemBytes = s->res_smem;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ra};
+      s->last_grid = s->cluster_ctas;
+      CK(cudaLaunchKernelExC(&cfg, cluster_resident_kernel(), args));
       CK(cudaGetLastError());
     } else if (s->kernel == RTEAAL_KERNEL_CLUSTER) {
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");

@@ -10,4 +10,6 @@ static const ClusterVariant kTable[] = {
 
 ClusterVariantTable variants_cluster() { return {kTable, sizeof(kTable) / sizeof(kTable[0])}; }
 
+const void* cluster_resident_kernel() { return (const void*)k_cluster_res<kResidentThreads>; }
+
 }  // namespace rteaal
