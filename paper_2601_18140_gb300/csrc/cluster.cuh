@@ -68,52 +68,98 @@ __device__ __forceinline__ Stage stage_of_cluster_cta(const FastDiv& tpo, uint32
   return st;
 }
 
-// Barrier between two phases of a tile: the CTA's threads are done with the
-// current descriptors, the next layer's are staged while the cluster waits.
-template <typename F>
-__device__ __forceinline__ void cluster_phase_sync(F&& stage) {
-  __syncthreads();
-  cluster_arrive();
-  stage();
-  cluster_wait();
+// Barrier between two phases of a tile.  The phase's own staging copies (the
+// next layer's descriptors, issued when the phase began) are complete in the
+// issuing threads first; the cluster barrier then orders every thread's
+// writes -- rows, staged descriptors -- before the next phase's reads, inside
+// the CTA as across the cluster.
+__device__ __forceinline__ void cluster_phase_sync() {
   cp_async_wait_all();
-  __syncthreads();
+  cluster_arrive();
+  cluster_wait();
+}
+
+// The per-layer row offsets (layer_off, layer_wide, layer_ext) in shared
+// memory, loaded once per launch: [0, L] offsets, then [L] wide, then [L] ext.
+__device__ __forceinline__ void load_layer_table(const DDesign& d, uint32_t* tab) {
+  const uint32_t nl = d.n_layers;
+  for (uint32_t i = threadIdx.x; i <= nl; i += blockDim.x) tab[i] = __ldg(&d.layer_off[i]);
+  for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) {
+    tab[nl + 1 + i] = __ldg(&d.layer_wide[i]);
+    tab[2 * nl + 1 + i] = __ldg(&d.layer_ext[i]);
+  }
+}
+
+// Issue the copies of layer L's descriptors for this CTA into one of the two
+// staging buffers (every thread takes a share); 0 rows if they do not fit.
+__device__ __forceinline__ void stage_layer_tab(const DDesign& d, const uint32_t* tab, uint32_t L, const Stage& st,
+                                                uint32_t cap, uint4* meta, uint32_t* dst) {
+  if (L >= d.n_layers) return;
+  const uint32_t o0 = tab[L], n = tab[L + 1] - o0;
+  const uint32_t total = stage_rows(st, n);
+  if (total > cap) return;
+  for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const uint32_t i = idx / st.span, j = idx - i * st.span;
+    const uint32_t r = st.R0 + i * st.per + j;
+    if (r < n) {
+      cp_async16(&meta[idx], &d.meta[o0 + r]);
+      cp_async4(&dst[idx], &d.dst[o0 + r]);
+    }
+  }
 }
 
 template <int V, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_cluster(DDesign d, DSim s, ClusterArgs ca) {
-  extern __shared__ __align__(16) uint4 sm_stage[];  // [stage_cap] descriptors, then [stage_cap] output rows
-  uint4* sm_meta = sm_stage;
-  uint32_t* sm_dst = reinterpret_cast<uint32_t*>(sm_stage + ca.stage_cap);
+  // dynamic shared memory: two staging buffers of stage_cap descriptors and
+  // output rows, then the layer table
+  extern __shared__ __align__(16) uint4 sm_stage[];
+  uint4* meta[2] = {sm_stage, sm_stage + ca.stage_cap};
+  uint32_t* dst0 = reinterpret_cast<uint32_t*>(sm_stage + 2 * ca.stage_cap);
+  uint32_t* dst[2] = {dst0, dst0 + ca.stage_cap};
+  uint32_t* tab = dst0 + 2 * ca.stage_cap;
   const uint32_t rank = cluster_rank(), nthreads = cluster_size() * blockDim.x;
   const uint32_t ct = rank * blockDim.x + threadIdx.x;
   const Stage st = stage_of_cluster_cta(ca.tpo, rank, nthreads);
+  load_layer_table(d, tab);
+  __syncthreads();
   for (uint32_t tile = cluster_id(); tile < ca.n_tiles; tile += cluster_count()) {
     const uint32_t ncyc = ca.tile_cycles ? ca.tile_cycles[tile] : s.uniform;
     const uint32_t base = tile * ca.tile_lanes;
 #define RT_SPACE make_space<V>(ca.tpo, base, ct, nthreads)
-#define RT_STAGE(L)                                                                                  \
-  [&] {                                                                                             \
-    if (ca.stage_cap && (L) < d.n_layers) stage_layer(d, (L), st, ca.stage_cap, sm_meta, sm_dst);   \
-  }
     for (uint32_t c = 0; c < ncyc; c++) {
+      if (ca.stage_cap) stage_layer_tab(d, tab, 0u, st, ca.stage_cap, meta[0], dst[0]);
       stim_items<V>(d, s, RT_SPACE, c);
-      cluster_phase_sync(RT_STAGE(0u));
+      cluster_phase_sync();
       for (uint32_t L = 0; L < d.n_layers; L++) {
-        if (ca.stage_cap)
-          eval_layer_staged<V, 1>(d, s, L, RT_SPACE, c, st, ca.stage_cap, sm_meta, sm_dst);
-        else
-          eval_layer<V, 1>(d, s, L, RT_SPACE, c);
-        cluster_phase_sync(RT_STAGE(L + 1u));
+        const uint32_t b = L & 1u;
+        if (ca.stage_cap) stage_layer_tab(d, tab, L + 1u, st, ca.stage_cap, meta[b ^ 1u], dst[b ^ 1u]);
+        const uint32_t o0 = tab[L], n = tab[L + 1] - o0;
+        const uint32_t total = stage_rows(st, n);
+        const ItemSpace is = RT_SPACE;
+        if (ca.stage_cap && is.row_stride && total && total <= ca.stage_cap) {
+          if (is.row0 != NO_ROW && is.row0 < n) {
+            const uint32_t am = act_mask<V>(s, is.lane, c);
+            if (am) {
+              const uint32_t nw = tab[d.n_layers + 1 + L] - o0, ne = tab[2 * d.n_layers + 1 + L] - o0;
+              const uint32_t j = is.row0 - st.R0;
+              uint32_t i = 0, r = is.row0;
+              walk_staged<V, ROW_NARROW, 1>(d, s, i, r, nw, st, j, is.lane, am, meta[b], dst[b]);
+              walk_staged<V, ROW_WIDE, 1>(d, s, i, r, ne, st, j, is.lane, am, meta[b], dst[b]);
+              walk_staged<V, ROW_EXT, 1>(d, s, i, r, n, st, j, is.lane, am, meta[b], dst[b]);
+            }
+          }
+        } else {
+          eval_layer<V, 1>(d, s, L, is, c);
+        }
+        cluster_phase_sync();
       }
       commit_items<V>(d, s, RT_SPACE, c);
-      cluster_phase_sync([] {});
+      cluster_phase_sync();
       if (s.n_probe) {
         probe_items<V>(s, RT_SPACE, c);
-        cluster_phase_sync([] {});
+        cluster_phase_sync();
       }
     }
-#undef RT_STAGE
 #undef RT_SPACE
   }
 }
@@ -195,12 +241,15 @@ __device__ __forceinline__ void res_item(const DDesign& d, const DSim& s, uint8_
 
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, ResidentArgs ra) {
-  extern __shared__ __align__(16) uint8_t sm_res[];  // [S] state slice, [stage_cap] descriptors, [stage_cap] rows
+  // dynamic shared memory: [S] state slice, two staging buffers, the layer table
+  extern __shared__ __align__(16) uint8_t sm_res[];
   __shared__ uint8_t* base[16];
   const uint32_t S = ra.slice.d;
   uint8_t* slice = sm_res;
-  uint4* sm_meta = reinterpret_cast<uint4*>(sm_res + S);
-  uint32_t* sm_dst = reinterpret_cast<uint32_t*>(sm_meta + ra.stage_cap);
+  uint4* meta[2] = {reinterpret_cast<uint4*>(sm_res + S), reinterpret_cast<uint4*>(sm_res + S) + ra.stage_cap};
+  uint32_t* dst0 = reinterpret_cast<uint32_t*>(meta[1] + ra.stage_cap);
+  uint32_t* dst[2] = {dst0, dst0 + ra.stage_cap};
+  uint32_t* tab = dst0 + 2 * ra.stage_cap;
   const uint32_t rank = cluster_rank(), cs = cluster_size(), nthreads = cs * blockDim.x;
   const uint32_t ct = rank * blockDim.x + threadIdx.x;
   if (threadIdx.x < cs) base[threadIdx.x] = dsmem_map(slice, threadIdx.x);
@@ -208,16 +257,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, Resi
     const uint32_t lo = rank * S, hi = min(lo + S, ra.bytes);
     for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) slice[i - lo] = s.state[i];
   }
+  load_layer_table(d, tab);
   const Stage st = stage_of_cluster_cta(ra.tpo, rank, nthreads);
   __syncthreads();
   cluster_arrive();
   cluster_wait();
 #define RT_SPACE make_space<1>(ra.tpo, 0u, ct, nthreads)
-#define RT_STAGE(L)                                                                                  \
-  [&] {                                                                                             \
-    if (ra.stage_cap && (L) < d.n_layers) stage_layer(d, (L), st, ra.stage_cap, sm_meta, sm_dst);   \
-  }
   for (uint32_t c = 0; c < ra.ncyc; c++) {
+    if (ra.stage_cap) stage_layer_tab(d, tab, 0u, st, ra.stage_cap, meta[0], dst[0]);
     // (a1) inputs
     if (s.stim_mode)
       for_rows<1>(RT_SPACE, d.n_inputs, [&](uint32_t j, uint32_t lane) {
@@ -234,11 +281,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, Resi
         }
         res_st(base, ra, __ldg(&d.in_ref[j]), lane, x & wmask(__ldg(&d.in_w[j])));
       });
-    cluster_phase_sync(RT_STAGE(0u));
+    cluster_phase_sync();
     // (a2) layers
     for (uint32_t L = 0; L < d.n_layers; L++) {
+      const uint32_t b = L & 1u;
+      if (ra.stage_cap) stage_layer_tab(d, tab, L + 1u, st, ra.stage_cap, meta[b ^ 1u], dst[b ^ 1u]);
       const ItemSpace is = RT_SPACE;
-      const uint32_t o0 = __ldg(&d.layer_off[L]), n = __ldg(&d.layer_off[L + 1]) - o0;
+      const uint32_t o0 = tab[L], n = tab[L + 1] - o0;
       const uint32_t total = stage_rows(st, n);
       if (is.row_stride && is.row0 != NO_ROW && lane_active(s, is.lane, c)) {
         const bool staged = ra.stage_cap && total && total <= ra.stage_cap;
@@ -248,8 +297,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, Resi
           uint4 m;
           uint32_t dref;
           if (staged) {
-            m = sm_meta[i * st.span + j];
-            dref = sm_dst[i * st.span + j];
+            m = meta[b][i * st.span + j];
+            dref = dst[b][i * st.span + j];
           } else {
             m = __ldg(&d.meta[o0 + r]);
             dref = __ldg(&d.dst[o0 + r]);
@@ -261,7 +310,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, Resi
           if (lane_active(s, lane, c)) res_item(d, s, base, ra, __ldg(&d.meta[o0 + r]), __ldg(&d.dst[o0 + r]), lane);
         });
       }
-      cluster_phase_sync(RT_STAGE(L + 1u));
+      cluster_phase_sync();
     }
     // (a5) clock edge: registers, then memory write ports
     for_rows<1>(RT_SPACE, d.n_regs + d.n_mems, [&](uint32_t r, uint32_t lane) {
@@ -285,7 +334,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, Resi
         }
       }
     });
-    cluster_phase_sync([] {});
+    cluster_phase_sync();
     // (a7) probes
     if (s.n_probe) {
       for_rows<1>(RT_SPACE, s.n_probe, [&](uint32_t p, uint32_t lane) {
@@ -307,10 +356,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, Resi
           s.probe_out[((size_t)c * s.n_probe + p) * s.n_user + user_of(s, lane)] = v;
         }
       });
-      cluster_phase_sync([] {});
+      cluster_phase_sync();
     }
   }
-#undef RT_STAGE
 #undef RT_SPACE
   {  // the slice back to global memory
     const uint32_t lo = rank * S, hi = min(lo + S, ra.bytes);

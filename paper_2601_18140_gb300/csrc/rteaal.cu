@@ -152,11 +152,15 @@ __global__ void k_scatter(uint64_t* dst, uint32_t n_pad, const uint32_t* rows, u
 
 // ------------------------------------------------------------------ host side
 
+// A failed call's error stays pending in the runtime and would be returned by
+// a later cudaGetLastError; it is cleared here, where it is reported.
 #define CK(call)                                                                            \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \
-    if (e_ != cudaSuccess)                                                                  \
+    if (e_ != cudaSuccess) {                                                                \
+      cudaGetLastError();                                                                   \
       throw Error(RTEAAL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    }                                                                                       \
   } while (0)
 
 FastDiv make_fastdiv(uint32_t d) {
@@ -658,6 +662,23 @@ uint32_t stage_capacity(uint32_t chunks, uint32_t grid, uint32_t threads, uint32
 }
 
 // Validate and apply a launch configuration (never changes results).
+// Dynamic shared memory of the cluster kernels besides the resident state: two
+// staging buffers of descriptors and output rows, and the layer table.
+uint64_t cluster_table_smem(uint32_t stage, uint32_t n_layers) {
+  return 2ull * stage * kStageBytes + 4ull * (3ull * n_layers + 1);
+}
+
+// Let a kernel take up to the opt-in shared memory less its static part.
+int allow_max_smem(const void* fn, int device) {
+  int optin = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  cudaFuncAttributes fa{};
+  CK(cudaFuncGetAttributes(&fa, fn));
+  const int dyn_max = std::max(optin - (int)fa.sharedSizeBytes, 0);
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+  return dyn_max;
+}
+
 // Resident cluster form (cluster.cuh): the smallest slice layout that fits,
 // for the given cluster size (0: the first of 8, 16, 4, 2 that fits).  Returns
 // the cluster size, 0 if none fits; sets the slice, staging capacity and
@@ -672,14 +693,13 @@ uint32_t plan_resident(rteaal_sim* s, uint32_t cluster_ctas, uint32_t& slice, ui
     if (cluster_ctas && cs != cluster_ctas) continue;
     const uint64_t S = ((bytes + cs - 1) / cs + 15) / 16 * 16;
     if (S + 16 > kBudget) continue;
+    const uint64_t table = cluster_table_smem(0, (uint32_t)(L.layer_off.size() - 1));
+    if (S + table > kBudget) continue;
     uint64_t st = stage_capacity(s->n_pad, cs, kResidentThreads, L.max_layer_ops, 1);
-    st = std::min<uint64_t>(st, (kBudget - S) / kStageBytes);
-    const uint64_t sm = S + st * kStageBytes;
-    // the opt-in maximum (a sim's launch asks for its own size, at most this)
-    int optin = 0;
-    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->design->device));
-    if (sm > (uint64_t)optin) continue;
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    st = std::min<uint64_t>(st, (kBudget - S - table) / (2 * kStageBytes));
+    const uint64_t sm = S + cluster_table_smem((uint32_t)st, (uint32_t)(L.layer_off.size() - 1));
+    // a sim's launch asks for its own size, at most the opt-in maximum
+    if (sm > (uint64_t)allow_max_smem(fn, s->design->device)) continue;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -785,10 +805,14 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     require(cluster_ctas == 0 || (cluster_ctas >= 1 && cluster_ctas <= 16), "cluster_ctas must be in 1..16");
     CK(cudaFuncSetAttribute(cv->fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     const Lowered& L = s->design->L;
+    const uint32_t n_layers = (uint32_t)(L.layer_off.size() - 1);
+    const int dyn_max = allow_max_smem(cv->fn, s->design->device);
     uint32_t best_cs = 0, best_ncl = 0;
     for (uint32_t cs : {16u, 8u, 4u, 2u, 1u}) {
       if (cluster_ctas && cs != cluster_ctas) continue;
       stage = stage_capacity(tile_lanes / (uint32_t)V, cs, threads, L.max_layer_ops, 1);
+      while (stage && cluster_table_smem(stage, n_layers) > (uint64_t)dyn_max) stage /= 2;
+      if (cluster_table_smem(stage, n_layers) > (uint64_t)dyn_max) continue;
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -797,7 +821,7 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
       attr[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(cs);
       cfg.blockDim = dim3(threads);
-      cfg.dynamicSmemBytes = (size_t)stage * kStageBytes;
+      cfg.dynamicSmemBytes = cluster_table_smem(stage, n_layers);
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       int ncl = 0;
@@ -813,6 +837,7 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     }
     if (!best_cs) throw Error(RTEAAL_E_UNSUPPORTED, "cluster kernel cannot be resident");
     stage = stage_capacity(tile_lanes / (uint32_t)V, best_cs, threads, L.max_layer_ops, 1);
+    while (stage && cluster_table_smem(stage, n_layers) > (uint64_t)dyn_max) stage /= 2;
     s->cluster_ctas = best_cs;
     s->n_clusters = std::min<uint32_t>(best_ncl, s->n_pad / tile_lanes);
     ctas_per_sm = 1;
@@ -1441,7 +1466,7 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       attr[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(n_cl * s->cluster_ctas);
       cfg.blockDim = dim3(s->threads);
-      cfg.dynamicSmemBytes = (size_t)s->stage_cap * kStageBytes;
+      cfg.dynamicSmemBytes = cluster_table_smem(s->stage_cap, D->dd.n_layers);
       cfg.stream = st;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
