@@ -369,18 +369,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster_res(DDesign d, DSim s, Resi
   cluster_wait();
 }
 
-// Compiled variants: lanes per thread V, threads per CTA (one CTA per SM).
+// Compiled variants: lanes per thread V, threads per CTA (one CTA per SM),
+// state in global memory or resident in the cluster's shared memory.
 struct ClusterVariant {
   int V, maxt;
   const void* fn;
+  bool resident;
 };
 struct ClusterVariantTable {
   const ClusterVariant* v;
   size_t n;
 };
-#define RT_CLUSTER_VARIANT(V, T) {V, T, (const void*)k_cluster<V, T>}
+#define RT_CLUSTER_VARIANT(V, T) {V, T, (const void*)k_cluster<V, T>, false}
+#define RT_CLUSTER_RES_VARIANT(T) {1, T, (const void*)k_cluster_res<T>, true}
 ClusterVariantTable variants_cluster();  // variants_cluster.cu
-const void* cluster_resident_kernel();   // variants_cluster.cu: k_cluster_res, 1,024 threads per CTA
-constexpr uint32_t kResidentThreads = 1024;
 
 }  // namespace rteaal

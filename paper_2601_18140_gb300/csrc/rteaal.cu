@@ -282,6 +282,7 @@ struct rteaal_sim {
   uint32_t cluster_ctas = 0;         // CLUSTER: CTAs per cluster
   uint32_t n_clusters = 0;           // CLUSTER: clusters resident at once
   bool resident = false;             // CLUSTER: state kept in the cluster's shared memory
+  const void* cluster_fn = nullptr;  // CLUSTER: the kernel variant in use
   uint32_t res_slice = 0;            // CLUSTER resident: state bytes per CTA
   uint32_t res_smem = 0;             // CLUSTER resident: dynamic shared memory per CTA
   uint32_t last_span = 0;            // lanes the last step visited
@@ -428,10 +429,14 @@ const std::vector<ActVariant>& all_act_variants() {
   return all;
 }
 
-const ClusterVariant* find_cluster_variant(int V) {
+// Cluster variant for (V, resident): the one with exactly `threads` per CTA,
+// else the first compiled for them.
+const ClusterVariant* find_cluster_variant(int V, bool resident = false, uint32_t threads = 0) {
   static const ClusterVariantTable t = variants_cluster();
   for (size_t i = 0; i < t.n; i++)
-    if (t.v[i].V == V) return &t.v[i];
+    if (t.v[i].V == V && t.v[i].resident == resident && (uint32_t)t.v[i].maxt == threads) return &t.v[i];
+  for (size_t i = 0; i < t.n; i++)
+    if (t.v[i].V == V && t.v[i].resident == resident) return &t.v[i];
   return nullptr;
 }
 
@@ -683,11 +688,14 @@ int allow_max_smem(const void* fn, int device) {
 // for the given cluster size (0: the first of 8, 16, 4, 2 that fits).  Returns
 // the cluster size, 0 if none fits; sets the slice, staging capacity and
 // shared memory per CTA.
-uint32_t plan_resident(rteaal_sim* s, uint32_t cluster_ctas, uint32_t& slice, uint32_t& stage, uint32_t& smem) {
+uint32_t plan_resident(rteaal_sim* s, const ClusterVariant* cv, uint32_t cluster_ctas, uint32_t& slice,
+                       uint32_t& stage, uint32_t& smem) {
   const Lowered& L = s->design->L;
   const uint64_t bytes = (uint64_t)s->n_pad * L.lane_bytes;
   constexpr uint64_t kBudget = 220 * 1024;
-  const void* fn = cluster_resident_kernel();
+  if (!cv) return 0;
+  const void* fn = cv->fn;
+  const uint32_t nthr = (uint32_t)cv->maxt;
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   for (uint32_t cs : {8u, 16u, 4u, 2u}) {
     if (cluster_ctas && cs != cluster_ctas) continue;
@@ -695,7 +703,7 @@ uint32_t plan_resident(rteaal_sim* s, uint32_t cluster_ctas, uint32_t& slice, ui
     if (S + 16 > kBudget) continue;
     const uint64_t table = cluster_table_smem(0, (uint32_t)(L.layer_off.size() - 1));
     if (S + table > kBudget) continue;
-    uint64_t st = stage_capacity(s->n_pad, cs, kResidentThreads, L.max_layer_ops, 1);
+    uint64_t st = stage_capacity(s->n_pad, cs, nthr, L.max_layer_ops, 1);
     st = std::min<uint64_t>(st, (kBudget - S - table) / (2 * kStageBytes));
     const uint64_t sm = S + cluster_table_smem((uint32_t)st, (uint32_t)(L.layer_off.size() - 1));
     // a sim's launch asks for its own size, at most the opt-in maximum
@@ -707,7 +715,7 @@ uint32_t plan_resident(rteaal_sim* s, uint32_t cluster_ctas, uint32_t& slice, ui
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(kResidentThreads);
+    cfg.blockDim = dim3(nthr);
     cfg.dynamicSmemBytes = sm;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -760,7 +768,7 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     const bool persistent = kernel == RTEAAL_KERNEL_TILE || kernel == RTEAAL_KERNEL_GRID;
     if (kernel == RTEAAL_KERNEL_CLUSTER) {
       for (int c : {8, 4, 2, 1})
-        if (span % (uint32_t)c == 0 && find_cluster_variant(c)) {
+        if (span % (uint32_t)c == 0 && find_cluster_variant(c, false)) {
           V = c;
           break;
         }
@@ -784,22 +792,27 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     ctas_per_sm = 0;
     grid = (uint32_t)((s->n_pad + kSpecThreads - 1) / kSpecThreads);
   } else if (kernel == RTEAAL_KERNEL_CLUSTER && cluster_resident >= 0 && tile_lanes == s->n_pad && s->n_pad <= 64 &&
-             (plan_resident(s, cluster_ctas, s->res_slice, stage, s->res_smem) != 0 || cluster_resident > 0)) {
+             (plan_resident(s, find_cluster_variant(1, true, threads), cluster_ctas, s->res_slice, stage,
+                            s->res_smem) != 0 ||
+              cluster_resident > 0)) {
     // the whole state in the cluster's distributed shared memory, one lane per thread
-    const uint32_t cs = plan_resident(s, cluster_ctas, s->res_slice, stage, s->res_smem);
+    const ClusterVariant* cv = find_cluster_variant(1, true, threads);
+    const uint32_t cs = plan_resident(s, cv, cluster_ctas, s->res_slice, stage, s->res_smem);
     if (!cs) throw Error(RTEAAL_E_UNSUPPORTED, "cluster form: the state does not fit the cluster's shared memory");
     s->resident = true;
+    s->cluster_fn = cv->fn;
     s->cluster_ctas = cs;
     s->n_clusters = 1;
     V = 1;
-    threads = kResidentThreads;
+    threads = (uint32_t)cv->maxt;
     unroll = 1;
     ctas_per_sm = 1;
     grid = cs;
   } else if (kernel == RTEAAL_KERNEL_CLUSTER) {
     s->resident = false;
-    const ClusterVariant* cv = find_cluster_variant(V);
+    const ClusterVariant* cv = find_cluster_variant(V, false, threads);
     if (!cv) throw Error(RTEAAL_E_UNSUPPORTED, "no compiled cluster variant for V=" + std::to_string(V));
+    s->cluster_fn = cv->fn;
     threads = (uint32_t)cv->maxt;
     unroll = 1;
     require(cluster_ctas == 0 || (cluster_ctas >= 1 && cluster_ctas <= 16), "cluster_ctas must be in 1..16");
@@ -1187,14 +1200,19 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
       for (uint32_t U : {2u, 4u}) cands.push_back({RTEAAL_KERNEL_LAYER_GRAPH, 0, 256, U, 0});
     if ((kernel_mask & (1u << RTEAAL_KERNEL_STREAM)) && np % 128 == 0)
       cands.push_back({RTEAAL_KERNEL_STREAM, 0, 0, 1, 0});
-    if (kernel_mask & (1u << RTEAAL_KERNEL_CLUSTER))  // ctas: CTAs per cluster
-      for (uint32_t T : {np <= 256 ? (uint32_t)np : 256u, np <= 128 ? (uint32_t)np : 128u})
-        if (np % T == 0)
-          for (uint32_t V : {1u, 2u, 4u, 8u})
-            if (T % V == 0 && find_cluster_variant((int)V))
-              for (uint32_t cs : {16u, 8u}) candx.push_back({RTEAAL_KERNEL_CLUSTER, T, 0, 1, V, cs});
-    if ((kernel_mask & (1u << RTEAAL_KERNEL_CLUSTER)) && np <= 64)  // resident state (U = 2 marks it)
-      for (uint32_t cs : {4u, 8u, 16u}) candx.push_back({RTEAAL_KERNEL_CLUSTER, (uint32_t)np, 0, 2, 1, cs});
+    if (kernel_mask & (1u << RTEAAL_KERNEL_CLUSTER)) {  // ctas: CTAs per cluster; U = 2 marks resident state
+      const ClusterVariantTable ct = variants_cluster();
+      for (size_t i = 0; i < ct.n; i++) {
+        const ClusterVariant& cv = ct.v[i];
+        if (cv.resident && np > 64) continue;
+        for (uint32_t T : {np <= 256 ? (uint32_t)np : 256u, np <= 128 ? (uint32_t)np : 128u}) {
+          if (np % T || T % (uint32_t)cv.V || (cv.resident && T != np)) continue;
+          for (uint32_t cs : {16u, 8u, 4u})
+            candx.push_back({RTEAAL_KERNEL_CLUSTER, T, (uint32_t)cv.maxt, cv.resident ? 2u : 1u, (uint32_t)cv.V, cs});
+          if (T == np) break;
+        }
+      }
+    }
     for (const Cand& c : cands) candx.push_back({c.kernel, c.T, c.threads, c.U, c.V, 0});
 
     const int saved[6] = {s->kernel, (int)s->tile_lanes, (int)s->threads, (int)s->ctas_per_sm, (int)s->unroll,
@@ -1430,14 +1448,14 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(s->cluster_ctas);
-      cfg.blockDim = dim3(kResidentThreads);
+      cfg.blockDim = dim3(s->threads);
       cfg.dynamicSmemBytes = s->res_smem;
       cfg.stream = st;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ra};
       s->last_grid = s->cluster_ctas;
-      CK(cudaLaunchKernelExC(&cfg, cluster_resident_kernel(), args));
+      CK(cudaLaunchKernelExC(&cfg, s->cluster_fn, args));
       CK(cudaGetLastError());
     } else if (s->kernel == RTEAAL_KERNEL_CLUSTER) {
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
@@ -1455,8 +1473,7 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
         CK(cudaMemcpyAsync(s->tile_cycles, tc.data(), n_tiles * 4, cudaMemcpyHostToDevice, st));
         ca.tile_cycles = s->tile_cycles;
       }
-      const ClusterVariant* cv = find_cluster_variant(s->V);
-      require(cv != nullptr, "rteaal_step: no cluster variant for this configuration");
+      require(s->cluster_fn != nullptr, "rteaal_step: no cluster variant for this configuration");
       const uint32_t n_cl = std::max<uint32_t>(1, std::min(s->n_clusters, n_tiles));
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute attr[1];
@@ -1472,7 +1489,7 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       cfg.numAttrs = 1;
       void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ca};
       s->last_grid = n_cl * s->cluster_ctas;
-      CK(cudaLaunchKernelExC(&cfg, cv->fn, args));
+      CK(cudaLaunchKernelExC(&cfg, s->cluster_fn, args));
       CK(cudaGetLastError());
     } else if (s->kernel == RTEAAL_KERNEL_TILE) {
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
