@@ -696,10 +696,209 @@ __device__ __forceinline__ void str(uint8_t* st, uint32_t ref, size_t np, uint32
     if (m & (1u << v)) st1(st, ref, np, lane + v, r.x[v]);
 }
 
+// ---- packed byte lanes (SIMD within a register).  A narrow op whose result
+// row is of class 0 (at most 8 bits) is evaluated for its V = 4 or 8 lanes as
+// one word of V bytes: class-0 operand rows are used as they are loaded, the
+// result is stored as it is computed, and no lane is unpacked.  That is exact
+// when every operand row is of class 0 (each byte is a whole value), and for
+// the ops whose low 8 result bits depend only on the operands' low 8 bits --
+// the bitwise ops, add, subtract, shift left, cat and mux (a mux's selector is
+// bit 0) -- whatever the operands' classes: wider operand rows are then cut to
+// their low bytes as they are loaded.  Multiply and the dynamic shifts, and
+// the ops that read whole operand values (right shifts, bit extraction,
+// compares, reductions) on wider operand rows, keep the lane-by-lane form.
+constexpr uint32_t PACK_LOW_OPS = (1u << OP_COPY) | (1u << OP_AND) | (1u << OP_OR) | (1u << OP_XOR) |
+                                  (1u << OP_NOT) | (1u << OP_ADD) | (1u << OP_SUB) | (1u << OP_SHL) |
+                                  (1u << OP_CAT) | (1u << OP_MUX);
+constexpr uint32_t PACK_BYTE_OPS = (1u << OP_SHR) | (1u << OP_BITS) | (1u << OP_EQ) | (1u << OP_NEQ) |
+                                   (1u << OP_LT) | (1u << OP_LEQ) | (1u << OP_GT) | (1u << OP_GEQ) |
+                                   (1u << OP_ANDR) | (1u << OP_ORR) | (1u << OP_XORR);
+
+// Whether a narrow op (descriptor m, result row dref) takes the packed form.
+__device__ __forceinline__ bool packable(const uint4& m, uint32_t dref) {
+  const uint32_t op = m.w & 31u;
+  const bool bytes_in = ((m.x | m.y | m.z) >> 30) == 0u;  // every operand row of class 0
+  return (dref >> 30) == 0u && (((PACK_LOW_OPS >> op) & 1u) || (bytes_in && ((PACK_BYTE_OPS >> op) & 1u)));
+}
+
+template <int V>
+struct Packed;
+template <>
+struct Packed<4> {
+  using T = uint32_t;
+};
+template <>
+struct Packed<8> {
+  using T = uint64_t;
+};
+
+// byte b in every byte of a packed word
+template <typename T>
+__device__ __forceinline__ T rep8(uint32_t b) {
+  return (T)0x0101010101010101ull * (T)(b & 0xFFu);
+}
+
+// low byte of each of four 32-bit words
+__device__ __forceinline__ uint32_t low_bytes4(uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  return __byte_perm(__byte_perm(x, y, 0x0040u), __byte_perm(z, w, 0x0040u), 0x5410u);
+}
+
+// V lanes of a row as V bytes: a class-0 row as stored, a class-1 or class-2
+// row cut to the low byte of every lane.
+template <int V>
+__device__ __forceinline__ typename Packed<V>::T ldp(const uint8_t* st, uint32_t ref, size_t np, uint32_t lane) {
+  const uint8_t* p = elem(st, ref, np, lane);
+  const uint32_t k = ref >> 30;
+  if constexpr (V == 8) {
+    if (k == 0) {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+      return (uint64_t)t.x | ((uint64_t)t.y << 32);
+    }
+    if (k == 1) {
+      const uint4 t = *reinterpret_cast<const uint4*>(p);
+      return (uint64_t)__byte_perm(t.x, t.y, 0x6420u) | ((uint64_t)__byte_perm(t.z, t.w, 0x6420u) << 32);
+    }
+    const uint4 t0 = reinterpret_cast<const uint4*>(p)[0];
+    const uint4 t1 = reinterpret_cast<const uint4*>(p)[1];
+    return (uint64_t)low_bytes4(t0.x, t0.y, t0.z, t0.w) | ((uint64_t)low_bytes4(t1.x, t1.y, t1.z, t1.w) << 32);
+  } else {
+    if (k == 0) return *reinterpret_cast<const uint32_t*>(p);
+    if (k == 1) {
+      const uint2 t = *reinterpret_cast<const uint2*>(p);
+      return __byte_perm(t.x, t.y, 0x6420u);
+    }
+    const uint4 t = *reinterpret_cast<const uint4*>(p);
+    return low_bytes4(t.x, t.y, t.z, t.w);
+  }
+}
+
+// Per byte: bit 7 set where the byte is not zero.
+template <typename T>
+__device__ __forceinline__ T nonzero8(T x) {
+  const T L7 = rep8<T>(0x7Fu);
+  return (((x & L7) + L7) | x) & rep8<T>(0x80u);
+}
+
+// Per byte: bit 7 set where a < b (unsigned).  (a | 0x80) - (b & 0x7F) keeps
+// every byte's difference in 1..255 (no borrow between bytes); its bit 7 says
+// whether a's low seven bits are at least b's.  Where the top bits of a and b
+// differ, a < b exactly when b's is set.
+template <typename T>
+__device__ __forceinline__ T ltu8(T a, T b) {
+  const T H = rep8<T>(0x80u);
+  const T d = (a | H) - (b & ~H);
+  const T x = a ^ b;
+  return ((x & b) | (~x & ~d)) & H;
+}
+
+// Per byte: a + b and a - b mod 256 (the seven low bits added or subtracted
+// without crossing into the next byte, the top bit fixed up by parity).
+template <typename T>
+__device__ __forceinline__ T add8(T a, T b) {
+  const T H = rep8<T>(0x80u);
+  return ((a & ~H) + (b & ~H)) ^ ((a ^ b) & H);
+}
+template <typename T>
+__device__ __forceinline__ T sub8(T a, T b) {
+  const T H = rep8<T>(0x80u);
+  return ((a | H) - (b & ~H)) ^ ((a ^ ~b) & H);
+}
+
+// Per byte: a << s and a >> s (s < 8), the bits that cross a byte boundary removed.
+template <typename T>
+__device__ __forceinline__ T shl8(T a, uint32_t s) {
+  return s >= 8u ? (T)0 : (a << s) & rep8<T>(0xFFu << s);
+}
+template <typename T>
+__device__ __forceinline__ T shr8(T a, uint32_t s) {
+  return s >= 8u ? (T)0 : (a >> s) & rep8<T>(0xFFu >> s);
+}
+
+// The op (ctl) on packed operand bytes a, b, c; the result masked to its width
+// (at most 8 bits).  Follows the definitions of alu32_v lane by lane.
+template <typename T>
+__device__ __forceinline__ T alu_packed(uint32_t ctl, T a, T b, T c) {
+  const uint32_t op = ctl & 31u, ar = (ctl >> 5) & 3u;
+  const uint32_t p0 = (ctl >> 16) & 255u, p1 = ctl >> 24;
+  const T ONE = rep8<T>(1u);
+  T r;
+  switch (op) {
+    case OP_COPY: r = a; break;
+    case OP_AND: r = a & b; if (ar == 3) r &= c; break;
+    case OP_OR: r = a | b; if (ar == 3) r |= c; break;
+    case OP_XOR: r = a ^ b; if (ar == 3) r ^= c; break;
+    case OP_NOT: r = ~a; break;
+    case OP_ADD: r = add8(a, b); if (ar == 3) r = add8(r, c); break;
+    case OP_SUB: r = sub8(a, b); break;
+    case OP_SHL: r = shl8(a, p0); break;
+    case OP_SHR: r = shr8(a, p0); break;
+    case OP_BITS: r = shr8(a, p1) & rep8<T>(wmask32(p0 - p1 + 1u)); break;
+    case OP_CAT: r = shl8(a, p0) | b; break;
+    case OP_EQ: r = (nonzero8(a ^ b) >> 7) ^ ONE; break;
+    case OP_NEQ: r = nonzero8(a ^ b) >> 7; break;
+    case OP_LT: r = ltu8(a, b) >> 7; break;
+    case OP_LEQ: r = (ltu8(b, a) >> 7) ^ ONE; break;
+    case OP_GT: r = ltu8(b, a) >> 7; break;
+    case OP_GEQ: r = (ltu8(a, b) >> 7) ^ ONE; break;
+    case OP_MUX: {
+      const T s = (a & ONE) * (T)0xFFu;  // 0xFF where the selector bit is set
+      r = (b & s) | (c & ~s);
+    } break;
+    case OP_ANDR: {  // all of the low p0 bits set (none can be above bit 7)
+      const T mm = rep8<T>(wmask32(p0));
+      r = p0 > 8u ? (T)0 : (nonzero8((a & mm) ^ mm) >> 7) ^ ONE;
+    } break;
+    case OP_ORR: r = nonzero8(a) >> 7; break;
+    case OP_XORR: {
+      T x = a ^ (a >> 4);  // bit 0 of each byte folds in its own bits only
+      x ^= x >> 2;
+      x ^= x >> 1;
+      r = x & ONE;
+    } break;
+    default: r = 0; break;
+  }
+  return r & rep8<T>(0xFFu >> (8u - ctl_width(ctl)));
+}
+
+// Store the active lanes (mask bit v = lane + v) of a packed class-0 result.
+template <int V>
+__device__ __forceinline__ void stp(uint8_t* st, uint32_t ref, size_t np, uint32_t lane,
+                                    typename Packed<V>::T r, uint32_t m) {
+  uint8_t* p = const_cast<uint8_t*>(elem(st, ref, np, lane));
+  if (m == (1u << V) - 1u) {
+    if constexpr (V == 8)
+      *reinterpret_cast<uint2*>(p) = make_uint2((uint32_t)r, (uint32_t)(r >> 32));
+    else
+      *reinterpret_cast<uint32_t*>(p) = r;
+    return;
+  }
+#pragma unroll
+  for (int v = 0; v < V; v++)
+    if (m & (1u << v)) p[v] = (uint8_t)(r >> (8 * v));
+}
+
+// One packed item: every operand load issued before the evaluation.
+template <int V>
+__device__ __forceinline__ void item_packed(uint8_t* st, size_t np, uint32_t lane, const uint4& m,
+                                            uint32_t dref, uint32_t am) {
+  using T = typename Packed<V>::T;
+  const uint32_t ar = (m.w >> 5) & 3u;
+  const T a = ldp<V>(st, m.x, np, lane);
+  const T b = ar >= 2 ? ldp<V>(st, m.y, np, lane) : (T)0;
+  const T c = ar >= 3 ? ldp<V>(st, m.z, np, lane) : (T)0;
+  stp<V>(st, dref, np, lane, alu_packed<T>(m.w, a, b, c), am);
+}
+
 // One narrow item: gather, evaluate, store.
 template <int V>
 __device__ __forceinline__ void item32(uint8_t* st, size_t np, uint32_t lane, const uint4& m,
                                        uint32_t dref, uint32_t am) {
+  if constexpr (V == 4 || V == 8) {
+    if (packable(m, dref)) {
+      item_packed<V>(st, np, lane, m, dref, am);
+      return;
+    }
+  }
   Lanes32<V> a, b, c;
   const uint32_t ar = (m.w >> 5) & 3u;
   a = ldr32<V>(st, m.x, np, lane);

@@ -53,8 +53,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_tile(DDesign d, DSim s, TileArgs
 }
 
 struct GridArgs {
-  uint32_t* count;        // scratch: arrivals at the current barrier
-  uint32_t* gen;          // scratch: barrier generation
+  unsigned long long* count;  // scratch (zeroed before the launch): arrivals at every barrier so far
   uint32_t expected;      // arrivals that complete a barrier (= gridDim.x)
   uint64_t timeout_ns;    // bounded wait per barrier
   uint32_t ncyc;
@@ -67,42 +66,60 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-// Software grid barrier (sense by generation counter).  Every wait is bounded:
-// after timeout_ns the block sets *err and returns false; blocks that see *err
-// leave at their next barrier, so the kernel always ends.
+// Software grid barrier on one arrival count that only grows: barrier k of a
+// launch is complete once the count reaches (k + 1) * expected, so a block's
+// arrival is one atomic add, the last block to arrive has nothing to reset and
+// no generation word is written.  The block's writes are ordered before its
+// arrival by __syncthreads and a fence (release); the fence after the wait
+// orders the next phase's reads after every block's arrival (acquire).  Every
+// wait is bounded: after timeout_ns the block sets *err and returns false;
+// blocks that see *err leave at their next barrier, so the kernel always ends.
+// Called by one thread of the block; returns whether the block goes on.
+__device__ __forceinline__ int grid_arrive_wait(const GridArgs& g, uint32_t* err) {
+  __threadfence();
+  uint32_t e = ld_relaxed(err);
+  const unsigned long long old = atomicAdd(g.count, 1ull);
+  const unsigned long long target = (old / g.expected + 1ull) * g.expected;
+  if (old + 1ull < target) {
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+      const unsigned long long c = ld_relaxed64(g.count);
+      e = ld_relaxed(err);
+      if (c >= target || e != 0u) break;
+      if (globaltimer() - t0 > g.timeout_ns) {
+        atomicOr(err, 1u);
+        e = 1u;
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  __threadfence();
+  return e == 0u;
+}
+
 __device__ __forceinline__ bool grid_sync(const GridArgs& g, uint32_t* err, int* sh_ok) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const uint32_t my = ld_acquire(g.gen);
-    __threadfence();
-    if (atomicAdd(g.count, 1u) == g.expected - 1u) {
-      atomicExch(g.count, 0u);
-      __threadfence();
-      atomicAdd(g.gen, 1u);
-    } else {
-      const uint64_t t0 = globaltimer();
-      while (ld_acquire(g.gen) == my) {
-        if (ld_acquire(err) != 0u) { ok = 0; break; }
-        if (globaltimer() - t0 > g.timeout_ns) { atomicOr(err, 1u); ok = 0; break; }
-        __nanosleep(100);
-      }
-    }
-    if (ld_acquire(err) != 0u) ok = 0;
-    __threadfence();
-    *sh_ok = ok;
-  }
+  if (threadIdx.x == 0) *sh_ok = grid_arrive_wait(g, err);
   __syncthreads();
   return *sh_ok != 0;
 }
-
 // ---- op descriptors staged in shared memory (the OIM of one layer for the
 // rows this CTA evaluates), copied with cp.async while the CTA waits at the
 // grid barrier before the layer, so that an item reads its descriptor from
@@ -168,26 +185,7 @@ template <typename F>
 __device__ __forceinline__ bool grid_sync_staging(const GridArgs& g, uint32_t* err, int* sh_ok, F&& stage) {
   __syncthreads();
   stage();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const uint32_t my = ld_acquire(g.gen);
-    __threadfence();
-    if (atomicAdd(g.count, 1u) == g.expected - 1u) {
-      atomicExch(g.count, 0u);
-      __threadfence();
-      atomicAdd(g.gen, 1u);
-    } else {
-      const uint64_t t0 = globaltimer();
-      while (ld_acquire(g.gen) == my) {
-        if (ld_acquire(err) != 0u) { ok = 0; break; }
-        if (globaltimer() - t0 > g.timeout_ns) { atomicOr(err, 1u); ok = 0; break; }
-        __nanosleep(100);
-      }
-    }
-    if (ld_acquire(err) != 0u) ok = 0;
-    __threadfence();
-    *sh_ok = ok;
-  }
+  if (threadIdx.x == 0) *sh_ok = grid_arrive_wait(g, err);
   cp_async_wait_all();
   __syncthreads();
   return *sh_ok != 0;

@@ -262,7 +262,7 @@ struct rteaal_sim {
   uint32_t* lane_of_user = nullptr;  // [n_user] or null
   uint32_t* tile_order = nullptr;    // [n_tiles]
   uint32_t* tile_cycles = nullptr;   // [n_tiles]
-  uint32_t* scratch = nullptr;       // [64]: 0 err, 1 tile counter, 2 bar count, 3 bar gen, 4 cycle
+  uint32_t* scratch = nullptr;       // [64]: 0 err, 1 tile counter, 2-3 barrier count (u64), 4 cycle
   uint64_t* staging = nullptr;       // grown on demand (host stimulus / probe buffers)
   size_t staging_bytes = 0;
   uint32_t* probe_slots = nullptr;   // grown on demand
@@ -1521,8 +1521,7 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
     } else if (s->kernel == RTEAAL_KERNEL_STREAM) {
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
       GridArgs ga{};
-      ga.count = s->scratch + 2;
-      ga.gen = s->scratch + 3;
+      ga.count = reinterpret_cast<unsigned long long*>(s->scratch + 2);
       ga.expected = s->grid + s->barrier_extra;
       ga.timeout_ns = s->barrier_timeout_ns;
       ga.ncyc = (uint32_t)max_cyc;
@@ -1543,8 +1542,7 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
       const uint32_t grid = grid_for_span(s, span, (uint32_t)s->V);
       GridArgs ga{};
-      ga.count = s->scratch + 2;
-      ga.gen = s->scratch + 3;
+      ga.count = reinterpret_cast<unsigned long long*>(s->scratch + 2);
       ga.expected = grid + s->barrier_extra;
       ga.timeout_ns = s->barrier_timeout_ns;
       ga.ncyc = (uint32_t)max_cyc;
@@ -1751,8 +1749,8 @@ RT_EXPORT int rteaal_stim_state_write(rteaal_sim* s, uint32_t inst0, uint32_t n_
 // ================================================================== allocation-free step
 //
 // For callers that cannot allocate device memory themselves: everything the
-// persistent grid kernel needs besides the caller's buffers (barrier arrival
-// count, barrier generation, error word, per-lane cycle budgets) lives in one
+// persistent grid kernel needs besides the caller's buffers (error word,
+// barrier arrival count, per-lane cycle budgets) lives in one
 // file-scope device array.  Every GPU that loads this library holds the array
 // (RTEAAL_STATIC_MAX_LANES * 4 + 256 bytes) until the process exits.
 
@@ -1833,8 +1831,7 @@ RT_EXPORT int rteaal_step_static(const rteaal_design* d, void* state, uint64_t* 
       ds.uniform = uniform_cycles;
     }
     GridArgs ga{};
-    ga.count = scratch + 1;
-    ga.gen = scratch + 2;
+    ga.count = reinterpret_cast<unsigned long long*>(scratch + 2);
     ga.expected = grid;
     ga.timeout_ns = 2000000000ull;
     // the same wait bound and test hook as the regular grid launch

@@ -95,7 +95,55 @@ def designs() -> dict:
     b.connect(r1, k)
     b.connect(r2, r0)
     out["copies-only"] = (b.build(), False)
+    out["byte results"] = (byte_results_design(), False)
     return out
+
+
+def byte_results_design() -> synth.Netlist:
+    """Ops with results of at most 8 bits (class-0 rows, the kernels' packed
+    byte-lane form) over operands of every narrow class: each opcode at result
+    widths 1, 4 and 8, once with operands of at most 8 bits and once with wider
+    ones, shift amounts and bit ranges on both sides of a byte, two- and
+    three-operand folds; registers feed results back so values change per cycle."""
+    b = Builder()
+    widths = (1, 3, 8, 12, 16, 24, 32)
+    ins = [b.input(w) for w in widths]
+    rw = (8, 5, 1, 16, 32, 7)
+    regs = [b.reg(w, init=(37 * i + 11) & ((1 << w) - 1)) for i, w in enumerate(rw)]
+    src = list(zip(ins + regs, widths + rw))
+    small = [x for x, w in src if w <= 8]
+    wide = [x for x, w in src if w > 8]
+    k = 0
+
+    def pick(pool, n):
+        nonlocal k
+        k += 1
+        return [pool[(k * 3 + j * 5) % len(pool)] for j in range(n)]
+
+    outs = []
+    for w in (1, 4, 8):
+        for pool in (small, wide, small + wide):
+            for name, n in (("COPY", 1), ("AND", 2), ("OR", 2), ("XOR", 2), ("NOT", 1), ("ADD", 2),
+                            ("SUB", 2), ("MUL", 2), ("DSHL", 2), ("DSHR", 2), ("EQ", 2), ("NEQ", 2),
+                            ("LT", 2), ("LEQ", 2), ("GT", 2), ("GEQ", 2), ("MUX", 3), ("ORR", 1),
+                            ("XORR", 1), ("AND", 3), ("XOR", 3), ("ADD", 3), ("OR", 3)):
+                outs.append(b.op(name, w, *pick(pool, n)))
+            for sh in (0, 1, 5, 7, 8, 9, 40):
+                outs.append(b.op("SHL", w, *pick(pool, 1), p0=sh))
+                outs.append(b.op("SHR", w, *pick(pool, 1), p0=sh))
+                outs.append(b.op("CAT", w, *pick(pool, 2), p0=max(sh, 1)))
+            for hi, lo in ((7, 0), (5, 2), (7, 7), (3, 0), (12, 9), (10, 3), (31, 8)):
+                outs.append(b.op("BITS", w, *pick(pool, 1), p0=hi, p1=lo))
+            for p0 in (1, 3, 8, 9, 16):
+                outs.append(b.op("ANDR", w, *pick(pool, 1), p0=p0))
+    # the ops' results feed the next cycle: byte results combined into each register
+    for i, (r, wr) in enumerate(zip(regs, rw)):
+        part = outs[i::len(regs)]
+        acc = part[0]
+        for x in part[1:]:
+            acc = b.op("XOR", 8, acc, x)
+        b.connect(r, b.op("ADD", wr, acc, *pick(wide, 1)))
+    return b.build()
 
 
 DESIGNS = designs()
@@ -219,6 +267,22 @@ KERNEL_MUTANTS = [
     ("reset ignores init values",
      "if (s.reset) {\n        const uint64_t init = __ldg(&d.reg_init[r]) & mk;",
      "if (s.reset) {\n        const uint64_t init = 0;"),
+    ("packed subtract: top bit of each byte not fixed up",
+     "return ((a | H) - (b & ~H)) ^ ((a ^ ~b) & H);", "return ((a | H) - (b & ~H)) ^ ((a ^ b) & H);"),
+    ("packed unsigned compare: the top bits ignored",
+     "return ((x & b) | (~x & ~d)) & H;", "return ~d & H;"),
+    ("packed shift left: bits crossing into the next byte kept",
+     "return s >= 8u ? (T)0 : (a << s) & rep8<T>(0xFFu << s);", "return s >= 8u ? (T)0 : (a << s);"),
+    ("packed parity: one fold dropped",
+     "own bits only\n      x ^= x >> 2;", "own bits only\n"),
+    ("8-lane 2-byte operand cut to its high bytes",
+     "return (uint64_t)__byte_perm(t.x, t.y, 0x6420u) | ((uint64_t)__byte_perm(t.z, t.w, 0x6420u) << 32);",
+     "return (uint64_t)__byte_perm(t.x, t.y, 0x7531u) | ((uint64_t)__byte_perm(t.z, t.w, 0x7531u) << 32);"),
+    ("packed store of a partial mask writes every lane",
+     "    if (m & (1u << v)) p[v] = (uint8_t)(r >> (8 * v));", "    p[v] = (uint8_t)(r >> (8 * v));"),
+    ("packed form taken for a right shift of a wider operand",
+     "return (dref >> 30) == 0u && (((PACK_LOW_OPS >> op) & 1u) || (bytes_in && ((PACK_BYTE_OPS >> op) & 1u)));",
+     "return (dref >> 30) == 0u && (((PACK_LOW_OPS >> op) & 1u) || ((PACK_BYTE_OPS >> op) & 1u));"),
 ]
 
 
@@ -236,7 +300,7 @@ def test_planted_kernel_mistakes_are_caught(tmp_path):
         (d / "kernels.cuh").write_text(src.replace(old, new))
         lib = build_harness(str(d), d, opt="-O0")   # quick to build; the runs are short
         caught = False
-        for name_d in ["random+mem", "wide+domains", "chains-fused", "copies-only"]:
+        for name_d in ["random+mem", "wide+domains", "chains-fused", "copies-only", "byte results"]:
             nl, fuse = DESIGNS[name_d]
             for V in (4, 8):
                 try:
