@@ -254,6 +254,16 @@ enum {
                                layer of every cycle of it with the hardware
                                cluster barrier between layers (for few lanes:
                                one instance, the tail of a job)                   */
+  RTEAAL_KERNEL_FLOW = 8,   /* persistent cooperative, one lane per item, no barrier
+                               between layers (Cascade 1's LI_{i+1} <- LO_i step
+                               as a per-operand wait): every result is also written
+                               to a word holding it next to the cycle's stamp, and
+                               an item waits (bounded) until the operands it reads
+                               carry this cycle's stamp; grid barriers only around
+                               the stimulus and the clock edge.  For few lanes (one
+                               instance); its stamped words take 16 bytes per row
+                               and lane of extra device memory, allocated at the
+                               first FLOW step.  Error word bit 8: a wait gave up */
   RTEAAL_KERNEL_SPECIALIZED = 6 /* design-specialised (Sec. 5.2 SU / TI on the GPU):
                                the op list unrolled into straight-line code compiled
                                at run time (NVRTC), every signal a local variable,
@@ -334,7 +344,7 @@ typedef struct {
 
 /* Autotuner: times every candidate launch configuration of the kernels in
  * kernel_mask (bit 1 << RTEAAL_KERNEL_*, 0 = TILE|GRID|STREAM, or
- * LAYER|GRID|CLUSTER for fewer than 64 lanes) on this sim, one warm-up and one timed step of
+ * LAYER|GRID|CLUSTER|FLOW for fewer than 64 lanes) on this sim, one warm-up and one timed step of
  * cycles_per_trial cycles each, keeps the fastest, and restores the state,
  * memories and stimulus states exactly (device-to-device snapshot: needs
  * free device memory equal to the sim's state).  trials (nullable) receives

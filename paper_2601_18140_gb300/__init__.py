@@ -28,7 +28,7 @@ RTEAAL_PROBE_LAST, RTEAAL_PROBE_EVERY, RTEAAL_PROBE_CHANGES = 0, 1, 2
 RTEAAL_STEP_RESET = 1
 
 KERNELS = {"auto": 0, "layer": 1, "tile": 2, "grid": 3, "layer_graph": 4, "stream": 5, "specialized": 6,
-           "cluster": 7}
+           "cluster": 7, "flow": 8}
 
 
 class RteaalError(RuntimeError):

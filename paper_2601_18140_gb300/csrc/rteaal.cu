@@ -27,6 +27,7 @@
 #include "host_api.hpp"
 #include "lower.hpp"
 #include "cluster.cuh"
+#include "flow.cuh"
 #include "persistent.cuh"
 #include "rteaal.h"
 
@@ -286,7 +287,14 @@ struct rteaal_sim {
   uint32_t res_slice = 0;            // CLUSTER resident: state bytes per CTA
   uint32_t res_smem = 0;             // CLUSTER resident: dynamic shared memory per CTA
   uint32_t last_span = 0;            // lanes the last step visited
-  uint32_t last_grid = 0;            // CTAs of the last GRID launch
+  uint32_t last_grid = 0;            // CTAs of the last GRID / FLOW launch
+  unsigned long long* flow_mirror = nullptr;  // FLOW: stamped result words, allocated on first use
+  uint32_t flow_epoch = 0;           // FLOW: stamps used so far (the next cycle stamps flow_epoch + 1)
+  const void* flow_fn = nullptr;     // FLOW: the kernel variant in use
+  uint4* flow_op = nullptr;          // FLOW: per op {operand rows, output row}, {ctl, output ref, ext}
+  uint32_t* flow_ext = nullptr;      // FLOW: operand rows of ops with more than three operands
+  uint2* flow_pool = nullptr;        // FLOW: {ref, row} of inputs, registers, constants
+  uint32_t flow_skew = 0;            // test hook: FLOW items wait for a stamp this far ahead
   // activity-aware evaluation (GRID only)
   bool activity = false;
   uint8_t* act = nullptr;            // [n_slots][act_chunks] 8-bit change stamps
@@ -343,12 +351,14 @@ DSim dsim(const rteaal_sim* s) {
 }
 
 // Which bounded device waits gave up (error word bits): 1 grid barrier,
-// 2 stream ring barrier, 4 stream drain of its own copies after a timeout.
+// 2 stream ring barrier, 4 stream drain of its own copies after a timeout,
+// 8 FLOW wait for an operand's stamp.
 std::string wait_kind(uint32_t e) {
   std::string k;
   if (e & 1u) k += "grid barrier";
   if (e & 2u) k += k.empty() ? "stream ring barrier" : ", stream ring barrier";
   if (e & 4u) k += k.empty() ? "stream drain of copies in flight" : ", stream drain of copies in flight";
+  if (e & 8u) k += k.empty() ? "FLOW operand stamp" : ", FLOW operand stamp";
   return k.empty() ? "unknown wait" : k;
 }
 
@@ -741,7 +751,7 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     throw Error(RTEAAL_E_UNSUPPORTED, "activity-aware evaluation runs with the GRID kernel only");
   if (s->activity && unroll > 1)
     throw Error(RTEAAL_E_UNSUPPORTED, "activity-aware evaluation has no unrolled variants");
-  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_CLUSTER, "unknown kernel");
+  require(kernel >= RTEAAL_KERNEL_LAYER && kernel <= RTEAAL_KERNEL_FLOW, "unknown kernel");
   if (kernel == RTEAAL_KERNEL_CLUSTER && !tile_lanes)  // a cluster tile: all lanes of a small sim, else 256 / 128
     tile_lanes = s->n_pad <= 256 ? s->n_pad : s->n_pad % 256 == 0 ? 256u : 128u;
   if (!unroll) unroll = 1;
@@ -855,6 +865,29 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
     s->n_clusters = std::min<uint32_t>(best_ncl, s->n_pad / tile_lanes);
     ctas_per_sm = 1;
     grid = s->n_clusters * best_cs;
+  } else if (kernel == RTEAAL_KERNEL_FLOW) {
+    // one lane per item; a grid sized to the widest phase (threads beyond it
+    // only add arrivals to the barriers around the stimulus and the edge)
+    const FlowVariantTable ft = variants_flow();
+    const FlowVariant* fv = nullptr;
+    for (size_t i = 0; i < ft.n; i++)
+      if ((uint32_t)ft.v[i].maxt == threads) fv = &ft.v[i];
+    if (!fv)
+      for (size_t i = 0; i < ft.n; i++)
+        if (ft.v[i].maxt == 128) fv = &ft.v[i];
+    require(fv != nullptr, "no compiled FLOW variant");
+    s->flow_fn = fv->fn;
+    threads = (uint32_t)fv->maxt;
+    V = 1;
+    unroll = 1;
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fv->fn, (int)threads, 0));
+    require(occ >= 1, "FLOW kernel cannot be resident");
+    ctas_per_sm = (uint32_t)occ;
+    const Lowered& L = s->design->L;
+    const uint64_t widest = std::max<uint64_t>(
+        {(uint64_t)L.max_layer_ops, L.reg_src.size() + (L.mem_info.size() / 4 - 1), (uint64_t)L.in_width.size(), 1});
+    grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * s->design->n_sms, (widest * s->n_pad + threads - 1) / threads);
   } else if (kernel == RTEAAL_KERNEL_STREAM) {
     // one CTA of STREAM_WARPS warps per SM; items of 256 lanes (128 when the
     // lane count is an odd multiple of 128); every warp keeps one chunk
@@ -1007,6 +1040,7 @@ RT_EXPORT int rteaal_sim_create(const rteaal_design* d, uint32_t n_instances, co
                 opts ? opts->ctas_per_sm : 0, opts ? opts->unroll : 0, opt_lanes(opts), opts ? opts->cluster_ctas : 0,
                 opts ? opts->cluster_resident : 0);
       if (const char* e = getenv("RTEAAL_TEST_WITHHOLD_ARRIVAL")) s->barrier_extra = (uint32_t)atoi(e);
+      if (const char* e = getenv("RTEAAL_TEST_FLOW_STAMP_SKEW")) s->flow_skew = (uint32_t)atoi(e);
       if (const char* e = getenv("RTEAAL_BARRIER_TIMEOUT_NS")) s->barrier_timeout_ns = strtoull(e, nullptr, 10);
 
       const Lowered& L = d->L;
@@ -1164,7 +1198,7 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
       kernel_mask = s->n_pad >= 64 ? ((1u << RTEAAL_KERNEL_TILE) | (1u << RTEAAL_KERNEL_GRID) |
                                       (1u << RTEAAL_KERNEL_STREAM))
                                    : ((1u << RTEAAL_KERNEL_LAYER) | (1u << RTEAAL_KERNEL_GRID) |
-                                      (1u << RTEAAL_KERNEL_CLUSTER));
+                                      (1u << RTEAAL_KERNEL_CLUSTER) | (1u << RTEAAL_KERNEL_FLOW));
     const Lowered& L = s->design->L;
     const size_t np = s->n_pad;
     const size_t b_state = np * L.lane_bytes, b_mem = np * 8 * L.mem_words_total,
@@ -1212,6 +1246,10 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
           if (T == np) break;
         }
       }
+    }
+    if (kernel_mask & (1u << RTEAAL_KERNEL_FLOW)) {
+      const FlowVariantTable ft = variants_flow();
+      for (size_t i = 0; i < ft.n; i++) cands.push_back({RTEAAL_KERNEL_FLOW, 0, (uint32_t)ft.v[i].maxt, 1, 1});
     }
     for (const Cand& c : cands) candx.push_back({c.kernel, c.T, c.threads, c.U, c.V, 0});
 
@@ -1381,6 +1419,7 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
     const uint32_t span = live_span(s, hb, s->kernel == RTEAAL_KERNEL_STREAM ? s->stream_chunk
                                            : s->kernel == RTEAAL_KERNEL_SPECIALIZED ? kSpecThreads
                                            : s->kernel == RTEAAL_KERNEL_CLUSTER ? s->tile_lanes
+                                           : s->kernel == RTEAAL_KERNEL_FLOW ? 1u
                                            : 32u * (uint32_t)s->V);
     s->last_span = span;
     if (s->kernel == RTEAAL_KERNEL_LAYER) {
@@ -1535,6 +1574,91 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       if (e == cudaErrorCooperativeLaunchTooLarge)
         throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
       CK(e);
+      CK(cudaMemcpyAsync(s->err_host, s->scratch, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaEventRecord(s->done, st));
+      s->pending = true;
+    } else if (s->kernel == RTEAAL_KERNEL_FLOW) {
+      require(max_cyc <= 0xFFFFFFFFull, "rteaal_step: too many cycles");
+      const size_t mirror_bytes = (size_t)L.n_slots * s->n_pad * 16;
+      if (!s->flow_mirror) {
+        s->flow_mirror = static_cast<unsigned long long*>(s->get(std::max<size_t>(mirror_bytes, 16)));
+        CK(cudaMemsetAsync(s->flow_mirror, 0, mirror_bytes, st));
+        s->flow_epoch = 0;
+        // row (layout order) of a reference; FLOW_CHECK on rows that ops write
+        // (rows of a class hold inputs, registers and constants, then op results)
+        const uint32_t c3 = L.class_rows[3], c2 = L.class_rows[2], c1 = L.class_rows[1];
+        const uint32_t coff[4] = {8 * c3 + 4 * c2 + 2 * c1, 8 * c3 + 4 * c2, 8 * c3, 0u};
+        const uint32_t cidx[4] = {c3 + c2 + c1, c3 + c2, c3, 0u};
+        uint32_t op_off[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+        for (uint32_t sl = L.op_base; sl < L.n_slots; sl++) {
+          const uint32_t k = L.slot_ref[sl] >> 30;
+          op_off[k] = std::min(op_off[k], L.slot_ref[sl] & REF_OFF_MASK);
+        }
+        auto row_of = [&](uint32_t ref) {
+          const uint32_t k = ref >> 30, off = ref & REF_OFF_MASK;
+          return (cidx[k] + ((off - coff[k]) >> k)) | (off >= op_off[k] ? FLOW_CHECK : 0u);
+        };
+        std::vector<uint4> fop(2 * L.meta.size());
+        for (size_t i = 0; i < L.meta.size(); i++) {
+          const OpMeta& m = L.meta[i];
+          const uint32_t drow = row_of(L.dst_ref[i]) & ~FLOW_CHECK;
+          if (m.ctl & CTL_EXT) {
+            fop[2 * i] = make_uint4(0u, 0u, 0u, drow);
+            fop[2 * i + 1] = make_uint4(m.ctl, L.dst_ref[i], m.a, m.b);
+          } else {
+            fop[2 * i] = make_uint4(row_of(m.a), row_of(m.b), row_of(m.c), drow);
+            fop[2 * i + 1] = make_uint4(m.ctl, L.dst_ref[i], 0u, 0u);
+          }
+        }
+        std::vector<uint32_t> fext(std::max<size_t>(L.ext_args.size(), 1), 0u);
+        for (size_t k = 0; k < L.ext_args.size(); k++) fext[k] = row_of(L.ext_args[k]);
+        std::vector<uint2> fpool;
+        for (uint32_t r : L.in_ref) fpool.push_back(make_uint2(r, row_of(r) & ~FLOW_CHECK));
+        for (uint32_t r : L.reg_ref) fpool.push_back(make_uint2(r, row_of(r) & ~FLOW_CHECK));
+        for (uint32_t r : L.const_ref) fpool.push_back(make_uint2(r, row_of(r) & ~FLOW_CHECK));
+        if (fpool.empty()) fpool.push_back(make_uint2(0u, 0u));
+        s->flow_op = static_cast<uint4*>(s->get(fop.size() * sizeof(uint4)));
+        s->flow_ext = static_cast<uint32_t*>(s->get(fext.size() * 4));
+        s->flow_pool = static_cast<uint2*>(s->get(fpool.size() * sizeof(uint2)));
+        CK(cudaMemcpyAsync(s->flow_op, fop.data(), fop.size() * sizeof(uint4), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s->flow_ext, fext.data(), fext.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s->flow_pool, fpool.data(), fpool.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+      }
+      if ((uint64_t)s->flow_epoch + max_cyc >= 0xFFFFFFFFull) {  // stamps would wrap: start over
+        CK(cudaMemsetAsync(s->flow_mirror, 0, mirror_bytes, st));
+        s->flow_epoch = 0;
+      }
+      const uint64_t widest = std::max<uint64_t>(
+          {(uint64_t)L.max_layer_ops, L.reg_src.size() + (L.mem_info.size() / 4 - 1), (uint64_t)L.in_width.size(), 1});
+      const uint32_t grid = (uint32_t)std::max<uint64_t>(
+          1, std::min<uint64_t>(s->grid, (widest * span + s->threads - 1) / s->threads));
+      GridArgs ga{};
+      ga.count = reinterpret_cast<unsigned long long*>(s->scratch + 2);
+      ga.expected = grid + s->barrier_extra;
+      ga.timeout_ns = 2 * s->barrier_timeout_ns;
+      ga.ncyc = (uint32_t)max_cyc;
+      ga.tpo = make_fastdiv(span);
+      FlowArgs fa{};
+      fa.timeout_ns = s->barrier_timeout_ns;
+      fa.mirror = s->flow_mirror;
+      fa.fop = s->flow_op;
+      fa.fext = s->flow_ext;
+      fa.fpool = s->flow_pool;
+      fa.n_in = (uint32_t)D->L.in_ref.size();
+      fa.n_reg = (uint32_t)D->L.reg_ref.size();
+      fa.n_const = (uint32_t)D->L.const_ref.size();
+      fa.epoch = s->flow_epoch;
+      fa.skew = s->flow_skew;
+      fa.span = make_fastdiv(span);
+      CK(cudaMemsetAsync(s->scratch, 0, 16, st));
+      void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ga, (void*)&fa};
+      s->last_grid = grid;
+      cudaError_t e = cudaLaunchCooperativeKernel(s->flow_fn, dim3(grid), dim3(s->threads), args, 0, st);
+      if (e == cudaErrorCooperativeLaunchTooLarge)
+        throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
+      CK(e);
+      s->flow_epoch += (uint32_t)max_cyc;
       CK(cudaMemcpyAsync(s->err_host, s->scratch, 4, cudaMemcpyDeviceToHost, st));
       CK(cudaEventRecord(s->done, st));
       s->pending = true;

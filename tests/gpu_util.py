@@ -13,11 +13,11 @@ MODES = {"hold": oracle.STIM_HOLD, "xorshift": oracle.STIM_XORSHIFT, "buffer": o
 
 class Pair:
     def __init__(self, nl: synth.Netlist, n_inst: int, kernel="auto", seed: int = 0,
-                 expected_cycles=None, oracle_instances=None, **sim_kw):
+                 expected_cycles=None, oracle_instances=None, fuse_mux_chains: bool = False, **sim_kw):
         self.nl = nl
         self.n = n_inst
         self.xs = synth.xorshift_seeds(seed, nl.n_inputs, n_inst)
-        self.design = rt.Design(nl.to_bytes())
+        self.design = rt.Design(nl.to_bytes(), fuse_mux_chains=fuse_mux_chains)
         self.sim = rt.Sim(self.design, n_inst, kernel=kernel, xorshift_seed=self.xs,
                           expected_cycles=expected_cycles, **sim_kw)
         # the oracle may follow only a sample of instances (large workloads)

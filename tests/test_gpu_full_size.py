@@ -2,7 +2,8 @@
 
 * single-200k: 200k-op DAG, 1 instance, plain per-layer form and the grid form;
   and the whole configuration -- reset + 100,000 cycles -- in the CUDA-graph
-  plain form, every signal checked (the oracle runs alongside on the host);
+  plain form, the cluster form and the FLOW form, every signal checked (the
+  oracle runs alongside on the host);
 * batch-1M: 1M ops, 4,096 instances with uneven cycle budgets, in the launch
   configuration the benchmark times (autotuned), five sampled instances
   (first, middle, last lane, shortest and longest budget) checked signal by signal;
@@ -50,13 +51,16 @@ def test_single_200k_full_length():
     t = threading.Thread(target=run_oracle)    # the C oracle runs without the GIL
     t.start()
     d = rt.Design(nl.to_bytes())
-    s = rt.Sim(d, 1, kernel="layer_graph", xorshift_seed=xs)
-    s.step(1, stimulus="xorshift", reset=True)
-    s.step(100_000, stimulus="xorshift")
-    g = s.read()
+    got = {}
+    for kernel in ["layer_graph", "cluster", "flow"]:   # the plain form and the two one-instance forms
+        s = rt.Sim(d, 1, kernel=kernel, xorshift_seed=xs)
+        s.step(1, stimulus="xorshift", reset=True)
+        s.step(100_000, stimulus="xorshift")
+        got[kernel] = s.read()
+        s.close()
     t.join()
-    assert np.array_equal(g, o.read())
-    s.close()
+    for kernel, g in got.items():
+        assert np.array_equal(g, o.read()), kernel
     d.close()
 
 

@@ -13,7 +13,7 @@ from tests.netlist_rules import fused_away
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kernel", ["layer", "grid", "stream"])
+@pytest.mark.parametrize("kernel", ["layer", "grid", "stream", "flow"])
 def test_fused_mux_chains_match_unfused_oracle(kernel):
     nl = synth.generate(DesignSpec(n_ops=4000, n_regs=150, depth=16, n_inputs=4, seed=71,
                                    input_widths=(8, 32, 1, 64), mux_chain_frac=0.7, n_mems=2,
