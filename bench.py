@@ -366,7 +366,7 @@ def run_ours(args) -> None:
     peaks = measured_peaks()
     achieved = per_launch_bytes / avg_launch_s / 1e9
     kname = {1: "k_layer_ops", 2: "k_tile", 3: "k_grid", 4: "k_layer_ops", 5: "k_stream",
-             6: "rteaal_spec"}[info["kernel"]]
+             6: "rteaal_spec", 7: "k_cluster", 8: "k_flow"}[info["kernel"]]
     # DRAM bytes per instance-cycle of this kernel on this workload (from an ncu
     # capture of one of its launch configurations; every configuration moves the
     # same rows, only L2 reuse differs)
@@ -488,6 +488,20 @@ def run_ours(args) -> None:
         plain = {"form": "layer_graph, 1 instance", "value": p_rate, "unit": "op-evals/s",
                  "cycles": args.plain_cycles, "batched_over_plain": value / p_rate}
         p_sim.close()
+        # the same instance in the FLOW form (no barrier between layers): the
+        # fastest one-instance form, beside the plain one
+        f_sim = rt.Sim(design, 1, kernel="flow", xorshift_seed=np.ascontiguousarray(xs[:, :1]))
+        f_sim.step(1, stimulus="xorshift", reset=True)
+        f_sim.step(2, stimulus="xorshift")
+        torch.cuda.synchronize()
+        p0.record(stream)
+        f_sim.step(args.plain_cycles, stimulus="xorshift", stream=stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        f_rate = args.plain_cycles * nl.n_ops / (p0.elapsed_time(p1) / 1e3)
+        plain["flow_one_instance"] = {"value": f_rate, "over_plain": f_rate / p_rate,
+                                      "batched_over_flow": value / f_rate}
+        f_sim.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -510,7 +524,7 @@ def run_ours(args) -> None:
                        "inputs_after_reset": run_stim,
                        "cycles_per_step": C, "kernel": args.kernel,
                        "kernel_used": {1: "layer", 2: "tile", 3: "grid", 4: "layer_graph", 5: "stream",
-                                       6: "specialized"}[info["kernel"]],
+                                       6: "specialized", 7: "cluster", 8: "flow"}[info["kernel"]],
                        "tile_lanes": info["tile_lanes"], "threads": info["threads"],
                        "ctas_per_sm": info["ctas_per_sm"], "unroll": info["unroll"],
                        "lanes_per_thread": info["lanes_per_thread"],

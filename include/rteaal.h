@@ -283,7 +283,9 @@ typedef struct {
    * RTEAAL_STIM_XORSHIFT (copied).  A zero state stays zero. */
   const uint64_t *xorshift_seed;
   int kernel;              /* RTEAAL_KERNEL_*                                   */
-  uint32_t tile_lanes;     /* TILE: lanes per tile (power of two <= 64), 0 auto */
+  uint32_t tile_lanes;     /* TILE: lanes per tile (power of two <= 64), 0 auto;
+                              CLUSTER: lanes per cluster tile; FLOW: items a warp
+                              takes per layer (1..32, 0 = 8)                     */
   uint32_t threads;        /* threads per CTA (multiple of 32, <= 1024), 0 auto */
   uint32_t ctas_per_sm;    /* TILE / GRID residency target, 0 auto              */
   uint32_t unroll;         /* operations in flight per thread (1, 2, 4), 0 auto */

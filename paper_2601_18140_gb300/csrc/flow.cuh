@@ -46,6 +46,8 @@ struct FlowArgs {
   uint32_t epoch;       // cycle c of the launch stamps its results epoch + c + 1
   uint32_t skew;        // 0; a test hook makes items wait for a stamp that never comes
   uint64_t timeout_ns;  // bound of every stamp wait (the launch's barriers wait twice as long)
+  int off_in_smem;      // the launch's dynamic shared memory holds the layer offsets
+  uint32_t kw;          // items a warp takes per layer and round (its first kw lanes), 1..32
   FastDiv span;         // lanes the launch visits
 };
 
@@ -108,14 +110,16 @@ __device__ __forceinline__ bool flow_value(const DSim& s, const FlowArgs& f, uin
 
 // One item per lane of a warp -- a lowered op (descriptor q) for one lane:
 // op_u / op_r / op_s of Cascade 1; `has` false: the lane has no item.  Every
-// operand is one 16-byte load of its words, issued before any is used.  The
-// warp waits as one: its lanes with at most three operands reload the operands
+// operand is one 16-byte load of its words, issued before any is used (by
+// flow_issue, while the warp finished its previous item).  The warp waits as
+// one: its lanes with at most three operands reload the operands
 // not yet stamped until every such lane has all of them (a spinning lane never
 // diverges from the others); lanes of extended ops wait operand by operand.
 // Returns false if a wait gave up (then the error word is set).
 __device__ __forceinline__ bool flow_items(const DDesign& d, const DSim& s, const FlowArgs& f, bool has,
-                                           const uint4& qa, const uint4& qb, uint32_t lane, uint32_t stamp,
-                                           uint32_t want, uint64_t timeout_ns) {
+                                           const uint4& qa, const uint4& qb, uint32_t lane, ulonglong2 wa,
+                                           ulonglong2 wb, ulonglong2 wc, uint32_t stamp, uint32_t want,
+                                           uint64_t timeout_ns) {
   const uint32_t ctl = qb.x;
   const bool ext = has && (ctl & CTL_EXT);
   const uint32_t plain = __ballot_sync(0xFFFFFFFFu, has && !ext);  // lanes that wait together
@@ -132,9 +136,6 @@ __device__ __forceinline__ bool flow_items(const DDesign& d, const DSim& s, cons
   } else if (has) {
     const uint32_t ar = (ctl >> 5) & 3u;
     const uint32_t rb = ar >= 2 ? qa.y : 0u, rc = ar >= 3 ? qa.z : 0u;  // row 0 unchecked: a spare load
-    ulonglong2 wa = ld_relaxed_v2(flow_word(s, f, qa.x, lane));
-    ulonglong2 wb = ld_relaxed_v2(flow_word(s, f, rb, lane));
-    ulonglong2 wc = ld_relaxed_v2(flow_word(s, f, rc, lane));
     auto ready = [&] {
       return flow_ready(qa.x, wa, want) && flow_ready(rb, wb, want) && flow_ready(rc, wc, want);
     };
@@ -171,21 +172,36 @@ __device__ __forceinline__ bool flow_items(const DDesign& d, const DSim& s, cons
   return __all_sync(0xFFFFFFFFu, ok);
 }
 
+// The operand words of an item with at most three operands, loaded ahead:
+// those written earlier (most of an item's operands, once its producers are
+// done) are then ready when the item is evaluated; the others are reloaded.
+__device__ __forceinline__ void flow_issue(const DSim& s, const FlowArgs& f, bool has, const uint4& qa,
+                                           const uint4& qb, uint32_t lane, ulonglong2& wa, ulonglong2& wb,
+                                           ulonglong2& wc) {
+  const uint32_t ar = (qb.x >> 5) & 3u;
+  const bool plain = has && !(qb.x & CTL_EXT);
+  wa = ld_relaxed_v2(flow_word(s, f, plain ? qa.x : 0u, lane));
+  wb = ld_relaxed_v2(flow_word(s, f, plain && ar >= 2 ? qa.y : 0u, lane));
+  wc = ld_relaxed_v2(flow_word(s, f, plain && ar >= 3 ? qa.z : 0u, lane));
+}
+
 // A warp's position in the evaluation phase: layer L (rows from o0, n items)
-// and the item index of its first thread.
+// and the item index of its first thread (warp w takes items w kw .. w kw +
+// kw - 1, then the same plus W kw, ... for W warps: fewer items per warp than
+// lanes make a warp wait for fewer producers).
 struct FlowPos {
   uint32_t L, o0, n, base;
 };
 
 // Move to the warp's next position with items (base + T in this layer, else
 // the first later layer that has items for it); false past the last layer.
-__device__ __forceinline__ bool flow_next(const DDesign& d, const FlowArgs& f, FlowPos& p, uint32_t t0,
-                                          uint32_t T) {
-  p.base += T;
+__device__ __forceinline__ bool flow_next(const DDesign& d, const FlowArgs& f, const uint32_t* off, FlowPos& p,
+                                          uint32_t t0, uint32_t T) {
+  p.base += T;  // T: items of one round (warps x kw)
   while (p.base >= p.n) {
     if (++p.L >= d.n_layers) return false;
-    p.o0 = __ldg(&d.layer_off[p.L]);
-    p.n = (__ldg(&d.layer_off[p.L + 1]) - p.o0) * f.span.d;
+    p.o0 = off[p.L];
+    p.n = (off[p.L + 1] - p.o0) * f.span.d;
     p.base = t0;
   }
   return true;
@@ -203,7 +219,7 @@ __device__ __forceinline__ FlowSlot flow_slot(const DSim& s, const FlowArgs& f, 
                                               uint32_t c) {
   FlowSlot q{make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u), 0u, false};
   const uint32_t i = p.base + (t & 31u);
-  if (i < p.n) {
+  if ((t & 31u) < f.kw && i < p.n) {
     const uint32_t r = fdiv(f.span, i);
     q.lane = i - r * f.span.d;
     q.has = lane_active(s, q.lane, c);  // a frozen lane's results are read only by itself
@@ -215,27 +231,32 @@ __device__ __forceinline__ FlowSlot flow_slot(const DSim& s, const FlowArgs& f, 
   return q;
 }
 
-// The evaluation phase of cycle c: thread t takes items t, t + T, ... of every
-// layer in turn, an item being (row, lane) with the lanes of a row adjacent;
-// a warp's 32 threads go through their items together.
-__device__ __forceinline__ bool flow_cycle(const DDesign& d, const DSim& s, const FlowArgs& f, uint32_t c,
-                                           uint32_t t, uint32_t T, uint64_t timeout_ns) {
-  const uint32_t stamp = f.epoch + c + 1u, t0 = t & ~31u;
+// The evaluation phase of cycle c: the warps take the items of every layer in
+// turn (an item being (row, lane), the lanes of a row adjacent), kw per warp
+// and round; a warp's threads go through their items together.  `off`: the
+// layer offsets (in shared memory when they fit).
+__device__ __forceinline__ bool flow_cycle(const DDesign& d, const DSim& s, const FlowArgs& f, const uint32_t* off,
+                                           uint32_t c, uint32_t t, uint32_t T, uint64_t timeout_ns) {
+  const uint32_t stamp = f.epoch + c + 1u, t0 = (t >> 5) * f.kw, R = (T >> 5) * f.kw;
   FlowPos p{0u, 0u, 0u, t0};
   bool more = false;
   if (d.n_layers > 0) {
-    p.o0 = __ldg(&d.layer_off[0]);
-    p.n = (__ldg(&d.layer_off[1]) - p.o0) * f.span.d;
-    more = p.base < p.n || flow_next(d, f, p, t0, T);
+    p.o0 = off[0];
+    p.n = (off[1] - p.o0) * f.span.d;
+    more = p.base < p.n || flow_next(d, f, off, p, t0, R);
   }
   FlowSlot cur = more ? flow_slot(s, f, p, t, c) : FlowSlot{};
+  ulonglong2 wa, wb, wc;
+  flow_issue(s, f, cur.has, cur.qa, cur.qb, cur.lane, wa, wb, wc);
   while (more) {
     FlowPos pn = p;
-    more = flow_next(d, f, pn, t0, T);
+    more = flow_next(d, f, off, pn, t0, R);
     const FlowSlot nx = more ? flow_slot(s, f, pn, t, c) : FlowSlot{};
-    if (!flow_items(d, s, f, cur.has, cur.qa, cur.qb, cur.lane, stamp, stamp + f.skew, timeout_ns)) return false;
+    if (!flow_items(d, s, f, cur.has, cur.qa, cur.qb, cur.lane, wa, wb, wc, stamp, stamp + f.skew, timeout_ns))
+      return false;
     p = pn;
     cur = nx;
+    flow_issue(s, f, cur.has, cur.qa, cur.qb, cur.lane, wa, wb, wc);
   }
   return true;
 }
@@ -243,7 +264,14 @@ __device__ __forceinline__ bool flow_cycle(const DDesign& d, const DSim& s, cons
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT) k_flow(DDesign d, DSim s, GridArgs g, FlowArgs f) {
   __shared__ int sh_ok;
+  extern __shared__ uint32_t sm_off[];  // [n_layers + 1] layer offsets, when the launch gives room
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, T = gridDim.x * blockDim.x;
+  const uint32_t* off = d.layer_off;
+  if (f.off_in_smem) {
+    for (uint32_t i = threadIdx.x; i <= d.n_layers; i += blockDim.x) sm_off[i] = __ldg(&d.layer_off[i]);
+    __syncthreads();
+    off = sm_off;
+  }
 #define RT_SPACE make_space<1>(f.span, 0u, t, T)
   // the rows no op writes, as they stand before the launch (registers and
   // inputs are refreshed again after the edge and the stimulus of each cycle)
@@ -252,7 +280,7 @@ __global__ void __launch_bounds__(MAXT) k_flow(DDesign d, DSim s, GridArgs g, Fl
     stim_items<1>(d, s, RT_SPACE, c);
     flow_refresh(s, f, RT_SPACE, 0u, f.n_in);
     if (!grid_sync(g, s.err, &sh_ok)) return;
-    flow_cycle(d, s, f, c, t, T, f.timeout_ns);  // a wait that gave up set the error word
+    flow_cycle(d, s, f, off, c, t, T, f.timeout_ns);  // a wait that gave up set the error word
     if (!grid_sync(g, s.err, &sh_ok)) return;
     commit_items<1>(d, s, RT_SPACE, c);
     flow_refresh(s, f, RT_SPACE, f.n_in, f.n_in + f.n_reg);

@@ -295,6 +295,7 @@ struct rteaal_sim {
   uint32_t* flow_ext = nullptr;      // FLOW: operand rows of ops with more than three operands
   uint2* flow_pool = nullptr;        // FLOW: {ref, row} of inputs, registers, constants
   uint32_t flow_skew = 0;            // test hook: FLOW items wait for a stamp this far ahead
+  uint32_t flow_kw = 8;              // FLOW: items a warp takes per layer and round
   // activity-aware evaluation (GRID only)
   bool activity = false;
   uint8_t* act = nullptr;            // [n_slots][act_chunks] 8-bit change stamps
@@ -504,6 +505,10 @@ uint32_t grid_for_span(const rteaal_sim* s, uint32_t span, uint32_t V) {
   const uint64_t items = widest * (span / V);
   return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(s->grid, (items + s->threads - 1) / s->threads));
 }
+
+// FLOW: layer offsets held in shared memory up to this many bytes (else read
+// from global memory)
+constexpr size_t kFlowOffSmem = 16384;
 
 void ensure_staging(rteaal_sim* s, size_t bytes) {
   if (s->staging_bytes >= bytes) return;
@@ -745,6 +750,7 @@ uint32_t plan_resident(rteaal_sim* s, const ClusterVariant* cv, uint32_t cluster
 
 void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads, uint32_t ctas_per_sm,
                uint32_t unroll, uint32_t lanes_per_thread, uint32_t cluster_ctas = 0, int cluster_resident = 0) {
+  const uint32_t tile_lanes_in = tile_lanes;  // as asked (FLOW: items per warp)
   if (kernel == RTEAAL_KERNEL_AUTO)
     kernel = s->activity ? RTEAAL_KERNEL_GRID : s->n_pad >= 64 ? RTEAAL_KERNEL_TILE : RTEAAL_KERNEL_LAYER;
   if (s->activity && kernel != RTEAAL_KERNEL_GRID)
@@ -877,17 +883,23 @@ void configure(rteaal_sim* s, int kernel, uint32_t tile_lanes, uint32_t threads,
         if (ft.v[i].maxt == 128) fv = &ft.v[i];
     require(fv != nullptr, "no compiled FLOW variant");
     s->flow_fn = fv->fn;
+    // tile_lanes: items a warp takes per layer (1..32; 0 = 8)
+    require(tile_lanes_in <= 32, "FLOW: tile_lanes (items per warp) must be in 1..32");
+    s->flow_kw = tile_lanes_in ? tile_lanes_in : 8u;
+    tile_lanes = s->flow_kw;
     threads = (uint32_t)fv->maxt;
     V = 1;
     unroll = 1;
-    int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fv->fn, (int)threads, 0));
+    int occ = 0;  // with the most shared memory a launch asks for (the layer offsets)
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fv->fn, (int)threads, kFlowOffSmem));
     require(occ >= 1, "FLOW kernel cannot be resident");
     ctas_per_sm = (uint32_t)occ;
     const Lowered& L = s->design->L;
     const uint64_t widest = std::max<uint64_t>(
         {(uint64_t)L.max_layer_ops, L.reg_src.size() + (L.mem_info.size() / 4 - 1), (uint64_t)L.in_width.size(), 1});
-    grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * s->design->n_sms, (widest * s->n_pad + threads - 1) / threads);
+    grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * s->design->n_sms,
+                                        (std::max<uint64_t>(widest, (uint64_t)L.max_layer_ops * 32 / s->flow_kw) *
+                                             s->n_pad + threads - 1) / threads);
   } else if (kernel == RTEAAL_KERNEL_STREAM) {
     // one CTA of STREAM_WARPS warps per SM; items of 256 lanes (128 when the
     // lane count is an odd multiple of 128); every warp keeps one chunk
@@ -1249,7 +1261,8 @@ RT_EXPORT int rteaal_sim_autotune(rteaal_sim* s, uint32_t cycles_per_trial, uint
     }
     if (kernel_mask & (1u << RTEAAL_KERNEL_FLOW)) {
       const FlowVariantTable ft = variants_flow();
-      for (size_t i = 0; i < ft.n; i++) cands.push_back({RTEAAL_KERNEL_FLOW, 0, (uint32_t)ft.v[i].maxt, 1, 1});
+      for (size_t i = 0; i < ft.n; i++)  // T: items per warp
+        for (uint32_t kw : {8u, 32u}) cands.push_back({RTEAAL_KERNEL_FLOW, kw, (uint32_t)ft.v[i].maxt, 1, 1});
     }
     for (const Cand& c : cands) candx.push_back({c.kernel, c.T, c.threads, c.U, c.V, 0});
 
@@ -1629,8 +1642,11 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
         CK(cudaMemsetAsync(s->flow_mirror, 0, mirror_bytes, st));
         s->flow_epoch = 0;
       }
+      // threads for the widest phase: a layer at flow_kw items per warp, the edge
+      // or the stimulus at one item per thread
       const uint64_t widest = std::max<uint64_t>(
-          {(uint64_t)L.max_layer_ops, L.reg_src.size() + (L.mem_info.size() / 4 - 1), (uint64_t)L.in_width.size(), 1});
+          {(uint64_t)L.max_layer_ops * 32 / s->flow_kw, L.reg_src.size() + (L.mem_info.size() / 4 - 1),
+           (uint64_t)L.in_width.size(), 1});
       const uint32_t grid = (uint32_t)std::max<uint64_t>(
           1, std::min<uint64_t>(s->grid, (widest * span + s->threads - 1) / s->threads));
       GridArgs ga{};
@@ -1651,10 +1667,14 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
       fa.epoch = s->flow_epoch;
       fa.skew = s->flow_skew;
       fa.span = make_fastdiv(span);
+      const size_t off_bytes = (size_t)D->L.layer_off.size() * 4;
+      fa.off_in_smem = off_bytes <= kFlowOffSmem;
+      fa.kw = s->flow_kw;
       CK(cudaMemsetAsync(s->scratch, 0, 16, st));
       void* args[] = {(void*)&D->dd, (void*)&ds, (void*)&ga, (void*)&fa};
       s->last_grid = grid;
-      cudaError_t e = cudaLaunchCooperativeKernel(s->flow_fn, dim3(grid), dim3(s->threads), args, 0, st);
+      cudaError_t e = cudaLaunchCooperativeKernel(s->flow_fn, dim3(grid), dim3(s->threads), args,
+                                                  fa.off_in_smem ? off_bytes : 0, st);
       if (e == cudaErrorCooperativeLaunchTooLarge)
         throw Error(RTEAAL_E_UNSUPPORTED, "cooperative grid does not fit on the device");
       CK(e);
