@@ -529,8 +529,11 @@ def run_ours(args) -> None:
                        "ctas_per_sm": info["ctas_per_sm"], "unroll": info["unroll"],
                        "lanes_per_thread": info["lanes_per_thread"],
                        "grid": info["grid"], "autotune": tune, "parallelism": "replicas" if world > 1 else "1 gpu",
-                       "l2": "state %.1f GB >> 129 MB L2 (no flush needed)"
-                             % (design.info["state_bytes_per_lane"] * n / 1e9)},
+                       "l2": ("state %.1f GB >> 129 MB L2 (no flush needed)"
+                              % (design.info["state_bytes_per_lane"] * n / 1e9)
+                              if design.info["state_bytes_per_lane"] * n > 129e6 else
+                              "state %.1f MB fits L2 and is not flushed (a latency-bound one-instance "
+                              "configuration)" % (design.info["state_bytes_per_lane"] * n / 1e6))},
             "roofline": ({"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                           "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                           "traffic": traffic, "peak_source": peaks["source"],
