@@ -8,7 +8,7 @@ from tests.gpu_util import Pair
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = ["layer", "layer_graph", "tile", "grid", "stream", "cluster"]
+KERNELS = ["layer", "layer_graph", "tile", "grid", "stream", "cluster", "flow"]
 
 
 def small_design(seed, n_ops=600, depth=10, n_regs=40, n_mems=0, inputs=(8, 32, 64, 1)):
@@ -89,7 +89,7 @@ def test_buffer_stimulus_and_probes(kernel, lanes):
 
 
 @pytest.mark.parametrize("kernel,lanes", [("layer", 0), ("tile", 0), ("grid", 0), ("grid", 8), ("stream", 0),
-                                          ("specialized", 0), ("cluster", 0)])
+                                          ("specialized", 0), ("cluster", 0), ("flow", 0)])
 def test_wide_ops_and_memories(kernel, lanes):
     """Variadic folds (> 3 operands), long mux chains, two write ports per memory;
     the grid form also at 8 lanes per thread (the benchmark's configuration)."""
@@ -255,7 +255,8 @@ def test_stream_chunks(n):
     p.close()
 
 
-@pytest.mark.parametrize("kernel,lanes", [("layer", 0), ("tile", 0), ("grid", 0), ("grid", 8), ("stream", 0)])
+@pytest.mark.parametrize("kernel,lanes", [("layer", 0), ("tile", 0), ("grid", 0), ("grid", 8), ("stream", 0),
+                                          ("flow", 0)])
 def test_waveform_changes(kernel, lanes):
     """Device-side change records equal the changes derived from the oracle's trace."""
     from oracle.waveform import changes
@@ -295,5 +296,25 @@ def test_stream_many_items_per_warp():
     p.step(1, reset=True)
     p.step(budgets)
     p.step(7)
+    p.compare()
+    p.close()
+
+
+@pytest.mark.parametrize("kernel,lanes", [("grid", 8), ("grid", 4), ("tile", 8), ("layer", 4), ("grid", 2)])
+def test_byte_results_packed_lanes(kernel, lanes):
+    """Every opcode with a result of at most 8 bits over operands of every narrow
+    class (the packed byte-lane path at 4 and 8 lanes per thread, the lane-by-lane
+    path at 2), shift amounts and bit ranges on both sides of a byte, with uneven
+    budgets so that partial lane masks are stored."""
+    from tests.test_layer_form_emulated_host import byte_results_design
+    nl = byte_results_design()
+    n = 96
+    budgets = synth.cycle_budgets(57, n, 5, 40)
+    p = Pair(nl, n, kernel=kernel, seed=57, expected_cycles=budgets, lanes_per_thread=lanes)
+    assert p.sim.info["lanes_per_thread"] == lanes
+    p.step(1, reset=True)
+    p.step(budgets)
+    p.compare()
+    p.step(13)
     p.compare()
     p.close()
