@@ -1380,43 +1380,81 @@ __device__ __forceinline__ void stim_items(const DDesign& d, const DSim& s, cons
   });
 }
 
+// One register's clock edge for V lanes (D row dsrc, Q row qref, width mask mk):
+// Q <- D, or the init value in reset cycles; with activity stamps, written
+// only where it changes.
+template <int V>
+__device__ __forceinline__ void commit_reg(const DDesign& d, const DSim& s, uint32_t r, uint32_t lane, uint32_t cyc,
+                                           uint32_t am, uint32_t dsrc, uint32_t qref, uint64_t mk) {
+  const size_t np = s.n_pad;
+  Lanes<V> v;
+  if (s.reset) {
+    const uint64_t init = __ldg(&d.reg_init[r]) & mk;
+#pragma unroll
+    for (int t = 0; t < V; t++) v.x[t] = init;
+  } else {
+    v = ldr<V>(s.state, dsrc, np, lane);
+#pragma unroll
+    for (int t = 0; t < V; t++) v.x[t] &= mk;
+    if (s.reset_lane) {  // instances still in their leading reset cycles
+      const uint64_t init = __ldg(&d.reg_init[r]) & mk;
+#pragma unroll
+      for (int t = 0; t < V; t++)
+        if (cyc < __ldg(&s.reset_lane[lane + t])) v.x[t] = init;
+    }
+  }
+  if (s.act) {  // write and stamp only what changes; visible from the next cycle
+    const Lanes<V> q = ldr<V>(s.state, qref, np, lane);
+    bool changed = false;
+#pragma unroll
+    for (int t = 0; t < V; t++) changed |= ((am >> t) & 1u) && q.x[t] != v.x[t];
+    if (!changed) return;
+    *act_at(d, s, qref, lane) = (uint8_t)(s.act_g0 + cyc + 1u);
+  }
+  str<V>(s.state, qref, np, lane, v, am);
+}
+
 // (a5) clock edge: registers (rows [0, n_regs)), then memory write ports
-// (rows [n_regs, n_regs + n_mems), ports of one memory in port order).
+// (rows [n_regs, n_regs + n_mems), ports of one memory in port order).  In the
+// fixed mapping a thread's registers are walked with the next register's
+// table entries loaded one row ahead, so that an item's dependent chain is
+// its D load and its store.
 template <int V>
 __device__ __forceinline__ void commit_items(const DDesign& d, const DSim& s, const ItemSpace& is,
                                              uint32_t cyc) {
   const size_t np = s.n_pad;
+  uint32_t r0 = 0;  // first row for the generic walk below
+  if (is.row_stride) {
+    if (is.row0 == NO_ROW) return;
+    const uint32_t am = act_mask<V>(s, is.lane, cyc);
+    if (!am) return;
+    uint32_t r = is.row0;
+    if (r < d.n_regs) {
+      uint32_t dsrc = __ldg(&d.reg_src[r]), qref = __ldg(&d.reg_ref[r]), w = __ldg(&d.reg_w[r]);
+      for (;;) {
+        const uint32_t rn = r + is.row_stride;
+        uint32_t dn = 0, qn = 0, wn = 1;
+        if (rn < d.n_regs) {
+          dn = __ldg(&d.reg_src[rn]);
+          qn = __ldg(&d.reg_ref[rn]);
+          wn = __ldg(&d.reg_w[rn]);
+        }
+        commit_reg<V>(d, s, r, is.lane, cyc, am, dsrc, qref, wmask(w));
+        r = rn;
+        if (r >= d.n_regs) break;
+        dsrc = dn;
+        qref = qn;
+        w = wn;
+      }
+    }
+    r0 = r;  // the thread's first row past the registers: its memory ports
+  }
   for_rows<V>(is, d.n_regs + d.n_mems, [&](uint32_t r, uint32_t lane) {
+    if (r < r0 && is.row_stride) return;  // fixed mapping: registers done above
     const uint32_t am = act_mask<V>(s, lane, cyc);
     if (!am) return;
     if (r < d.n_regs) {
-      const uint64_t mk = wmask(__ldg(&d.reg_w[r]));
-      Lanes<V> v;
-      if (s.reset) {
-        const uint64_t init = __ldg(&d.reg_init[r]) & mk;
-#pragma unroll
-        for (int t = 0; t < V; t++) v.x[t] = init;
-      } else {
-        v = ldr<V>(s.state, __ldg(&d.reg_src[r]), np, lane);
-#pragma unroll
-        for (int t = 0; t < V; t++) v.x[t] &= mk;
-        if (s.reset_lane) {  // instances still in their leading reset cycles
-          const uint64_t init = __ldg(&d.reg_init[r]) & mk;
-#pragma unroll
-          for (int t = 0; t < V; t++)
-            if (cyc < __ldg(&s.reset_lane[lane + t])) v.x[t] = init;
-        }
-      }
-      const uint32_t qref = __ldg(&d.reg_ref[r]);
-      if (s.act) {  // write and stamp only what changes; visible from the next cycle
-        const Lanes<V> q = ldr<V>(s.state, qref, np, lane);
-        bool changed = false;
-#pragma unroll
-        for (int t = 0; t < V; t++) changed |= ((am >> t) & 1u) && q.x[t] != v.x[t];
-        if (!changed) return;
-        *act_at(d, s, qref, lane) = (uint8_t)(s.act_g0 + cyc + 1u);
-      }
-      str<V>(s.state, qref, np, lane, v, am);
+      commit_reg<V>(d, s, r, lane, cyc, am, __ldg(&d.reg_src[r]), __ldg(&d.reg_ref[r]), wmask(__ldg(&d.reg_w[r])));
     } else {
       const uint32_t mi = r - d.n_regs;
       const uint4 info = __ldg(&d.mem_info[mi]);

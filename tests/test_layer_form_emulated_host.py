@@ -265,8 +265,10 @@ KERNEL_MUTANTS = [
     ("mux chain: the last set selector wins",
      "const bool take = (sel.x[v] & 1u) && !((done >> v) & 1u);", "const bool take = (sel.x[v] & 1u);"),
     ("reset ignores init values",
-     "if (s.reset) {\n        const uint64_t init = __ldg(&d.reg_init[r]) & mk;",
-     "if (s.reset) {\n        const uint64_t init = 0;"),
+     "if (s.reset) {\n    const uint64_t init = __ldg(&d.reg_init[r]) & mk;",
+     "if (s.reset) {\n    const uint64_t init = 0;"),
+    ("register commit: the next register's table entries never advance",
+     "        dsrc = dn;\n        qref = qn;", "        qref = qn;"),
     ("packed subtract: top bit of each byte not fixed up",
      "return ((a | H) - (b & ~H)) ^ ((a ^ ~b) & H);", "return ((a | H) - (b & ~H)) ^ ((a ^ b) & H);"),
     ("packed unsigned compare: the top bits ignored",
@@ -370,7 +372,7 @@ def test_activity_aware_evaluation_warp_cooperative(harness, V):
 ACTIVITY_MUTANTS = [
     ("a row's third operand never makes it hot", "  if (ar >= 3) h |= hot_ref(m.z);\n", "\n", 4, NP),
     ("a register change left unstamped",
-     "        *act_at(d, s, qref, lane) = (uint8_t)(s.act_g0 + cyc + 1u);\n", "\n", 4, NP),
+     "    *act_at(d, s, qref, lane) = (uint8_t)(s.act_g0 + cyc + 1u);\n", "\n", 4, NP),
     ("a warp checks only the first stamp chunk of its lanes",
      "const uint32_t ch_lo = first >> 7, ch_hi = (first + 32u * V - 1u) >> 7;",
      "const uint32_t ch_lo = first >> 7, ch_hi = ch_lo;", 8, 256),
