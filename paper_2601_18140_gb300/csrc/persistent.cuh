@@ -226,10 +226,10 @@ __device__ __forceinline__ void walk_staged(const DDesign& d, const DSim& s, uin
 }
 
 // (a2) one layer with staged descriptors; falls back to eval_layer where the
-// CTA could not stage them.
+// CTA could not stage them.  am: the thread's lane activity this cycle.
 template <int V, int U>
 __device__ __forceinline__ void eval_layer_staged(const DDesign& d, const DSim& s, uint32_t L, const ItemSpace& is,
-                                                  uint32_t cyc, const Stage& st, uint32_t cap,
+                                                  uint32_t cyc, uint32_t am, const Stage& st, uint32_t cap,
                                                   const uint4* sm_meta, const uint32_t* sm_dst) {
   const uint32_t o0 = __ldg(&d.layer_off[L]), n = __ldg(&d.layer_off[L + 1]) - o0;
   const uint32_t total = stage_rows(st, n);
@@ -237,9 +237,7 @@ __device__ __forceinline__ void eval_layer_staged(const DDesign& d, const DSim& 
     eval_layer<V, 1>(d, s, L, is, cyc);
     return;
   }
-  if (is.row0 == NO_ROW || is.row0 >= n) return;
-  const uint32_t am = act_mask<V>(s, is.lane, cyc);
-  if (!am) return;
+  if (is.row0 == NO_ROW || is.row0 >= n || !am) return;
   const uint32_t nw = __ldg(&d.layer_wide[L]) - o0, ne = __ldg(&d.layer_ext[L]) - o0;
   const uint32_t j = is.row0 - st.R0;
   uint32_t i = 0, r = is.row0;
@@ -263,10 +261,15 @@ __global__ void __launch_bounds__(MAXT, MINB) k_grid(DDesign d, DSim s, GridArgs
   }
   for (uint32_t c = 0; c < g.ncyc; c++) {
     stim_items<V>(d, s, RT_SPACE, c);
+    uint32_t am = 0;  // the thread's lane activity this cycle (fixed mapping), loaded during the barrier
+    {
+      const ItemSpace is = RT_SPACE;
+      if (is.row_stride && is.row0 != NO_ROW) am = act_mask<V>(s, is.lane, c);
+    }
     if (!grid_sync_staging(g, s.err, &sh_ok, RT_STAGE(0u))) return;
     for (uint32_t L = 0; L < d.n_layers; L++) {
       if (g.stage_cap)
-        eval_layer_staged<V, U>(d, s, L, RT_SPACE, c, stage_of_cta(g.tpo), g.stage_cap, sm_meta, sm_dst);
+        eval_layer_staged<V, U>(d, s, L, RT_SPACE, c, am, stage_of_cta(g.tpo), g.stage_cap, sm_meta, sm_dst);
       else
         eval_layer<V, 1>(d, s, L, RT_SPACE, c);
       if (!grid_sync_staging(g, s.err, &sh_ok, RT_STAGE(L + 1u))) return;
