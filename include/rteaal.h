@@ -360,7 +360,9 @@ int rteaal_sim_autotune(rteaal_sim *sim, uint32_t cycles_per_trial, uint32_t ker
  * creation.  Synchronises stream.  Errors: E_INVALID. */
 int rteaal_sim_activity(rteaal_sim *sim, uint64_t *evaluated, uint64_t *skipped, void *stream);
 
-/* Bytes of device memory rteaal_sim_create would take (footprint admission). */
+/* Bytes of device memory rteaal_sim_create would take (footprint admission).
+ * Steps in the FLOW kernel add, at their first launch, 16 bytes per row and
+ * padded lane (the stamped words) and 32 bytes per op (their descriptors). */
 uint64_t rteaal_sim_footprint(const rteaal_design *design, uint32_t n_instances);
 
 typedef struct {

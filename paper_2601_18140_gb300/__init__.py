@@ -504,7 +504,13 @@ class Design:
 
 
 class Sim:
-    """n_instances independent instances of a design, resident on the device."""
+    """n_instances independent instances of a design, resident on the device.
+
+    kernel: "grid" (persistent, the whole GPU walks each layer: the batched form),
+    "tile", "stream", "layer" / "layer_graph" (the plain form), "cluster", "flow"
+    (one instance or a few: no barrier between layers; tile_lanes = items per warp),
+    "specialized" or "auto"; the state is the same in every form, so configure()
+    may switch between steps."""
 
     def __init__(self, design: Design, n_instances: int, kernel: str | int = "auto",
                  xorshift_seed: np.ndarray | None = None, expected_cycles=None,
