@@ -299,7 +299,8 @@ def run_ours(args) -> None:
     if args.autotune:
         t0 = time.perf_counter()
         trials = sim.autotune(cycles_per_trial=1,
-                              kernels=["grid"] if args.activity else args.tune_kernels.split(","))
+                              kernels=["grid"] if args.activity else
+                              (args.tune_kernels.split(",") if args.tune_kernels else None))
         info = sim.info
         tune = {"trials": len(trials), "seconds": round(time.perf_counter() - t0, 2),
                 "best_ms_per_cycle": round(min(t["ms"] for t in trials), 3) if trials else None}
@@ -661,7 +662,9 @@ def main():
     ap.add_argument("--job-points", type=int, default=12,
                     help="points of the job at which the per-cycle time is measured (0: skip the job leg)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
-    ap.add_argument("--tune-kernels", default="tile,grid,stream")
+    ap.add_argument("--tune-kernels", default="",
+                    help="comma-separated forms to autotune over (default: the library's choice for the "
+                         "lane count: tile, grid, stream from 64 lanes, else layer, grid, cluster, flow)")
     ap.add_argument("--tune-log", default="")
     ap.add_argument("--no-verify", dest="verify", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
