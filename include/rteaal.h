@@ -215,6 +215,23 @@ int rteaal_design_lowered_netlist(const void *netlist, size_t nbytes, const rtea
  * read).  Errors: E_INVALID (null argument, wrong n_rows), E_FORMAT. */
 int rteaal_design_rows(const void *netlist, size_t nbytes, const rteaal_load_opts *opts, uint32_t *refs,
                        uint64_t n_rows);
+/* The FLOW form's tables for the lowered design (host only; the tables the
+ * library uploads at a sim's first FLOW step).  Rows are counted in layout
+ * order: class-3 rows first, then 2, 1, 0, each class in reference order.
+ * op (nullable, caller-owned, 8 uint32 per lowered op, in slot order): rows of
+ * operands a, b, c -- bit 31 set on a row that an op writes in the cycle, whose
+ * stamp the item waits for (Cascade 1's LI_{i+1} <- LO_i step as a per-operand
+ * wait); 0 for an absent operand and for ops with more than three operands --
+ * then the output's row, ctl, the output's reference, and for ops with more
+ * than three operands the offset and count of their operand rows in ext
+ * (nullable, caller-owned, *n_ext entries, flagged the same way).  pool
+ * (nullable, caller-owned, 2 uint32 per row): {reference, row} of every input,
+ * register and constant, in that order.  *n_op, *n_ext, *n_pool: on entry the
+ * capacities of the arrays given (checked), on return the counts; call with
+ * null arrays to size them.  opts nullable (only fuse_mux_chains is read).
+ * Errors: E_INVALID (null count pointer, wrong capacity), E_FORMAT. */
+int rteaal_design_flow_tables(const void *netlist, size_t nbytes, const rteaal_load_opts *opts, uint32_t *op,
+                              uint64_t *n_op, uint32_t *ext, uint64_t *n_ext, uint32_t *pool, uint64_t *n_pool);
 /* The design-specialised kernel's generation and NVRTC compile for sm_103a
  * alone, on the host (no device is touched, nothing is kept): checks that a
  * netlist's straight-line kernel (Sec. 5.2, unrolled S rank and inlined

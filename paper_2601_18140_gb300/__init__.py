@@ -110,7 +110,7 @@ EXPORTS = ["rteaal_design_load", "rteaal_design_info", "rteaal_design_free", "rt
            "rteaal_last_error", "rteaal_step_static", "rteaal_sim_reset_lanes",
            "rteaal_design_signals", "rteaal_sim_activity", "rteaal_design_specialize",
            "rteaal_design_lower", "rteaal_design_specialize_host", "rteaal_design_single_clock",
-           "rteaal_design_lowered_netlist", "rteaal_design_rows",
+           "rteaal_design_lowered_netlist", "rteaal_design_rows", "rteaal_design_flow_tables",
            "rteaal_design_specialized_source"]
 STATIC_MAX_LANES = 65536
 
@@ -138,6 +138,9 @@ def lib() -> ctypes.CDLL:
                                                        ctypes.POINTER(rteaal_load_opts), _P, ctypes.c_size_t,
                                                        ctypes.POINTER(ctypes.c_size_t)]
         L.rteaal_design_rows.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts), _P, _U64]
+        L.rteaal_design_flow_tables.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
+                                                _P, ctypes.POINTER(_U64), _P, ctypes.POINTER(_U64), _P,
+                                                ctypes.POINTER(_U64)]
         L.rteaal_design_single_clock.argtypes = [ctypes.c_char_p, ctypes.c_size_t, _P, ctypes.c_size_t,
                                                  ctypes.POINTER(ctypes.c_size_t), _P, _U64]
         L.rteaal_design_lower.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(rteaal_load_opts),
@@ -303,6 +306,27 @@ def rteaal_design_rows(netlist: bytes, n_rows: int, fuse_mux_chains: bool = Fals
     refs = np.zeros(n_rows, np.uint32)
     _check(lib().rteaal_design_rows(netlist, len(netlist), ctypes.byref(opts), refs.ctypes.data, n_rows))
     return refs
+
+
+def rteaal_design_flow_tables(netlist: bytes, fuse_mux_chains: bool = False):
+    """The FLOW form's tables of the lowered design (host only): op [n_ops][8]
+    (operand rows a, b, c with bit 31 on rows written in the cycle, output row,
+    ctl, output reference, side-array offset, operand count), ext [n_ext]
+    (flagged operand rows of ops with more than three operands) and pool
+    [n_pool][2] ({reference, row} of inputs, registers, constants)."""
+    opts = rteaal_load_opts()
+    opts.device = -1
+    opts.fuse_mux_chains = int(bool(fuse_mux_chains))
+    n_op, n_ext, n_pool = _U64(0), _U64(0), _U64(0)
+    _check(lib().rteaal_design_flow_tables(netlist, len(netlist), ctypes.byref(opts), None, ctypes.byref(n_op),
+                                           None, ctypes.byref(n_ext), None, ctypes.byref(n_pool)))
+    op = np.zeros((n_op.value, 8), np.uint32)
+    ext = np.zeros(n_ext.value, np.uint32)
+    pool = np.zeros((n_pool.value, 2), np.uint32)
+    _check(lib().rteaal_design_flow_tables(netlist, len(netlist), ctypes.byref(opts), op.ctypes.data,
+                                           ctypes.byref(n_op), ext.ctypes.data, ctypes.byref(n_ext),
+                                           pool.ctypes.data, ctypes.byref(n_pool)))
+    return op, ext, pool
 
 
 def rteaal_design_specialized_source(netlist: bytes, fuse_mux_chains: bool = False) -> str:

@@ -51,8 +51,6 @@ struct FlowArgs {
   FastDiv span;         // lanes the launch visits
 };
 
-constexpr uint32_t FLOW_CHECK = 1u << 31;
-
 __device__ __forceinline__ void st_relaxed_v2(unsigned long long* p, unsigned long long a, unsigned long long b) {
   asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }

@@ -179,6 +179,38 @@ RT_EXPORT int rteaal_design_rows(const void* netlist, size_t nbytes, const rteaa
   });
 }
 
+RT_EXPORT int rteaal_design_flow_tables(const void* netlist, size_t nbytes, const rteaal_load_opts* opts,
+                                        uint32_t* op, uint64_t* n_op, uint32_t* ext, uint64_t* n_ext, uint32_t* pool,
+                                        uint64_t* n_pool) {
+  return guarded([&] {
+    require(netlist && n_op && n_ext && n_pool, "rteaal_design_flow_tables: null argument");
+    Netlist nl;
+    std::string err;
+    if (!parse_netlist(netlist, nbytes, nl, err)) throw Error(RTEAAL_E_FORMAT, err);
+    std::vector<uint32_t> user2x;
+    const Netlist nlx = lower_clock_domains(nl, user2x);
+    Lowered L;
+    lower_netlist(nlx, L, opts && opts->fuse_mux_chains);
+    std::vector<uint32_t> o, e, p;
+    flow_tables(L, o, e, p);
+    if (op) {
+      require(*n_op == o.size() / 8, "rteaal_design_flow_tables: n_op differs from the lowered op count");
+      std::copy(o.begin(), o.end(), op);
+    }
+    if (ext) {
+      require(*n_ext == e.size(), "rteaal_design_flow_tables: n_ext differs from the side array's length");
+      std::copy(e.begin(), e.end(), ext);
+    }
+    if (pool) {
+      require(*n_pool == p.size() / 2, "rteaal_design_flow_tables: n_pool differs from the pool row count");
+      std::copy(p.begin(), p.end(), pool);
+    }
+    *n_op = o.size() / 8;
+    *n_ext = e.size();
+    *n_pool = p.size() / 2;
+  });
+}
+
 RT_EXPORT int rteaal_design_single_clock(const void* netlist, size_t nbytes, void* out, size_t capacity,
                                          size_t* out_bytes, uint32_t* user2x, uint64_t n_user) {
   return guarded([&] {

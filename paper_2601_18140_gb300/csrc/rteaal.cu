@@ -1597,45 +1597,17 @@ RT_EXPORT int rteaal_step(rteaal_sim* s, const rteaal_cycles* cycles, const rtea
         s->flow_mirror = static_cast<unsigned long long*>(s->get(std::max<size_t>(mirror_bytes, 16)));
         CK(cudaMemsetAsync(s->flow_mirror, 0, mirror_bytes, st));
         s->flow_epoch = 0;
-        // row (layout order) of a reference; FLOW_CHECK on rows that ops write
-        // (rows of a class hold inputs, registers and constants, then op results)
-        const uint32_t c3 = L.class_rows[3], c2 = L.class_rows[2], c1 = L.class_rows[1];
-        const uint32_t coff[4] = {8 * c3 + 4 * c2 + 2 * c1, 8 * c3 + 4 * c2, 8 * c3, 0u};
-        const uint32_t cidx[4] = {c3 + c2 + c1, c3 + c2, c3, 0u};
-        uint32_t op_off[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-        for (uint32_t sl = L.op_base; sl < L.n_slots; sl++) {
-          const uint32_t k = L.slot_ref[sl] >> 30;
-          op_off[k] = std::min(op_off[k], L.slot_ref[sl] & REF_OFF_MASK);
-        }
-        auto row_of = [&](uint32_t ref) {
-          const uint32_t k = ref >> 30, off = ref & REF_OFF_MASK;
-          return (cidx[k] + ((off - coff[k]) >> k)) | (off >= op_off[k] ? FLOW_CHECK : 0u);
-        };
-        std::vector<uint4> fop(2 * L.meta.size());
-        for (size_t i = 0; i < L.meta.size(); i++) {
-          const OpMeta& m = L.meta[i];
-          const uint32_t drow = row_of(L.dst_ref[i]) & ~FLOW_CHECK;
-          if (m.ctl & CTL_EXT) {
-            fop[2 * i] = make_uint4(0u, 0u, 0u, drow);
-            fop[2 * i + 1] = make_uint4(m.ctl, L.dst_ref[i], m.a, m.b);
-          } else {
-            fop[2 * i] = make_uint4(row_of(m.a), row_of(m.b), row_of(m.c), drow);
-            fop[2 * i + 1] = make_uint4(m.ctl, L.dst_ref[i], 0u, 0u);
-          }
-        }
-        std::vector<uint32_t> fext(std::max<size_t>(L.ext_args.size(), 1), 0u);
-        for (size_t k = 0; k < L.ext_args.size(); k++) fext[k] = row_of(L.ext_args[k]);
-        std::vector<uint2> fpool;
-        for (uint32_t r : L.in_ref) fpool.push_back(make_uint2(r, row_of(r) & ~FLOW_CHECK));
-        for (uint32_t r : L.reg_ref) fpool.push_back(make_uint2(r, row_of(r) & ~FLOW_CHECK));
-        for (uint32_t r : L.const_ref) fpool.push_back(make_uint2(r, row_of(r) & ~FLOW_CHECK));
-        if (fpool.empty()) fpool.push_back(make_uint2(0u, 0u));
-        s->flow_op = static_cast<uint4*>(s->get(fop.size() * sizeof(uint4)));
+        std::vector<uint32_t> fop, fext, fpool;
+        flow_tables(L, fop, fext, fpool);
+        if (fop.empty()) fop.assign(8, 0u);
+        if (fext.empty()) fext.push_back(0u);
+        if (fpool.empty()) fpool.assign(2, 0u);
+        s->flow_op = static_cast<uint4*>(s->get(fop.size() * 4));      // 2 uint4 per op
         s->flow_ext = static_cast<uint32_t*>(s->get(fext.size() * 4));
-        s->flow_pool = static_cast<uint2*>(s->get(fpool.size() * sizeof(uint2)));
-        CK(cudaMemcpyAsync(s->flow_op, fop.data(), fop.size() * sizeof(uint4), cudaMemcpyHostToDevice, st));
+        s->flow_pool = static_cast<uint2*>(s->get(fpool.size() * 4));  // 1 uint2 per row
+        CK(cudaMemcpyAsync(s->flow_op, fop.data(), fop.size() * 4, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(s->flow_ext, fext.data(), fext.size() * 4, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(s->flow_pool, fpool.data(), fpool.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s->flow_pool, fpool.data(), fpool.size() * 4, cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
       }
       if ((uint64_t)s->flow_epoch + max_cyc >= 0xFFFFFFFFull) {  // stamps would wrap: start over

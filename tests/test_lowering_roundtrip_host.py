@@ -159,3 +159,46 @@ def test_compact_layout(fuse):
         end += int(size[ids].sum())
     info, _ = rt.rteaal_design_lower(nl.to_bytes(), fuse_mux_chains=fuse)
     assert end == info["state_bytes_per_lane"]
+
+
+@pytest.mark.parametrize("fuse", [False, True])
+def test_flow_tables(fuse):
+    """The FLOW form's tables against the compact layout: every op's operand
+    rows are its operands' ranks in layout order (class 3 first, then by
+    offset), flagged exactly when the operand is an op result (written in the
+    cycle, so its stamp is waited for); absent operands are 0; extended ops list
+    their operand rows in the side array in O order; the output row and
+    reference are the op's own; the pool lists inputs, registers and constants
+    with their rows."""
+    nl = synth.generate(DesignSpec(n_ops=4000, n_regs=150, depth=16, n_inputs=4, seed=73,
+                                   input_widths=(8, 32, 1, 64), mux_chain_frac=0.7, n_mems=2, mem_words=8))
+    low, _ = rt.rteaal_design_lowered_netlist(nl.to_bytes(), nl.n_signals, fuse_mux_chains=fuse)
+    x = synth.Netlist.from_bytes(low)
+    refs = rt.rteaal_design_rows(nl.to_bytes(), x.n_signals, fuse_mux_chains=fuse).astype(np.int64)
+    op, ext, pool = rt.rteaal_design_flow_tables(nl.to_bytes(), fuse_mux_chains=fuse)
+    k, off = refs >> 30, refs & ((1 << 30) - 1)
+    order = np.lexsort((off, -k))                  # layout order: class 3 first, then by offset
+    row = np.empty(x.n_signals, np.int64)
+    row[order] = np.arange(x.n_signals)
+    check = 1 << 31
+
+    def want(sig: int) -> int:
+        return int(row[sig]) | (check if sig >= x.op_base else 0)
+
+    assert op.shape == (x.n_ops, 8)
+    n_ext = 0
+    for i in range(x.n_ops):
+        q = [int(v) for v in op[i]]
+        args = [int(a) for a in x.op_args(i)]
+        assert q[3] == row[x.op_base + i] and q[5] == refs[x.op_base + i]
+        assert (q[4] >> 8) & 127 == x.op_width[i]
+        if len(args) <= 3:
+            assert q[:3] == [want(a) for a in args] + [0] * (3 - len(args)), i
+        else:
+            n_ext += 1
+            assert q[:3] == [0, 0, 0]
+            assert [int(v) for v in ext[q[6]:q[6] + q[7]]] == [want(a) for a in args], i
+    assert (n_ext > 0) == fuse
+    sigs = list(range(x.n_inputs)) + list(range(x.reg_base, x.reg_base + x.n_regs)) + \
+        list(range(x.const_base, x.const_base + x.n_consts))
+    assert pool.tolist() == [[int(refs[s]), int(row[s])] for s in sigs]
