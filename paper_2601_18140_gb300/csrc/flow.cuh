@@ -25,6 +25,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "flow_tables.hpp"
 #include "persistent.cuh"
 
 namespace rteaal {

@@ -2,9 +2,10 @@
 // points that expose what the kernels will execute -- the lowering's figures,
 // the compact layout's row references, the one-clock netlist of the clock-domain
 // lowering and the descriptors decoded back into a netlist -- so that all of it
-// can be checked against the oracle without a GPU.  Also the thread-local
-// failure message of every entry point (rteaal_last_error).  Plain C++: this
-// unit and lower.cpp build without the CUDA toolkit.
+// can be checked against the oracle without a GPU.  Also the FLOW form's tables
+// (flow_tables, which the runtime uploads as they are built here) and the
+// thread-local failure message of every entry point (rteaal_last_error).  Plain
+// C++: this unit and lower.cpp build without the CUDA toolkit.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -12,9 +13,54 @@
 #include <vector>
 
 #include "host_api.hpp"
+#include "flow_tables.hpp"
 #include "lower.hpp"
 
 namespace rteaal {
+
+void flow_tables(const Lowered& L, std::vector<uint32_t>& op, std::vector<uint32_t>& ext,
+                 std::vector<uint32_t>& pool) {
+  // region of each class in the compact layout (class 3 first) and the first
+  // op row of each class (inside a class, pool rows come before op rows)
+  const uint64_t c3 = L.class_rows[3], c2 = L.class_rows[2], c1 = L.class_rows[1];
+  const uint64_t coff[4] = {8 * c3 + 4 * c2 + 2 * c1, 8 * c3 + 4 * c2, 8 * c3, 0};
+  const uint64_t cidx[4] = {c3 + c2 + c1, c3 + c2, c3, 0};
+  uint32_t op_off[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+  for (uint32_t sl = L.op_base; sl < L.n_slots; sl++) {
+    const uint32_t k = L.slot_ref[sl] >> 30;
+    op_off[k] = std::min(op_off[k], L.slot_ref[sl] & REF_OFF_MASK);
+  }
+  auto row_of = [&](uint32_t ref) {
+    const uint32_t k = ref >> 30, off = ref & REF_OFF_MASK;
+    return (uint32_t)(cidx[k] + ((off - coff[k]) >> k)) | (off >= op_off[k] ? FLOW_CHECK : 0u);
+  };
+  op.assign(8 * L.meta.size(), 0u);
+  for (size_t i = 0; i < L.meta.size(); i++) {
+    const OpMeta& m = L.meta[i];
+    uint32_t* q = &op[8 * i];
+    q[3] = row_of(L.dst_ref[i]) & ~FLOW_CHECK;
+    q[4] = m.ctl;
+    q[5] = L.dst_ref[i];
+    if (m.ctl & CTL_EXT) {
+      q[6] = m.a;
+      q[7] = m.b;
+    } else {
+      const uint32_t ar = (m.ctl >> 5) & 3u;
+      q[0] = row_of(m.a);
+      q[1] = ar >= 2 ? row_of(m.b) : 0u;
+      q[2] = ar >= 3 ? row_of(m.c) : 0u;
+    }
+  }
+  ext.resize(L.ext_args.size());
+  for (size_t k = 0; k < L.ext_args.size(); k++) ext[k] = row_of(L.ext_args[k]);
+  pool.clear();
+  for (const std::vector<uint32_t>* v : {&L.in_ref, &L.reg_ref, &L.const_ref})
+    for (uint32_t r : *v) {
+      pool.push_back(r);
+      pool.push_back(row_of(r) & ~FLOW_CHECK);
+    }
+}
+
 
 std::string& last_error() {
   thread_local std::string msg;
