@@ -10,7 +10,11 @@
 #include <cuda_runtime.h>  // vector types (uint4, ...) and qualifiers for a host compile
 
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <cstdlib>
 #include <cstring>
 #include <thread>
@@ -44,6 +48,37 @@ struct Warp {
 };
 static thread_local Warp* warp = nullptr;
 
+// The FLOW form's collectives: lanes of one warp (host threads) vote on a mask
+// of the warp; each lane's n-th call with a given mask joins the n-th round of
+// that mask, which ends once every lane of the mask has voted (lanes of the
+// mask reach the same calls in the same order).  A round that does not fill
+// within a minute aborts instead of hanging.
+struct FlowWarp {
+  std::mutex mu;
+  std::condition_variable cv;
+  struct Round {
+    unsigned arrived = 0, left = 0, bits = 0;
+  };
+  std::map<std::pair<unsigned, unsigned>, Round> rounds;
+  std::map<unsigned, unsigned> seq[32];
+  unsigned vote(unsigned lane, unsigned mask, bool pred) {
+    std::unique_lock<std::mutex> lk(mu);
+    const auto key = std::make_pair(mask, seq[lane][mask]++);
+    Round& r = rounds[key];
+    if (pred) r.bits |= 1u << lane;
+    const unsigned need = (unsigned)__builtin_popcount(mask);
+    if (++r.arrived == need) {
+      cv.notify_all();
+    } else if (!cv.wait_for(lk, std::chrono::seconds(60), [&] { return r.arrived == need; })) {
+      abort();
+    }
+    const unsigned bits = r.bits;
+    if (++r.left == need) rounds.erase(key);
+    return bits;
+  }
+};
+static thread_local FlowWarp* flow_warp = nullptr;
+
 template <typename T>
 static inline T __ldg(const T* p) {
   return *p;
@@ -58,7 +93,8 @@ static inline unsigned __byte_perm(unsigned x, unsigned y, unsigned s) {
 static inline int __popc(unsigned x) { return __builtin_popcount(x); }
 static inline int __popcll(unsigned long long x) { return __builtin_popcountll(x); }
 static inline int __ffs(int x) { return __builtin_ffs(x); }
-static inline unsigned __ballot_sync(unsigned, int pred) {
+static inline unsigned __ballot_sync(unsigned mask, int pred) {
+  if (flow_warp) return flow_warp->vote(threadIdx.x & 31u, mask, pred != 0);
   if (!warp) abort();
   const unsigned lid = threadIdx.x & 31u;
   warp->slot[lid] = pred ? 1u : 0u;
@@ -77,6 +113,9 @@ static inline T __shfl_sync(unsigned, T v, int src, int = 32) {
   warp->wait();
   return r;
 }
+static inline int __all_sync(unsigned mask, int pred) { return __ballot_sync(mask, pred) == mask; }
+static inline int __any_sync(unsigned mask, int pred) { return __ballot_sync(mask, pred) != 0u; }
+static inline unsigned atomicOr(unsigned* p, unsigned v) { return __atomic_fetch_or(p, v, __ATOMIC_RELAXED); }
 static inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
   const unsigned long long o = *p;
   *p += v;
@@ -84,6 +123,7 @@ static inline unsigned long long atomicAdd(unsigned long long* p, unsigned long 
 }
 
 #include "kernels.cuh"
+#include "flow_items.cuh"
 #include "lower.hpp"
 
 using namespace rteaal;
@@ -105,6 +145,10 @@ struct Emu {
   bool act_force = true;             // next step's first cycle evaluates every op
   unsigned long long act_count[2] = {0, 0};
   uint32_t np = 0, err = 0;
+  // FLOW form: stamped words, tables, stamps used so far
+  std::vector<unsigned long long> flow_words;
+  std::vector<uint32_t> flow_op, flow_ext, flow_pool;
+  uint32_t flow_epoch = 0;
 };
 
 template <class T>
@@ -268,6 +312,67 @@ extern "C" void* emu_create(const void* bytes, size_t nbytes, int fuse, uint32_t
   s.n_user = np;
   s.err = &e->err;
   return e;
+}
+
+// One step of the FLOW form: n_warps warps of 32 host threads (one per lane of
+// a warp) run every cycle's evaluation phase concurrently and wait on one
+// another's stamped words; kw items per warp and round.  The stimulus, the
+// clock edge and the copies of rows no op writes run thread index by thread
+// index between the phases, as the kernel's grid barriers separate them.
+// Returns the error word (0: every wait ended).
+extern "C" int emu_step_flow(void* p, uint32_t n_warps, uint32_t kw, uint32_t ncyc, const uint32_t* budget,
+                             int reset) {
+  Emu& e = *static_cast<Emu*>(p);
+  e.s.budget = budget;
+  e.s.uniform = ncyc;
+  e.s.reset = reset;
+  e.s.stim_mode = e.L.in_width.empty() ? 0 : 1;
+  if (e.flow_words.empty()) {
+    e.flow_words.assign((size_t)e.L.n_slots * e.np * 2 + 2, 0ull);
+    flow_tables(e.L, e.flow_op, e.flow_ext, e.flow_pool);
+    if (e.flow_op.empty()) e.flow_op.assign(8, 0u);
+    if (e.flow_ext.empty()) e.flow_ext.push_back(0u);
+    if (e.flow_pool.empty()) e.flow_pool.assign(2, 0u);
+  }
+  FlowArgs f{};
+  f.mirror = e.flow_words.data();
+  f.fop = reinterpret_cast<const uint4*>(e.flow_op.data());
+  f.fext = e.flow_ext.data();
+  f.fpool = reinterpret_cast<const uint2*>(e.flow_pool.data());
+  f.n_in = (uint32_t)e.L.in_ref.size();
+  f.n_reg = (uint32_t)e.L.reg_ref.size();
+  f.n_const = (uint32_t)e.L.const_ref.size();
+  f.epoch = e.flow_epoch;
+  f.skew = 0;
+  f.timeout_ns = 20000000000ull;
+  f.off_in_smem = 0;
+  f.kw = kw;
+  f.span = fastdiv(e.np);
+  const uint32_t T = 32 * n_warps;
+  auto space = [&](uint32_t t) { return make_space<1>(f.span, 0u, t, T); };
+  for (uint32_t t = 0; t < T; t++) flow_refresh(e.s, f, space(t), 0u, f.n_in + f.n_reg + f.n_const);
+  for (uint32_t c = 0; c < ncyc && e.err == 0; c++) {
+    for (uint32_t t = 0; t < T; t++) {
+      stim_items<1>(e.d, e.s, space(t), c);
+      flow_refresh(e.s, f, space(t), 0u, f.n_in);
+    }
+    std::vector<FlowWarp> warps(n_warps);
+    std::vector<std::thread> th;
+    for (uint32_t t = 0; t < T; t++)
+      th.emplace_back([&, t] {
+        threadIdx.x = t;
+        flow_warp = &warps[t / 32];
+        flow_cycle(e.d, e.s, f, e.d.layer_off, c, t, T, f.timeout_ns);
+        flow_warp = nullptr;
+      });
+    for (auto& x : th) x.join();
+    for (uint32_t t = 0; t < T; t++) {
+      commit_items<1>(e.d, e.s, space(t), c);
+      flow_refresh(e.s, f, space(t), f.n_in, f.n_in + f.n_reg);
+    }
+  }
+  e.flow_epoch += ncyc;
+  return (int)e.err;
 }
 
 // One step of ncyc cycles at V lanes per item, U rows in flight, with nthreads

@@ -35,7 +35,7 @@ def build_harness(csrc: str, out_dir, opt: str = "-O1") -> ctypes.CDLL:
     so = os.path.join(str(out_dir), "harness.so")
     subprocess.run(["g++", "-std=c++17", opt, "-w", "-pthread", "-shared", "-fPIC", "-I", CUDA_INCLUDE, "-I", INCLUDE,
                     "-I", csrc, "-o", so, os.path.join(HERE, "layer_form_harness.cpp"),
-                    os.path.join(csrc, "lower.cpp")], check=True)
+                    os.path.join(csrc, "lower.cpp"), os.path.join(csrc, "inspect.cpp")], check=True)
     lib = ctypes.CDLL(so)
     lib.emu_create.restype = P
     lib.emu_create.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, P]
@@ -48,6 +48,7 @@ def build_harness(csrc: str, out_dir, opt: str = "-O1") -> ctypes.CDLL:
     lib.emu_free.argtypes = [P]
     lib.emu_probe.argtypes = [P, P, ctypes.c_uint32, ctypes.c_int, P, ctypes.c_uint64, P]
     lib.emu_step_act.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int, ctypes.c_int, P]
+    lib.emu_step_flow.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int]
     return lib
 
 
@@ -297,7 +298,7 @@ def test_planted_kernel_mistakes_are_caught(tmp_path):
         assert src.count(old) == 1, "mutation site not found exactly once: " + name
         d = tmp_path / ("m%d" % k)
         d.mkdir()
-        for f in ["lower.hpp", "lower.cpp"]:
+        for f in ["lower.hpp", "lower.cpp", "inspect.cpp", "host_api.hpp", "flow_tables.hpp", "flow_items.cuh"]:
             shutil.copy(os.path.join(CSRC, f), str(d / f))
         (d / "kernels.cuh").write_text(src.replace(old, new))
         lib = build_harness(str(d), d, opt="-O0")   # quick to build; the runs are short
@@ -388,9 +389,76 @@ def test_planted_activity_mistakes_are_caught(tmp_path):
         assert src.count(old) == 1, "mutation site not found exactly once: " + name
         d = tmp_path / ("a%d" % k)
         d.mkdir()
-        for f in ["lower.hpp", "lower.cpp"]:
+        for f in ["lower.hpp", "lower.cpp", "inspect.cpp", "host_api.hpp", "flow_tables.hpp", "flow_items.cuh"]:
             shutil.copy(os.path.join(CSRC, f), str(d / f))
         (d / "kernels.cuh").write_text(src.replace(old, new))
         lib = build_harness(str(d), d, opt="-O0")   # quick to build; the runs are short
         with pytest.raises(AssertionError):
             run_activity(lib, V, True, np_=lanes)
+
+
+def run_flow_and_compare(lib, nl: synth.Netlist, fuse: bool, n_warps: int, kw: int, np_: int = 4,
+                         seed: int = 1) -> None:
+    """The FLOW form's evaluation phase run by concurrent host threads (one per
+    lane of each warp, waiting on one another's stamped words) over reset, even
+    and uneven budgets and a second reset; every signal, memory word and
+    stimulus state against the oracle after every step."""
+    nb = nl.to_bytes()
+    xs = np.ascontiguousarray(synth.xorshift_seeds(seed, nl.n_inputs, np_))
+    e = lib.emu_create(nb, len(nb), int(fuse), np_, xs.ctypes.data if nl.n_inputs else None)
+    assert e
+    orc = oracle.OracleSim(nb, np_)
+    xo = xs.copy()
+    rng = np.random.default_rng(seed)
+    out = np.zeros(np_, np.uint64)
+    try:
+        for cycles, reset in [(1, True), (9, False), (None, False), (1, True), (4, False)]:
+            budget = rng.integers(0, 7, np_).astype(np.uint32) if cycles is None else None
+            ncyc = int(budget.max()) if budget is not None else cycles
+            assert lib.emu_step_flow(e, n_warps, kw, ncyc, None if budget is None else budget.ctypes.data,
+                                     int(reset)) == 0
+            orc.step(budget if budget is not None else cycles, reset=reset, mode=oracle.STIM_XORSHIFT, xs=xo)
+            for sig in range(nl.n_signals):
+                if lib.emu_read(e, sig, out.ctypes.data) == 0:
+                    assert np.array_equal(out[:np_], orc.vals[:, sig]), (sig, n_warps, kw)
+            words = orc.mem_total
+            mem = np.ctypeslib.as_array(ctypes.cast(lib.emu_mem(e), ctypes.POINTER(ctypes.c_uint64)),
+                                        (max(words, 1) * np_,))
+            assert np.array_equal(mem[:words * np_].reshape(words, np_).T, orc.mems[:, :words])
+    finally:
+        lib.emu_free(e)
+
+
+@pytest.mark.parametrize("n_warps,kw", [(1, 32), (2, 8), (3, 5)])
+@pytest.mark.parametrize("name", ["random+mem", "chains-fused", "wide+domains", "byte results"])
+def test_flow_form_matches_oracle(harness, name, n_warps, kw):
+    nl, fuse = DESIGNS[name]
+    run_flow_and_compare(harness, nl, fuse, n_warps, kw)
+
+
+FLOW_MUTANTS = [
+    ("an operand's high word dropped", "return (w.x & 0xFFFFFFFFull) | (w.y << 32);", "return w.x & 0xFFFFFFFFull;"),
+    ("inputs, registers and constants copied without their high words",
+     "st_relaxed_v2(flow_word(s, f, e.y, lane), v & 0xFFFFFFFFull, v >> 32);",
+     "st_relaxed_v2(flow_word(s, f, e.y, lane), v & 0xFFFFFFFFull, 0ull);"),
+    ("a result's high word stored without its value",
+     "(r & 0xFFFFFFFFull) | sv, (r >> 32) | sv", "(r & 0xFFFFFFFFull) | sv, sv"),
+]
+
+
+def test_planted_flow_mistakes_are_caught(tmp_path):
+    if not os.path.isdir(CUDA_INCLUDE):
+        pytest.skip("CUDA headers not found")
+    with open(os.path.join(CSRC, "flow_items.cuh")) as f:
+        src = f.read()
+    for k, (name, old, new) in enumerate(FLOW_MUTANTS):
+        assert src.count(old) == 1, "mutation site not found exactly once: " + name
+        d = tmp_path / ("f%d" % k)
+        d.mkdir()
+        for f in ["lower.hpp", "lower.cpp", "inspect.cpp", "host_api.hpp", "flow_tables.hpp", "kernels.cuh"]:
+            shutil.copy(os.path.join(CSRC, f), str(d / f))
+        (d / "flow_items.cuh").write_text(src.replace(old, new))
+        lib = build_harness(str(d), d, opt="-O0")
+        nl, fuse = DESIGNS["wide+domains"]
+        with pytest.raises(AssertionError):
+            run_flow_and_compare(lib, nl, fuse, 1, 32)
